@@ -1,0 +1,200 @@
+"""The DD-alpha-AMG multilevel method: cycles (Alg. 1, Alg. 2), setup (Alg. 3, Alg. 4), solve.
+
+Levels are numbered 0 .. L-1 here (the paper: 1 .. L).  Level 0 carries the
+Wilson-clover operator, level l+1 the Galerkin operator P_l^+ D_l P_l.
+
+K-cycle at level l (Alg. 2 = Alg. 1 with the recursion replaced):
+    z = 0;  mu times z += M_l (b - D_l z)
+    b_{l+1} = P_l^+ (b - D_l z)
+    z_{l+1} = coarsest even-odd GMRES          if l+1 = L-1
+            = FGMRES(D_{l+1}, b_{l+1}) preconditioned by the K-cycle at l+1, otherwise
+              (restart length 5, at most 2 cycles, relative tolerance 0.1, Table 1)
+    z += P_l z_{l+1};  nu times z += M_l (b - D_l z)
+Readings where the paper is silent: "maximal restarts 2" = at most two cycles
+of the inner FGMRES; the coarsest GMRES uses restart length 50 and at most 20
+cycles; the coarsest tolerance is on the Schur-complement residual.
+
+Outer solver: FGMRES in FP64 on D preconditioned by the K-cycle at level 0
+(restart n_kv = 10, tol 1e-10, Table 1).
+
+Setup (Alg. 3, Alg. 4), readings: Alg. 3's "l = 0" is the finest level;
+Alg. 4's right-hand side v_{l-1} is read as v_l (the current test vector of
+the level the cycle starts on); "z_l" for the coarser levels are the last
+iterates produced on those levels during that cycle (the inner FGMRES
+results); a coarser level with more test vectors than the level above takes
+the restricted ones first and fresh random ones for the rest.  The random
+start vectors are inputs.
+
+Parity of the setup against the paper is pinned by the call sequence it
+makes (a test replays Alg. 3/4 by hand on a tiny hierarchy); its numerical
+outcome is "parity unpinned" beyond "given identical test vectors".
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .lattice import norm
+from .smoother import SAP
+from .stencil import EvenOdd
+from .transfer import build_interpolation, restrict, prolong, galerkin
+from .krylov import fgmres, coarsest_solve
+
+
+@dataclass
+class Params:
+    levels: int = 3
+    agg: tuple = ((4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2))   # aggregate block per level l (l -> l+1)
+    n_tv: tuple = (20, 20, 20)                                 # test vectors of level l (defines P_l)
+    sap_block: tuple = ((2, 2, 2, 2), (2, 2, 2, 2), (2, 2, 2, 2), (2, 2, 2, 2))
+    mr_steps: int = 3
+    nu: int = 5
+    mu: int = 0
+    n_inv: int = 6
+    eta_passes: int = 3
+    outer_restart: int = 10
+    outer_max_cycles: int = 200
+    kcycle_len: int = 5
+    kcycle_cycles: int = 2
+    kcycle_tol: float = 1e-1
+    coarse_tol: float = 5e-2
+    coarse_restart: int = 50
+    coarse_cycles: int = 20
+
+
+@dataclass
+class Level:
+    op: object
+    sap: SAP = None
+    P: np.ndarray = None          # N fields on this level (interpolation to this level from l+1)
+    tv: np.ndarray = None         # test vectors of this level
+    eo: EvenOdd = None            # coarsest level only
+
+
+@dataclass
+class Trace:
+    """Record of the setup's steps, for the tests that replay Alg. 3 / Alg. 4."""
+    events: list = field(default_factory=list)
+
+    def add(self, *ev):
+        self.events.append(ev)
+
+
+class Hierarchy:
+    def __init__(self, fine_op, params: Params):
+        self.p = params
+        self.levels = [Level(op=fine_op)]
+        self.trace = None
+        self.last_iterate = {}
+
+    @property
+    def L(self):
+        return self.p.levels
+
+    # --- construction of one level ------------------------------------------------
+    def _make_sap(self, l):
+        lev = self.levels[l]
+        lev.sap = SAP(lev.op, self.p.sap_block[l], self.p.mr_steps)
+
+    def rebuild(self, l):
+        """Construct P_l from the test vectors of level l and set D_{l+1} = P_l^+ D_l P_l."""
+        lev = self.levels[l]
+        lev.P = build_interpolation(lev.tv, self.p.agg[l])
+        Dc = galerkin(lev.op, lev.P, self.p.agg[l])
+        if len(self.levels) <= l + 1:
+            self.levels.append(Level(op=Dc))
+        else:
+            self.levels[l + 1].op = Dc
+        if self.trace is not None:
+            self.trace.add("build", l)
+        if l + 1 == self.L - 1:
+            self.levels[l + 1].eo = EvenOdd(Dc)
+        else:
+            self._make_sap(l + 1)
+
+    # --- cycles -------------------------------------------------------------------
+    def kcycle(self, l, b):
+        """One K-cycle from level l (Alg. 2); also records the last iterate of every level."""
+        if self.trace is not None:
+            self.trace.add("kcycle", l)
+        lev = self.levels[l]
+        D = lev.op.apply
+        z = np.zeros_like(b)
+        if self.p.mu > 0:
+            z = lev.sap.smooth(b, z, self.p.mu)
+        bc = restrict(lev.P, self.p.agg[l], b - D(z))
+        if l + 1 == self.L - 1:
+            zc, _ = coarsest_solve(self.levels[l + 1].eo, bc, self.p.coarse_tol,
+                                   self.p.coarse_restart, self.p.coarse_cycles)
+        else:
+            zc, _ = fgmres(self.levels[l + 1].op.apply, bc, M=lambda v: self.kcycle(l + 1, v),
+                           m=self.p.kcycle_len, tol=self.p.kcycle_tol,
+                           max_cycles=self.p.kcycle_cycles, final_residual=False)
+        self.last_iterate[l + 1] = zc
+        z = z + prolong(lev.P, self.p.agg[l], zc)
+        z = lev.sap.smooth(b, z, self.p.nu)
+        self.last_iterate[l] = z
+        return z
+
+    def solve(self, b, tol=1e-10, restart=None, max_cycles=None):
+        """Outer FGMRES on D preconditioned by the K-cycle (all FP64)."""
+        D = self.levels[0].op.apply
+        return fgmres(D, b, M=lambda v: self.kcycle(0, v), m=restart or self.p.outer_restart,
+                      tol=tol, max_cycles=max_cycles or self.p.outer_max_cycles)
+
+    # --- setup (Alg. 3, Alg. 4) ---------------------------------------------------
+    def initial_setup_phase(self, l, random_tv):
+        lev = self.levels[l]
+        N = self.p.n_tv[l]
+        if l == 0:
+            v = random_tv[0].copy()
+        else:
+            up = self.levels[l - 1]
+            Nup = self.p.n_tv[l - 1]
+            take = min(N, Nup)
+            v = restrict(up.P, self.p.agg[l - 1], up.tv[:take])
+            if N > take:
+                v = np.concatenate([v, random_tv[l][:N - take]], axis=0)
+        if lev.sap is None:
+            self._make_sap(l)
+        for eta in range(1, self.p.eta_passes + 1):
+            for j in range(N):
+                x = np.zeros_like(v[j])
+                for _ in range(eta):
+                    x = x + lev.sap(v[j] - lev.op.apply(x))
+                v[j] = x
+                if self.trace is not None:
+                    self.trace.add("smooth", l, eta, j)
+        lev.tv = v
+        self.rebuild(l)
+        if l < self.L - 2:
+            self.initial_setup_phase(l + 1, random_tv)
+
+    def iterative_setup_phase(self, l, i):
+        if l >= self.L - 1:
+            return
+        for j in range(self.p.n_tv[l]):
+            self.last_iterate = {}
+            if self.trace is not None:
+                self.trace.add("iterate", l, i, j)
+            self.kcycle(l, self.levels[l].tv[j])
+            for k in range(l, self.L - 1):
+                if j < self.p.n_tv[k] and k in self.last_iterate:
+                    zk = self.last_iterate[k]
+                    self.levels[k].tv[j] = zk / norm(zk)
+        for k in range(l, self.L - 1):
+            self.rebuild(k)
+        for q in range(1, i + 1):
+            self.iterative_setup_phase(l + 1, q)
+
+    def setup(self, random_tv, trace: bool = False):
+        self.trace = Trace() if trace else None
+        self.initial_setup_phase(0, random_tv)
+        for i in range(1, self.p.n_inv + 1):
+            self.iterative_setup_phase(0, i)
+        return self
+
+
+def build_hierarchy(fine_op, params: Params, random_tv, trace=False) -> Hierarchy:
+    return Hierarchy(fine_op, params).setup(random_tv, trace=trace)

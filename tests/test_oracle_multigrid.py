@@ -1,0 +1,122 @@
+"""Pins of the multilevel cycle (Alg. 1/2, the E_2g form of Sec. 1) and of the setup (Alg. 3/4)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle.lattice import norm
+from oracle.wilson import WilsonOp
+from oracle.spectrum import sparse_matrix
+from oracle.smoother import SAP
+from oracle.transfer import build_interpolation, galerkin, prolong, restrict, coarse_dims
+from oracle.multigrid import Params, Hierarchy, build_hierarchy
+from oracle.stencil import EvenOdd
+
+DIMS = (4, 4, 4, 4)
+
+
+def _dense_P(Pf, agg):
+    dims = Pf.shape[1:5]
+    cd = coarse_dims(dims, agg)
+    nc = 2 * Pf.shape[0]
+    I = np.eye(int(np.prod(cd)) * nc)
+    return np.stack([prolong(Pf, agg, e.reshape(cd + (nc,))).ravel() for e in I], axis=1)
+
+
+def _two_level(nu, exact_sap):
+    op = WilsonOp.build(synth.su3_field(DIMS, 0.4, 1), -0.2, 1.0, -1)
+    p = Params(levels=2, agg=((2, 2, 2, 2),), n_tv=(3,), sap_block=((2, 2, 2, 2), None),
+               mr_steps=3, nu=nu, mu=0, coarse_tol=1e-15, coarse_restart=100, coarse_cycles=5)
+    h = Hierarchy(op, p)
+    h.levels[0].tv = synth.random_fields(3, DIMS, 12, 2)
+    h.rebuild(0)
+    h.levels[0].sap = SAP(op, (2, 2, 2, 2), 3, exact=exact_sap)
+    return op, h
+
+
+def test_two_level_cycle_without_smoothing_is_coarse_correction():
+    op, h = _two_level(nu=0, exact_sap=False)
+    b = synth.random_spinors(1, DIMS, 3)[0]
+    z = h.kcycle(0, b)
+    Pd = _dense_P(h.levels[0].P, (2, 2, 2, 2))
+    D = sparse_matrix(op).toarray()
+    Dc = Pd.conj().T @ D @ Pd
+    ref = Pd @ np.linalg.solve(Dc, Pd.conj().T @ b.ravel())
+    assert norm(z.ravel() - ref) <= 1e-11 * norm(ref)
+    # I - P Dc^{-1} P^+ D is a projector
+    C = np.eye(D.shape[0]) - Pd @ np.linalg.solve(Dc, Pd.conj().T @ D)
+    assert np.abs(C @ C - C).max() < 1e-10
+
+
+def test_two_level_error_propagator_E2g():
+    """With exact block solves (linear M) and exact coarse solve, e -> e - z(De) equals
+    E_2g e = (I - M D)^nu (I - P Dc^{-1} P^+ D) e  (Sec. 1, mu = 0)."""
+    nu = 2
+    op, h = _two_level(nu=nu, exact_sap=True)
+    D = sparse_matrix(op).toarray()
+    e = synth.random_spinors(1, DIMS, 4)[0]
+    b = op.apply(e)
+    z = h.kcycle(0, b)
+    Pd = _dense_P(h.levels[0].P, (2, 2, 2, 2))
+    Dc = Pd.conj().T @ D @ Pd
+    n = D.shape[0]
+    M = np.stack([h.levels[0].sap(col.reshape(DIMS + (12,))).ravel() for col in np.eye(n)], axis=1)
+    E = np.linalg.matrix_power(np.eye(n) - M @ D, nu) @ (np.eye(n) - Pd @ np.linalg.solve(Dc, Pd.conj().T @ D))
+    assert norm((e - z).ravel() - E @ e.ravel()) <= 1e-10 * norm(e)
+
+
+def test_setup_call_sequence_replays_alg3_alg4():
+    """The setup's steps in order, replayed by hand from Alg. 3 and Alg. 4 (L = 3, n_inv = 2)."""
+    dims = (8, 4, 4, 4)
+    op = WilsonOp.build(synth.su3_field(dims, 0.3, 1), -0.1, 0.0, -1)
+    N0, N1 = 2, 3
+    p = Params(levels=3, agg=((2, 2, 2, 2), (2, 1, 1, 1)), n_tv=(N0, N1),
+               sap_block=((2, 2, 2, 2), (2, 2, 2, 2), None), mr_steps=2, nu=1, n_inv=2)
+    c1 = coarse_dims(dims, (2, 2, 2, 2))
+    rtv = [synth.random_fields(N0, dims, 12, 2), synth.random_fields(N1 - N0, c1, 2 * N0, 3)]
+    h = build_hierarchy(op, p, rtv, trace=True)
+    got = [e for e in h.trace.events if e[0] != "kcycle"]
+    exp = []
+    # Alg. 3 on level 0, then on level 1
+    for lvl, N in ((0, N0), (1, N1)):
+        for eta in (1, 2, 3):
+            for j in range(N):
+                exp.append(("smooth", lvl, eta, j))
+        exp.append(("build", lvl))
+    # Alg. 4: for i = 1..n_inv: iterative_setup_phase(0, i)
+    for i in (1, 2):
+        exp += [("iterate", 0, i, j) for j in range(N0)]
+        exp += [("build", 0), ("build", 1)]
+        for q in range(1, i + 1):                      # iterative_setup_phase(1, q)
+            exp += [("iterate", 1, q, j) for j in range(N1)]
+            exp += [("build", 1)]
+    assert got == exp
+    # the updated test vectors are normalised and P stays orthonormal
+    for lvl in (0, 1):
+        for v in h.levels[lvl].tv:
+            assert abs(norm(v) - 1.0) < 1e-12
+
+
+def test_two_level_solve_matches_dense_lu():
+    op = WilsonOp.build(synth.su3_field(DIMS, 0.3, 0), -0.35, 0.0, -1)
+    p = Params(levels=2, agg=((2, 2, 2, 2),), n_tv=(6,), sap_block=((2, 2, 2, 2), None),
+               mr_steps=4, nu=3, n_inv=2, outer_restart=25)
+    h = build_hierarchy(op, p, [synth.random_fields(6, DIMS, 12, 5)])
+    b = synth.random_spinors(1, DIMS, 1)[0]
+    x, info = h.solve(b, tol=1e-10)
+    D = sparse_matrix(op).toarray()
+    xd = np.linalg.solve(D, b.ravel())
+    s = np.linalg.svd(D, compute_uv=False)
+    assert info.converged and norm(op.apply(x) - b) <= 1e-10 * norm(b)
+    assert norm(x.ravel() - xd) <= (s[0] / s[-1]) * 1e-10 * norm(xd)
+
+
+def test_three_level_solve_converges():
+    dims = (8, 4, 4, 4)
+    op = WilsonOp.build(synth.su3_field(dims, 0.4, 2), -0.4, 1.0, -1)
+    p = Params(levels=3, agg=((2, 2, 2, 2), (2, 1, 1, 1)), n_tv=(4, 6),
+               sap_block=((2, 2, 2, 2), (2, 2, 2, 2), None), mr_steps=3, nu=2, n_inv=1)
+    c1 = coarse_dims(dims, (2, 2, 2, 2))
+    h = build_hierarchy(op, p, [synth.random_fields(4, dims, 12, 2), synth.random_fields(2, c1, 8, 3)])
+    b = synth.random_spinors(1, dims, 4)[0]
+    x, info = h.solve(b, tol=1e-10)
+    assert info.converged and norm(op.apply(x) - b) <= 1e-10 * norm(b)
