@@ -1,0 +1,155 @@
+/*
+ * ddamg.h -- C ABI of the GB300 DD-alpha-AMG solver for the lattice
+ * Wilson-clover Dirac system D z = b (Frommer, Kahl, Krieg, Leder, Rottmann,
+ * "An adaptive aggregation based domain decomposition multilevel method for
+ * the lattice Wilson Dirac operator: multilevel results").
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Lattice: dims = {T, Z, Y, X}; direction mu = 0..3 is t, z, y, x.  A site's
+ *   lexicographic index is ((t*Z + z)*Y + y)*X + x.
+ * Gauge field (input to ddamg_setup): FP64 complex, [site lex][mu][3][3][re,im],
+ *   i.e. 4*9 complex per site.  The time-direction boundary sign (bc_t = -1 for
+ *   antiperiodic) is applied by the library; it is not part of the links.
+ * Fine fields (level 0): FP64 complex, [n][site lex][spin][colour][re,im]:
+ *   12 complex per site, index spin*3 + colour, chiral basis with
+ *   Gamma_5 = diag(+1, +1, -1, -1) in spin (Sec. 1 of the paper).
+ * Coarse fields (level l >= 1): FP64 complex, [n][coarse site lex][dof][re,im];
+ *   level l carries ndof = 2 * n_tv[l-1] dof per site, chirality + first.
+ * Pointers may be host or device memory (cudaPointerGetAttributes decides);
+ *   the caller owns them.  Host pointers are copied through library-owned
+ *   device staging buffers.  Every call returns after its results are
+ *   complete (the library stream is synchronised before returning).
+ * The library owns every device allocation it makes; ddamg_free releases them.
+ * Return values: DDAMG_OK (0) or a negative DDAMG_ERR_* code;
+ *   ddamg_last_error() returns a message for the last failure of the thread.
+ * Thread safety: one handle must not be used by two threads at once.
+ */
+#ifndef DDAMG_H
+#define DDAMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DDAMG_OK = 0,
+  DDAMG_ERR_ARG = -1,       /* invalid argument or unsupported geometry        */
+  DDAMG_ERR_OOM = -2,       /* device allocation failed / admission refused    */
+  DDAMG_ERR_NOCONV = -3,    /* outer FGMRES did not reach tol within its limit */
+  DDAMG_ERR_CUDA = -4,      /* a CUDA call failed                              */
+  DDAMG_ERR_SINGULAR = -5   /* rank-deficient test vectors / singular block    */
+};
+
+#define DDAMG_MAX_LEVELS 4
+
+/* Parameters of the method (Table 1 of the paper gives the defaults that
+ * ddamg_default_params fills in). */
+typedef struct ddamg_params {
+  int levels;                          /* L >= 2                                         */
+  int agg[DDAMG_MAX_LEVELS][4];        /* aggregate of level l (defines P_l), t,z,y,x    */
+  int n_tv[DDAMG_MAX_LEVELS];          /* test vectors N_l of level l (P_l has 2N_l cols) */
+  int sap_block[DDAMG_MAX_LEVELS][4];  /* SAP block of level l (l < L-1)                 */
+  int mr_steps;                        /* MR steps per SAP block solve (Table 1: 3)      */
+  int nu;                              /* post-smoothing steps (Table 1: 5)              */
+  int mu;                              /* pre-smoothing steps (Table 1: 0)               */
+  int n_inv;                           /* iterative setup iterations (Table 1: 6)        */
+  int eta_passes;                      /* passes of Alg. 3's smoothing loop (3)          */
+  int outer_restart;                   /* n_kv (Table 1: 10), at most 63                 */
+  int outer_max_cycles;                /* restart cycles before DDAMG_ERR_NOCONV          */
+  int kcycle_len;                      /* K-cycle FGMRES length (Table 1: 5)             */
+  int kcycle_cycles;                   /* K-cycle FGMRES cycles (Table 1: 2 restarts)    */
+  double kcycle_tol;                   /* K-cycle relative tolerance (Table 1: 0.1)      */
+  double coarse_tol;                   /* coarsest relative tolerance (Table 1: 5e-2)    */
+  int coarse_restart;                  /* coarsest GMRES restart length (<= 63)          */
+  int coarse_cycles;                   /* coarsest GMRES cycles                          */
+  int precision;                       /* 0: preconditioner FP64; 1: FP32 (mixed)        */
+  int max_rhs;                         /* right-hand sides per batch                     */
+} ddamg_params;
+
+typedef struct ddamg_stats {
+  int iterations;        /* outer FGMRES iterations                          */
+  int cycles;            /* outer restart cycles                             */
+  int converged;         /* 1 if ||b - D x|| <= tol ||b|| (FP64, true residual) */
+  double true_residual;  /* ||b - D x|| / ||b|| at return                    */
+} ddamg_stats;
+
+typedef struct ddamg_handle ddamg_handle;
+
+/* Table 1 defaults: L = 3, aggregates 4^4 then 2^4, N = 20, SAP blocks 2^4,
+ * 3 MR steps, nu = 5, mu = 0, n_inv = 6, n_kv = 10, K-cycle 5/2/0.1,
+ * coarsest tolerance 5e-2 (restart 50, 20 cycles), mixed precision, 1 rhs. */
+void ddamg_default_params(ddamg_params* p);
+
+/* Builds the hierarchy: imports the gauge field, builds the clover term
+ * (c_sw), runs the initial setup (Alg. 3) and n_inv iterative setup phases
+ * (Alg. 4).  tv_random[l] are the random start vectors of the setup:
+ * tv_random[0] holds n_tv[0] fine fields; tv_random[l] (l >= 1) holds
+ * max(0, n_tv[l] - n_tv[l-1]) level-l fields (may be NULL when that is 0).
+ * On success *out is a new handle.  Errors: ARG (geometry: extents must be
+ * divisible by aggregates and SAP blocks, SAP block counts even or 1, coarsest
+ * extents even), OOM, SINGULAR, CUDA. */
+int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, double csw,
+                const ddamg_params* params, const double* const* tv_random, ddamg_handle** out);
+
+/* Solves D x_i = rhs_i, i < n, with FGMRES(n_kv) in FP64 right-preconditioned
+ * by one K-cycle (Alg. 2) per iteration (the preconditioner in FP32 when
+ * precision = 1).  Batches of up to max_rhs right-hand sides share every
+ * kernel launch; larger n is split into consecutive batches.  per_rhs may be
+ * NULL.  Returns NOCONV (x holds the last iterate) if any rhs missed tol. */
+int ddamg_solve(ddamg_handle* h, const double* rhs, double* x, int n, double tol, ddamg_stats* per_rhs);
+
+void ddamg_free(ddamg_handle* h);
+
+const char* ddamg_last_error(void);
+
+/* Runs the library's kernels on this CUDA stream from now on (cudaStream_t;
+ * NULL = the library's own stream). */
+int ddamg_set_stream(ddamg_handle* h, void* stream);
+
+/* ---- building blocks of the method, exposed for parity tests ------------ */
+
+/* Level geometry: dims of level l, its dof per site, its test vectors N_l
+ * (0 on the coarsest level). */
+int ddamg_level_info(ddamg_handle* h, int level, int dims[4], int* ndof, int* ntv);
+
+/* out = D_l in (n fields of level l). precision 0 = FP64, 1 = FP32 copy. */
+int ddamg_apply(ddamg_handle* h, int level, int precision, const double* in, double* out, int n);
+
+/* iterations x { z <- z + M_SAP (b - D_l z) } on level l < L-1 (z in/out). */
+int ddamg_smooth(ddamg_handle* h, int level, int precision, const double* b, double* z, int n, int iterations);
+
+/* coarse = P_l^dagger fine (level l -> l+1). */
+int ddamg_restrict(ddamg_handle* h, int level, int precision, const double* fine, double* coarse, int n);
+
+/* fine = P_l coarse (level l+1 -> l). */
+int ddamg_prolong(ddamg_handle* h, int level, int precision, const double* coarse, double* fine, int n);
+
+/* z = K-cycle(l, b) (Alg. 2, one application, mu/nu from the parameters). */
+int ddamg_kcycle(ddamg_handle* h, int level, int precision, const double* b, double* z, int n);
+
+/* z = coarsest-level solve of b: even-odd preconditioned GMRES to coarse_tol. */
+int ddamg_coarse_solve(ddamg_handle* h, int precision, const double* b, double* z, int n);
+
+/* Test vectors of level l (N_l fields of level l). */
+int ddamg_set_testvectors(ddamg_handle* h, int level, const double* tv, int n);
+int ddamg_get_testvectors(ddamg_handle* h, int level, double* tv, int n);
+
+/* Rebuilds P_l (CGS2 per aggregate and chirality) from the current test
+ * vectors and D_{l+1} = P_l^dagger D_l P_l. */
+int ddamg_rebuild(ddamg_handle* h, int level);
+
+/* P_l as N_l fields of level l (the orthonormalised test vectors). */
+int ddamg_get_interpolation(ddamg_handle* h, int level, double* P);
+
+/* D_l (l >= 1) as blocks [coarse site lex][k][row][col] complex, k = 0 self,
+ * 1..4 forward mu = t,z,y,x (couples to site + mu), 5..8 backward mu. */
+int ddamg_get_coarse_operator(ddamg_handle* h, int level, double* blocks);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDAMG_H */

@@ -1,0 +1,553 @@
+// Fine-level (Wilson-clover) kernels.
+//
+// D psi(x) = A(x) psi(x) - 1/2 sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+//                                     + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu) ]
+// with A(x) = (m0 + 4) + C(x), C the clover term (the operator of Sec. 1 of
+// the paper, whose gamma_5-symmetry D Gamma_5 = Gamma_5 D^+ needs a chiral basis
+// where Gamma_5 = diag(1, 1, -1, -1)).  In that basis
+//   gamma_t = [[0, 1], [1, 0]],  gamma_k = [[0, -i sigma_k], [i sigma_k, 0]],
+// so (1 -+ gamma_mu) has rank 2 in spin: each hop projects the neighbour onto a
+// two-spin half spinor h, multiplies the two colour vectors of h by the link,
+// and reconstructs the lower two spins from the upper two:
+//   forward  (1 - gamma_t): h = up - dn,            lower = -h
+//   backward (1 + gamma_t): h = up + dn,            lower = +h
+//   forward  (1 - gamma_k): h = up + i sigma_k dn,  lower = -i sigma_k h
+//   backward (1 + gamma_k): h = up - i sigma_k dn,  lower = +i sigma_k h
+// The antiperiodic sign of the time direction multiplies the hop that wraps.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+template <typename T>
+DD_HD void isigma(int mu, const cplx<T>* v0, const cplx<T>* v1, cplx<T>* w0, cplx<T>* w1) {
+  // (w0, w1) = i sigma (v0, v1), sigma = sigma_z (mu = 1), sigma_y (mu = 2), sigma_x (mu = 3)
+  if (mu == 3) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { w0[a] = times_i(v1[a]); w1[a] = times_i(v0[a]); }
+  } else if (mu == 2) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { w0[a] = v1[a]; w1[a] = -v0[a]; }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { w0[a] = times_i(v0[a]); w1[a] = times_mi(v1[a]); }
+  }
+}
+
+template <typename T>
+DD_HD void su3_mul(const cplx<T> u[9], const cplx<T> v[3], cplx<T> w[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cplx<T> s = u[a * 3 + 0] * v[0];
+    cfma(s, u[a * 3 + 1], v[1]);
+    cfma(s, u[a * 3 + 2], v[2]);
+    w[a] = s;
+  }
+}
+
+template <typename T>
+DD_HD void su3_dag_mul(const cplx<T> u[9], const cplx<T> v[3], cplx<T> w[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cplx<T> s = cdotc(u[0 * 3 + a], v[0]);
+    cfmac(s, u[1 * 3 + a], v[1]);
+    cfmac(s, u[2 * 3 + a], v[2]);
+    w[a] = s;
+  }
+}
+
+// acc += (1 - gamma_mu) U psi   (forward, fwd = true)  or  (1 + gamma_mu) U^+ psi (backward)
+template <typename T>
+DD_HD void hop_accumulate(int mu, bool fwd, const cplx<T> u[9], const cplx<T> psi[12], cplx<T> acc[12]) {
+  cplx<T> h0[3], h1[3];
+  const cplx<T>* up0 = psi + 0;
+  const cplx<T>* up1 = psi + 3;
+  const cplx<T>* dn0 = psi + 6;
+  const cplx<T>* dn1 = psi + 9;
+  if (mu == 0) {
+    const T s = fwd ? T(-1) : T(1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { h0[a] = up0[a] + s * dn0[a]; h1[a] = up1[a] + s * dn1[a]; }
+  } else {
+    cplx<T> q0[3], q1[3];
+    isigma(mu, dn0, dn1, q0, q1);
+    if (fwd) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { h0[a] = up0[a] + q0[a]; h1[a] = up1[a] + q1[a]; }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { h0[a] = up0[a] - q0[a]; h1[a] = up1[a] - q1[a]; }
+    }
+  }
+  cplx<T> g0[3], g1[3];
+  if (fwd) { su3_mul(u, h0, g0); su3_mul(u, h1, g1); }
+  else { su3_dag_mul(u, h0, g0); su3_dag_mul(u, h1, g1); }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) { acc[a] = acc[a] + g0[a]; acc[3 + a] = acc[3 + a] + g1[a]; }
+  if (mu == 0) {
+    const T s = fwd ? T(-1) : T(1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { acc[6 + a] = acc[6 + a] + s * g0[a]; acc[9 + a] = acc[9 + a] + s * g1[a]; }
+  } else {
+    cplx<T> q0[3], q1[3];
+    isigma(mu, g0, g1, q0, q1);
+    if (fwd) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { acc[6 + a] = acc[6 + a] - q0[a]; acc[9 + a] = acc[9 + a] - q1[a]; }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { acc[6 + a] = acc[6 + a] + q0[a]; acc[9 + a] = acc[9 + a] + q1[a]; }
+    }
+  }
+}
+
+// packed Hermitian 6x6: 6 real diagonals, then the 15 upper off-diagonals (row-major) as re, im
+DD_HD int herm_off(int i, int j) { return i * 6 - (i * (i + 1)) / 2 + (j - i - 1); }
+
+template <typename T>
+DD_HD void clover_apply(const T* __restrict__ clov, int V, int x, const cplx<T> in[12], cplx<T> out[12]) {
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch) {
+    const T* a = clov + (size_t)ch * 36 * V + x;
+    const cplx<T>* v = in + 6 * ch;
+    cplx<T>* w = out + 6 * ch;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) w[i] = a[(size_t)i * V] * v[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        const int p = 6 + 2 * herm_off(i, j);
+        cplx<T> e = cmk<T>(a[(size_t)p * V], a[(size_t)(p + 1) * V]);
+        cfma(w[i], e, v[j]);
+        cfmac(w[j], e, v[i]);
+      }
+    }
+  }
+}
+
+template <typename T>
+DD_HD void load_link(const cplx<T>* __restrict__ U, int V, int mu, int x, cplx<T> u[9]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = U[(size_t)(mu * 9 + k) * V + x];
+}
+
+template <typename T>
+DD_HD void load_spinor(const cplx<T>* __restrict__ p, int V, int x, cplx<T> s[12], T sign, int chir) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const bool keep = chir < 0 || (k / 6) == chir;
+    s[k] = keep ? sign * p[(size_t)k * V + x] : czero<T>();
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, bool RESID>
+__global__ void k_fine_dslash(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in,
+                              const cplx<T>* __restrict__ bsrc, const cplx<T>* __restrict__ U,
+                              const T* __restrict__ clov, Geom g, int bc_t, size_t rstride,
+                              int sel, int sel_mu, int in_chir) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.V) return;
+  const size_t ro = (size_t)blockIdx.y * rstride;
+  const cplx<T>* ps = in + ro;
+  const int V = g.V;
+  int c[4];
+  geom_coords(g, x, c);
+  cplx<T> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = czero<T>();
+  cplx<T> nb[12], u[9];
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    const bool inf = hop_internal(g, c, mu, +1, g.A);
+    const bool inb = hop_internal(g, c, mu, -1, g.A);
+    bool tf = true, tb = true;
+    if (sel == SEL_AGG_SELF) { tf = inf; tb = inb; }
+    else if (sel == SEL_AGG_FWD) { tf = (mu == sel_mu) && !inf; tb = false; }
+    else if (sel == SEL_AGG_BWD) { tf = false; tb = (mu == sel_mu) && !inb; }
+    if (tf) {
+      const int n = geom_neighbor(g, c, mu, +1);
+      const T sgn = (mu == 0 && c[0] == g.L[0] - 1) ? T(bc_t) : T(1);
+      load_spinor(ps, V, n, nb, sgn, in_chir);
+      load_link(U, V, mu, x, u);
+      hop_accumulate(mu, true, u, nb, acc);
+    }
+    if (tb) {
+      const int n = geom_neighbor(g, c, mu, -1);
+      const T sgn = (mu == 0 && c[0] == 0) ? T(bc_t) : T(1);
+      load_spinor(ps, V, n, nb, sgn, in_chir);
+      load_link(U, V, mu, n, u);
+      hop_accumulate(mu, false, u, nb, acc);
+    }
+  }
+  cplx<T> d[12];
+  if (sel == SEL_FULL || sel == SEL_AGG_SELF) {
+    load_spinor(ps, V, x, nb, T(1), in_chir);
+    clover_apply(clov, V, x, nb, d);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) d[k] = czero<T>();
+  }
+  cplx<T>* po = out + ro;
+  if (RESID) {
+    const cplx<T>* pb = bsrc + ro;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) po[(size_t)k * V + x] = pb[(size_t)k * V + x] - (d[k] - T(0.5) * acc[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) po[(size_t)k * V + x] = d[k] - T(0.5) * acc[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Segmented sum over groups of `seg` consecutive threads (seg a power of two);
+// groups wider than a warp combine warp partials through shared memory.
+template <typename T>
+__device__ void seg_sum3(T& a, T& b, T& c, int seg, T* scratch) {
+  const int w = seg < 32 ? seg : 32;
+  for (int off = w >> 1; off >= 1; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+    c += __shfl_xor_sync(0xffffffffu, c, off);
+  }
+  if (seg > 32) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { scratch[3 * warp] = a; scratch[3 * warp + 1] = b; scratch[3 * warp + 2] = c; }
+    __syncthreads();
+    const int wps = seg >> 5;
+    const int first = (warp / wps) * wps;
+    a = b = c = T(0);
+    for (int i = 0; i < wps; ++i) {
+      a += scratch[3 * (first + i)];
+      b += scratch[3 * (first + i) + 1];
+      c += scratch[3 * (first + i) + 2];
+    }
+    __syncthreads();
+  }
+}
+
+// One colour sweep of SAP on the fine level (multiplicative Schwarz, Sec. 1):
+// for every SAP block B of the colour, rho_B = (b - D z)_B, k minimal-residual
+// steps on D_B e = rho_B (hops leaving B dropped), then z_B += e_B.  Written in
+// terms of z: the black sweep's rho = b - D z sees the red update, which is the
+// same as r - D e with e the red correction.  One CTA segment of `seg` threads
+// per block, one thread per site; the block's residual lives in shared memory.
+template <typename T>
+__global__ void k_fine_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
+                           const cplx<T>* __restrict__ U, const T* __restrict__ clov, Geom g, int bc_t,
+                           size_t rstride, const int* __restrict__ blocks, int nblocks, int seg,
+                           int k_mr) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);            // [blockDim.x][12]
+  T* scratch = reinterpret_cast<T*>(rs + (size_t)blockDim.x * 12);  // [warps][3]
+  const int segs = blockDim.x / seg;
+  const int s = threadIdx.x / seg;
+  const int loc = threadIdx.x - s * seg;
+  const int bi = blockIdx.x * segs + s;
+  const bool active = (bi < nblocks) && (loc < g.vB);
+  const int blk = active ? blocks[bi] : 0;
+  const int x = blk * g.vB + loc;
+  const int V = g.V;
+  const size_t ro = (size_t)blockIdx.y * rstride;
+  cplx<T>* pz = z + ro;
+  int c[4] = {0, 0, 0, 0};
+  cplx<T> r[12], xs[12], p[12], nb[12], u[9];
+  if (active) {
+    geom_coords(g, x, c);
+    // rho = b - D z at x
+    cplx<T> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = czero<T>();
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+      int n = geom_neighbor(g, c, mu, +1);
+      T sgn = (mu == 0 && c[0] == g.L[0] - 1) ? T(bc_t) : T(1);
+      load_spinor(pz, V, n, nb, sgn, -1);
+      load_link(U, V, mu, x, u);
+      hop_accumulate(mu, true, u, nb, acc);
+      n = geom_neighbor(g, c, mu, -1);
+      sgn = (mu == 0 && c[0] == 0) ? T(bc_t) : T(1);
+      load_spinor(pz, V, n, nb, sgn, -1);
+      load_link(U, V, mu, n, u);
+      hop_accumulate(mu, false, u, nb, acc);
+    }
+    load_spinor(pz, V, x, nb, T(1), -1);
+    clover_apply(clov, V, x, nb, p);
+    const cplx<T>* pb = bsrc + ro;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      r[k] = pb[(size_t)k * V + x] - (p[k] - T(0.5) * acc[k]);
+      xs[k] = czero<T>();
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { r[k] = czero<T>(); xs[k] = czero<T>(); }
+  }
+  const int base = s * seg;   // shared-memory slot of the block's first site
+#pragma unroll 1
+  for (int it = 0; it < k_mr; ++it) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) rs[(size_t)threadIdx.x * 12 + k] = r[k];
+    __syncthreads();
+    T nre = T(0), nim = T(0), den = T(0);
+    if (active) {
+      cplx<T> acc[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = czero<T>();
+#pragma unroll 1
+      for (int mu = 0; mu < 4; ++mu) {
+        if (hop_internal(g, c, mu, +1, g.B)) {
+          const int n = geom_neighbor(g, c, mu, +1);
+          const int sl = base + (n - blk * g.vB);
+#pragma unroll
+          for (int k = 0; k < 12; ++k) nb[k] = rs[(size_t)sl * 12 + k];
+          load_link(U, V, mu, x, u);
+          hop_accumulate(mu, true, u, nb, acc);
+        }
+        if (hop_internal(g, c, mu, -1, g.B)) {
+          const int n = geom_neighbor(g, c, mu, -1);
+          const int sl = base + (n - blk * g.vB);
+#pragma unroll
+          for (int k = 0; k < 12; ++k) nb[k] = rs[(size_t)sl * 12 + k];
+          load_link(U, V, mu, n, u);
+          hop_accumulate(mu, false, u, nb, acc);
+        }
+      }
+      clover_apply(clov, V, x, r, p);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        p[k] = p[k] - T(0.5) * acc[k];
+        const cplx<T> t = cdotc(p[k], r[k]);
+        nre += t.re;
+        nim += t.im;
+        den += cnorm2(p[k]);
+      }
+    }
+    seg_sum3(nre, nim, den, seg, scratch);
+    const cplx<T> alpha = den > T(0) ? cmk<T>(nre / den, nim / den) : czero<T>();
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      cfma(xs[k], alpha, r[k]);
+      r[k] = r[k] - alpha * p[k];
+    }
+    __syncthreads();
+  }
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) pz[(size_t)k * V + x] = pz[(size_t)k * V + x] + xs[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Clover construction (FP64).  Q_mu_nu(x) = sum of the four plaquette leaves
+// at x in the mu-nu plane; A(x) = (m0 + 4) - (c_sw / 16) sum_{mu<nu}
+// (gamma_mu gamma_nu) (x) (Q_mu_nu - Q_mu_nu^+), which is the sum over ordered
+// pairs with weight -(c_sw/32).  Stored as two packed Hermitian 6x6 blocks.
+__constant__ double2 c_gg[6][4][4];   // gamma_mu gamma_nu for the 6 planes mu < nu
+
+using cd = cplx<double>;
+
+DD_HD void m3_mul(const cd* a, const cd* b, cd* c) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      cd s = a[i * 3] * b[j];
+      cfma(s, a[i * 3 + 1], b[3 + j]);
+      cfma(s, a[i * 3 + 2], b[6 + j]);
+      c[i * 3 + j] = s;
+    }
+}
+DD_HD void m3_dag(const cd* a, cd* c) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) c[i * 3 + j] = cconj(a[j * 3 + i]);
+}
+
+__device__ void lex_link(const cd* __restrict__ gl, const int L[4], const int c[4], int dshift0, int s0,
+                         int dshift1, int s1, int mu, cd* out) {
+  int n[4] = {c[0], c[1], c[2], c[3]};
+  if (s0) { n[dshift0] = (n[dshift0] + s0 + L[dshift0]) % L[dshift0]; }
+  if (s1) { n[dshift1] = (n[dshift1] + s1 + L[dshift1]) % L[dshift1]; }
+  const size_t site = (size_t)lin4(n, L);
+  for (int k = 0; k < 9; ++k) out[k] = gl[(site * 4 + mu) * 9 + k];
+}
+
+__global__ void k_clover_build(double* __restrict__ clov, const cd* __restrict__ gl, Geom g, double m0,
+                               double csw) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.V) return;
+  int c[4];
+  geom_coords(g, x, c);
+  cd A[2][6][6];
+  for (int ch = 0; ch < 2; ++ch)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) A[ch][i][j] = cmk(i == j ? m0 + 4.0 : 0.0, 0.0);
+  if (csw != 0.0) {
+    int plane = 0;
+    for (int mu = 0; mu < 4; ++mu)
+      for (int nu = mu + 1; nu < 4; ++nu, ++plane) {
+        cd Q[9], t1[9], t2[9], a[9], b[9], cc[9], d[9], da[9];
+        for (int k = 0; k < 9; ++k) Q[k] = czero<double>();
+        // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+        lex_link(gl, g.L, c, 0, 0, 0, 0, mu, a);
+        lex_link(gl, g.L, c, mu, 1, 0, 0, nu, b);
+        lex_link(gl, g.L, c, nu, 1, 0, 0, mu, cc);
+        lex_link(gl, g.L, c, 0, 0, 0, 0, nu, d);
+        m3_mul(a, b, t1); m3_dag(cc, da); m3_mul(t1, da, t2); m3_dag(d, da); m3_mul(t2, da, t1);
+        for (int k = 0; k < 9; ++k) Q[k] = Q[k] + t1[k];
+        // leaf 2: U_nu(x) U_mu(x+nu-mu)^+ U_nu(x-mu)^+ U_mu(x-mu)
+        lex_link(gl, g.L, c, 0, 0, 0, 0, nu, a);
+        lex_link(gl, g.L, c, nu, 1, mu, -1, mu, b);
+        lex_link(gl, g.L, c, mu, -1, 0, 0, nu, cc);
+        lex_link(gl, g.L, c, mu, -1, 0, 0, mu, d);
+        m3_dag(b, da); m3_mul(a, da, t1); m3_dag(cc, da); m3_mul(t1, da, t2); m3_mul(t2, d, t1);
+        for (int k = 0; k < 9; ++k) Q[k] = Q[k] + t1[k];
+        // leaf 3: U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
+        lex_link(gl, g.L, c, mu, -1, 0, 0, mu, a);
+        lex_link(gl, g.L, c, mu, -1, nu, -1, nu, b);
+        lex_link(gl, g.L, c, mu, -1, nu, -1, mu, cc);
+        lex_link(gl, g.L, c, nu, -1, 0, 0, nu, d);
+        m3_dag(a, da); m3_dag(b, t2); m3_mul(da, t2, t1); m3_mul(t1, cc, t2); m3_mul(t2, d, t1);
+        for (int k = 0; k < 9; ++k) Q[k] = Q[k] + t1[k];
+        // leaf 4: U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^+
+        lex_link(gl, g.L, c, nu, -1, 0, 0, nu, a);
+        lex_link(gl, g.L, c, nu, -1, 0, 0, mu, b);
+        lex_link(gl, g.L, c, nu, -1, mu, 1, nu, cc);
+        lex_link(gl, g.L, c, 0, 0, 0, 0, mu, d);
+        m3_dag(a, da); m3_mul(da, b, t1); m3_mul(t1, cc, t2); m3_dag(d, da); m3_mul(t2, da, t1);
+        for (int k = 0; k < 9; ++k) Q[k] = Q[k] + t1[k];
+        cd F[9];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) F[i * 3 + j] = Q[i * 3 + j] - cconj(Q[j * 3 + i]);
+        const double w = -csw / 16.0;
+        for (int ch = 0; ch < 2; ++ch)
+          for (int s = 0; s < 2; ++s)
+            for (int t = 0; t < 2; ++t) {
+              const double2 gv = c_gg[plane][2 * ch + s][2 * ch + t];
+              const cd gs = cmk(w * gv.x, w * gv.y);
+              for (int a3 = 0; a3 < 3; ++a3)
+                for (int b3 = 0; b3 < 3; ++b3) cfma(A[ch][s * 3 + a3][t * 3 + b3], gs, F[a3 * 3 + b3]);
+            }
+      }
+  }
+  for (int ch = 0; ch < 2; ++ch) {
+    double* o = clov + (size_t)ch * 36 * g.V + x;
+    for (int i = 0; i < 6; ++i) o[(size_t)i * g.V] = A[ch][i][i].re;
+    for (int i = 0; i < 6; ++i)
+      for (int j = i + 1; j < 6; ++j) {
+        const int p = 6 + 2 * herm_off(i, j);
+        o[(size_t)p * g.V] = A[ch][i][j].re;
+        o[(size_t)(p + 1) * g.V] = A[ch][i][j].im;
+      }
+  }
+}
+
+// gauge field from the ABI layout [lex site][mu][3][3] (FP64) to [mu][9][V]
+template <typename T>
+__global__ void k_links_import(cplx<T>* __restrict__ U, const cd* __restrict__ gl, Geom g) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.V) return;
+  int c[4];
+  geom_coords(g, x, c);
+  const size_t site = (size_t)lin4(c, g.L);
+  for (int mu = 0; mu < 4; ++mu)
+    for (int k = 0; k < 9; ++k) U[(size_t)(mu * 9 + k) * g.V + x] = ccast<T>(gl[(site * 4 + mu) * 9 + k]);
+}
+
+// fine fields between the ABI layout [n][lex site][12] (FP64) and [n][12][V] of T
+template <typename T>
+__global__ void k_fine_import(cplx<T>* __restrict__ dst, const cd* __restrict__ src, Geom g, size_t rstride) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.V) return;
+  int c[4];
+  geom_coords(g, x, c);
+  const size_t site = (size_t)lin4(c, g.L);
+  const cd* s = src + (size_t)blockIdx.y * g.V * 12 + site * 12;
+  cplx<T>* d = dst + (size_t)blockIdx.y * rstride;
+  for (int k = 0; k < 12; ++k) d[(size_t)k * g.V + x] = ccast<T>(s[k]);
+}
+
+template <typename T>
+__global__ void k_fine_export(cd* __restrict__ dst, const cplx<T>* __restrict__ src, Geom g, size_t rstride) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.V) return;
+  int c[4];
+  geom_coords(g, x, c);
+  const size_t site = (size_t)lin4(c, g.L);
+  cd* d = dst + (size_t)blockIdx.y * g.V * 12 + site * 12;
+  const cplx<T>* s = src + (size_t)blockIdx.y * rstride;
+  for (int k = 0; k < 12; ++k) d[k] = ccast<double>(s[(size_t)k * g.V + x]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+namespace dd {
+
+void set_gamma_products(const double* gg /* [6][4][4][2] */) {
+  cudaMemcpyToSymbol(c_gg, gg, sizeof(double) * 6 * 16 * 2);
+}
+
+template <typename T>
+void fine_dslash(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const FineOp<T>& op, int nrhs,
+                 size_t rstride, int sel, int sel_mu, int in_chir, cudaStream_t st) {
+  dim3 grid(div_up(op.g.V, 128), nrhs);
+  if (b)
+    k_fine_dslash<T, true><<<grid, 128, 0, st>>>(out, in, b, op.U, op.clov, op.g, op.bc_t, rstride, sel, sel_mu,
+                                                  in_chir);
+  else
+    k_fine_dslash<T, false><<<grid, 128, 0, st>>>(out, in, b, op.U, op.clov, op.g, op.bc_t, rstride, sel,
+                                                   sel_mu, in_chir);
+}
+
+template <typename T>
+void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int* blocks, int nblocks, int nrhs,
+                    size_t rstride, int k_mr, cudaStream_t st) {
+  int seg = 1;
+  while (seg < op.g.vB) seg <<= 1;
+  const int threads = seg >= 256 ? seg : 256;
+  const int segs = threads / seg;
+  const size_t sm = (size_t)threads * 12 * sizeof(cplx<T>) + (size_t)(threads / 32) * 3 * sizeof(T);
+  static bool attr_set[2] = {false, false};
+  bool& done = attr_set[sizeof(T) == 8];
+  if (!done) {
+    cudaFuncSetAttribute(k_fine_sap<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    done = true;
+  }
+  dim3 grid(div_up(nblocks, segs), nrhs);
+  k_fine_sap<T><<<grid, threads, sm, st>>>(z, b, op.U, op.clov, op.g, op.bc_t, rstride, blocks, nblocks, seg, k_mr);
+}
+
+void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, double m0, double csw,
+                  cudaStream_t st) {
+  k_clover_build<<<div_up(g.V, 64), 64, 0, st>>>(clov, gauge_lex, g, m0, csw);
+}
+
+template <typename T>
+void links_import(cplx<T>* U, const cplx<double>* gauge_lex, const Geom& g, cudaStream_t st) {
+  k_links_import<T><<<div_up(g.V, 128), 128, 0, st>>>(U, gauge_lex, g);
+}
+
+template <typename T>
+void fine_import(cplx<T>* dst, const cplx<double>* src, const Geom& g, int nrhs, size_t rstride, cudaStream_t st) {
+  k_fine_import<T><<<dim3(div_up(g.V, 128), nrhs), 128, 0, st>>>(dst, src, g, rstride);
+}
+
+template <typename T>
+void fine_export(cplx<double>* dst, const cplx<T>* src, const Geom& g, int nrhs, size_t rstride, cudaStream_t st) {
+  k_fine_export<T><<<dim3(div_up(g.V, 128), nrhs), 128, 0, st>>>(dst, src, g, rstride);
+}
+
+#define INST(T)                                                                                              \
+  template void fine_dslash<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const FineOp<T>&, int, size_t, int, \
+                               int, int, cudaStream_t);                                                      \
+  template void fine_sap_sweep<T>(cplx<T>*, const cplx<T>*, const FineOp<T>&, const int*, int, int, size_t, \
+                                  int, cudaStream_t);                                                        \
+  template void links_import<T>(cplx<T>*, const cplx<double>*, const Geom&, cudaStream_t);                  \
+  template void fine_import<T>(cplx<T>*, const cplx<double>*, const Geom&, int, size_t, cudaStream_t);      \
+  template void fine_export<T>(cplx<double>*, const cplx<T>*, const Geom&, int, size_t, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace dd

@@ -1,0 +1,129 @@
+// Internal launch API of the DD-alpha-AMG CUDA library (not part of the C ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace dd {
+
+template <typename T>
+struct FineOp {
+  Geom g;
+  int bc_t;
+  cplx<T>* U;    // [4][9][V]
+  T* clov;       // [2][36][V]  (m0 + 4) + clover, packed Hermitian
+};
+
+template <typename T>
+struct CoarseOp {
+  Geom g;
+  int n;                // dof per site
+  cplx<T>* blk;         // [V][9][n][n] column-major blocks
+  cplx<T>* selfinv;     // [V][n][n] inverse of the self block (coarsest level), or null
+};
+
+// ---- fine level -----------------------------------------------------------
+void set_gamma_products(const double* gg);
+template <typename T>
+void fine_dslash(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const FineOp<T>& op, int nrhs, size_t rstride,
+                 int sel, int sel_mu, int in_chir, cudaStream_t st);
+template <typename T>
+void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int* blocks, int nblocks, int nrhs,
+                    size_t rstride, int k_mr, cudaStream_t st);
+void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, double m0, double csw,
+                  cudaStream_t st);
+template <typename T>
+void links_import(cplx<T>* U, const cplx<double>* gauge_lex, const Geom& g, cudaStream_t st);
+template <typename T>
+void fine_import(cplx<T>* dst, const cplx<double>* src, const Geom& g, int nrhs, size_t rstride, cudaStream_t st);
+template <typename T>
+void fine_export(cplx<double>* dst, const cplx<T>* src, const Geom& g, int nrhs, size_t rstride, cudaStream_t st);
+
+// ---- coarse levels --------------------------------------------------------
+template <typename T>
+void coarse_apply(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const CoarseOp<T>& op, int nrhs,
+                  size_t rstride, int sel, int sel_mu, int in_chir, cudaStream_t st);
+template <typename T>
+void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks,
+                      int nrhs, size_t rstride, int k_mr, cudaStream_t st);
+void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int n, int* err, cudaStream_t st);
+template <typename T>
+void coarse_selfinv_apply(cplx<T>* out, const cplx<T>* in, const CoarseOp<T>& op, int parity, int nrhs,
+                          size_t rstride, cudaStream_t st);
+template <typename T>
+void coarse_sub_parity(cplx<T>* y, const cplx<T>* a, const cplx<T>* b, const Geom& g, int n, int parity, int nrhs,
+                       size_t rstride, cudaStream_t st);
+template <typename T>
+void coarse_import(cplx<T>* dst, const cplx<double>* src, const Geom& g, int n, int nrhs, size_t rstride,
+                   cudaStream_t st);
+template <typename T>
+void coarse_export(cplx<double>* dst, const cplx<T>* src, const Geom& g, int n, int nrhs, size_t rstride,
+                   cudaStream_t st);
+void coarse_blocks_export(cplx<double>* dst, const cplx<double>* blk, const Geom& g, int n, cudaStream_t st);
+
+// ---- transfer ---------------------------------------------------------------
+// out(A)[s*N + j] = sum_{x in A, f in s} conj(P_j(x, f)) in(x, f)
+template <typename T>
+void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine,
+                 int n, int N, int nrhs, size_t in_rstride, size_t out_rstride, size_t out_site_stride,
+                 cudaStream_t st);
+// out(x, f) = [out +] sum_j P_j(x, f) in(A(x))[s(f)*N + j]
+template <typename T>
+void prolong_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine, int n,
+                int N, int nrhs, size_t out_rstride, size_t in_rstride, bool accumulate, cudaStream_t st);
+// in-place CGS2 per aggregate and chirality of N fields (FP64); err set on rank deficiency
+void orthonormalise(cplx<double>* P, const Geom& g, bool fine, int n, int N, int* err, cudaStream_t st);
+
+// ---- BLAS-1 (batched over rhs, rstride complex elements between rhs) ----------
+template <typename T>
+void blas_dot(cplx<double>* res, const cplx<T>* x, const cplx<T>* y, size_t len, int nrhs, size_t rstride,
+              cudaStream_t st);
+template <typename T>
+void blas_norm2(double* res, const cplx<T>* x, size_t len, int nrhs, size_t rstride, cudaStream_t st);
+// res[rhs*res_stride + i] = V_i^+ w, V_i at V + i*vstride + rhs*rstride
+template <typename T>
+void blas_multidot(cplx<double>* res, int res_stride, const cplx<T>* V, size_t vstride, int m, const cplx<T>* w,
+                   size_t len, int nrhs, size_t rstride, cudaStream_t st);
+void reserve_partials(int nrhs, int m);
+// a[i] = 1 / a[i] (0 where a[i] = 0)
+void blas_recip(double* a, int n, cudaStream_t st);
+// y += sign * sum_i c[rhs*cstride + i] V_i
+template <typename T>
+void blas_multiaxpy(cplx<T>* y, const cplx<T>* V, size_t vstride, int m, const cplx<double>* c, int cstride,
+                    double sign, size_t len, int nrhs, size_t rstride, cudaStream_t st);
+// y = a[rhs] * x   (a real, from device memory)
+template <typename T>
+void blas_scale_to(cplx<T>* y, const cplx<T>* x, const double* a, size_t len, int nrhs, size_t rstride,
+                   cudaStream_t st);
+template <typename T>
+void blas_axpy(cplx<T>* y, const cplx<T>* x, double a, size_t len, int nrhs, size_t rstride, cudaStream_t st);
+template <typename To, typename Ti>
+void blas_convert(cplx<To>* y, const cplx<Ti>* x, size_t len, int nrhs, size_t ystride, size_t xstride,
+                  cudaStream_t st);
+template <typename T>
+void blas_zero(cplx<T>* y, size_t len, int nrhs, size_t rstride, cudaStream_t st);
+template <typename T>
+void real_convert(T* y, const double* x, size_t len, cudaStream_t st);
+
+// ---- GMRES bookkeeping (per rhs, FP64 scalars) ---------------------------------
+struct GmresState {
+  cplx<double>* H;      // [rhs][m+1][m] Hessenberg, rotated to R in place
+  double* cs;           // [rhs][m]
+  cplx<double>* sn;     // [rhs][m]
+  cplx<double>* g;      // [rhs][m+1]
+  cplx<double>* h1;     // [rhs][m+1] first CGS pass coefficients
+  cplx<double>* h2;     // [rhs][m+1] second CGS pass
+  double* wnorm;        // [rhs]
+  double* inv;          // [rhs] 1 / ||w||
+  double* beta;         // [rhs] initial residual norm of the cycle
+  double* target;       // [rhs] absolute stopping threshold
+  double* est;          // [rhs] |g_{j+1}|
+  int* done;            // [rhs] stopped in this cycle
+  int* kr;              // [rhs] iterations taken in this cycle
+  cplx<double>* y;      // [rhs][m]
+  int m;
+};
+void gmres_begin(const GmresState& s, int nrhs, cudaStream_t st);                // g = beta e1, inv = 1/beta
+void gmres_step(const GmresState& s, int j, int nrhs, cudaStream_t st);          // rotations, new g, done flags
+void gmres_solve_y(const GmresState& s, int nrhs, cudaStream_t st);              // y = R^{-1} g (k_r per rhs)
+
+}  // namespace dd

@@ -1,0 +1,1047 @@
+// Host orchestration of the DD-alpha-AMG method and the C ABI (include/ddamg.h).
+//
+// Paper references: the cycle is Alg. 2 (the K-cycle: Alg. 1 with the
+// recursion replaced by FGMRES on D_{l+1} preconditioned by the K-cycle at
+// l+1), the setup is Alg. 3 followed by n_inv applications of Alg. 4, the
+// outer solver is FP64 FGMRES (Sec. 3), the coarsest system is solved by
+// odd-even preconditioned GMRES to relative accuracy epsilon (Sec. 3), and the
+// parameters default to Table 1.  Every arithmetic step runs in the CUDA
+// kernels of this library; the host only sequences launches and reads one
+// small per-rhs status array per Krylov iteration.
+#include "ddamg.h"
+#include "kernels.h"
+
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+using namespace dd;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct DdError {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& m) { throw DdError{code, m}; }
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) fail(DDAMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+struct Work {
+  cplx<T>* bc = nullptr;   // right-hand side of this level's inner solve
+  cplx<T>* xs = nullptr;   // result of this level's inner solve (last iterate of the level)
+  cplx<T>* V = nullptr;    // Krylov basis [m+1][max_rhs][vlen]
+  cplx<T>* Z = nullptr;    // preconditioned vectors [m][max_rhs][vlen] (flexible only)
+  cplx<T>* r = nullptr;    // residual
+  cplx<T>* t[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  GmresState gs{};
+  int m = 0;
+};
+
+struct Level {
+  int idx = 0;
+  bool fine = false, coarsest = false;
+  Geom g{};
+  int n = 0;          // dof per site
+  size_t vlen = 0;    // complex elements per field
+  int N = 0;          // test vectors (columns of P per chirality)
+  FineOp<double> f64{};
+  FineOp<float> f32{};
+  CoarseOp<double> c64{};
+  CoarseOp<float> c32{};
+  cplx<double>* tv64 = nullptr;
+  cplx<double>* P64 = nullptr;
+  cplx<float>* P32 = nullptr;
+  int* blocks[2] = {nullptr, nullptr};
+  int nblocks[2] = {0, 0};
+  Work<double> w64;
+  Work<float> w32;
+};
+
+template <typename T> FineOp<T>& fop(Level& L);
+template <> FineOp<double>& fop<double>(Level& L) { return L.f64; }
+template <> FineOp<float>& fop<float>(Level& L) { return L.f32; }
+template <typename T> CoarseOp<T>& cop(Level& L);
+template <> CoarseOp<double>& cop<double>(Level& L) { return L.c64; }
+template <> CoarseOp<float>& cop<float>(Level& L) { return L.c32; }
+template <typename T> Work<T>& work(Level& L);
+template <> Work<double>& work<double>(Level& L) { return L.w64; }
+template <> Work<float>& work<float>(Level& L) { return L.w32; }
+template <typename T> cplx<T>* Pptr(Level& L);
+template <> cplx<double>* Pptr<double>(Level& L) { return L.P64; }
+template <> cplx<float>* Pptr<float>(Level& L) { return L.P32; }
+
+struct Scratch {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace
+
+struct ddamg_handle {
+  ddamg_params p{};
+  int dims[4] = {0, 0, 0, 0};
+  int bc_t = -1;
+  double m0 = 0, csw = 0;
+  int L = 0;
+  std::vector<Level> lv;
+  cudaStream_t own = nullptr;
+  cudaStream_t st = nullptr;
+  std::vector<void*> allocs;
+  Scratch scr[8];
+  // outer FGMRES (FP64, level 0)
+  Work<double> outer;
+  cplx<double>* ob = nullptr;
+  cplx<double>* ox = nullptr;
+  cplx<float>* pin32 = nullptr;
+  cplx<float>* pout32 = nullptr;
+  int* d_err = nullptr;
+  int* h_done = nullptr;      // pinned
+  double* h_scal = nullptr;   // pinned
+  int* h_kr = nullptr;        // pinned
+  int max_batch = 0;
+};
+
+namespace {
+
+template <typename T>
+T* dalloc(ddamg_handle* h, size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(DDAMG_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  h->allocs.push_back(p);
+  return static_cast<T*>(p);
+}
+
+void* scratch(ddamg_handle* h, int slot, size_t bytes) {
+  Scratch& s = h->scr[slot];
+  if (bytes > s.cap) {
+    if (s.p) {
+      CK(cudaStreamSynchronize(h->st));
+      cudaFree(s.p);
+      s.p = nullptr;
+      s.cap = 0;
+    }
+    if (cudaMalloc(&s.p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      fail(DDAMG_ERR_OOM, "scratch allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    s.cap = bytes;
+  }
+  return s.p;
+}
+
+void sync(ddamg_handle* h) {
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->st));
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device view of a caller buffer of `bytes` (copied to staging slot if host)
+const void* dev_in(ddamg_handle* h, const void* p, size_t bytes, int slot) {
+  if (is_device_ptr(p)) return p;
+  void* d = scratch(h, slot, bytes);
+  CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, h->st));
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// operators on one level
+template <typename T>
+void apply_D(ddamg_handle* h, Level& L, cplx<T>* out, const cplx<T>* in, const cplx<T>* b, int nrhs,
+             int sel = SEL_FULL, int mu = 0, int chir = -1) {
+  if (L.fine) fine_dslash<T>(out, in, b, fop<T>(L), nrhs, L.vlen, sel, mu, chir, h->st);
+  else coarse_apply<T>(out, in, b, cop<T>(L), nrhs, L.vlen, sel, mu, chir, h->st);
+}
+
+// iterations x { z <- z + M_SAP (b - D z) }: each SAP application is a red then a black sweep
+template <typename T>
+void sap(ddamg_handle* h, Level& L, cplx<T>* z, const cplx<T>* b, int nrhs, int iterations) {
+  for (int it = 0; it < iterations; ++it)
+    for (int c = 0; c < 2; ++c) {
+      if (L.nblocks[c] == 0) continue;
+      if (L.fine)
+        fine_sap_sweep<T>(z, b, fop<T>(L), L.blocks[c], L.nblocks[c], nrhs, L.vlen, h->p.mr_steps, h->st);
+      else
+        coarse_sap_sweep<T>(z, b, cop<T>(L), L.blocks[c], L.nblocks[c], nrhs, L.vlen, h->p.mr_steps, h->st);
+    }
+}
+
+template <typename T>
+void restrict_lv(ddamg_handle* h, int l, cplx<T>* out, const cplx<T>* in, int nrhs) {
+  Level& F = h->lv[l];
+  Level& C = h->lv[l + 1];
+  restrict_op<T>(out, in, Pptr<T>(F), F.g, C.g, F.fine, F.n, F.N, nrhs, F.vlen, C.vlen, C.n, h->st);
+}
+
+template <typename T>
+void prolong_lv(ddamg_handle* h, int l, cplx<T>* out, const cplx<T>* in, int nrhs, bool acc) {
+  Level& F = h->lv[l];
+  Level& C = h->lv[l + 1];
+  prolong_op<T>(out, in, Pptr<T>(F), F.g, C.g, F.fine, F.n, F.N, nrhs, F.vlen, C.vlen, acc, h->st);
+}
+
+// ---------------------------------------------------------------------------
+// (F)GMRES with per-rhs stopping (Saad's FGMRES with CGS2 Arnoldi and Givens
+// rotations).  A(out, in, b): out = A in, or out = b - A in when b != null.
+// M(out, in): preconditioner (flexible only).
+struct KrylovResult {
+  std::vector<int> iterations, cycles, converged;
+  std::vector<double> true_residual;
+};
+
+template <typename T, class AOp, class MOp>
+void krylov(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>* b, int nrhs, int m, double tol,
+            int max_cycles, bool final_residual, bool flexible, AOp A, MOp M, KrylovResult* res) {
+  cudaStream_t st = h->st;
+  const size_t rs = vlen;
+  const size_t vs = (size_t)h->max_batch * vlen;
+  GmresState& gs = ws.gs;
+  if (m > ws.m) fail(DDAMG_ERR_ARG, "Krylov length exceeds the workspace");
+  GmresState s = gs;
+  s.m = m;
+  blas_norm2<T>(s.beta, b, vlen, nrhs, rs, st);
+  CK(cudaMemcpyAsync(h->h_scal, s.beta, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  sync(h);
+  std::vector<double> bnorm(h->h_scal, h->h_scal + nrhs), target(nrhs);
+  for (int r = 0; r < nrhs; ++r) target[r] = tol * bnorm[r];
+  CK(cudaMemcpyAsync(s.target, target.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+  blas_zero<T>(x, vlen, nrhs, rs, st);
+  blas_convert<T, T>(ws.r, b, vlen, nrhs, rs, rs, st);
+  if (res) {
+    res->iterations.assign(nrhs, 0);
+    res->cycles.assign(nrhs, 0);
+    res->converged.assign(nrhs, 0);
+    res->true_residual.assign(nrhs, 1.0);
+  }
+  std::vector<int> conv(nrhs, 0);
+  for (int r = 0; r < nrhs; ++r) conv[r] = bnorm[r] == 0.0;
+  for (int cycle = 0; cycle < max_cycles; ++cycle) {
+    gmres_begin(s, nrhs, st);
+    blas_scale_to<T>(ws.V, ws.r, s.inv, vlen, nrhs, rs, st);
+    int kmax = 0;
+    for (int j = 0; j < m; ++j) {
+      cplx<T>* vj = ws.V + (size_t)j * vs;
+      cplx<T>* zj = flexible ? ws.Z + (size_t)j * vs : vj;
+      cplx<T>* w = ws.V + (size_t)(j + 1) * vs;
+      if (flexible) M(zj, vj);
+      A(w, zj, nullptr);
+      blas_multidot<T>(s.h1, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
+      blas_multiaxpy<T>(w, ws.V, vs, j + 1, s.h1, m + 1, -1.0, vlen, nrhs, rs, st);
+      blas_multidot<T>(s.h2, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
+      blas_multiaxpy<T>(w, ws.V, vs, j + 1, s.h2, m + 1, -1.0, vlen, nrhs, rs, st);
+      blas_norm2<T>(s.wnorm, w, vlen, nrhs, rs, st);
+      gmres_step(s, j, nrhs, st);
+      blas_scale_to<T>(w, w, s.inv, vlen, nrhs, rs, st);
+      kmax = j + 1;
+      CK(cudaMemcpyAsync(h->h_done, s.done, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+      sync(h);
+      bool all = true;
+      for (int r = 0; r < nrhs; ++r) all = all && h->h_done[r];
+      if (all) break;
+    }
+    gmres_solve_y(s, nrhs, st);
+    blas_multiaxpy<T>(x, flexible ? ws.Z : ws.V, vs, kmax, s.y, m, 1.0, vlen, nrhs, rs, st);
+    if (res) {
+      CK(cudaMemcpyAsync(h->h_kr, s.kr, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+      sync(h);
+      for (int r = 0; r < nrhs; ++r)
+        if (!conv[r]) {
+          res->iterations[r] += h->h_kr[r];
+          res->cycles[r] = cycle + 1;
+        }
+    }
+    if (cycle == max_cycles - 1 && !final_residual) break;
+    A(ws.r, x, b);   // r = b - A x
+    blas_norm2<T>(s.beta, ws.r, vlen, nrhs, rs, st);
+    CK(cudaMemcpyAsync(h->h_scal, s.beta, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    sync(h);
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) {
+      const double beta = h->h_scal[r];
+      if (res && !conv[r]) res->true_residual[r] = bnorm[r] > 0 ? beta / bnorm[r] : 0.0;
+      if (beta <= target[r]) conv[r] = 1;
+      all = all && conv[r];
+    }
+    if (all) break;
+  }
+  if (res)
+    for (int r = 0; r < nrhs; ++r) {
+      res->converged[r] = conv[r];
+      if (bnorm[r] == 0.0) res->true_residual[r] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// coarsest level: odd-even preconditioned GMRES (Sec. 3)
+template <typename T>
+void coarse_solve(ddamg_handle* h, cplx<T>* x, const cplx<T>* b, int nrhs) {
+  Level& C = h->lv[h->L - 1];
+  Work<T>& w = work<T>(C);
+  CoarseOp<T>& op = cop<T>(C);
+  cudaStream_t st = h->st;
+  const size_t rs = C.vlen;
+  cplx<T>*t1 = w.t[0], *t2 = w.t[1], *t3 = w.t[2], *bh = w.t[3], *xe = w.t[4];
+  // bhat_e = b_e - D_eo D_oo^{-1} b_o
+  coarse_selfinv_apply<T>(t1, b, op, 1, nrhs, rs, st);
+  apply_D<T>(h, C, t2, t1, nullptr, nrhs);
+  coarse_sub_parity<T>(bh, b, t2, C.g, C.n, 0, nrhs, rs, st);
+  auto schur = [&](cplx<T>* out, const cplx<T>* in, const cplx<T>* bb) {
+    apply_D<T>(h, C, t1, in, nullptr, nrhs);                  // t1_e = D_ee in, t1_o = D_oe in
+    coarse_selfinv_apply<T>(t2, t1, op, 1, nrhs, rs, st);     // t2 = D_oo^{-1} t1_o
+    apply_D<T>(h, C, t3, t2, nullptr, nrhs);                  // t3_e = D_eo t2
+    coarse_sub_parity<T>(t1, t1, t3, C.g, C.n, 0, nrhs, rs, st);
+    if (bb) coarse_sub_parity<T>(out, bb, t1, C.g, C.n, 0, nrhs, rs, st);
+    else blas_convert<T, T>(out, t1, rs, nrhs, rs, rs, st);
+  };
+  auto none = [](cplx<T>*, const cplx<T>*) {};
+  krylov<T>(h, w, C.vlen, xe, bh, nrhs, h->p.coarse_restart, h->p.coarse_tol, h->p.coarse_cycles, true, false, schur,
+            none, nullptr);
+  // z_o = D_oo^{-1} (b_o - D_oe x_e);  z = x_e + z_o
+  apply_D<T>(h, C, t1, xe, nullptr, nrhs);
+  coarse_sub_parity<T>(t2, b, t1, C.g, C.n, 1, nrhs, rs, st);
+  coarse_selfinv_apply<T>(t3, t2, op, 1, nrhs, rs, st);
+  coarse_sub_parity<T>(x, xe, nullptr, C.g, C.n, 0, nrhs, rs, st);
+  blas_axpy<T>(x, t3, 1.0, rs, nrhs, rs, st);
+}
+
+// one K-cycle from level l (Alg. 2): z = K(l, b)
+template <typename T>
+void kcycle(ddamg_handle* h, int l, cplx<T>* z, const cplx<T>* b, int nrhs) {
+  Level& F = h->lv[l];
+  Level& C = h->lv[l + 1];
+  Work<T>& wc = work<T>(C);
+  cudaStream_t st = h->st;
+  blas_zero<T>(z, F.vlen, nrhs, F.vlen, st);
+  if (h->p.mu > 0) {
+    sap<T>(h, F, z, b, nrhs, h->p.mu);
+    cplx<T>* r = work<T>(F).r;
+    apply_D<T>(h, F, r, z, b, nrhs);
+    restrict_lv<T>(h, l, wc.bc, r, nrhs);
+  } else {
+    restrict_lv<T>(h, l, wc.bc, b, nrhs);
+  }
+  if (l + 1 == h->L - 1) {
+    coarse_solve<T>(h, wc.xs, wc.bc, nrhs);
+  } else {
+    auto A = [&](cplx<T>* out, const cplx<T>* in, const cplx<T>* bb) { apply_D<T>(h, C, out, in, bb, nrhs); };
+    auto M = [&](cplx<T>* out, const cplx<T>* in) { kcycle<T>(h, l + 1, out, in, nrhs); };
+    krylov<T>(h, wc, C.vlen, wc.xs, wc.bc, nrhs, h->p.kcycle_len, h->p.kcycle_tol, h->p.kcycle_cycles, false, true,
+              A, M, nullptr);
+  }
+  prolong_lv<T>(h, l, z, wc.xs, nrhs, h->p.mu > 0);
+  sap<T>(h, F, z, b, nrhs, h->p.nu);
+}
+
+// ---------------------------------------------------------------------------
+// hierarchy construction
+void make_geom(Geom& g, const int L[4], const int A[4], const int B[4]) {
+  bool b_in_a = true, a_in_b = true;
+  for (int d = 0; d < 4; ++d) {
+    if (L[d] <= 0 || A[d] <= 0 || B[d] <= 0 || L[d] % A[d] || L[d] % B[d])
+      fail(DDAMG_ERR_ARG, "lattice extent " + std::to_string(L[d]) + " is not tiled by aggregate " +
+                              std::to_string(A[d]) + " and SAP block " + std::to_string(B[d]) + " in direction " +
+                              std::to_string(d));
+    b_in_a = b_in_a && (A[d] % B[d] == 0);
+    a_in_b = a_in_b && (B[d] % A[d] == 0);
+  }
+  if (!b_in_a && !a_in_b) fail(DDAMG_ERR_ARG, "aggregates and SAP blocks must nest (one must tile the other)");
+  const int* O = b_in_a ? A : B;
+  const int* I = b_in_a ? B : A;
+  g.V = g.vA = g.vB = g.vI = g.nIO = g.nAgg = 1;
+  for (int d = 0; d < 4; ++d) {
+    g.L[d] = L[d];
+    g.A[d] = A[d];
+    g.B[d] = B[d];
+    g.O[d] = O[d];
+    g.I[d] = I[d];
+    g.nO[d] = L[d] / O[d];
+    g.nI[d] = O[d] / I[d];
+    g.V *= L[d];
+    g.vA *= A[d];
+    g.vB *= B[d];
+    g.vI *= I[d];
+    g.nIO *= g.nI[d];
+    g.nAgg *= L[d] / A[d];
+  }
+  g.nBlk = g.V / g.vB;
+}
+
+void build_block_lists(ddamg_handle* h, Level& L) {
+  const Geom& g = L.g;
+  for (int d = 0; d < 4; ++d) {
+    const int nb = g.L[d] / g.B[d];
+    if (nb != 1 && nb % 2)
+      fail(DDAMG_ERR_ARG, "red-black SAP needs an even number of blocks per direction on level " +
+                              std::to_string(L.idx));
+  }
+  if (L.fine ? g.vB > 1024 : g.vB * L.n > 1024)
+    fail(DDAMG_ERR_ARG, "SAP block too large for one CTA on level " + std::to_string(L.idx));
+  std::vector<int> lists[2];
+  for (int b = 0; b < g.nBlk; ++b) {
+    int c[4];
+    geom_coords(g, b * g.vB, c);
+    lists[geom_block_colour(g, c)].push_back(b);
+  }
+  for (int c = 0; c < 2; ++c) {
+    L.nblocks[c] = (int)lists[c].size();
+    L.blocks[c] = dalloc<int>(h, lists[c].size());
+    if (!lists[c].empty())
+      CK(cudaMemcpy(L.blocks[c], lists[c].data(), sizeof(int) * lists[c].size(), cudaMemcpyHostToDevice));
+  }
+}
+
+template <typename T>
+void alloc_work(ddamg_handle* h, Level& L, Work<T>& w, int m, bool flexible, int batch) {
+  const size_t vl = L.vlen * (size_t)batch;
+  w.m = m;
+  w.bc = dalloc<cplx<T>>(h, vl);
+  w.xs = dalloc<cplx<T>>(h, vl);
+  w.r = dalloc<cplx<T>>(h, vl);
+  for (int k = 0; k < 5; ++k) w.t[k] = dalloc<cplx<T>>(h, vl);
+  if (m > 0) {
+    w.V = dalloc<cplx<T>>(h, vl * (m + 1));
+    if (flexible) w.Z = dalloc<cplx<T>>(h, vl * m);
+  }
+  GmresState& s = w.gs;
+  const int mm = m > 0 ? m : 1;
+  s.m = mm;
+  s.H = dalloc<cplx<double>>(h, (size_t)batch * (mm + 1) * mm);
+  s.cs = dalloc<double>(h, (size_t)batch * mm);
+  s.sn = dalloc<cplx<double>>(h, (size_t)batch * mm);
+  s.g = dalloc<cplx<double>>(h, (size_t)batch * (mm + 1));
+  s.h1 = dalloc<cplx<double>>(h, (size_t)batch * (mm + 1));
+  s.h2 = dalloc<cplx<double>>(h, (size_t)batch * (mm + 1));
+  s.y = dalloc<cplx<double>>(h, (size_t)batch * mm);
+  s.wnorm = dalloc<double>(h, batch);
+  s.inv = dalloc<double>(h, batch);
+  s.beta = dalloc<double>(h, batch);
+  s.target = dalloc<double>(h, batch);
+  s.est = dalloc<double>(h, batch);
+  s.done = dalloc<int>(h, batch);
+  s.kr = dalloc<int>(h, batch);
+}
+
+void gamma_products(double* out /* [6][4][4][2] */) {
+  // chiral basis: gamma_t = [[0,1],[1,0]], gamma_k = [[0,-i s_k],[i s_k,0]]; mu = (t, z, y, x)
+  typedef double c2[2];
+  c2 gam[4][4][4];
+  memset(gam, 0, sizeof(gam));
+  const double sig[3][2][2][2] = {
+      {{{0, 0}, {1, 0}}, {{1, 0}, {0, 0}}},     // sigma_x
+      {{{0, 0}, {0, -1}}, {{0, 1}, {0, 0}}},    // sigma_y
+      {{{1, 0}, {0, 0}}, {{0, 0}, {-1, 0}}}};   // sigma_z
+  for (int i = 0; i < 2; ++i) {
+    gam[0][i][2 + i][0] = 1;
+    gam[0][2 + i][i][0] = 1;
+  }
+  const int which[4] = {-1, 2, 1, 0};   // mu = z, y, x use sigma_z, sigma_y, sigma_x
+  for (int mu = 1; mu < 4; ++mu) {
+    const int k = which[mu];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        const double re = sig[k][i][j][0], im = sig[k][i][j][1];
+        // upper right block: -i sigma = (im, -re) ; lower left: i sigma = (-im, re)
+        gam[mu][i][2 + j][0] = im;
+        gam[mu][i][2 + j][1] = -re;
+        gam[mu][2 + i][j][0] = -im;
+        gam[mu][2 + i][j][1] = re;
+      }
+  }
+  int p = 0;
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = mu + 1; nu < 4; ++nu, ++p)
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          double re = 0, im = 0;
+          for (int k = 0; k < 4; ++k) {
+            const double ar = gam[mu][i][k][0], ai = gam[mu][i][k][1];
+            const double br = gam[nu][k][j][0], bi = gam[nu][k][j][1];
+            re += ar * br - ai * bi;
+            im += ar * bi + ai * br;
+          }
+          out[((p * 4 + i) * 4 + j) * 2 + 0] = re;
+          out[((p * 4 + i) * 4 + j) * 2 + 1] = im;
+        }
+}
+
+void check_err_flag(ddamg_handle* h, const char* what) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  sync(h);
+  if (e) {
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
+    sync(h);
+    fail(DDAMG_ERR_SINGULAR, what);
+  }
+}
+
+// P_l from the test vectors, D_{l+1} = P_l^+ D_l P_l (FP64), FP32 copies, coarsest self inverses
+void rebuild(ddamg_handle* h, int l) {
+  Level& F = h->lv[l];
+  Level& C = h->lv[l + 1];
+  cudaStream_t st = h->st;
+  const size_t tot = F.vlen * (size_t)F.N;
+  blas_convert<double, double>(F.P64, F.tv64, tot, 1, 0, 0, st);
+  orthonormalise(F.P64, F.g, F.fine, F.n, F.N, h->d_err, st);
+  check_err_flag(h, "test vectors are linearly dependent on an aggregate");
+  blas_convert<float, double>(F.P32, F.P64, tot, 1, 0, 0, st);
+  // Galerkin: column (s', j) of every block = P^+ (term of D applied to P_j restricted to chirality s')
+  cplx<double>* tmp = static_cast<cplx<double>*>(scratch(h, 4, sizeof(cplx<double>) * tot));
+  const int nc = C.n;
+  for (int sp = 0; sp < 2; ++sp)
+    for (int k = 0; k < 9; ++k) {
+      const int sel = k == 0 ? SEL_AGG_SELF : (k <= 4 ? SEL_AGG_FWD : SEL_AGG_BWD);
+      const int mu = k == 0 ? 0 : (k - 1) % 4;
+      apply_D<double>(h, F, tmp, F.P64, nullptr, F.N, sel, mu, sp);
+      restrict_op<double>(C.c64.blk + (size_t)k * nc * nc + (size_t)sp * F.N * nc, tmp, F.P64, F.g, C.g, F.fine, F.n,
+                          F.N, F.N, F.vlen, (size_t)nc, (size_t)9 * nc * nc, st);
+    }
+  const size_t nb = (size_t)C.g.V * 9 * nc * nc;
+  blas_convert<float, double>(C.c32.blk, C.c64.blk, nb, 1, 0, 0, st);
+  if (C.coarsest) {
+    coarse_selfinv_build(C.c64.selfinv, C.c64.blk, C.g.V, nc, h->d_err, st);
+    check_err_flag(h, "singular self block on the coarsest level");
+    blas_convert<float, double>(C.c32.selfinv, C.c64.selfinv, (size_t)C.g.V * nc * nc, 1, 0, 0, st);
+  }
+  sync(h);
+}
+
+template <typename T>
+void setup_smooth(ddamg_handle* h, int l) {
+  Level& L = h->lv[l];
+  const size_t tot = L.vlen * (size_t)L.N;
+  cplx<T>* bT = static_cast<cplx<T>*>(scratch(h, 5, sizeof(cplx<T>) * tot));
+  cplx<T>* xT = static_cast<cplx<T>*>(scratch(h, 6, sizeof(cplx<T>) * tot));
+  for (int eta = 1; eta <= h->p.eta_passes; ++eta) {
+    blas_convert<T, double>(bT, L.tv64, tot, 1, 0, 0, h->st);
+    blas_zero<T>(xT, tot, 1, 0, h->st);
+    sap<T>(h, L, xT, bT, L.N, eta);
+    blas_convert<double, T>(L.tv64, xT, tot, 1, 0, 0, h->st);
+  }
+  sync(h);
+}
+
+void import_fields(ddamg_handle* h, Level& L, cplx<double>* dst, const double* src, int n) {
+  if (n <= 0) return;
+  const size_t bytes = sizeof(cplx<double>) * L.vlen * n;
+  const cplx<double>* d = static_cast<const cplx<double>*>(dev_in(h, src, bytes, 0));
+  if (L.fine) fine_import<double>(dst, d, L.g, n, L.vlen, h->st);
+  else coarse_import<double>(dst, d, L.g, L.n, n, L.vlen, h->st);
+}
+
+void initial_setup_phase(ddamg_handle* h, int l, const double* const* tv_random) {
+  Level& L = h->lv[l];
+  if (l == 0) {
+    if (!tv_random || !tv_random[0]) fail(DDAMG_ERR_ARG, "random test vectors of level 0 missing");
+    import_fields(h, L, L.tv64, tv_random[0], L.N);
+  } else {
+    Level& U = h->lv[l - 1];
+    const int take = L.N < U.N ? L.N : U.N;
+    restrict_op<double>(L.tv64, U.tv64, U.P64, U.g, L.g, U.fine, U.n, U.N, take, U.vlen, L.vlen, L.n, h->st);
+    if (L.N > take) {
+      if (!tv_random || !tv_random[l]) fail(DDAMG_ERR_ARG, "random test vectors of a coarse level missing");
+      import_fields(h, L, L.tv64 + (size_t)take * L.vlen, tv_random[l], L.N - take);
+    }
+  }
+  sync(h);
+  if (h->p.precision == 1) setup_smooth<float>(h, l);
+  else setup_smooth<double>(h, l);
+  rebuild(h, l);
+  if (l < h->L - 2) initial_setup_phase(h, l + 1, tv_random);
+}
+
+template <typename T>
+void iterative_setup_phase(ddamg_handle* h, int l, int i) {
+  if (l >= h->L - 1) return;
+  Level& L = h->lv[l];
+  cudaStream_t st = h->st;
+  cplx<T>* bT = static_cast<cplx<T>*>(scratch(h, 5, sizeof(cplx<T>) * L.vlen));
+  cplx<T>* zT = static_cast<cplx<T>*>(scratch(h, 6, sizeof(cplx<T>) * L.vlen));
+  double* nrm = static_cast<double*>(scratch(h, 7, sizeof(double) * 8));
+  for (int j = 0; j < L.N; ++j) {
+    blas_convert<T, double>(bT, L.tv64 + (size_t)j * L.vlen, L.vlen, 1, 0, 0, st);
+    kcycle<T>(h, l, zT, bT, 1);
+    for (int k = l; k < h->L - 1; ++k) {
+      Level& K = h->lv[k];
+      if (j >= K.N) continue;
+      const cplx<T>* src = (k == l) ? zT : work<T>(K).xs;
+      cplx<double>* dst = K.tv64 + (size_t)j * K.vlen;
+      blas_convert<double, T>(dst, src, K.vlen, 1, 0, 0, st);
+      blas_norm2<double>(nrm, dst, K.vlen, 1, 0, st);
+      blas_recip(nrm, 1, st);
+      blas_scale_to<double>(dst, dst, nrm, K.vlen, 1, 0, st);
+    }
+    sync(h);
+  }
+  for (int k = l; k < h->L - 1; ++k) rebuild(h, k);
+  for (int q = 1; q <= i; ++q) iterative_setup_phase<T>(h, l + 1, q);
+}
+
+void build_hierarchy(ddamg_handle* h) {
+  const ddamg_params& p = h->p;
+  h->L = p.levels;
+  h->lv.resize(h->L);
+  int dims[4] = {h->dims[0], h->dims[1], h->dims[2], h->dims[3]};
+  for (int l = 0; l < h->L; ++l) {
+    Level& L = h->lv[l];
+    L.idx = l;
+    L.fine = l == 0;
+    L.coarsest = l == h->L - 1;
+    L.n = l == 0 ? 12 : 2 * h->lv[l - 1].N;
+    L.N = L.coarsest ? 0 : p.n_tv[l];
+    if (!L.coarsest && (L.N <= 0 || 2 * L.N > 64)) fail(DDAMG_ERR_ARG, "n_tv must be in 1..32");
+    if (L.coarsest) {
+      const int one[4] = {1, 1, 1, 1};
+      make_geom(L.g, dims, dims, one);
+      for (int d = 0; d < 4; ++d)
+        if (dims[d] % 2) fail(DDAMG_ERR_ARG, "the coarsest lattice needs even extents for the odd-even solve");
+    } else {
+      make_geom(L.g, dims, p.agg[l], p.sap_block[l]);
+    }
+    L.vlen = (size_t)L.g.V * L.n;
+    if (!L.coarsest)
+      for (int d = 0; d < 4; ++d) dims[d] /= p.agg[l][d];
+  }
+}
+
+void allocate_hierarchy(ddamg_handle* h) {
+  const int B = h->max_batch;
+  for (int l = 0; l < h->L; ++l) {
+    Level& L = h->lv[l];
+    if (L.fine) {
+      L.f64.g = L.f32.g = L.g;
+      L.f64.bc_t = L.f32.bc_t = h->bc_t;
+      L.f64.U = dalloc<cplx<double>>(h, (size_t)36 * L.g.V);
+      L.f32.U = dalloc<cplx<float>>(h, (size_t)36 * L.g.V);
+      L.f64.clov = dalloc<double>(h, (size_t)72 * L.g.V);
+      L.f32.clov = dalloc<float>(h, (size_t)72 * L.g.V);
+    } else {
+      L.c64.g = L.c32.g = L.g;
+      L.c64.n = L.c32.n = L.n;
+      const size_t nb = (size_t)L.g.V * 9 * L.n * L.n;
+      L.c64.blk = dalloc<cplx<double>>(h, nb);
+      L.c32.blk = dalloc<cplx<float>>(h, nb);
+      if (L.coarsest) {
+        L.c64.selfinv = dalloc<cplx<double>>(h, (size_t)L.g.V * L.n * L.n);
+        L.c32.selfinv = dalloc<cplx<float>>(h, (size_t)L.g.V * L.n * L.n);
+      }
+    }
+    if (!L.coarsest) {
+      L.tv64 = dalloc<cplx<double>>(h, L.vlen * L.N);
+      L.P64 = dalloc<cplx<double>>(h, L.vlen * L.N);
+      L.P32 = dalloc<cplx<float>>(h, L.vlen * L.N);
+      build_block_lists(h, L);
+    }
+    // workspaces: inner FGMRES on levels 1..L-2, GMRES on the coarsest, temps on level 0
+    const int m = L.coarsest ? h->p.coarse_restart : (l >= 1 ? h->p.kcycle_len : 0);
+    const int batch = B;
+    alloc_work<float>(h, L, L.w32, m, !L.coarsest, batch);
+    alloc_work<double>(h, L, L.w64, m, !L.coarsest, batch);
+  }
+  alloc_work<double>(h, h->lv[0], h->outer, h->p.outer_restart, true, B);
+  h->ob = dalloc<cplx<double>>(h, h->lv[0].vlen * B);
+  h->ox = dalloc<cplx<double>>(h, h->lv[0].vlen * B);
+  h->pin32 = dalloc<cplx<float>>(h, h->lv[0].vlen * B);
+  h->pout32 = dalloc<cplx<float>>(h, h->lv[0].vlen * B);
+  int mx = h->p.outer_restart;
+  if (h->p.coarse_restart > mx) mx = h->p.coarse_restart;
+  int bmax = B;
+  for (auto& L : h->lv)
+    if (L.N > bmax) bmax = L.N;
+  reserve_partials(bmax, mx + 1);
+}
+
+void validate(const ddamg_params& p) {
+  if (p.levels < 2 || p.levels > DDAMG_MAX_LEVELS) fail(DDAMG_ERR_ARG, "levels must be 2..4");
+  if (p.outer_restart < 1 || p.outer_restart > 63 || p.coarse_restart < 1 || p.coarse_restart > 63 ||
+      p.kcycle_len < 1 || p.kcycle_len > 63)
+    fail(DDAMG_ERR_ARG, "Krylov lengths must be 1..63");
+  if (p.mr_steps < 0 || p.nu < 0 || p.mu < 0 || p.n_inv < 0 || p.eta_passes < 0) fail(DDAMG_ERR_ARG, "negative count");
+  if (p.max_rhs < 1 || p.max_rhs > 64) fail(DDAMG_ERR_ARG, "max_rhs must be 1..64");
+  if (p.precision != 0 && p.precision != 1) fail(DDAMG_ERR_ARG, "precision must be 0 or 1");
+}
+
+template <typename T>
+void precond_outer(ddamg_handle* h, cplx<double>* z, const cplx<double>* v, int nrhs);
+
+template <>
+void precond_outer<double>(ddamg_handle* h, cplx<double>* z, const cplx<double>* v, int nrhs) {
+  kcycle<double>(h, 0, z, v, nrhs);
+}
+
+template <>
+void precond_outer<float>(ddamg_handle* h, cplx<double>* z, const cplx<double>* v, int nrhs) {
+  const size_t vl = h->lv[0].vlen;
+  blas_convert<float, double>(h->pin32, v, vl, nrhs, vl, vl, h->st);
+  kcycle<float>(h, 0, h->pout32, h->pin32, nrhs);
+  blas_convert<double, float>(z, h->pout32, vl, nrhs, vl, vl, h->st);
+}
+
+}  // namespace
+
+namespace {
+int guard(const std::function<void()>& f) {
+  try {
+    f();
+    return DDAMG_OK;
+  } catch (const DdError& e) {
+    g_err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return DDAMG_ERR_ARG;
+  }
+}
+
+Level& level_of(ddamg_handle* h, int level) {
+  if (!h || level < 0 || level >= h->L) fail(DDAMG_ERR_ARG, "level out of range");
+  return h->lv[level];
+}
+
+// run f on n fields of level l in chunks of the batch size; in/out are ABI (FP64 lex) buffers
+template <typename T, class F>
+void hook(ddamg_handle* h, int l, const double* in, double* out, int n, bool out_is_in_out, int out_level, F f) {
+  Level& L = h->lv[l];
+  Level& O = h->lv[out_level];
+  const size_t in_bytes = sizeof(cplx<double>) * L.vlen * n;
+  const size_t out_bytes = sizeof(cplx<double>) * O.vlen * n;
+  const cplx<double>* din = in ? static_cast<const cplx<double>*>(dev_in(h, in, in_bytes, 0)) : nullptr;
+  const bool out_dev = is_device_ptr(out);
+  cplx<double>* dout = out_dev ? reinterpret_cast<cplx<double>*>(out)
+                               : static_cast<cplx<double>*>(scratch(h, 1, out_bytes));
+  if (!out_dev && out_is_in_out) CK(cudaMemcpyAsync(dout, out, out_bytes, cudaMemcpyHostToDevice, h->st));
+  cplx<T>* ti = static_cast<cplx<T>*>(scratch(h, 2, sizeof(cplx<T>) * L.vlen * n));
+  cplx<T>* to = static_cast<cplx<T>*>(scratch(h, 3, sizeof(cplx<T>) * O.vlen * n));
+  auto imp = [&](Level& X, cplx<T>* dst, const cplx<double>* src) {
+    if (X.fine) fine_import<T>(dst, src, X.g, n, X.vlen, h->st);
+    else coarse_import<T>(dst, src, X.g, X.n, n, X.vlen, h->st);
+  };
+  auto exp = [&](Level& X, cplx<double>* dst, const cplx<T>* src) {
+    if (X.fine) fine_export<T>(dst, src, X.g, n, X.vlen, h->st);
+    else coarse_export<T>(dst, src, X.g, X.n, n, X.vlen, h->st);
+  };
+  if (din) imp(L, ti, din);
+  if (out_is_in_out) imp(O, to, dout);
+  f(to, ti);
+  exp(O, dout, to);
+  if (!out_dev) CK(cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, h->st));
+  sync(h);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+extern "C" {
+
+void ddamg_default_params(ddamg_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->levels = 3;
+  for (int l = 0; l < DDAMG_MAX_LEVELS; ++l)
+    for (int d = 0; d < 4; ++d) {
+      p->agg[l][d] = l == 0 ? 4 : 2;
+      p->sap_block[l][d] = 2;
+    }
+  for (int l = 0; l < DDAMG_MAX_LEVELS; ++l) p->n_tv[l] = 20;
+  p->mr_steps = 3;
+  p->nu = 5;
+  p->mu = 0;
+  p->n_inv = 6;
+  p->eta_passes = 3;
+  p->outer_restart = 10;
+  p->outer_max_cycles = 100;
+  p->kcycle_len = 5;
+  p->kcycle_cycles = 2;
+  p->kcycle_tol = 1e-1;
+  p->coarse_tol = 5e-2;
+  p->coarse_restart = 50;
+  p->coarse_cycles = 20;
+  p->precision = 1;
+  p->max_rhs = 1;
+}
+
+const char* ddamg_last_error(void) { return g_err.c_str(); }
+
+int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, double csw, const ddamg_params* params,
+                const double* const* tv_random, ddamg_handle** out) {
+  if (!out || !gauge || !dims || !params) {
+    g_err = "null argument";
+    return DDAMG_ERR_ARG;
+  }
+  *out = nullptr;
+  ddamg_handle* h = new ddamg_handle();
+  const int rc = guard([&] {
+    validate(*params);
+    h->p = *params;
+    for (int d = 0; d < 4; ++d) h->dims[d] = dims[d];
+    h->bc_t = bc_t;
+    h->m0 = m0;
+    h->csw = csw;
+    h->max_batch = params->max_rhs;
+    CK(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
+    h->st = h->own;
+    CK(cudaMallocHost(&h->h_done, sizeof(int) * 64));
+    CK(cudaMallocHost(&h->h_kr, sizeof(int) * 64));
+    CK(cudaMallocHost(&h->h_scal, sizeof(double) * 64));
+    build_hierarchy(h);
+    allocate_hierarchy(h);
+    h->d_err = dalloc<int>(h, 1);
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
+    double gg[6 * 16 * 2];
+    gamma_products(gg);
+    set_gamma_products(gg);
+    Level& F = h->lv[0];
+    const size_t gbytes = sizeof(cplx<double>) * 36 * (size_t)F.g.V;
+    const cplx<double>* gd = static_cast<const cplx<double>*>(dev_in(h, gauge, gbytes, 0));
+    links_import<double>(F.f64.U, gd, F.g, h->st);
+    links_import<float>(F.f32.U, gd, F.g, h->st);
+    clover_build(F.f64.clov, gd, F.g, m0, csw, h->st);
+    real_convert<float>(F.f32.clov, F.f64.clov, (size_t)72 * F.g.V, h->st);
+    sync(h);
+    initial_setup_phase(h, 0, tv_random);
+    for (int i = 1; i <= h->p.n_inv; ++i) {
+      if (h->p.precision == 1) iterative_setup_phase<float>(h, 0, i);
+      else iterative_setup_phase<double>(h, 0, i);
+    }
+    sync(h);
+  });
+  if (rc != DDAMG_OK) {
+    ddamg_free(h);
+    return rc;
+  }
+  *out = h;
+  return DDAMG_OK;
+}
+
+void ddamg_free(ddamg_handle* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (void* p : h->allocs) cudaFree(p);
+  for (auto& s : h->scr)
+    if (s.p) cudaFree(s.p);
+  if (h->h_done) cudaFreeHost(h->h_done);
+  if (h->h_kr) cudaFreeHost(h->h_kr);
+  if (h->h_scal) cudaFreeHost(h->h_scal);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+}
+
+int ddamg_set_stream(ddamg_handle* h, void* stream) {
+  if (!h) return DDAMG_ERR_ARG;
+  return guard([&] {
+    sync(h);
+    h->st = stream ? static_cast<cudaStream_t>(stream) : h->own;
+  });
+}
+
+int ddamg_solve(ddamg_handle* h, const double* rhs, double* x, int n, double tol, ddamg_stats* per_rhs) {
+  if (!h || !rhs || !x || n < 0 || !(tol > 0)) {
+    g_err = "invalid argument";
+    return DDAMG_ERR_ARG;
+  }
+  bool all_conv = true;
+  const int rc = guard([&] {
+    Level& F = h->lv[0];
+    const size_t fbytes = sizeof(cplx<double>) * F.vlen;
+    const bool xdev = is_device_ptr(x);
+    for (int s0 = 0; s0 < n; s0 += h->max_batch) {
+      const int nb = (n - s0) < h->max_batch ? (n - s0) : h->max_batch;
+      const cplx<double>* din =
+          static_cast<const cplx<double>*>(dev_in(h, rhs + (size_t)s0 * F.vlen * 2, fbytes * nb, 0));
+      fine_import<double>(h->ob, din, F.g, nb, F.vlen, h->st);
+      auto A = [&](cplx<double>* o, const cplx<double>* in, const cplx<double>* bb) {
+        apply_D<double>(h, F, o, in, bb, nb);
+      };
+      auto M = [&](cplx<double>* z, const cplx<double>* v) {
+        if (h->p.precision == 1) precond_outer<float>(h, z, v, nb);
+        else precond_outer<double>(h, z, v, nb);
+      };
+      KrylovResult res;
+      krylov<double>(h, h->outer, F.vlen, h->ox, h->ob, nb, h->p.outer_restart, tol, h->p.outer_max_cycles, true,
+                     true, A, M, &res);
+      cplx<double>* dx = xdev ? reinterpret_cast<cplx<double>*>(x + (size_t)s0 * F.vlen * 2)
+                              : static_cast<cplx<double>*>(scratch(h, 1, fbytes * nb));
+      fine_export<double>(dx, h->ox, F.g, nb, F.vlen, h->st);
+      if (!xdev) CK(cudaMemcpyAsync(x + (size_t)s0 * F.vlen * 2, dx, fbytes * nb, cudaMemcpyDeviceToHost, h->st));
+      sync(h);
+      for (int r = 0; r < nb; ++r) {
+        if (per_rhs) {
+          per_rhs[s0 + r].iterations = res.iterations[r];
+          per_rhs[s0 + r].cycles = res.cycles[r];
+          per_rhs[s0 + r].converged = res.converged[r];
+          per_rhs[s0 + r].true_residual = res.true_residual[r];
+        }
+        all_conv = all_conv && res.converged[r];
+      }
+    }
+  });
+  if (rc != DDAMG_OK) return rc;
+  if (!all_conv) {
+    g_err = "outer FGMRES did not reach the tolerance";
+    return DDAMG_ERR_NOCONV;
+  }
+  return DDAMG_OK;
+}
+
+int ddamg_level_info(ddamg_handle* h, int level, int dims[4], int* ndof, int* ntv) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (dims)
+      for (int d = 0; d < 4; ++d) dims[d] = L.g.L[d];
+    if (ndof) *ndof = L.n;
+    if (ntv) *ntv = L.N;
+  });
+}
+
+int ddamg_apply(ddamg_handle* h, int level, int precision, const double* in, double* out, int n) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (n < 1 || !in || !out) fail(DDAMG_ERR_ARG, "invalid fields");
+    if (precision == 1)
+      hook<float>(h, level, in, out, n, false, level,
+                  [&](cplx<float>* o, cplx<float>* i) { apply_D<float>(h, L, o, i, nullptr, n); });
+    else
+      hook<double>(h, level, in, out, n, false, level,
+                   [&](cplx<double>* o, cplx<double>* i) { apply_D<double>(h, L, o, i, nullptr, n); });
+  });
+}
+
+int ddamg_smooth(ddamg_handle* h, int level, int precision, const double* b, double* z, int n, int iterations) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (L.coarsest || n < 1 || !b || !z) fail(DDAMG_ERR_ARG, "no smoother on this level");
+    if (precision == 1)
+      hook<float>(h, level, b, z, n, true, level,
+                  [&](cplx<float>* o, cplx<float>* i) { sap<float>(h, L, o, i, n, iterations); });
+    else
+      hook<double>(h, level, b, z, n, true, level,
+                   [&](cplx<double>* o, cplx<double>* i) { sap<double>(h, L, o, i, n, iterations); });
+  });
+}
+
+int ddamg_restrict(ddamg_handle* h, int level, int precision, const double* fine, double* coarse, int n) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (L.coarsest || n < 1) fail(DDAMG_ERR_ARG, "no restriction from the coarsest level");
+    if (precision == 1)
+      hook<float>(h, level, fine, coarse, n, false, level + 1,
+                  [&](cplx<float>* o, cplx<float>* i) { restrict_lv<float>(h, level, o, i, n); });
+    else
+      hook<double>(h, level, fine, coarse, n, false, level + 1,
+                   [&](cplx<double>* o, cplx<double>* i) { restrict_lv<double>(h, level, o, i, n); });
+  });
+}
+
+int ddamg_prolong(ddamg_handle* h, int level, int precision, const double* coarse, double* fine, int n) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (L.coarsest || n < 1) fail(DDAMG_ERR_ARG, "no prolongation to the coarsest level");
+    if (precision == 1)
+      hook<float>(h, level + 1, coarse, fine, n, false, level,
+                  [&](cplx<float>* o, cplx<float>* i) { prolong_lv<float>(h, level, o, i, n, false); });
+    else
+      hook<double>(h, level + 1, coarse, fine, n, false, level,
+                   [&](cplx<double>* o, cplx<double>* i) { prolong_lv<double>(h, level, o, i, n, false); });
+  });
+}
+
+int ddamg_kcycle(ddamg_handle* h, int level, int precision, const double* b, double* z, int n) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (L.coarsest || n < 1 || n > h->max_batch) fail(DDAMG_ERR_ARG, "K-cycle needs a non-coarsest level, n <= max_rhs");
+    if (precision == 1)
+      hook<float>(h, level, b, z, n, false, level,
+                  [&](cplx<float>* o, cplx<float>* i) { kcycle<float>(h, level, o, i, n); });
+    else
+      hook<double>(h, level, b, z, n, false, level,
+                   [&](cplx<double>* o, cplx<double>* i) { kcycle<double>(h, level, o, i, n); });
+  });
+}
+
+int ddamg_coarse_solve(ddamg_handle* h, int precision, const double* b, double* z, int n) {
+  return guard([&] {
+    if (!h || n < 1 || n > h->max_batch) fail(DDAMG_ERR_ARG, "n must be 1..max_rhs");
+    const int l = h->L - 1;
+    if (precision == 1)
+      hook<float>(h, l, b, z, n, false, l, [&](cplx<float>* o, cplx<float>* i) { coarse_solve<float>(h, o, i, n); });
+    else
+      hook<double>(h, l, b, z, n, false, l,
+                   [&](cplx<double>* o, cplx<double>* i) { coarse_solve<double>(h, o, i, n); });
+  });
+}
+
+int ddamg_set_testvectors(ddamg_handle* h, int level, const double* tv, int n) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (L.coarsest || n != L.N || !tv) fail(DDAMG_ERR_ARG, "n must equal n_tv of the level");
+    import_fields(h, L, L.tv64, tv, n);
+    sync(h);
+  });
+}
+
+int ddamg_get_testvectors(ddamg_handle* h, int level, double* tv, int n) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (L.coarsest || n != L.N || !tv) fail(DDAMG_ERR_ARG, "n must equal n_tv of the level");
+    hook<double>(h, level, nullptr, tv, n, false, level, [&](cplx<double>* o, cplx<double>*) {
+      blas_convert<double, double>(o, L.tv64, L.vlen * n, 1, 0, 0, h->st);
+    });
+  });
+}
+
+int ddamg_rebuild(ddamg_handle* h, int level) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (L.coarsest) fail(DDAMG_ERR_ARG, "no interpolation on the coarsest level");
+    rebuild(h, level);
+  });
+}
+
+int ddamg_get_interpolation(ddamg_handle* h, int level, double* P) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (L.coarsest || !P) fail(DDAMG_ERR_ARG, "no interpolation on the coarsest level");
+    hook<double>(h, level, nullptr, P, L.N, false, level, [&](cplx<double>* o, cplx<double>*) {
+      blas_convert<double, double>(o, L.P64, L.vlen * L.N, 1, 0, 0, h->st);
+    });
+  });
+}
+
+int ddamg_get_coarse_operator(ddamg_handle* h, int level, double* blocks) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (L.fine || !blocks) fail(DDAMG_ERR_ARG, "coarse operators exist on levels >= 1");
+    const size_t bytes = sizeof(cplx<double>) * (size_t)L.g.V * 9 * L.n * L.n;
+    const bool dev = is_device_ptr(blocks);
+    cplx<double>* d = dev ? reinterpret_cast<cplx<double>*>(blocks) : static_cast<cplx<double>*>(scratch(h, 1, bytes));
+    coarse_blocks_export(d, L.c64.blk, L.g, L.n, h->st);
+    if (!dev) CK(cudaMemcpyAsync(blocks, d, bytes, cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+  });
+}
+
+}  // extern "C"

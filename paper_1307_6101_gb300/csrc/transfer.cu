@@ -1,0 +1,198 @@
+// Aggregation-based transfer operators (Sec. 1, Sec. 2.2 of the paper).
+//
+// P_l is stored as the N orthonormalised test-vector fields of level l.  For
+// aggregate A and chirality s (spins 0,1 / 2,3 on the fine level, first and
+// second half of the dof on a coarse level), column j of the block
+// Q_{A,s} is field j restricted to (A, s); coarse dof (A, s, j) has index s*N + j.
+// Aggregates are contiguous index ranges [A*vA, (A+1)*vA) in the site order.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+// address of (site x, component f) in a level field: fine [12][V], coarse [V][n]
+DD_HD size_t faddr(bool fine, int V, int n, int x, int f) {
+  return fine ? (size_t)f * V + x : (size_t)x * n + f;
+}
+
+constexpr int JC = 4;   // coarse columns per chirality handled per pass
+
+template <typename T>
+__device__ void block_sum(T* v, int cnt, T* sh) {
+  // sum cnt values per thread over the CTA; result valid in every thread
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < cnt; ++k)
+    for (int off = 16; off >= 1; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+  if (lane == 0)
+    for (int k = 0; k < cnt; ++k) sh[warp * cnt + k] = v[k];
+  __syncthreads();
+  for (int k = 0; k < cnt; ++k) {
+    T s = T(0);
+    for (int w = 0; w < nw; ++w) s += sh[w * cnt + k];
+    v[k] = s;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const cplx<T>* __restrict__ P,
+                           Geom gf, Geom gc, bool fine, int n, int N, size_t in_rstride, size_t pstride,
+                           size_t out_rstride, size_t out_site_stride) {
+  __shared__ T sh[32 * 4 * JC];
+  const int agg = blockIdx.x;
+  const int V = gf.V;
+  const cplx<T>* pin = in + (size_t)blockIdx.y * in_rstride;
+  int c0[4];
+  geom_coords(gf, agg * gf.vA, c0);   // first site of the aggregate (aggregates are contiguous)
+  const int cs = coarse_site_of(gf, gc, c0);
+  cplx<T>* po = out + (size_t)blockIdx.y * out_rstride + (size_t)cs * out_site_stride;
+  const int h = n / 2;
+  for (int j0 = 0; j0 < N; j0 += JC) {
+    T acc[4 * JC];
+#pragma unroll
+    for (int k = 0; k < 4 * JC; ++k) acc[k] = T(0);
+    for (int xl = threadIdx.x; xl < gf.vA; xl += blockDim.x) {
+      const int x = agg * gf.vA + xl;
+      for (int f = 0; f < n; ++f) {
+        const cplx<T> v = pin[faddr(fine, V, n, x, f)];
+        const int s = f < h ? 0 : 1;
+#pragma unroll
+        for (int jj = 0; jj < JC; ++jj) {
+          if (j0 + jj < N) {
+            const cplx<T> p = P[(size_t)(j0 + jj) * pstride + faddr(fine, V, n, x, f)];
+            const cplx<T> t = cdotc(p, v);
+            acc[(s * JC + jj) * 2] += t.re;
+            acc[(s * JC + jj) * 2 + 1] += t.im;
+          }
+        }
+      }
+    }
+    block_sum(acc, 4 * JC, sh);
+    if (threadIdx.x < 2 * JC) {
+      const int s = threadIdx.x / JC, jj = threadIdx.x % JC;
+      if (j0 + jj < N) po[s * N + j0 + jj] = cmk<T>(acc[(s * JC + jj) * 2], acc[(s * JC + jj) * 2 + 1]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_prolong(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const cplx<T>* __restrict__ P,
+                          Geom gf, Geom gc, bool fine, int n, int N, size_t out_rstride, size_t in_rstride,
+                          size_t pstride, bool accumulate) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int V = gf.V;
+  if (t >= (size_t)V * n) return;
+  int x, f;
+  if (fine) { f = (int)(t / V); x = (int)(t % V); }
+  else { x = (int)(t / n); f = (int)(t % n); }
+  int c[4];
+  geom_coords(gf, x, c);
+  const int cs = coarse_site_of(gf, gc, c);
+  const int s = f < n / 2 ? 0 : 1;
+  const cplx<T>* pc = in + (size_t)blockIdx.y * in_rstride + (size_t)cs * (2 * N) + s * N;
+  cplx<T> acc = czero<T>();
+  const size_t a = faddr(fine, V, n, x, f);
+  for (int j = 0; j < N; ++j) cfma(acc, P[(size_t)j * pstride + a], pc[j]);
+  cplx<T>* po = out + (size_t)blockIdx.y * out_rstride + a;
+  *po = accumulate ? *po + acc : acc;
+}
+
+// CGS2 of the N test vectors restricted to (aggregate, chirality), in column order.
+__global__ void k_orthonormalise(cplx<double>* __restrict__ P, Geom g, bool fine, int n, int N, size_t pstride,
+                                 int* err) {
+  __shared__ double sh[32 * 2 * 8];
+  __shared__ cplx<double> hs[64];
+  const int agg = blockIdx.x;
+  const int s = blockIdx.y;
+  const int h = n / 2;
+  const int ne = g.vA * h;
+  const int V = g.V;
+  auto addr = [&](int e) {
+    const int x = agg * g.vA + e / h;
+    const int f = s * h + e % h;
+    return faddr(fine, V, n, x, f);
+  };
+  for (int j = 0; j < N; ++j) {
+    cplx<double>* w = P + (size_t)j * pstride;
+    double n0 = 0.0;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) n0 += cnorm2(w[addr(e)]);
+    block_sum(&n0, 1, sh);
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i0 = 0; i0 < j; i0 += 8) {
+        double acc[16];
+        for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+          const size_t a = addr(e);
+          const cplx<double> we = w[a];
+          for (int ii = 0; ii < 8 && i0 + ii < j; ++ii) {
+            const cplx<double> t = cdotc(P[(size_t)(i0 + ii) * pstride + a], we);
+            acc[2 * ii] += t.re;
+            acc[2 * ii + 1] += t.im;
+          }
+        }
+        block_sum(acc, 16, sh);
+        if (threadIdx.x < 8 && i0 + threadIdx.x < j) hs[i0 + threadIdx.x] = cmk(acc[2 * threadIdx.x], acc[2 * threadIdx.x + 1]);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const size_t a = addr(e);
+        cplx<double> we = w[a];
+        for (int i = 0; i < j; ++i) we = we - hs[i] * P[(size_t)i * pstride + a];
+        w[a] = we;
+      }
+      __syncthreads();
+    }
+    double nn = 0.0;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) nn += cnorm2(w[addr(e)]);
+    block_sum(&nn, 1, sh);
+    const double nrm = sqrt(nn);
+    if (!(nrm > 1e-12 * sqrt(n0)) || n0 == 0.0) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      return;
+    }
+    const double inv = 1.0 / nrm;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const size_t a = addr(e);
+      w[a] = inv * w[a];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+namespace dd {
+
+template <typename T>
+void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine, int n,
+                 int N, int nrhs, size_t in_rstride, size_t out_rstride, size_t out_site_stride, cudaStream_t st) {
+  const size_t pstride = (size_t)gf.V * n;
+  const int threads = gf.vA >= 256 ? 256 : (gf.vA >= 128 ? 128 : (gf.vA >= 64 ? 64 : 32));
+  k_restrict<T><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, P, gf, gc, fine, n, N, in_rstride, pstride,
+                                                          out_rstride, out_site_stride);
+}
+
+template <typename T>
+void prolong_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine, int n,
+                int N, int nrhs, size_t out_rstride, size_t in_rstride, bool accumulate, cudaStream_t st) {
+  const size_t pstride = (size_t)gf.V * n;
+  const size_t tot = (size_t)gf.V * n;
+  k_prolong<T><<<dim3(div_up(tot, 128), nrhs), 128, 0, st>>>(out, in, P, gf, gc, fine, n, N, out_rstride, in_rstride,
+                                                              pstride, accumulate);
+}
+
+void orthonormalise(cplx<double>* P, const Geom& g, bool fine, int n, int N, int* err, cudaStream_t st) {
+  const size_t pstride = (size_t)g.V * n;
+  k_orthonormalise<<<dim3(g.nAgg, 2), 256, 0, st>>>(P, g, fine, n, N, pstride, err);
+}
+
+#define INST(T)                                                                                                  \
+  template void restrict_op<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const Geom&, const Geom&, bool, int, int, \
+                               int, size_t, size_t, size_t, cudaStream_t);                                      \
+  template void prolong_op<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const Geom&, const Geom&, bool, int, int,  \
+                              int, size_t, size_t, bool, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace dd
