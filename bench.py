@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 DD-alpha-AMG solver: RHS/s and s/RHS at true relative residual 1e-10.
+
+One step = one complete solve (outer FP64 FGMRES preconditioned by the
+three-level K-cycle) of one batch of right-hand sides that are already
+resident in HBM; the hierarchy (setup, Alg. 3 + Alg. 4) is built before the
+timed region and reported separately.  The headline `value` is the mixed
+precision path (FP32 preconditioner, FP16-free in this version, FP64 outer
+FGMRES); the plain FP64 path is measured the same way and reported beside it.
+
+Workload (default): 16^3 x 32 lattice, seeded SU(3) links exp(i 0.4 H), c_sw = 1,
+m0 from tests/golden/masses.json (tuned on an 8^4 field at the same epsilon),
+levels 3 with aggregates 4^4 (20 test vectors) then 2^4 (28 test vectors), SAP
+blocks 4^4 on level 1 and 2^4 on level 2 with 4 MR steps, Table 1 otherwise,
+one complex N(0,1) right-hand side.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+With N > 1 (torchrun, one process per GPU) every rank solves its own seeded
+right-hand sides on its own hierarchy (replicas, weak scaling); rank 0 prints
+the whole-job RHS/s.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RHS/s and s/RHS at true rel. residual 1e-10, mixed vs plain FP64; p50/p99 ms"
+
+WORKLOADS = {
+    "three_level_16c32": dict(
+        name="three-level 16^3x32, eps 0.4, csw 1.0, 20/28 test vectors, SAP 4^4, 1 RHS",
+        dims=(32, 16, 16, 16), eps=0.4, csw=1.0, mass="eps0.4_csw1", levels=3,
+        agg=[(4, 4, 4, 4), (2, 2, 2, 2)], n_tv=[20, 28], sap=[(4, 4, 4, 4), (2, 2, 2, 2)],
+        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=1, seed=0, tv_seed=100, rhs_seed=1),
+    "two_level_8c4": dict(
+        name="two-level 8^4, eps 0.3, csw 0, 8 test vectors, SAP 2^4, 1 RHS",
+        dims=(8, 8, 8, 8), eps=0.3, csw=0.0, mass="eps0.3_csw0", levels=2,
+        agg=[(4, 4, 4, 4)], n_tv=[8], sap=[(2, 2, 2, 2)],
+        mr_steps=4, nu=3, n_inv=3, outer_restart=25, nrhs=1, seed=0, tv_seed=100, rhs_seed=1),
+}
+TOL = 1e-10
+PAPER_OUTER_ITERATIONS = 22   # three-level outer FGMRES iterations on P2 (Table 3 of the paper)
+
+
+def mass(name):
+    with open(os.path.join(ROOT, "tests", "golden", "masses.json")) as f:
+        return json.load(f)["masses"][name]["m0"]
+
+
+def inputs(w, rank=0):
+    import synth
+    U = synth.su3_field(w["dims"], w["eps"], w["seed"])
+    dims_l = [tuple(w["dims"])]
+    for a in w["agg"]:
+        dims_l.append(tuple(d // x for d, x in zip(dims_l[-1], a)))
+    tv = synth.random_test_vectors(dims_l, w["n_tv"], w["tv_seed"])
+    rhs = synth.random_spinors(w["nrhs"], w["dims"], w["rhs_seed"] + 1000 * rank)
+    return U, tv, np.ascontiguousarray(rhs)
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_file):
+    """DRAM bytes per launch of the fine SAP sweep from the committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "fine_sap_sweep_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
+        if d.get("source_sha256") != h:
+            return None
+        return d.get("dram_bytes_per_launch_scaled")
+    except (OSError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args, w):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1307_6101_gb300 as dd
+
+    U, tv, rhs_h = inputs(w, rank)
+    m0 = mass(w["mass"])
+    nb = w["nrhs"]
+
+    def params(precision):
+        return dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
+                                       mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
+                                       outer_restart=w["outer_restart"], precision=precision, max_rhs=nb)
+
+    stream = torch.cuda.current_stream()
+    setup_s = {}
+    handles = {}
+    for name, prec in (("mixed", 1), ("fp64", 0)):
+        t0 = time.perf_counter()
+        h = dd.ddamg_setup(U, w["dims"], -1, m0, w["csw"], params(prec), tv)
+        setup_s[name] = time.perf_counter() - t0
+        dd.ddamg_set_stream(h, stream.cuda_stream)
+        if args.eager:
+            dd.ddamg_set_option(h, dd.DDAMG_OPT_GRAPHS, 0)
+        handles[name] = h
+
+    rhs = torch.from_numpy(rhs_h).cuda()
+    x = torch.zeros_like(rhs)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (126 MB)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(h, steps, warm, profile_mask=0, tag="timed"):
+        for _ in range(warm):
+            dd.ddamg_solve(h, rhs, x, nb, TOL)
+        barrier()
+        ms, stats = [], []
+        launches0 = dd.ddamg_launch_count()
+        if profile_mask:
+            dd.ddamg_profile(h, profile_mask)
+        torch.cuda.nvtx.range_push(tag)
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = dd.ddamg_solve(h, rhs, x, nb, TOL)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            stats.append(st)
+        torch.cuda.nvtx.range_pop()
+        barrier()
+        launches = dd.ddamg_launch_count() - launches0 - 0
+        prof = None
+        if profile_mask:
+            prof = dd.ddamg_profile_read(h, "fine_sap")
+            dd.ddamg_profile(h, 0)
+        return ms, stats, launches, prof
+
+    clk = Clocks(local)
+    clk.start()
+    steps0 = [dd.ddamg_krylov_steps(handles["mixed"], l, 1) for l in range(w["levels"])]
+    ms_mixed, st_mixed, launches, prof = timed(handles["mixed"], args.steps, args.warmup, profile_mask=1,
+                                               tag="timed_mixed")
+    steps1 = [dd.ddamg_krylov_steps(handles["mixed"], l, 1) for l in range(w["levels"])]
+    clocks = clk.stop()
+    ms_fp64, st_fp64, _, _ = timed(handles["fp64"], args.steps, max(1, min(args.warmup, 3)), tag="timed_fp64")
+
+    for st in st_mixed + st_fp64:
+        for s in st:
+            if not (s["converged"] and s["true_residual"] <= TOL):
+                raise SystemExit(f"solve missed the tolerance: {s}")
+
+    def agg(ms):
+        tot = sum(ms)
+        if dist is not None:
+            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        return tot
+
+    tot_mixed = agg(ms_mixed)
+    tot_fp64 = agg(ms_fp64)
+    rhs_total = nb * args.steps * world
+    value = rhs_total / (tot_mixed / 1e3)
+    value_fp64 = rhs_total / (tot_fp64 / 1e3)
+
+    def pct(ms):
+        s = sorted(ms)
+        p50 = statistics.median(s)
+        p99 = s[min(len(s) - 1, int(np.ceil(0.99 * len(s))) - 1)]
+        return p50, p99
+
+    p50, p99 = pct(ms_mixed)
+    q50, q99 = pct(ms_fp64)
+
+    # end to end through the C ABI with host buffers (H2D of the rhs and D2H of x inside every step)
+    rhs_np = np.ascontiguousarray(rhs_h)
+    x_np = np.zeros_like(rhs_np)
+    dd.ddamg_solve(handles["mixed"], rhs_np, x_np, nb, TOL)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dd.ddamg_solve(handles["mixed"], rhs_np, x_np, nb, TOL)
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": rhs_total / t_e2e, "unit": "RHS/s",
+           "h2d_bytes_per_step": int(rhs_np.nbytes), "d2h_bytes_per_step": int(x_np.nbytes)}
+
+    # roofline of the dominant kernel: the fine SAP colour sweep
+    pk, pk_src = peaks()
+    p_ms, p_n, p_bytes = prof
+    avg_ms = p_ms / max(1, p_n)
+    per_launch = p_bytes / max(1, p_n)
+    achieved = per_launch / (avg_ms / 1e3) / 1e9
+    roof = {"kernel": "k_fine_sap<float> (one SAP colour sweep, 4 MR steps)", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": pk, "unit": "GB/s", "frac": round(achieved / pk, 4),
+            "peak_source": pk_src, "traffic": ncu_traffic(os.path.join(ROOT, "paper_1307_6101_gb300", "csrc",
+                                                                        "fine.cu")),
+            "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms, "launches": p_n,
+            "share_of_step": round(p_ms / max(1e-9, sum(ms_mixed)), 4)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(tot_mixed / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 preconditioner / f64 outer FGMRES",
+        "data": "synthetic (seeded SU(3) links, complex N(0,1) rhs)",
+        "config": {"workload": w["name"], "lattice": "x".join(str(d) for d in w["dims"][::-1]),
+                   "levels": w["levels"], "rhs_per_step": nb, "global_batch": nb * world,
+                   "tol": TOL, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "s_per_rhs": round(tot_mixed / 1e3 / (nb * args.steps), 6),
+        "p50_ms": round(p50, 3), ("p99_ms" if len(ms_mixed) >= 100 else "p99_ms_is_max_of_steps"): round(p99, 3),
+        "iterations": [s["iterations"] for st in st_mixed[:1] for s in st],
+        "true_residual": max(s["true_residual"] for st in st_mixed for s in st),
+        "plain_fp64": {"value": round(value_fp64, 4), "unit": "RHS/s",
+                       "s_per_rhs": round(tot_fp64 / 1e3 / (nb * args.steps), 6),
+                       "p50_ms": round(q50, 3), "p99_ms_is_max_of_steps": round(q99, 3),
+                       "iterations": [s["iterations"] for st in st_fp64[:1] for s in st],
+                       "true_residual": max(s["true_residual"] for st in st_fp64 for s in st)},
+        "mixed_over_fp64": round(value / value_fp64, 3),
+        "setup_s": {k: round(v, 2) for k, v in setup_s.items()},
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "krylov_steps_per_solve": [round((b - a) / args.steps, 1) for a, b in zip(steps0, steps1)],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, out["iterations"][0] if out["iterations"] else None)
+    for h in handles.values():
+        h.free()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(w, steps, warmup, iterations_per_solve):
+    """Oracle timing: one outer FGMRES iteration (K-cycle + D + CGS2) per step on the same workload.
+
+    The oracle hierarchy is built by Alg. 3 without smoothing passes (random test
+    vectors orthonormalised, Galerkin operators) so that its construction stays
+    bounded; the per-iteration cost does not depend on the test vectors.
+    """
+    import oracle.multigrid as omg
+    from oracle.krylov import fgmres
+    from oracle.wilson import WilsonOp
+    U, tv, rhs = inputs(w)
+    op = WilsonOp.build(U, mass(w["mass"]), w["csw"], -1)
+    p = omg.Params(levels=w["levels"], agg=tuple(w["agg"]), n_tv=tuple(w["n_tv"]),
+                   sap_block=tuple(w["sap"]) + (None,), mr_steps=w["mr_steps"], nu=w["nu"], n_inv=0,
+                   eta_passes=0, outer_restart=w["outer_restart"])
+    t0 = time.perf_counter()
+    h = omg.Hierarchy(op, p).setup(tv)
+    t_setup = time.perf_counter() - t0
+    b = rhs[0]
+    for _ in range(warmup):
+        fgmres(op.apply, b, M=lambda v: h.kcycle(0, v), m=1, tol=TOL, max_cycles=1, final_residual=False)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        fgmres(op.apply, b, M=lambda v: h.kcycle(0, v), m=1, tol=TOL, max_cycles=1, final_residual=False)
+        times.append(time.perf_counter() - t0)
+    t_iter = statistics.mean(times)
+    its = iterations_per_solve or PAPER_OUTER_ITERATIONS
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    return {"value": 1.0 / (t_iter * its), "unit": "RHS/s", "cores": 1, "host_cores_available": cores,
+            "kind": "oracle",
+            "sample": (f"{steps} outer FGMRES iteration(s) of the FP64 numpy oracle on the same workload "
+                       f"(hierarchy from Alg. 3 without smoothing, built in {t_setup:.0f} s, untimed); "
+                       f"{t_iter:.2f} s per iteration scaled by {its} iterations per solve"),
+            "seconds_per_iteration": t_iter, "iterations_per_solve": its}
+
+
+def cpu_baseline(w, its):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    return oracle_sample(w, steps=1, warmup=0, iterations_per_solve=its)
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    s = oracle_sample(w, steps=args.steps, warmup=min(args.warmup, 1), iterations_per_solve=None)
+    v = s["value"]
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "RHS/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": s["seconds_per_iteration"] * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded SU(3) links, complex N(0,1) rhs)",
+           "config": {"workload": w["name"], "lattice": "x".join(str(d) for d in w["dims"][::-1]),
+                      "levels": w["levels"], "rhs_per_step": w["nrhs"], "tol": TOL,
+                      "step": "one outer FGMRES iteration of the oracle"},
+           "cpu_baseline": {"value": v, "unit": "RHS/s", "cores": 1, "kind": "oracle", "sample": s["sample"]},
+           "e2e": {"value": v, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="three_level_16c32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="host-driven inner solves instead of captured graphs (for kernel-level profiling)")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -109,6 +109,46 @@ const char* ddamg_last_error(void);
  * NULL = the library's own stream). */
 int ddamg_set_stream(ddamg_handle* h, void* stream);
 
+/* Options (ddamg_set_option). */
+enum {
+  DDAMG_OPT_GRAPHS = 0   /* 1 (default): each K-cycle runs as one captured CUDA graph whose inner
+                            Krylov loops are device-driven conditional WHILE nodes; 0: host-driven */
+};
+int ddamg_set_option(ddamg_handle* h, int option, int value);
+
+/* ---- measurement ----------------------------------------------------------- */
+
+/* Kernel classes timed by ddamg_profile. */
+enum {
+  DDAMG_PROF_FINE_SAP = 0,      /* one SAP colour sweep on the fine level          */
+  DDAMG_PROF_FINE_DSLASH = 1,   /* one fine Wilson-clover application              */
+  DDAMG_PROF_COARSE_APPLY = 2,  /* one coarse stencil application                  */
+  DDAMG_PROF_COARSE_SAP = 3,    /* one SAP colour sweep on a coarse level          */
+  DDAMG_PROF_TRANSFER = 4,      /* one restriction or prolongation                 */
+  DDAMG_PROF_PRECOND = 5,       /* one outer preconditioner application (K-cycle)  */
+  DDAMG_PROF_OUTER_ORTHO = 6,   /* outer FGMRES Gram-Schmidt + norms of one step    */
+  DDAMG_PROF_KINDS = 7
+};
+
+/* enable = bitmask (1 << DDAMG_PROF_*): reset the counters and record a CUDA
+ * event pair around every launch of the selected classes (on the launching
+ * stream); enable = 0 stops recording. */
+int ddamg_profile(ddamg_handle* h, int enable);
+
+/* Totals since the last ddamg_profile(h, 1): summed event time in ms, launch
+ * count, and the algorithmic bytes those launches move (operator data once per
+ * launch, vectors once per right-hand side). */
+int ddamg_profile_read(ddamg_handle* h, int kind, double* total_ms, long long* launches, double* algo_bytes);
+
+/* Kernels launched by this library since it was loaded (all handles).  A
+ * captured K-cycle graph counts as one launch. */
+long long ddamg_launch_count(void);
+
+/* Arnoldi steps taken on a level since setup by its Krylov solver in the given
+ * precision (level 0: the outer FGMRES; coarse levels: K-cycle FGMRES or the
+ * coarsest GMRES). */
+int ddamg_krylov_steps(ddamg_handle* h, int level, int precision, long long* steps);
+
 /* ---- building blocks of the method, exposed for parity tests ------------ */
 
 /* Level geometry: dims of level l, its dof per site, its test vectors N_l

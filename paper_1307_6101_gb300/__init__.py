@@ -30,7 +30,12 @@ EXPORTED = (
     "ddamg_set_stream", "ddamg_level_info", "ddamg_apply", "ddamg_smooth", "ddamg_restrict",
     "ddamg_prolong", "ddamg_kcycle", "ddamg_coarse_solve", "ddamg_set_testvectors",
     "ddamg_get_testvectors", "ddamg_rebuild", "ddamg_get_interpolation", "ddamg_get_coarse_operator",
+    "ddamg_profile", "ddamg_profile_read", "ddamg_launch_count", "ddamg_set_option",
+    "ddamg_krylov_steps",
 )
+DDAMG_OPT_GRAPHS = 0
+PROF_KINDS = {"fine_sap": 0, "fine_dslash": 1, "coarse_apply": 2, "coarse_sap": 3, "transfer": 4, "precond": 5,
+              "outer_ortho": 6}
 
 
 class DdamgParams(C.Structure):
@@ -93,6 +98,12 @@ def _load():
     lib.ddamg_rebuild.argtypes = [vp, ip]
     lib.ddamg_get_interpolation.argtypes = [vp, ip, vp]
     lib.ddamg_get_coarse_operator.argtypes = [vp, ip, vp]
+    lib.ddamg_profile.argtypes = [vp, ip]
+    lib.ddamg_profile_read.argtypes = [vp, ip, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
+    lib.ddamg_set_option.argtypes = [vp, ip, ip]
+    lib.ddamg_krylov_steps.argtypes = [vp, ip, ip, C.POINTER(C.c_longlong)]
+    lib.ddamg_launch_count.restype = C.c_longlong
+    lib.ddamg_launch_count.argtypes = []
     del dp
     return lib
 
@@ -248,3 +259,29 @@ def ddamg_get_interpolation(h, level, P):
 
 def ddamg_get_coarse_operator(h, level, blocks):
     _check(lib().ddamg_get_coarse_operator(h.raw, level, _ptr(blocks)))
+
+
+def ddamg_profile(h, enable):
+    _check(lib().ddamg_profile(h.raw, int(enable)))
+
+
+def ddamg_profile_read(h, kind):
+    """(total ms, launches, algorithmic bytes) of a kernel class since profiling was enabled."""
+    k = PROF_KINDS[kind] if isinstance(kind, str) else int(kind)
+    ms, n, b = C.c_double(), C.c_longlong(), C.c_double()
+    _check(lib().ddamg_profile_read(h.raw, k, C.byref(ms), C.byref(n), C.byref(b)))
+    return ms.value, n.value, b.value
+
+
+def ddamg_launch_count():
+    return int(lib().ddamg_launch_count())
+
+
+def ddamg_set_option(h, option, value):
+    _check(lib().ddamg_set_option(h.raw, int(option), int(value)))
+
+
+def ddamg_krylov_steps(h, level, precision):
+    n = C.c_longlong()
+    _check(lib().ddamg_krylov_steps(h.raw, int(level), int(precision), C.byref(n)))
+    return n.value

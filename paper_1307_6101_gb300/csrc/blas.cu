@@ -8,6 +8,7 @@
 #include "kernels.h"
 
 #include <cstdio>
+#include <atomic>
 #include <mutex>
 
 namespace {
@@ -15,7 +16,9 @@ namespace {
 constexpr int RT = 256;         // threads per reduction CTA
 constexpr int MAXCHUNKS = 512;  // partials per rhs (and per dot in a multidot)
 
-// scratch for the partials, grown on demand (library-owned device memory)
+// scratch for the partials, grown on demand (library-owned device memory).  A
+// buffer that was replaced is kept until the library is unloaded, because
+// captured CUDA graphs may still refer to it.
 double* g_partials = nullptr;
 size_t g_partials_cap = 0;
 std::mutex g_partials_mu;
@@ -23,7 +26,6 @@ std::mutex g_partials_mu;
 double* partials(size_t count) {
   std::lock_guard<std::mutex> lk(g_partials_mu);
   if (count > g_partials_cap) {
-    if (g_partials) cudaFree(g_partials);
     size_t cap = count < (1u << 20) ? (1u << 20) : count;
     if (cudaMalloc(&g_partials, cap * sizeof(double)) != cudaSuccess) {
       g_partials = nullptr;
@@ -82,18 +84,22 @@ __global__ void k_multidot1(double* __restrict__ part, const cplx<T>* __restrict
   chunk_range(len, nc, chunk, lo, hi);
   const cplx<T>* pw = w + (size_t)rhs * rstride;
   for (int d0 = 0; d0 < m; d0 += 4) {
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // per-thread partials in the precision of the data (FP32 data: FP32 sums)
+    T at[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
       const cplx<T> we = pw[e];
 #pragma unroll
       for (int dd = 0; dd < 4; ++dd) {
         if (d0 + dd < m) {
           const cplx<T> v = V[(size_t)(d0 + dd) * vstride + (size_t)rhs * rstride + e];
-          acc[2 * dd] += (double)v.re * (double)we.re + (double)v.im * (double)we.im;
-          acc[2 * dd + 1] += (double)v.re * (double)we.im - (double)v.im * (double)we.re;
+          at[2 * dd] += v.re * we.re + v.im * we.im;
+          at[2 * dd + 1] += v.re * we.im - v.im * we.re;
         }
       }
     }
+    double acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = (double)at[k];
     cta_sum(acc, 8, sh);
     if (threadIdx.x == 0)
       for (int dd = 0; dd < 4 && d0 + dd < m; ++dd) {
@@ -123,11 +129,12 @@ __global__ void k_norm1(double* __restrict__ part, const cplx<T>* __restrict__ x
   size_t lo, hi;
   chunk_range(len, nc, chunk, lo, hi);
   const cplx<T>* px = x + (size_t)rhs * rstride;
-  double acc[1] = {0.0};
+  T at = T(0);
   for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
     const cplx<T> v = px[e];
-    acc[0] += (double)v.re * (double)v.re + (double)v.im * (double)v.im;
+    at += v.re * v.re + v.im * v.im;
   }
+  double acc[1] = {(double)at};
   cta_sum(acc, 1, sh);
   if (threadIdx.x == 0) part[(size_t)rhs * nc + chunk] = acc[0];
 }
@@ -284,13 +291,19 @@ __global__ void k_gmres_solve_y(dd::GmresState s, int nrhs) {
 
 namespace dd {
 
+static std::atomic<long long> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 template <typename T>
 void blas_multidot(cplx<double>* res, int res_stride, const cplx<T>* V, size_t vstride, int m, const cplx<T>* w,
                    size_t len, int nrhs, size_t rstride, cudaStream_t st) {
   if (m <= 0) return;
   const int nc = nchunks(len);
   double* part = partials((size_t)nrhs * m * nc * 2);
+  count_launch();
   k_multidot1<T><<<dim3(nc, nrhs), RT, 0, st>>>(part, V, vstride, m, w, len, rstride, nc);
+  count_launch();
   k_multidot2<<<dim3(m, nrhs), 128, 0, st>>>(res, part, m, nc, res_stride);
 }
 
@@ -306,7 +319,9 @@ template <typename T>
 void blas_norm2(double* res, const cplx<T>* x, size_t len, int nrhs, size_t rstride, cudaStream_t st) {
   const int nc = nchunks(len);
   double* part = partials((size_t)nrhs * nc);
+  count_launch();
   k_norm1<T><<<dim3(nc, nrhs), RT, 0, st>>>(part, x, len, rstride, nc);
+  count_launch();
   k_norm2<<<nrhs, 128, 0, st>>>(res, part, nc);
 }
 
@@ -314,33 +329,39 @@ template <typename T>
 void blas_multiaxpy(cplx<T>* y, const cplx<T>* V, size_t vstride, int m, const cplx<double>* c, int cstride,
                     double sign, size_t len, int nrhs, size_t rstride, cudaStream_t st) {
   if (m <= 0) return;
+  count_launch();
   k_multiaxpy<T><<<dim3(div_up(len, 256), nrhs), 256, 0, st>>>(y, V, vstride, m, c, cstride, sign, len, rstride);
 }
 
 template <typename T>
 void blas_scale_to(cplx<T>* y, const cplx<T>* x, const double* a, size_t len, int nrhs, size_t rstride,
                    cudaStream_t st) {
+  count_launch();
   k_scale_to<T><<<dim3(div_up(len, 256), nrhs), 256, 0, st>>>(y, x, a, len, rstride);
 }
 
 template <typename T>
 void blas_axpy(cplx<T>* y, const cplx<T>* x, double a, size_t len, int nrhs, size_t rstride, cudaStream_t st) {
+  count_launch();
   k_axpy<T><<<dim3(div_up(len, 256), nrhs), 256, 0, st>>>(y, x, a, len, rstride);
 }
 
 template <typename To, typename Ti>
 void blas_convert(cplx<To>* y, const cplx<Ti>* x, size_t len, int nrhs, size_t ystride, size_t xstride,
                   cudaStream_t st) {
+  count_launch();
   k_convert<To, Ti><<<dim3(div_up(len, 256), nrhs), 256, 0, st>>>(y, x, len, ystride, xstride);
 }
 
 template <typename T>
 void blas_zero(cplx<T>* y, size_t len, int nrhs, size_t rstride, cudaStream_t st) {
+  count_launch();
   k_zero<T><<<dim3(div_up(len, 256), nrhs), 256, 0, st>>>(y, len, rstride);
 }
 
 template <typename T>
 void real_convert(T* y, const double* x, size_t len, cudaStream_t st) {
+  count_launch();
   k_real_convert<T><<<div_up(len, 256), 256, 0, st>>>(y, x, len);
 }
 
@@ -348,9 +369,11 @@ void blas_recip(double* a, int n, cudaStream_t st) { k_recip<<<div_up(n, 128), 1
 
 void gmres_begin(const GmresState& s, int nrhs, cudaStream_t st) { k_gmres_begin<<<div_up(nrhs, 32), 32, 0, st>>>(s, nrhs); }
 void gmres_step(const GmresState& s, int j, int nrhs, cudaStream_t st) {
+  count_launch();
   k_gmres_step<<<div_up(nrhs, 32), 32, 0, st>>>(s, j, nrhs);
 }
 void gmres_solve_y(const GmresState& s, int nrhs, cudaStream_t st) {
+  count_launch();
   k_gmres_solve_y<<<div_up(nrhs, 32), 32, 0, st>>>(s, nrhs);
 }
 

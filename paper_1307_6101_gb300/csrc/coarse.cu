@@ -26,43 +26,175 @@ __device__ void cta_sum3(T& a, T& b, T& c, T* sh) {
   __syncthreads();
 }
 
+// (D phi)(A): one CTA per coarse site, one thread per (row i, block k); the
+// neighbour vectors are staged in shared memory and the 9 partial rows are
+// summed in shared memory.  Blocks are column-major, so the threads of one k
+// read consecutive words for every column j.
 template <typename T, bool RESID>
 __global__ void k_coarse_apply(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in,
                                const cplx<T>* __restrict__ bsrc, const cplx<T>* __restrict__ blk, Geom g, int n,
                                size_t rstride, int sel, int sel_mu, int in_chir) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)g.V * n) return;
-  const int site = (int)(t / n), i = (int)(t % n);
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);   // [9][n] neighbour vectors
+  cplx<T>* part = xs + 9 * n;                           // [9][n] partial rows
+  __shared__ int nbr[9];
+  __shared__ int take[9];
+  const int site = blockIdx.x;
   const size_t ro = (size_t)blockIdx.y * rstride;
   const cplx<T>* pin = in + ro;
-  int c[4];
-  geom_coords(g, site, c);
+  if (threadIdx.x < 9) {
+    int c[4];
+    geom_coords(g, site, c);
+    const int k = threadIdx.x;
+    int nb = site;
+    bool tk = sel == SEL_FULL || sel == SEL_AGG_SELF;
+    if (k > 0) {
+      const int mu = (k - 1) % 4, dir = k <= 4 ? +1 : -1;
+      nb = geom_neighbor(g, c, mu, dir);
+      const bool internal = hop_internal(g, c, mu, dir, g.A);
+      if (sel == SEL_FULL) tk = true;
+      else if (sel == SEL_AGG_SELF) tk = internal;
+      else if (sel == SEL_AGG_FWD) tk = dir > 0 && mu == sel_mu && !internal;
+      else tk = dir < 0 && mu == sel_mu && !internal;
+    }
+    nbr[k] = nb;
+    take[k] = tk;
+  }
+  __syncthreads();
   const int h = n / 2;
-  const int j0 = in_chir == 1 ? h : 0;
-  const int j1 = in_chir == 0 ? h : n;
-  cplx<T> acc = czero<T>();
-  if (sel == SEL_FULL || sel == SEL_AGG_SELF) {
-    const cplx<T>* v = pin + (size_t)site * n;
-    for (int j = j0; j < j1; ++j) cfma(acc, blk[bidx(site, 0, n, i, j)], v[j]);
+  for (int e = threadIdx.x; e < 9 * n; e += blockDim.x) {
+    const int k = e / n, j = e % n;
+    const bool keep = take[k] && (in_chir < 0 || (j < h) == (in_chir == 0));
+    xs[e] = keep ? pin[(size_t)nbr[k] * n + j] : czero<T>();
   }
-  for (int mu = 0; mu < 4; ++mu) {
-    const bool inf = hop_internal(g, c, mu, +1, g.A);
-    const bool inb = hop_internal(g, c, mu, -1, g.A);
-    bool tf = true, tb = true;
-    if (sel == SEL_AGG_SELF) { tf = inf; tb = inb; }
-    else if (sel == SEL_AGG_FWD) { tf = (mu == sel_mu) && !inf; tb = false; }
-    else if (sel == SEL_AGG_BWD) { tf = false; tb = (mu == sel_mu) && !inb; }
-    if (tf) {
-      const cplx<T>* v = pin + (size_t)geom_neighbor(g, c, mu, +1) * n;
-      for (int j = j0; j < j1; ++j) cfma(acc, blk[bidx(site, 1 + mu, n, i, j)], v[j]);
+  __syncthreads();
+  const int k = threadIdx.x / n, i = threadIdx.x % n;
+  if (k < 9) {
+    cplx<T> acc = czero<T>();
+    if (take[k]) {
+      const cplx<T>* M = blk + (((size_t)site * 9 + k) * n) * n + i;
+      const cplx<T>* x = xs + k * n;
+#pragma unroll 8
+      for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], x[j]);
     }
-    if (tb) {
-      const cplx<T>* v = pin + (size_t)geom_neighbor(g, c, mu, -1) * n;
-      for (int j = j0; j < j1; ++j) cfma(acc, blk[bidx(site, 5 + mu, n, i, j)], v[j]);
-    }
+    part[k * n + i] = acc;
   }
-  if (RESID) out[ro + t] = bsrc[ro + t] - acc;
-  else out[ro + t] = acc;
+  __syncthreads();
+  if (threadIdx.x < n) {
+    cplx<T> y = czero<T>();
+#pragma unroll
+    for (int q = 0; q < 9; ++q) y = y + part[q * n + threadIdx.x];
+    const size_t a = ro + (size_t)site * n + threadIdx.x;
+    out[a] = RESID ? bsrc[a] - y : y;
+  }
+}
+
+// Even-odd pieces of the coarsest solve (Sec. 3: odd-even preconditioned GMRES),
+// with D = [[S_ee, D_eo], [D_oe, S_oo]] and the self blocks S inverted at setup.
+// k_schur_odd: on every odd site A,  t(A) = S(A)^{-1} ( a*b(A) + c*(D_oe x)(A) )
+//              (even entries of t are not written)
+// k_schur_even: on every even site A, y(A) = a*b(A) + s*S(A) x(A) + c*(D_eo t)(A);
+//              odd entries of y are set to zero.
+template <typename T>
+__global__ void k_schur_odd(cplx<T>* __restrict__ t, const cplx<T>* __restrict__ x, const cplx<T>* __restrict__ b,
+                            const cplx<T>* __restrict__ blk, const cplx<T>* __restrict__ inv,
+                            const int* __restrict__ odd_sites, Geom g, int n, size_t rstride, double a, double c) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);   // [8][n]
+  cplx<T>* part = xs + 8 * n;                           // [8][n]
+  cplx<T>* u = part + 8 * n;                            // [n]
+  __shared__ int nbr[8];
+  const size_t ro = (size_t)blockIdx.y * rstride;
+  const int site = odd_sites[blockIdx.x];
+  if (threadIdx.x < 8) {
+    int cc[4];
+    geom_coords(g, site, cc);
+    const int k = threadIdx.x;
+    nbr[k] = geom_neighbor(g, cc, k % 4, k < 4 ? +1 : -1);
+  }
+  __syncthreads();
+  if (x && c != 0.0)
+    for (int e = threadIdx.x; e < 8 * n; e += blockDim.x) xs[e] = x[ro + (size_t)nbr[e / n] * n + e % n];
+  __syncthreads();
+  const int k = threadIdx.x / n, i = threadIdx.x % n;
+  if (k < 8) {
+    cplx<T> acc = czero<T>();
+    if (x && c != 0.0) {
+      const cplx<T>* M = blk + (((size_t)site * 9 + 1 + k) * n) * n + i;
+      const cplx<T>* xv = xs + k * n;
+#pragma unroll 8
+      for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], xv[j]);
+    }
+    part[k * n + i] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    cplx<T> y = czero<T>();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) y = y + part[q * n + threadIdx.x];
+    y = T(c) * y;
+    if (b && a != 0.0) y = y + T(a) * b[ro + (size_t)site * n + threadIdx.x];
+    u[threadIdx.x] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    cplx<T> acc = czero<T>();
+    const cplx<T>* Mi = inv + ((size_t)site * n) * n + threadIdx.x;
+#pragma unroll 8
+    for (int j = 0; j < n; ++j) cfma(acc, Mi[(size_t)j * n], u[j]);
+    t[ro + (size_t)site * n + threadIdx.x] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_schur_even(cplx<T>* __restrict__ y, const cplx<T>* __restrict__ x, const cplx<T>* __restrict__ t,
+                             const cplx<T>* __restrict__ b, const cplx<T>* __restrict__ blk, Geom g, int n,
+                             size_t rstride, double a, double s, double c) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);   // [9][n]
+  cplx<T>* part = xs + 9 * n;                           // [9][n]
+  __shared__ int nbr[9];
+  const int site = blockIdx.x;
+  const size_t ro = (size_t)blockIdx.y * rstride;
+  int cc[4];
+  geom_coords(g, site, cc);
+  if (geom_parity(cc) != 0) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[ro + (size_t)site * n + i] = czero<T>();
+    return;
+  }
+  if (threadIdx.x < 9) {
+    const int k = threadIdx.x;
+    nbr[k] = k == 0 ? site : geom_neighbor(g, cc, (k - 1) % 4, k <= 4 ? +1 : -1);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 9 * n; e += blockDim.x) {
+    const int k = e / n, j = e % n;
+    const cplx<T>* src = k == 0 ? x : t;
+    const double w = k == 0 ? s : c;
+    xs[e] = (src && w != 0.0) ? src[ro + (size_t)nbr[k] * n + j] : czero<T>();
+  }
+  __syncthreads();
+  const int k = threadIdx.x / n, i = threadIdx.x % n;
+  if (k < 9) {
+    cplx<T> acc = czero<T>();
+    const double w = k == 0 ? s : c;
+    if (w != 0.0 && (k == 0 ? x : t)) {
+      const cplx<T>* M = blk + (((size_t)site * 9 + k) * n) * n + i;
+      const cplx<T>* xv = xs + k * n;
+#pragma unroll 8
+      for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], xv[j]);
+    }
+    part[k * n + i] = T(w) * acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    cplx<T> v = czero<T>();
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v = v + part[q * n + threadIdx.x];
+    const size_t o = ro + (size_t)site * n + threadIdx.x;
+    if (b && a != 0.0) v = v + T(a) * b[o];
+    y[o] = v;
+  }
 }
 
 // One colour sweep of SAP on a coarse level: one CTA per SAP block, one thread
@@ -102,16 +234,19 @@ __global__ void k_coarse_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict_
     cplx<T> p = czero<T>();
     if (active) {
       const cplx<T>* v = rs + (size_t)loc * n;
+#pragma unroll 8
       for (int j = 0; j < n; ++j) cfma(p, blk[bidx(site, 0, n, i, j)], v[j]);
       for (int mu = 0; mu < 4; ++mu) {
         if (hop_internal(g, c, mu, +1, g.B)) {
           const int nl = geom_neighbor(g, c, mu, +1) - b * g.vB;
           v = rs + (size_t)nl * n;
+#pragma unroll 8
           for (int j = 0; j < n; ++j) cfma(p, blk[bidx(site, 1 + mu, n, i, j)], v[j]);
         }
         if (hop_internal(g, c, mu, -1, g.B)) {
           const int nl = geom_neighbor(g, c, mu, -1) - b * g.vB;
           v = rs + (size_t)nl * n;
+#pragma unroll 8
           for (int j = 0; j < n; ++j) cfma(p, blk[bidx(site, 5 + mu, n, i, j)], v[j]);
         }
       }
@@ -263,12 +398,14 @@ namespace dd {
 template <typename T>
 void coarse_apply(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const CoarseOp<T>& op, int nrhs, size_t rstride,
                   int sel, int sel_mu, int in_chir, cudaStream_t st) {
-  const size_t tot = (size_t)op.g.V * op.n;
-  dim3 grid(div_up(tot, 128), nrhs);
+  const int threads = ((9 * op.n + 31) / 32) * 32;
+  const size_t sm = (size_t)18 * op.n * sizeof(cplx<T>);
+  dim3 grid(op.g.V, nrhs);
+  count_launch();
   if (b)
-    k_coarse_apply<T, true><<<grid, 128, 0, st>>>(out, in, b, op.blk, op.g, op.n, rstride, sel, sel_mu, in_chir);
+    k_coarse_apply<T, true><<<grid, threads, sm, st>>>(out, in, b, op.blk, op.g, op.n, rstride, sel, sel_mu, in_chir);
   else
-    k_coarse_apply<T, false><<<grid, 128, 0, st>>>(out, in, b, op.blk, op.g, op.n, rstride, sel, sel_mu, in_chir);
+    k_coarse_apply<T, false><<<grid, threads, sm, st>>>(out, in, b, op.blk, op.g, op.n, rstride, sel, sel_mu, in_chir);
 }
 
 template <typename T>
@@ -282,7 +419,27 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
     cudaFuncSetAttribute(k_coarse_sap<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     done = true;
   }
+  count_launch();
   k_coarse_sap<T><<<dim3(nblocks, nrhs), threads, sm, st>>>(z, b, op.blk, op.g, op.n, rstride, blocks, k_mr);
+}
+
+template <typename T>
+void coarse_schur_odd(cplx<T>* t, const cplx<T>* x, const cplx<T>* b, const CoarseOp<T>& op, double a, double c,
+                      int nrhs, size_t rstride, cudaStream_t st) {
+  const int threads = ((8 * op.n + 31) / 32) * 32;
+  const size_t sm = (size_t)17 * op.n * sizeof(cplx<T>);
+  count_launch();
+  k_schur_odd<T><<<dim3(op.n_odd, nrhs), threads, sm, st>>>(t, x, b, op.blk, op.selfinv, op.odd_sites, op.g, op.n,
+                                                            rstride, a, c);
+}
+
+template <typename T>
+void coarse_schur_even(cplx<T>* y, const cplx<T>* x, const cplx<T>* t, const cplx<T>* b, const CoarseOp<T>& op,
+                       double a, double s, double c, int nrhs, size_t rstride, cudaStream_t st) {
+  const int threads = ((9 * op.n + 31) / 32) * 32;
+  const size_t sm = (size_t)18 * op.n * sizeof(cplx<T>);
+  count_launch();
+  k_schur_even<T><<<dim3(op.g.V, nrhs), threads, sm, st>>>(y, x, t, b, op.blk, op.g, op.n, rstride, a, s, c);
 }
 
 void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int n, int* err, cudaStream_t st) {
@@ -292,6 +449,7 @@ void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int
     cudaFuncSetAttribute(k_selfinv_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
+  count_launch();
   k_selfinv_build<<<V, 256, sm, st>>>(inv, blk, n, err);
 }
 
@@ -299,6 +457,7 @@ template <typename T>
 void coarse_selfinv_apply(cplx<T>* out, const cplx<T>* in, const CoarseOp<T>& op, int parity, int nrhs, size_t rstride,
                           cudaStream_t st) {
   const size_t tot = (size_t)op.g.V * op.n;
+  count_launch();
   k_selfinv_apply<T><<<dim3(div_up(tot, 128), nrhs), 128, 0, st>>>(out, in, op.selfinv, op.g, op.n, parity, rstride);
 }
 
@@ -306,28 +465,36 @@ template <typename T>
 void coarse_sub_parity(cplx<T>* y, const cplx<T>* a, const cplx<T>* b, const Geom& g, int n, int parity, int nrhs,
                        size_t rstride, cudaStream_t st) {
   const size_t tot = (size_t)g.V * n;
+  count_launch();
   k_sub_parity<T><<<dim3(div_up(tot, 128), nrhs), 128, 0, st>>>(y, a, b, g, n, parity, rstride);
 }
 
 template <typename T>
 void coarse_import(cplx<T>* dst, const cplx<double>* src, const Geom& g, int n, int nrhs, size_t rstride,
                    cudaStream_t st) {
+  count_launch();
   k_coarse_import<T><<<dim3(div_up((size_t)g.V * n, 128), nrhs), 128, 0, st>>>(dst, src, g, n, rstride);
 }
 
 template <typename T>
 void coarse_export(cplx<double>* dst, const cplx<T>* src, const Geom& g, int n, int nrhs, size_t rstride,
                    cudaStream_t st) {
+  count_launch();
   k_coarse_export<T><<<dim3(div_up((size_t)g.V * n, 128), nrhs), 128, 0, st>>>(dst, src, g, n, rstride);
 }
 
 void coarse_blocks_export(cplx<double>* dst, const cplx<double>* blk, const Geom& g, int n, cudaStream_t st) {
+  count_launch();
   k_blocks_export<<<div_up((size_t)g.V * 9 * n * n, 128), 128, 0, st>>>(dst, blk, g, n);
 }
 
 #define INST(T)                                                                                                   \
   template void coarse_apply<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const CoarseOp<T>&, int, size_t, int,     \
                                 int, int, cudaStream_t);                                                          \
+  template void coarse_schur_odd<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const CoarseOp<T>&, double, double, \
+                                    int, size_t, cudaStream_t);                                                   \
+  template void coarse_schur_even<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const cplx<T>*, const CoarseOp<T>&, \
+                                     double, double, double, int, size_t, cudaStream_t);                          \
   template void coarse_sap_sweep<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, const int*, int, int, size_t,   \
                                     int, cudaStream_t);                                                           \
   template void coarse_selfinv_apply<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, int, int, size_t,           \

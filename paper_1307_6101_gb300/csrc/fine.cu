@@ -340,6 +340,213 @@ __global__ void k_fine_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// SAP colour sweep with the SAP block staged in shared memory by TMA.
+//
+// One CTA per SAP block (or several small blocks).  A single thread arms an
+// mbarrier and issues 1-D bulk copies (cp.async.bulk, global -> shared) of the
+// block's 36 link components and 72 clover components, each a contiguous run
+// of vB words in the component-major layout.  After the barrier completes,
+// the k minimal-residual steps on D_B read links, clover and the residual only
+// from shared memory; the neighbour slots inside the block are computed once.
+// The CTA loops over the right-hand sides, so the operator is staged once per
+// batch.  Waits are bounded: on a timeout the kernel records an error code,
+// waits (bounded) for its copies and returns without touching z.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait (about a second of clock); false on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > 4000000000LL) return false;
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
+                                                      const cplx<T>* __restrict__ U, const T* __restrict__ clov, Geom g,
+                                                      int bc_t, size_t rstride, int nrhs, const int* __restrict__ blocks,
+                                                      int nblocks, int seg, int k_mr, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int vB = g.vB;
+  const int segs = blockDim.x / seg;
+  // per segment: links [36][vB] cplx, clover [72][vB] T, residual [12][vB] cplx
+  const size_t seg_bytes = (size_t)vB * (36 * sizeof(cplx<T>) + 72 * sizeof(T) + 12 * sizeof(cplx<T>));
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + (size_t)segs * seg_bytes);
+  T* scratch = reinterpret_cast<T*>(bar + 2);
+  const int s = threadIdx.x / seg;
+  const int loc = threadIdx.x - s * seg;
+  const int bi = blockIdx.x * segs + s;
+  const bool active = (bi < nblocks) && (loc < vB);
+  const int blk = (bi < nblocks) ? blocks[bi] : 0;
+  unsigned char* sb = smem_raw + (size_t)s * seg_bytes;
+  cplx<T>* Ls = reinterpret_cast<cplx<T>*>(sb);
+  T* Cs = reinterpret_cast<T*>(Ls + 36 * vB);
+  cplx<T>* Rs = reinterpret_cast<cplx<T>*>(Cs + 72 * vB);
+  const int V = g.V;
+  // stage the operator of every segment's block
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int nseg = 0;
+    for (int q = 0; q < segs; ++q) nseg += (blockIdx.x * segs + q < nblocks) ? 1 : 0;
+    const unsigned bytes = (unsigned)(nseg * vB * (36 * sizeof(cplx<T>) + 72 * sizeof(T)));
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, bytes);
+    __syncwarp();
+    for (int q = 0; q < nseg; ++q) {
+      const int bq = blocks[blockIdx.x * segs + q];
+      unsigned char* sq = smem_raw + (size_t)q * seg_bytes;
+      cplx<T>* Lq = reinterpret_cast<cplx<T>*>(sq);
+      T* Cq = reinterpret_cast<T*>(Lq + 36 * vB);
+      for (int cpy = threadIdx.x; cpy < 108; cpy += 32) {
+        if (cpy < 36)
+          bulk_g2s(Lq + (size_t)cpy * vB, U + (size_t)cpy * V + (size_t)bq * vB, (unsigned)(vB * sizeof(cplx<T>)), bar);
+        else
+          bulk_g2s(Cq + (size_t)(cpy - 36) * vB, clov + (size_t)(cpy - 36) * V + (size_t)bq * vB,
+                   (unsigned)(vB * sizeof(T)), bar);
+      }
+    }
+  }
+  // geometry of this thread's site (overlaps the copies)
+  int l[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+  int nslot[8];
+  T nsign[8];
+  const int x = blk * vB + loc;
+  if (active) {
+    geom_coords(g, x, c);
+    delin4(loc, g.B, l);
+    const int st[4] = {g.B[1] * g.B[2] * g.B[3], g.B[2] * g.B[3], g.B[3], 1};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int mu = k >> 1, dir = (k & 1) ? -1 : +1;
+      int nl = l[mu] + dir;
+      bool internal = nl >= 0 && nl < g.B[mu];
+      if (!internal && g.B[mu] == g.L[mu]) {
+        internal = true;
+        nl = (nl + g.B[mu]) % g.B[mu];
+      }
+      nslot[k] = internal ? loc + (nl - l[mu]) * st[mu] : -1;
+      nsign[k] = (mu == 0 && ((dir > 0 && c[0] == g.L[0] - 1) || (dir < 0 && c[0] == 0))) ? T(bc_t) : T(1);
+    }
+  }
+  const int ok = __syncthreads_and(mbar_wait_bounded(bar, 0) ? 1 : 0);
+  if (!ok) {   // uniform across the CTA
+    if (threadIdx.x == 0) atomicExch(err, 2);
+    mbar_wait_bounded(bar, 0);
+    return;
+  }
+  cplx<T> r[12], xs[12], p[12], nb[12], u[9];
+  for (int rh = 0; rh < nrhs; ++rh) {
+    cplx<T>* pz = z + (size_t)rh * rstride;
+    if (active) {
+      // rho = b - D z at x: hops to neighbours inside the block use the staged links
+      cplx<T> acc[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = czero<T>();
+#pragma unroll 1
+      for (int k = 0; k < 8; ++k) {
+        const int mu = k >> 1;
+        const bool fwd = (k & 1) == 0;
+        const int n = nslot[k] >= 0 ? blk * vB + nslot[k] : geom_neighbor(g, c, mu, fwd ? +1 : -1);
+        load_spinor(pz, V, n, nb, nsign[k], -1);
+        if (fwd) {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) u[q] = Ls[(size_t)(mu * 9 + q) * vB + loc];
+        } else if (nslot[k] >= 0) {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) u[q] = Ls[(size_t)(mu * 9 + q) * vB + nslot[k]];
+        } else {
+          load_link(U, V, mu, n, u);
+        }
+        hop_accumulate(mu, fwd, u, nb, acc);
+      }
+      load_spinor(pz, V, x, nb, T(1), -1);
+      clover_apply(Cs, vB, loc, nb, p);
+      const cplx<T>* pb = bsrc + (size_t)rh * rstride;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        r[k] = pb[(size_t)k * V + x] - (p[k] - T(0.5) * acc[k]);
+        xs[k] = czero<T>();
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) { r[k] = czero<T>(); xs[k] = czero<T>(); }
+    }
+#pragma unroll 1
+    for (int it = 0; it < k_mr; ++it) {
+      if (active) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) Rs[(size_t)k * vB + loc] = r[k];
+      }
+      __syncthreads();
+      T nre = T(0), nim = T(0), den = T(0);
+      if (active) {
+        cplx<T> acc[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = czero<T>();
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+          const int sl = nslot[k];
+          if (sl < 0) continue;
+          const int mu = k >> 1;
+          const bool fwd = (k & 1) == 0;
+#pragma unroll
+          for (int q = 0; q < 12; ++q) nb[q] = nsign[k] * Rs[(size_t)q * vB + sl];
+          const int ls = fwd ? loc : sl;
+#pragma unroll
+          for (int q = 0; q < 9; ++q) u[q] = Ls[(size_t)(mu * 9 + q) * vB + ls];
+          hop_accumulate(mu, fwd, u, nb, acc);
+        }
+        clover_apply(Cs, vB, loc, r, p);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          p[k] = p[k] - T(0.5) * acc[k];
+          const cplx<T> t = cdotc(p[k], r[k]);
+          nre += t.re;
+          nim += t.im;
+          den += cnorm2(p[k]);
+        }
+      }
+      seg_sum3(nre, nim, den, seg, scratch);
+      const cplx<T> alpha = den > T(0) ? cmk<T>(nre / den, nim / den) : czero<T>();
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cfma(xs[k], alpha, r[k]);
+        r[k] = r[k] - alpha * p[k];
+      }
+      __syncthreads();
+    }
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) pz[(size_t)k * V + x] = pz[(size_t)k * V + x] + xs[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Clover construction (FP64).  Q_mu_nu(x) = sum of the four plaquette leaves
 // at x in the mu-nu plane; A(x) = (m0 + 4) - (c_sw / 16) sum_{mu<nu}
 // (gamma_mu gamma_nu) (x) (Q_mu_nu - Q_mu_nu^+), which is the sum over ordered
@@ -492,6 +699,7 @@ template <typename T>
 void fine_dslash(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const FineOp<T>& op, int nrhs,
                  size_t rstride, int sel, int sel_mu, int in_chir, cudaStream_t st) {
   dim3 grid(div_up(op.g.V, 128), nrhs);
+  count_launch();
   if (b)
     k_fine_dslash<T, true><<<grid, 128, 0, st>>>(out, in, b, op.U, op.clov, op.g, op.bc_t, rstride, sel, sel_mu,
                                                   in_chir);
@@ -500,9 +708,37 @@ void fine_dslash(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const FineOp
                                                    sel_mu, in_chir);
 }
 
+// the staged kernel needs: FP32, the SAP block tiling the aggregate (inner tile),
+// 16-byte aligned component runs, and the staged block fitting in shared memory
+template <typename T>
+bool sap_tma_ok(const FineOp<T>& op) {
+  if (sizeof(T) != 4) return false;
+  for (int d = 0; d < 4; ++d)
+    if (op.g.I[d] != op.g.B[d]) return false;
+  if (op.g.vB % 4 || op.g.V % 4 || op.g.vB > 256) return false;
+  return true;
+}
+
 template <typename T>
 void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int* blocks, int nblocks, int nrhs,
                     size_t rstride, int k_mr, cudaStream_t st) {
+  if (sap_tma_ok(op) && op.err) {
+    int seg = 1;
+    while (seg < op.g.vB) seg <<= 1;
+    const int threads = 256;
+    const int segs = threads / seg;
+    const size_t seg_bytes = (size_t)op.g.vB * (36 * sizeof(cplx<T>) + 72 * sizeof(T) + 12 * sizeof(cplx<T>));
+    const size_t sm = segs * seg_bytes + 16 + (threads / 32) * 3 * sizeof(T) + 16;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_fine_sap_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      attr = true;
+    }
+    count_launch();
+    k_fine_sap_tma<T><<<div_up(nblocks, segs), threads, sm, st>>>(z, b, op.U, op.clov, op.g, op.bc_t, rstride, nrhs,
+                                                                   blocks, nblocks, seg, k_mr, op.err);
+    return;
+  }
   int seg = 1;
   while (seg < op.g.vB) seg <<= 1;
   const int threads = seg >= 256 ? seg : 256;
@@ -515,26 +751,31 @@ void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int
     done = true;
   }
   dim3 grid(div_up(nblocks, segs), nrhs);
+  count_launch();
   k_fine_sap<T><<<grid, threads, sm, st>>>(z, b, op.U, op.clov, op.g, op.bc_t, rstride, blocks, nblocks, seg, k_mr);
 }
 
 void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, double m0, double csw,
                   cudaStream_t st) {
+  count_launch();
   k_clover_build<<<div_up(g.V, 64), 64, 0, st>>>(clov, gauge_lex, g, m0, csw);
 }
 
 template <typename T>
 void links_import(cplx<T>* U, const cplx<double>* gauge_lex, const Geom& g, cudaStream_t st) {
+  count_launch();
   k_links_import<T><<<div_up(g.V, 128), 128, 0, st>>>(U, gauge_lex, g);
 }
 
 template <typename T>
 void fine_import(cplx<T>* dst, const cplx<double>* src, const Geom& g, int nrhs, size_t rstride, cudaStream_t st) {
+  count_launch();
   k_fine_import<T><<<dim3(div_up(g.V, 128), nrhs), 128, 0, st>>>(dst, src, g, rstride);
 }
 
 template <typename T>
 void fine_export(cplx<double>* dst, const cplx<T>* src, const Geom& g, int nrhs, size_t rstride, cudaStream_t st) {
+  count_launch();
   k_fine_export<T><<<dim3(div_up(g.V, 128), nrhs), 128, 0, st>>>(dst, src, g, rstride);
 }
 

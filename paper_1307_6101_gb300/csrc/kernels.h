@@ -5,12 +5,17 @@
 
 namespace dd {
 
+// number of kernels this library has launched (all streams, all handles)
+void count_launch(int k = 1);
+long long launch_count();
+
 template <typename T>
 struct FineOp {
   Geom g;
   int bc_t;
   cplx<T>* U;    // [4][9][V]
   T* clov;       // [2][36][V]  (m0 + 4) + clover, packed Hermitian
+  int* err;      // device error flag (bounded waits), may be null
 };
 
 template <typename T>
@@ -19,6 +24,8 @@ struct CoarseOp {
   int n;                // dof per site
   cplx<T>* blk;         // [V][9][n][n] column-major blocks
   cplx<T>* selfinv;     // [V][n][n] inverse of the self block (coarsest level), or null
+  const int* odd_sites; // indices of the odd sites (coarsest level), or null
+  int n_odd;
 };
 
 // ---- fine level -----------------------------------------------------------
@@ -46,6 +53,14 @@ template <typename T>
 void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks,
                       int nrhs, size_t rstride, int k_mr, cudaStream_t st);
 void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int n, int* err, cudaStream_t st);
+// t(A odd) = S^{-1}(a b + c D_oe x)     (even entries of t untouched)
+template <typename T>
+void coarse_schur_odd(cplx<T>* t, const cplx<T>* x, const cplx<T>* b, const CoarseOp<T>& op, double a, double c,
+                      int nrhs, size_t rstride, cudaStream_t st);
+// y(A even) = a b + s S x + c D_eo t;  y(A odd) = 0
+template <typename T>
+void coarse_schur_even(cplx<T>* y, const cplx<T>* x, const cplx<T>* t, const cplx<T>* b, const CoarseOp<T>& op,
+                       double a, double s, double c, int nrhs, size_t rstride, cudaStream_t st);
 template <typename T>
 void coarse_selfinv_apply(cplx<T>* out, const cplx<T>* in, const CoarseOp<T>& op, int parity, int nrhs,
                           size_t rstride, cudaStream_t st);
@@ -120,10 +135,24 @@ struct GmresState {
   int* done;            // [rhs] stopped in this cycle
   int* kr;              // [rhs] iterations taken in this cycle
   cplx<double>* y;      // [rhs][m]
+  int* conv;            // [rhs] converged (device-driven solver)
+  int* iters;           // [rhs] iterations over all cycles (device-driven solver)
+  double* bnorm;        // [rhs] ||b||
+  int* ctl;             // [4]: j, cycle, arrival counter
   int m;
 };
 void gmres_begin(const GmresState& s, int nrhs, cudaStream_t st);                // g = beta e1, inv = 1/beta
 void gmres_step(const GmresState& s, int j, int nrhs, cudaStream_t st);          // rotations, new g, done flags
 void gmres_solve_y(const GmresState& s, int nrhs, cudaStream_t st);              // y = R^{-1} g (k_r per rhs)
+
+// device-driven variant (graph capture with conditional WHILE nodes)
+void kry_start(const GmresState& s, int nrhs, double tol, cudaGraphConditionalHandle hcycle, cudaStream_t st);
+template <typename T>
+void kry_cycle_begin(const GmresState& s, cplx<T>* V0, cplx<T>* cur, const cplx<T>* r, size_t vlen, int nrhs,
+                     cudaGraphConditionalHandle hinner, cudaStream_t st);
+template <typename T>
+void kry_arnoldi(const GmresState& s, cplx<T>* V, size_t vstride, cplx<T>* Z, const cplx<T>* zcur, cplx<T>* w,
+                 cplx<T>* cur, size_t vlen, int nrhs, cudaGraphConditionalHandle hinner, cudaStream_t st);
+void kry_cycle_end(const GmresState& s, int nrhs, int max_cycles, cudaGraphConditionalHandle hcycle, cudaStream_t st);
 
 }  // namespace dd

@@ -44,8 +44,14 @@ struct Work {
   cplx<T>* Z = nullptr;    // preconditioned vectors [m][max_rhs][vlen] (flexible only)
   cplx<T>* r = nullptr;    // residual
   cplx<T>* t[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cplx<T>* cur = nullptr;  // current basis vector (device-driven solver)
+  cplx<T>* zc = nullptr;   // preconditioned current vector (device-driven solver)
+  cplx<T>* wv = nullptr;   // new Krylov direction (device-driven solver)
+  cplx<T>* gin = nullptr;  // fixed input of a captured K-cycle starting on this level
+  cplx<T>* gout = nullptr; // fixed output of a captured K-cycle starting on this level
   GmresState gs{};
   int m = 0;
+  long long host_steps = 0;   // Arnoldi steps taken by the host-driven solver
 };
 
 struct Level {
@@ -86,6 +92,22 @@ struct Scratch {
   size_t cap = 0;
 };
 
+// stream capture of a K-cycle into a CUDA graph; bodies of conditional nodes are
+// captured on deeper streams
+struct CaptureCtx {
+  bool active = false;
+  int depth = 0;
+  cudaStream_t s[12] = {};
+};
+
+struct GraphEntry {
+  int l0 = 0, tsize = 0, nrhs = 0, prof = 0;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> ev_kind;
+  std::vector<double> ev_bytes;
+  std::vector<cudaEvent_t> ev;   // pairs
+};
+
 }  // namespace
 
 struct ddamg_handle {
@@ -110,6 +132,20 @@ struct ddamg_handle {
   double* h_scal = nullptr;   // pinned
   int* h_kr = nullptr;        // pinned
   int max_batch = 0;
+  // per-kernel-class CUDA-event timing (ddamg_profile)
+  int prof = 0;   // bitmask of recorded kernel classes
+  std::vector<cudaEvent_t> ev[DDAMG_PROF_KINDS];
+  size_t ev_used[DDAMG_PROF_KINDS] = {};
+  double prof_bytes[DDAMG_PROF_KINDS] = {};
+  long long prof_count[DDAMG_PROF_KINDS] = {};
+  double prof_graph_ms[DDAMG_PROF_KINDS] = {};
+  // CUDA graphs of K-cycles (device-driven inner solves)
+  bool use_graphs = true;
+  CaptureCtx cap;
+  std::vector<GraphEntry*> graphs;
+  GraphEntry* capturing = nullptr;
+  cplx<double>* pin64 = nullptr;
+  cplx<double>* pout64 = nullptr;
 };
 
 namespace {
@@ -150,6 +186,51 @@ void sync(ddamg_handle* h) {
   CK(cudaStreamSynchronize(h->st));
 }
 
+// record an event pair around one launch of kind k when profiling; bytes = its algorithmic bytes
+struct Prof {
+  ddamg_handle* h;
+  int k;
+  size_t i;
+  bool on;
+  Prof(ddamg_handle* hh, int kind, double bytes) : h(hh), k(kind), i(0), on(((hh->prof >> kind) & 1) != 0) {
+    if (!on) return;
+    if (h->cap.active) {
+      // inside a captured graph: event nodes only at the top level (not inside conditional bodies)
+      if (h->cap.depth > 0 || !h->capturing) {
+        on = false;
+        return;
+      }
+      GraphEntry* e = h->capturing;
+      cudaEvent_t a, b;
+      CK(cudaEventCreate(&a));
+      CK(cudaEventCreate(&b));
+      i = e->ev.size();
+      e->ev.push_back(a);
+      e->ev.push_back(b);
+      e->ev_kind.push_back(k);
+      e->ev_bytes.push_back(bytes);
+      CK(cudaEventRecordWithFlags(a, h->st, cudaEventRecordExternal));   // an event node, not a capture join
+      return;
+    }
+    auto& v = h->ev[k];
+    i = h->ev_used[k];
+    while (v.size() < i + 2) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      v.push_back(e);
+    }
+    h->ev_used[k] = i + 2;
+    h->prof_bytes[k] += bytes;
+    h->prof_count[k] += 1;
+    CK(cudaEventRecord(v[i], h->st));
+  }
+  ~Prof() {
+    if (!on) return;
+    if (h->cap.active) cudaEventRecordWithFlags(h->capturing->ev[i + 1], h->st, cudaEventRecordExternal);
+    else cudaEventRecord(h->ev[k][i + 1], h->st);
+  }
+};
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -172,8 +253,30 @@ const void* dev_in(ddamg_handle* h, const void* p, size_t bytes, int slot) {
 template <typename T>
 void apply_D(ddamg_handle* h, Level& L, cplx<T>* out, const cplx<T>* in, const cplx<T>* b, int nrhs,
              int sel = SEL_FULL, int mu = 0, int chir = -1) {
-  if (L.fine) fine_dslash<T>(out, in, b, fop<T>(L), nrhs, L.vlen, sel, mu, chir, h->st);
-  else coarse_apply<T>(out, in, b, cop<T>(L), nrhs, L.vlen, sel, mu, chir, h->st);
+  const double cs = 2.0 * sizeof(T);
+  const double vec = (double)L.vlen * cs * nrhs * (b ? 3 : 2);
+  if (L.fine) {
+    Prof pr(h, DDAMG_PROF_FINE_DSLASH, vec + (double)L.g.V * (36 * cs + 72 * sizeof(T)));
+    fine_dslash<T>(out, in, b, fop<T>(L), nrhs, L.vlen, sel, mu, chir, h->st);
+  } else {
+    Prof pr(h, DDAMG_PROF_COARSE_APPLY, vec + (double)L.g.V * 9 * L.n * L.n * cs);
+    coarse_apply<T>(out, in, b, cop<T>(L), nrhs, L.vlen, sel, mu, chir, h->st);
+  }
+}
+
+// algorithmic bytes of one SAP colour sweep: per site of the colour b, z in, z out
+// and the operator once; per block the neighbour values across its faces (and
+// on the fine level the links of the backward hops entering the block)
+template <typename T>
+double sap_bytes(const Level& L, int c, int nrhs) {
+  const double cs = 2.0 * sizeof(T);
+  const double nsite = (double)L.nblocks[c] * L.g.vB;
+  double faces = 0;
+  for (int d = 0; d < 4; ++d) faces += (double)L.g.vB / L.g.B[d];
+  if (L.fine)
+    return nsite * (nrhs * 36 * cs + 36 * cs + 72 * sizeof(T)) +
+           L.nblocks[c] * (nrhs * 2 * faces * 12 * cs + faces * 9 * cs);
+  return nsite * (nrhs * 3.0 * L.n * cs + 9.0 * L.n * L.n * cs) + L.nblocks[c] * nrhs * 2 * faces * L.n * cs;
 }
 
 // iterations x { z <- z + M_SAP (b - D z) }: each SAP application is a red then a black sweep
@@ -182,6 +285,7 @@ void sap(ddamg_handle* h, Level& L, cplx<T>* z, const cplx<T>* b, int nrhs, int 
   for (int it = 0; it < iterations; ++it)
     for (int c = 0; c < 2; ++c) {
       if (L.nblocks[c] == 0) continue;
+      Prof pr(h, L.fine ? DDAMG_PROF_FINE_SAP : DDAMG_PROF_COARSE_SAP, sap_bytes<T>(L, c, nrhs));
       if (L.fine)
         fine_sap_sweep<T>(z, b, fop<T>(L), L.blocks[c], L.nblocks[c], nrhs, L.vlen, h->p.mr_steps, h->st);
       else
@@ -193,6 +297,8 @@ template <typename T>
 void restrict_lv(ddamg_handle* h, int l, cplx<T>* out, const cplx<T>* in, int nrhs) {
   Level& F = h->lv[l];
   Level& C = h->lv[l + 1];
+  const double cs = 2.0 * sizeof(T);
+  Prof pr(h, DDAMG_PROF_TRANSFER, (double)F.vlen * cs * (nrhs + F.N) + (double)C.vlen * cs * nrhs);
   restrict_op<T>(out, in, Pptr<T>(F), F.g, C.g, F.fine, F.n, F.N, nrhs, F.vlen, C.vlen, C.n, h->st);
 }
 
@@ -200,6 +306,8 @@ template <typename T>
 void prolong_lv(ddamg_handle* h, int l, cplx<T>* out, const cplx<T>* in, int nrhs, bool acc) {
   Level& F = h->lv[l];
   Level& C = h->lv[l + 1];
+  const double cs = 2.0 * sizeof(T);
+  Prof pr(h, DDAMG_PROF_TRANSFER, (double)F.vlen * cs * (nrhs * (acc ? 2 : 1) + F.N) + (double)C.vlen * cs * nrhs);
   prolong_op<T>(out, in, Pptr<T>(F), F.g, C.g, F.fine, F.n, F.N, nrhs, F.vlen, C.vlen, acc, h->st);
 }
 
@@ -213,8 +321,8 @@ struct KrylovResult {
 };
 
 template <typename T, class AOp, class MOp>
-void krylov(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>* b, int nrhs, int m, double tol,
-            int max_cycles, bool final_residual, bool flexible, AOp A, MOp M, KrylovResult* res) {
+void krylov_host(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>* b, int nrhs, int m, double tol,
+                 int max_cycles, bool final_residual, bool flexible, AOp A, MOp M, KrylovResult* res) {
   cudaStream_t st = h->st;
   const size_t rs = vlen;
   const size_t vs = (size_t)h->max_batch * vlen;
@@ -248,14 +356,18 @@ void krylov(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>
       cplx<T>* w = ws.V + (size_t)(j + 1) * vs;
       if (flexible) M(zj, vj);
       A(w, zj, nullptr);
-      blas_multidot<T>(s.h1, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
-      blas_multiaxpy<T>(w, ws.V, vs, j + 1, s.h1, m + 1, -1.0, vlen, nrhs, rs, st);
-      blas_multidot<T>(s.h2, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
-      blas_multiaxpy<T>(w, ws.V, vs, j + 1, s.h2, m + 1, -1.0, vlen, nrhs, rs, st);
-      blas_norm2<T>(s.wnorm, w, vlen, nrhs, rs, st);
-      gmres_step(s, j, nrhs, st);
-      blas_scale_to<T>(w, w, s.inv, vlen, nrhs, rs, st);
+      {
+        Prof pr(h, DDAMG_PROF_OUTER_ORTHO, (double)(2 * (j + 1) + 3) * 2 * vlen * nrhs * 2.0 * sizeof(T));
+        blas_multidot<T>(s.h1, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
+        blas_multiaxpy<T>(w, ws.V, vs, j + 1, s.h1, m + 1, -1.0, vlen, nrhs, rs, st);
+        blas_multidot<T>(s.h2, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
+        blas_multiaxpy<T>(w, ws.V, vs, j + 1, s.h2, m + 1, -1.0, vlen, nrhs, rs, st);
+        blas_norm2<T>(s.wnorm, w, vlen, nrhs, rs, st);
+        gmres_step(s, j, nrhs, st);
+        blas_scale_to<T>(w, w, s.inv, vlen, nrhs, rs, st);
+      }
       kmax = j + 1;
+      ws.host_steps += 1;
       CK(cudaMemcpyAsync(h->h_done, s.done, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
       sync(h);
       bool all = true;
@@ -295,36 +407,115 @@ void krylov(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>
 }
 
 // ---------------------------------------------------------------------------
+// Device-driven (F)GMRES, emitted into a stream capture: the restart cycles and
+// the Arnoldi steps are conditional WHILE nodes whose conditions are set by the
+// kernels (k_kry_start / k_cycle_begin / k_arnoldi / k_cycle_end), so the
+// solve needs no host round trip.  Same arithmetic and stopping rules as
+// krylov_host.
+cudaGraphConditionalHandle create_cond(ddamg_handle* h) {
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamGetCaptureInfo(h->st, &status, nullptr, &g, nullptr, nullptr, nullptr));
+  if (status != cudaStreamCaptureStatusActive || !g) fail(DDAMG_ERR_CUDA, "conditional node outside a capture");
+  cudaGraphConditionalHandle hc;
+  CK(cudaGraphConditionalHandleCreate(&hc, g, 0, 0));
+  return hc;
+}
+
+template <class F>
+void emit_while(ddamg_handle* h, cudaGraphConditionalHandle hc, F body) {
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(h->st, &status, nullptr, &g, &deps, &ed, &nd));
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = hc;
+  prm.conditional.type = cudaGraphCondTypeWhile;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, ed, nd, &prm));
+  CK(cudaStreamUpdateCaptureDependencies(h->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t bodyg = prm.conditional.phGraph_out[0];
+  const int d = h->cap.depth + 1;
+  if (d >= 12) fail(DDAMG_ERR_ARG, "conditional nesting too deep");
+  cudaStream_t saved = h->st;
+  h->cap.depth = d;
+  h->st = h->cap.s[d];
+  CK(cudaStreamBeginCaptureToGraph(h->st, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  body();
+  cudaGraph_t out = nullptr;
+  CK(cudaStreamEndCapture(h->st, &out));
+  h->st = saved;
+  h->cap.depth = d - 1;
+}
+
+template <typename T, class AOp, class MOp>
+void krylov_dev(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>* b, int nrhs, int m, double tol,
+                int max_cycles, bool flexible, AOp A, MOp M) {
+  if (m > ws.m) fail(DDAMG_ERR_ARG, "Krylov length exceeds the workspace");
+  const size_t vs = (size_t)h->max_batch * vlen;
+  GmresState s = ws.gs;
+  s.m = m;
+  blas_zero<T>(x, vlen, nrhs, vlen, h->st);
+  blas_convert<T, T>(ws.r, b, vlen, nrhs, vlen, vlen, h->st);
+  blas_norm2<T>(s.beta, b, vlen, nrhs, vlen, h->st);
+  const cudaGraphConditionalHandle hcycle = create_cond(h);
+  kry_start(s, nrhs, tol, hcycle, h->st);
+  emit_while(h, hcycle, [&] {
+    const cudaGraphConditionalHandle hinner = create_cond(h);
+    kry_cycle_begin<T>(s, ws.V, ws.cur, ws.r, vlen, nrhs, hinner, h->st);
+    emit_while(h, hinner, [&] {
+      if (flexible) {
+        M(ws.zc, ws.cur);
+        A(ws.wv, ws.zc, nullptr);
+      } else {
+        A(ws.wv, ws.cur, nullptr);
+      }
+      kry_arnoldi<T>(s, ws.V, vs, flexible ? ws.Z : nullptr, ws.zc, ws.wv, ws.cur, vlen, nrhs, hinner, h->st);
+    });
+    gmres_solve_y(s, nrhs, h->st);
+    blas_multiaxpy<T>(x, flexible ? ws.Z : ws.V, vs, m, s.y, m, 1.0, vlen, nrhs, vlen, h->st);
+    A(ws.r, x, b);
+    blas_norm2<T>(s.beta, ws.r, vlen, nrhs, vlen, h->st);
+    kry_cycle_end(s, nrhs, max_cycles, hcycle, h->st);
+  });
+}
+
+// host-driven while eager, device-driven while capturing a graph
+template <typename T, class AOp, class MOp>
+void krylov(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>* b, int nrhs, int m, double tol,
+            int max_cycles, bool final_residual, bool flexible, AOp A, MOp M, KrylovResult* res) {
+  if (h->cap.active) krylov_dev<T>(h, ws, vlen, x, b, nrhs, m, tol, max_cycles, flexible, A, M);
+  else krylov_host<T>(h, ws, vlen, x, b, nrhs, m, tol, max_cycles, final_residual, flexible, A, M, res);
+}
+
+// ---------------------------------------------------------------------------
 // coarsest level: odd-even preconditioned GMRES (Sec. 3)
 template <typename T>
 void coarse_solve(ddamg_handle* h, cplx<T>* x, const cplx<T>* b, int nrhs) {
   Level& C = h->lv[h->L - 1];
   Work<T>& w = work<T>(C);
   CoarseOp<T>& op = cop<T>(C);
-  cudaStream_t st = h->st;
   const size_t rs = C.vlen;
-  cplx<T>*t1 = w.t[0], *t2 = w.t[1], *t3 = w.t[2], *bh = w.t[3], *xe = w.t[4];
+  cplx<T>*t1 = w.t[0], *bh = w.t[3], *xe = w.t[4];
   // bhat_e = b_e - D_eo D_oo^{-1} b_o
-  coarse_selfinv_apply<T>(t1, b, op, 1, nrhs, rs, st);
-  apply_D<T>(h, C, t2, t1, nullptr, nrhs);
-  coarse_sub_parity<T>(bh, b, t2, C.g, C.n, 0, nrhs, rs, st);
+  coarse_schur_odd<T>(t1, nullptr, b, op, 1.0, 0.0, nrhs, rs, h->st);
+  coarse_schur_even<T>(bh, nullptr, t1, b, op, 1.0, 0.0, -1.0, nrhs, rs, h->st);
+  // Dhat x_e = D_ee x_e - D_eo D_oo^{-1} D_oe x_e (residual form: b - Dhat x_e)
   auto schur = [&](cplx<T>* out, const cplx<T>* in, const cplx<T>* bb) {
-    apply_D<T>(h, C, t1, in, nullptr, nrhs);                  // t1_e = D_ee in, t1_o = D_oe in
-    coarse_selfinv_apply<T>(t2, t1, op, 1, nrhs, rs, st);     // t2 = D_oo^{-1} t1_o
-    apply_D<T>(h, C, t3, t2, nullptr, nrhs);                  // t3_e = D_eo t2
-    coarse_sub_parity<T>(t1, t1, t3, C.g, C.n, 0, nrhs, rs, st);
-    if (bb) coarse_sub_parity<T>(out, bb, t1, C.g, C.n, 0, nrhs, rs, st);
-    else blas_convert<T, T>(out, t1, rs, nrhs, rs, rs, st);
+    coarse_schur_odd<T>(t1, in, nullptr, op, 0.0, 1.0, nrhs, rs, h->st);
+    if (bb) coarse_schur_even<T>(out, in, t1, bb, op, 1.0, -1.0, 1.0, nrhs, rs, h->st);
+    else coarse_schur_even<T>(out, in, t1, nullptr, op, 0.0, 1.0, -1.0, nrhs, rs, h->st);
   };
   auto none = [](cplx<T>*, const cplx<T>*) {};
   krylov<T>(h, w, C.vlen, xe, bh, nrhs, h->p.coarse_restart, h->p.coarse_tol, h->p.coarse_cycles, true, false, schur,
             none, nullptr);
-  // z_o = D_oo^{-1} (b_o - D_oe x_e);  z = x_e + z_o
-  apply_D<T>(h, C, t1, xe, nullptr, nrhs);
-  coarse_sub_parity<T>(t2, b, t1, C.g, C.n, 1, nrhs, rs, st);
-  coarse_selfinv_apply<T>(t3, t2, op, 1, nrhs, rs, st);
-  coarse_sub_parity<T>(x, xe, nullptr, C.g, C.n, 0, nrhs, rs, st);
-  blas_axpy<T>(x, t3, 1.0, rs, nrhs, rs, st);
+  // z_e = x_e;  z_o = D_oo^{-1} (b_o - D_oe x_e)
+  blas_convert<T, T>(x, xe, rs, nrhs, rs, rs, h->st);
+  coarse_schur_odd<T>(x, xe, b, op, 1.0, -1.0, nrhs, rs, h->st);
 }
 
 // one K-cycle from level l (Alg. 2): z = K(l, b)
@@ -333,8 +524,7 @@ void kcycle(ddamg_handle* h, int l, cplx<T>* z, const cplx<T>* b, int nrhs) {
   Level& F = h->lv[l];
   Level& C = h->lv[l + 1];
   Work<T>& wc = work<T>(C);
-  cudaStream_t st = h->st;
-  blas_zero<T>(z, F.vlen, nrhs, F.vlen, st);
+  blas_zero<T>(z, F.vlen, nrhs, F.vlen, h->st);
   if (h->p.mu > 0) {
     sap<T>(h, F, z, b, nrhs, h->p.mu);
     cplx<T>* r = work<T>(F).r;
@@ -353,6 +543,93 @@ void kcycle(ddamg_handle* h, int l, cplx<T>* z, const cplx<T>* b, int nrhs) {
   }
   prolong_lv<T>(h, l, z, wc.xs, nrhs, h->p.mu > 0);
   sap<T>(h, F, z, b, nrhs, h->p.nu);
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs of whole K-cycles, one per (start level, precision, batch size,
+// profiling mask); captured on first use, replayed afterwards.  The graph reads
+// its right-hand side from Work.gin of the start level and writes Work.gout.
+template <typename T>
+GraphEntry* get_graph(ddamg_handle* h, int l0, int nrhs) {
+  for (GraphEntry* e : h->graphs)
+    if (e->l0 == l0 && e->tsize == (int)sizeof(T) && e->nrhs == nrhs && e->prof == h->prof) return e;
+  GraphEntry* e = new GraphEntry();
+  e->l0 = l0;
+  e->tsize = (int)sizeof(T);
+  e->nrhs = nrhs;
+  e->prof = h->prof;
+  Work<T>& w = work<T>(h->lv[l0]);
+  cudaStream_t saved = h->st;
+  sync(h);
+  h->cap.active = true;
+  h->cap.depth = 0;
+  h->capturing = e;
+  h->st = h->cap.s[0];
+  cudaGraph_t graph = nullptr;
+  try {
+    CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
+    kcycle<T>(h, l0, w.gout, w.gin, nrhs);
+    CK(cudaStreamEndCapture(h->st, &graph));
+  } catch (...) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(h->cap.s[0], &junk);
+    if (junk) cudaGraphDestroy(junk);
+    cudaGetLastError();
+    h->st = saved;
+    h->cap.active = false;
+    h->capturing = nullptr;
+    for (cudaEvent_t ev : e->ev) cudaEventDestroy(ev);
+    delete e;
+    throw;
+  }
+  h->st = saved;
+  h->cap.active = false;
+  h->cap.depth = 0;
+  h->capturing = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&e->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    for (cudaEvent_t ev : e->ev) cudaEventDestroy(ev);
+    delete e;
+    fail(DDAMG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+  }
+  h->graphs.push_back(e);
+  return e;
+}
+
+// z = K-cycle(l0, b) through the captured graph (or eagerly when graphs are off)
+template <typename T>
+void kcycle_run(ddamg_handle* h, int l0, cplx<T>* z, const cplx<T>* b, int nrhs) {
+  if (!h->use_graphs) {
+    kcycle<T>(h, l0, z, b, nrhs);
+    return;
+  }
+  GraphEntry* e = get_graph<T>(h, l0, nrhs);
+  Work<T>& w = work<T>(h->lv[l0]);
+  const size_t vl = h->lv[l0].vlen;
+  blas_convert<T, T>(w.gin, b, vl, nrhs, vl, vl, h->st);
+  count_launch(1);
+  CK(cudaGraphLaunch(e->exec, h->st));
+  blas_convert<T, T>(z, w.gout, vl, nrhs, vl, vl, h->st);
+  if (!e->ev.empty()) {
+    sync(h);
+    for (size_t q = 0; q < e->ev_kind.size(); ++q) {
+      float t = 0;
+      CK(cudaEventElapsedTime(&t, e->ev[2 * q], e->ev[2 * q + 1]));
+      h->prof_graph_ms[e->ev_kind[q]] += t;
+      h->prof_count[e->ev_kind[q]] += 1;
+      h->prof_bytes[e->ev_kind[q]] += e->ev_bytes[q];
+    }
+  }
+}
+
+void free_graphs(ddamg_handle* h) {
+  for (GraphEntry* e : h->graphs) {
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    for (cudaEvent_t ev : e->ev) cudaEventDestroy(ev);
+    delete e;
+  }
+  h->graphs.clear();
 }
 
 // ---------------------------------------------------------------------------
@@ -421,6 +698,11 @@ void alloc_work(ddamg_handle* h, Level& L, Work<T>& w, int m, bool flexible, int
   w.xs = dalloc<cplx<T>>(h, vl);
   w.r = dalloc<cplx<T>>(h, vl);
   for (int k = 0; k < 5; ++k) w.t[k] = dalloc<cplx<T>>(h, vl);
+  w.cur = dalloc<cplx<T>>(h, vl);
+  w.zc = dalloc<cplx<T>>(h, vl);
+  w.wv = dalloc<cplx<T>>(h, vl);
+  w.gin = dalloc<cplx<T>>(h, vl);
+  w.gout = dalloc<cplx<T>>(h, vl);
   if (m > 0) {
     w.V = dalloc<cplx<T>>(h, vl * (m + 1));
     if (flexible) w.Z = dalloc<cplx<T>>(h, vl * m);
@@ -442,6 +724,11 @@ void alloc_work(ddamg_handle* h, Level& L, Work<T>& w, int m, bool flexible, int
   s.est = dalloc<double>(h, batch);
   s.done = dalloc<int>(h, batch);
   s.kr = dalloc<int>(h, batch);
+  s.conv = dalloc<int>(h, batch);
+  s.iters = dalloc<int>(h, batch);
+  s.bnorm = dalloc<double>(h, batch);
+  s.ctl = dalloc<int>(h, 4);
+  CK(cudaMemset(s.ctl, 0, sizeof(int) * 4));
 }
 
 void gamma_products(double* out /* [6][4][4][2] */) {
@@ -583,7 +870,7 @@ void iterative_setup_phase(ddamg_handle* h, int l, int i) {
   double* nrm = static_cast<double*>(scratch(h, 7, sizeof(double) * 8));
   for (int j = 0; j < L.N; ++j) {
     blas_convert<T, double>(bT, L.tv64 + (size_t)j * L.vlen, L.vlen, 1, 0, 0, st);
-    kcycle<T>(h, l, zT, bT, 1);
+    kcycle_run<T>(h, l, zT, bT, 1);
     for (int k = l; k < h->L - 1; ++k) {
       Level& K = h->lv[k];
       if (j >= K.N) continue;
@@ -647,6 +934,16 @@ void allocate_hierarchy(ddamg_handle* h) {
       if (L.coarsest) {
         L.c64.selfinv = dalloc<cplx<double>>(h, (size_t)L.g.V * L.n * L.n);
         L.c32.selfinv = dalloc<cplx<float>>(h, (size_t)L.g.V * L.n * L.n);
+        std::vector<int> odd;
+        for (int x = 0; x < L.g.V; ++x) {
+          int c[4];
+          geom_coords(L.g, x, c);
+          if (geom_parity(c) == 1) odd.push_back(x);
+        }
+        int* d = dalloc<int>(h, odd.size());
+        CK(cudaMemcpy(d, odd.data(), sizeof(int) * odd.size(), cudaMemcpyHostToDevice));
+        L.c64.odd_sites = L.c32.odd_sites = d;
+        L.c64.n_odd = L.c32.n_odd = (int)odd.size();
       }
     }
     if (!L.coarsest) {
@@ -689,14 +986,16 @@ void precond_outer(ddamg_handle* h, cplx<double>* z, const cplx<double>* v, int 
 
 template <>
 void precond_outer<double>(ddamg_handle* h, cplx<double>* z, const cplx<double>* v, int nrhs) {
-  kcycle<double>(h, 0, z, v, nrhs);
+  Prof pr(h, DDAMG_PROF_PRECOND, 0.0);
+  kcycle_run<double>(h, 0, z, v, nrhs);
 }
 
 template <>
 void precond_outer<float>(ddamg_handle* h, cplx<double>* z, const cplx<double>* v, int nrhs) {
   const size_t vl = h->lv[0].vlen;
+  Prof pr(h, DDAMG_PROF_PRECOND, 0.0);
   blas_convert<float, double>(h->pin32, v, vl, nrhs, vl, vl, h->st);
-  kcycle<float>(h, 0, h->pout32, h->pin32, nrhs);
+  kcycle_run<float>(h, 0, h->pout32, h->pin32, nrhs);
   blas_convert<double, float>(z, h->pout32, vl, nrhs, vl, vl, h->st);
 }
 
@@ -804,6 +1103,7 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
     h->max_batch = params->max_rhs;
     CK(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
     h->st = h->own;
+    for (int d = 0; d < 12; ++d) CK(cudaStreamCreateWithFlags(&h->cap.s[d], cudaStreamNonBlocking));
     CK(cudaMallocHost(&h->h_done, sizeof(int) * 64));
     CK(cudaMallocHost(&h->h_kr, sizeof(int) * 64));
     CK(cudaMallocHost(&h->h_scal, sizeof(double) * 64));
@@ -811,6 +1111,7 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
     allocate_hierarchy(h);
     h->d_err = dalloc<int>(h, 1);
     CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
+    h->lv[0].f64.err = h->lv[0].f32.err = h->d_err;
     double gg[6 * 16 * 2];
     gamma_products(gg);
     set_gamma_products(gg);
@@ -840,12 +1141,17 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
 void ddamg_free(ddamg_handle* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
+  free_graphs(h);
+  for (int d = 0; d < 12; ++d)
+    if (h->cap.s[d]) cudaStreamDestroy(h->cap.s[d]);
   for (void* p : h->allocs) cudaFree(p);
   for (auto& s : h->scr)
     if (s.p) cudaFree(s.p);
   if (h->h_done) cudaFreeHost(h->h_done);
   if (h->h_kr) cudaFreeHost(h->h_kr);
   if (h->h_scal) cudaFreeHost(h->h_scal);
+  for (auto& v : h->ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
 }
@@ -886,6 +1192,15 @@ int ddamg_solve(ddamg_handle* h, const double* rhs, double* x, int n, double tol
       cplx<double>* dx = xdev ? reinterpret_cast<cplx<double>*>(x + (size_t)s0 * F.vlen * 2)
                               : static_cast<cplx<double>*>(scratch(h, 1, fbytes * nb));
       fine_export<double>(dx, h->ox, F.g, nb, F.vlen, h->st);
+      {
+        int e = 0;
+        CK(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        sync(h);
+        if (e == 2) {
+          CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
+          fail(DDAMG_ERR_CUDA, "a shared-memory staging wait of the SAP kernel timed out");
+        }
+      }
       if (!xdev) CK(cudaMemcpyAsync(x + (size_t)s0 * F.vlen * 2, dx, fbytes * nb, cudaMemcpyDeviceToHost, h->st));
       sync(h);
       for (int r = 0; r < nb; ++r) {
@@ -905,6 +1220,66 @@ int ddamg_solve(ddamg_handle* h, const double* rhs, double* x, int n, double tol
     return DDAMG_ERR_NOCONV;
   }
   return DDAMG_OK;
+}
+
+int ddamg_set_option(ddamg_handle* h, int option, int value) {
+  if (!h) return DDAMG_ERR_ARG;
+  return guard([&] {
+    sync(h);
+    if (option == DDAMG_OPT_GRAPHS) h->use_graphs = value != 0;
+    else fail(DDAMG_ERR_ARG, "unknown option");
+  });
+}
+
+int ddamg_profile(ddamg_handle* h, int enable) {
+  if (!h) return DDAMG_ERR_ARG;
+  return guard([&] {
+    sync(h);
+    if (enable) {
+      for (int k = 0; k < DDAMG_PROF_KINDS; ++k) {
+        h->ev_used[k] = 0;
+        h->prof_bytes[k] = 0;
+        h->prof_count[k] = 0;
+        h->prof_graph_ms[k] = 0;
+      }
+    }
+    h->prof = enable;
+  });
+}
+
+int ddamg_profile_read(ddamg_handle* h, int kind, double* total_ms, long long* launches, double* algo_bytes) {
+  if (!h || kind < 0 || kind >= DDAMG_PROF_KINDS) return DDAMG_ERR_ARG;
+  return guard([&] {
+    sync(h);
+    double ms = h->prof_graph_ms[kind];
+    for (size_t i = 0; i + 1 < h->ev_used[kind]; i += 2) {
+      float t = 0;
+      CK(cudaEventElapsedTime(&t, h->ev[kind][i], h->ev[kind][i + 1]));
+      ms += t;
+    }
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = h->prof_count[kind];
+    if (algo_bytes) *algo_bytes = h->prof_bytes[kind];
+  });
+}
+
+long long ddamg_launch_count(void) { return launch_count(); }
+
+int ddamg_krylov_steps(ddamg_handle* h, int level, int precision, long long* steps) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (!steps) fail(DDAMG_ERR_ARG, "null output");
+    int dev = 0;
+    long long host = 0;
+    if (precision == 1) {
+      CK(cudaMemcpy(&dev, L.w32.gs.ctl + 3, sizeof(int), cudaMemcpyDeviceToHost));
+      host = L.w32.host_steps;
+    } else {
+      CK(cudaMemcpy(&dev, L.w64.gs.ctl + 3, sizeof(int), cudaMemcpyDeviceToHost));
+      host = L.w64.host_steps;
+    }
+    *steps = host + dev + (level == 0 ? h->outer.host_steps : 0);
+  });
 }
 
 int ddamg_level_info(ddamg_handle* h, int level, int dims[4], int* ndof, int* ntv) {
@@ -975,10 +1350,10 @@ int ddamg_kcycle(ddamg_handle* h, int level, int precision, const double* b, dou
     if (L.coarsest || n < 1 || n > h->max_batch) fail(DDAMG_ERR_ARG, "K-cycle needs a non-coarsest level, n <= max_rhs");
     if (precision == 1)
       hook<float>(h, level, b, z, n, false, level,
-                  [&](cplx<float>* o, cplx<float>* i) { kcycle<float>(h, level, o, i, n); });
+                  [&](cplx<float>* o, cplx<float>* i) { kcycle_run<float>(h, level, o, i, n); });
     else
       hook<double>(h, level, b, z, n, false, level,
-                   [&](cplx<double>* o, cplx<double>* i) { kcycle<double>(h, level, o, i, n); });
+                   [&](cplx<double>* o, cplx<double>* i) { kcycle_run<double>(h, level, o, i, n); });
   });
 }
 

@@ -168,6 +168,7 @@ void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& 
                  int N, int nrhs, size_t in_rstride, size_t out_rstride, size_t out_site_stride, cudaStream_t st) {
   const size_t pstride = (size_t)gf.V * n;
   const int threads = gf.vA >= 256 ? 256 : (gf.vA >= 128 ? 128 : (gf.vA >= 64 ? 64 : 32));
+  count_launch();
   k_restrict<T><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, P, gf, gc, fine, n, N, in_rstride, pstride,
                                                           out_rstride, out_site_stride);
 }
@@ -177,12 +178,14 @@ void prolong_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& g
                 int N, int nrhs, size_t out_rstride, size_t in_rstride, bool accumulate, cudaStream_t st) {
   const size_t pstride = (size_t)gf.V * n;
   const size_t tot = (size_t)gf.V * n;
+  count_launch();
   k_prolong<T><<<dim3(div_up(tot, 128), nrhs), 128, 0, st>>>(out, in, P, gf, gc, fine, n, N, out_rstride, in_rstride,
                                                               pstride, accumulate);
 }
 
 void orthonormalise(cplx<double>* P, const Geom& g, bool fine, int n, int N, int* err, cudaStream_t st) {
   const size_t pstride = (size_t)g.V * n;
+  count_launch();
   k_orthonormalise<<<dim3(g.nAgg, 2), 256, 0, st>>>(P, g, fine, n, N, pstride, err);
 }
 

@@ -172,9 +172,12 @@ def test_coarsest_even_odd_gmres(dd, spec):
         assert np.linalg.norm(rh) <= 5e-2 * np.linalg.norm(eo.schur_rhs(b[i])) * 1.01
 
 
+@pytest.mark.parametrize("graphs", [1, 0])
 @pytest.mark.parametrize("spec", [SMALL2, THREE])
-def test_kcycle(dd, spec):
+def test_kcycle(dd, spec, graphs):
+    """One K-cycle (Alg. 2) vs the oracle: captured CUDA graph with device-driven inner solves, and eager."""
     c, h, o = _pair(spec)
+    dd.ddamg_set_option(h, dd.DDAMG_OPT_GRAPHS, graphs)
     b = _fields(1, c.dims, 12, 70)
     z = np.zeros_like(b)
     dd.ddamg_kcycle(h, 0, 0, b, z, 1)
@@ -273,10 +276,12 @@ def test_solve_three_level_and_edge_rhs(dd):
         assert st[i]["converged"] and _check_solution(op, b[i], x[i]) <= 1e-10
 
 
-def test_batch_invariance(dd):
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_batch_invariance(dd, graphs):
     """Each right-hand side gives the same bits alone and inside a batch (fixed reduction partitions)."""
     c = Case(**THREE, n_inv=1, eta_passes=2, max_rhs=4, m0=-0.3)
     h = c.gpu(1)
+    dd.ddamg_set_option(h, dd.DDAMG_OPT_GRAPHS, graphs)
     b = np.ascontiguousarray(synth.random_spinors(4, c.dims, 3))
     xb = np.zeros_like(b)
     dd.ddamg_solve(h, b, xb, 4, 1e-10)
