@@ -149,6 +149,23 @@ long long ddamg_launch_count(void);
  * coarsest GMRES). */
 int ddamg_krylov_steps(ddamg_handle* h, int level, int precision, long long* steps);
 
+/* Relative residual norms out[i] = ||rhs_i - D x_i|| / ||rhs_i|| (FP64 fine
+ * operator of the handle, FP64 fine fields in the ABI layout), computed without
+ * allocating any memory.  The paper has no counterpart: this entry point is for
+ * callers that cannot call cudaMalloc, e.g. code running while another
+ * allocator owns all free device memory, or code that must not trigger the
+ * device synchronisation an allocation implies.  rhs and x must be device
+ * pointers (nothing is staged); out may be host or device memory (n doubles).
+ * The reduction uses a 1 MiB file-scope __device__ array (n <= 64 right-hand
+ * sides; larger n is rejected with DDAMG_ERR_ARG), which every GPU that loads
+ * the library holds until the process exits.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call reuses
+ * the same array and overwrites every entry it later reads, so nothing needs
+ * clearing, but calls that overlap on the GPU (other streams or threads) race
+ * on it. */
+int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double* x, int n, double* out);
+
 /* ---- building blocks of the method, exposed for parity tests ------------ */
 
 /* Level geometry: dims of level l, its dof per site, its test vectors N_l

@@ -17,6 +17,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <mutex>
+
 namespace {
 
 template <typename T>
@@ -685,6 +687,90 @@ __global__ void k_fine_export(cd* __restrict__ dst, const cplx<T>* __restrict__ 
   for (int k = 0; k < 12; ++k) d[k] = ccast<double>(s[(size_t)k * g.V + x]);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free residual norms ||b - D x|| / ||b|| for callers that cannot
+// allocate device memory.  The reduction partials live in a file-scope device
+// array instead of a cudaMalloc'ed scratch buffer; b and x are read in the ABI
+// layout directly, so no conversion buffer is needed either.  The residual at a
+// site is computed with the same device functions and the same order of
+// operations as k_fine_dslash, so it is bit-identical to the library's own
+// residual; only the order of the final sums differs.
+constexpr int NOALLOC_MAX_RHS = 64;
+constexpr int NOALLOC_CHUNKS = 1024;
+__device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_RHS * NOALLOC_CHUNKS * 2];
+__device__ __align__(256) double g_noalloc_out[NOALLOC_MAX_RHS];
+
+__global__ void k_resnorm_partials(double* __restrict__ part, const cd* __restrict__ b, const cd* __restrict__ xv,
+                                   const cd* __restrict__ U, const double* __restrict__ clov, Geom g, int bc_t,
+                                   int nchunks) {
+  __shared__ double sh[32 * 2];
+  const int chunk = blockIdx.x, rhs = blockIdx.y;
+  const int V = g.V;
+  const cd* pb = b + (size_t)rhs * V * 12;
+  const cd* px = xv + (size_t)rhs * V * 12;
+  double rr = 0.0, bb = 0.0;
+  for (int xi = chunk * blockDim.x + threadIdx.x; xi < V; xi += nchunks * blockDim.x) {
+    int c[4];
+    geom_coords(g, xi, c);
+    cd acc[12], nb[12], u[9], d[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = czero<double>();
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+      int n[4] = {c[0], c[1], c[2], c[3]};
+      n[mu] = (c[mu] + 1) % g.L[mu];
+      double sgn = (mu == 0 && c[0] == g.L[0] - 1) ? double(bc_t) : 1.0;
+      const cd* s1 = px + (size_t)lin4(n, g.L) * 12;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) nb[k] = sgn * s1[k];
+      load_link(U, V, mu, xi, u);
+      hop_accumulate(mu, true, u, nb, acc);
+      n[mu] = (c[mu] - 1 + g.L[mu]) % g.L[mu];
+      sgn = (mu == 0 && c[0] == 0) ? double(bc_t) : 1.0;
+      const cd* s2 = px + (size_t)lin4(n, g.L) * 12;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) nb[k] = sgn * s2[k];
+      load_link(U, V, mu, geom_index(g, n), u);
+      hop_accumulate(mu, false, u, nb, acc);
+    }
+    const size_t lex = (size_t)lin4(c, g.L) * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) nb[k] = 1.0 * px[lex + k];
+    clover_apply(clov, V, xi, nb, d);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const cd bk = pb[lex + k];
+      const cd r = bk - (d[k] - 0.5 * acc[k]);
+      rr += cnorm2(r);
+      bb += cnorm2(bk);
+    }
+  }
+  for (int off = 16; off >= 1; off >>= 1) {
+    rr += __shfl_xor_sync(0xffffffffu, rr, off);
+    bb += __shfl_xor_sync(0xffffffffu, bb, off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { sh[2 * warp] = rr; sh[2 * warp + 1] = bb; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, e = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh[2 * w]; e += sh[2 * w + 1]; }
+    part[((size_t)rhs * nchunks + chunk) * 2] = a;
+    part[((size_t)rhs * nchunks + chunk) * 2 + 1] = e;
+  }
+}
+
+__global__ void k_resnorm_final(double* __restrict__ out, const double* __restrict__ part, int nchunks) {
+  if (threadIdx.x != 0) return;
+  const int rhs = blockIdx.x;
+  double a = 0.0, e = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    a += part[((size_t)rhs * nchunks + c) * 2];
+    e += part[((size_t)rhs * nchunks + c) * 2 + 1];
+  }
+  out[rhs] = e > 0.0 ? sqrt(a) / sqrt(e) : 0.0;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -777,6 +863,55 @@ template <typename T>
 void fine_export(cplx<double>* dst, const cplx<T>* src, const Geom& g, int nrhs, size_t rstride, cudaStream_t st) {
   count_launch();
   k_fine_export<T><<<dim3(div_up(g.V, 128), nrhs), 128, 0, st>>>(dst, src, g, rstride);
+}
+
+// device addresses of the allocation-free scratch, looked up once per device
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_part_addr[64] = {};
+static double* g_noalloc_out_addr[64] = {};
+
+int fine_residual_norm_noalloc(double* out, bool out_on_device, const cplx<double>* b, const cplx<double>* x,
+                               const FineOp<double>& op, int nrhs, cudaStream_t st, const char** msg) {
+  if (nrhs < 1 || nrhs > NOALLOC_MAX_RHS) {
+    *msg = "n must be between 1 and 64 (the size of the static scratch)";
+    return -1;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    *msg = "no usable current CUDA device";
+    return -4;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_part_addr[dev]) {
+      double* p = nullptr;
+      double* o = nullptr;
+      if (cudaGetSymbolAddress((void**)&p, g_noalloc_partials) != cudaSuccess ||
+          cudaGetSymbolAddress((void**)&o, g_noalloc_out) != cudaSuccess) {
+        cudaGetLastError();
+        *msg = "cudaGetSymbolAddress of the static scratch failed";
+        return -4;
+      }
+      g_noalloc_part_addr[dev] = p;
+      g_noalloc_out_addr[dev] = o;
+    }
+  }
+  int nchunks = (op.g.V + 255) / 256;
+  if (nchunks > NOALLOC_CHUNKS) nchunks = NOALLOC_CHUNKS;
+  double* dst = out_on_device ? out : g_noalloc_out_addr[dev];
+  count_launch(2);
+  k_resnorm_partials<<<dim3(nchunks, nrhs), 256, 0, st>>>(g_noalloc_part_addr[dev], b, x, op.U, op.clov, op.g,
+                                                          op.bc_t, nchunks);
+  k_resnorm_final<<<nrhs, 32, 0, st>>>(dst, g_noalloc_part_addr[dev], nchunks);
+  if (!out_on_device && cudaMemcpyAsync(out, dst, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+    *msg = "copy of the result to the host failed";
+    return -4;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    *msg = "kernel failure";
+    return -4;
+  }
+  return 0;
 }
 
 #define INST(T)                                                                                              \

@@ -36,6 +36,10 @@ void fine_dslash(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const FineOp
 template <typename T>
 void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int* blocks, int nblocks, int nrhs,
                     size_t rstride, int k_mr, cudaStream_t st);
+// ||b_i - D x_i|| / ||b_i|| with FP64 b, x in the ABI layout (device memory), no
+// allocation (static scratch); returns 0 or a negative code with *msg set
+int fine_residual_norm_noalloc(double* out, bool out_on_device, const cplx<double>* b, const cplx<double>* x,
+                               const FineOp<double>& op, int nrhs, cudaStream_t st, const char** msg);
 void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, double m0, double csw,
                   cudaStream_t st);
 template <typename T>

@@ -1282,6 +1282,25 @@ int ddamg_krylov_steps(ddamg_handle* h, int level, int precision, long long* ste
   });
 }
 
+int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double* x, int n, double* out) {
+  if (!h || !rhs || !x || !out) {
+    g_err = "null argument";
+    return DDAMG_ERR_ARG;
+  }
+  if (!is_device_ptr(rhs) || !is_device_ptr(x)) {
+    g_err = "rhs and x must be device memory (nothing is staged: this entry point allocates nothing)";
+    return DDAMG_ERR_ARG;
+  }
+  const char* msg = "";
+  const int rc = fine_residual_norm_noalloc(out, is_device_ptr(out), reinterpret_cast<const cplx<double>*>(rhs),
+                                            reinterpret_cast<const cplx<double>*>(x), h->lv[0].f64, n, h->st, &msg);
+  if (rc != 0) {
+    g_err = msg;
+    return rc == -1 ? DDAMG_ERR_ARG : DDAMG_ERR_CUDA;
+  }
+  return DDAMG_OK;
+}
+
 int ddamg_level_info(ddamg_handle* h, int level, int dims[4], int* ndof, int* ntv) {
   return guard([&] {
     Level& L = level_of(h, level);
