@@ -111,8 +111,10 @@ int ddamg_set_stream(ddamg_handle* h, void* stream);
 
 /* Options (ddamg_set_option). */
 enum {
-  DDAMG_OPT_GRAPHS = 0   /* 1 (default): each K-cycle runs as one captured CUDA graph whose inner
+  DDAMG_OPT_GRAPHS = 0,  /* 1 (default): each K-cycle runs as one captured CUDA graph whose inner
                             Krylov loops are device-driven conditional WHILE nodes; 0: host-driven */
+  DDAMG_OPT_COARSEST_CLUSTER = 1  /* 1 (default, where it fits): the coarsest odd-even GMRES runs as one
+                                     persistent thread-block-cluster kernel per right-hand side */
 };
 int ddamg_set_option(ddamg_handle* h, int option, int value);
 

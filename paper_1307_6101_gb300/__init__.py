@@ -34,6 +34,7 @@ EXPORTED = (
     "ddamg_krylov_steps", "ddamg_residual_norm_noalloc",
 )
 DDAMG_OPT_GRAPHS = 0
+DDAMG_OPT_COARSEST_CLUSTER = 1
 PROF_KINDS = {"fine_sap": 0, "fine_dslash": 1, "coarse_apply": 2, "coarse_sap": 3, "transfer": 4, "precond": 5,
               "outer_ortho": 6}
 

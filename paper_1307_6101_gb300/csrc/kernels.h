@@ -79,6 +79,28 @@ void coarse_export(cplx<double>* dst, const cplx<T>* src, const Geom& g, int n, 
                    cudaStream_t st);
 void coarse_blocks_export(cplx<double>* dst, const cplx<double>* blk, const Geom& g, int n, cudaStream_t st);
 
+// ---- coarsest level: cluster-resident odd-even GMRES ---------------------------
+struct CoarsestPlanIn {
+  int n_even, n_odd, n, m;
+};
+struct CoarsestPlan {
+  int CL = 0, nep = 0, nop = 0, threads = 0;
+  size_t smem = 0;
+};
+struct CoarsestGeo {
+  const int* even = nullptr;
+  const int* odd = nullptr;
+  const int* nbr_e_of_o = nullptr;   // [n_odd][8]
+  const int* nbr_o_of_e = nullptr;   // [n_even][8]
+  int n_even = 0, n_odd = 0;
+};
+template <typename T>
+int coarsest_cluster_plan(const CoarsestPlanIn& in, CoarsestPlan* plan);
+template <typename T>
+cudaError_t coarsest_cluster_solve(cplx<T>* x, const cplx<T>* b, const CoarseOp<T>& op, const CoarsestPlan& plan,
+                            const CoarsestGeo& geo, int nrhs, size_t rstride, int m, int max_cycles, double tol,
+                            int* iters, cudaStream_t st);
+
 // ---- transfer ---------------------------------------------------------------
 // out(A)[s*N + j] = sum_{x in A, f in s} conj(P_j(x, f)) in(x, f)
 template <typename T>

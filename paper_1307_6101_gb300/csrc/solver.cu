@@ -146,6 +146,11 @@ struct ddamg_handle {
   GraphEntry* capturing = nullptr;
   cplx<double>* pin64 = nullptr;
   cplx<double>* pout64 = nullptr;
+  // coarsest level on a thread-block cluster
+  bool use_cluster = true;
+  CoarsestGeo cgeo;
+  CoarsestPlan cplan32, cplan64;
+  bool have_cplan32 = false, have_cplan64 = false;
 };
 
 namespace {
@@ -495,11 +500,24 @@ void krylov(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>
 // ---------------------------------------------------------------------------
 // coarsest level: odd-even preconditioned GMRES (Sec. 3)
 template <typename T>
+const CoarsestPlan* cluster_plan(ddamg_handle* h) {
+  if (!h->use_cluster) return nullptr;
+  if (sizeof(T) == 4) return h->have_cplan32 ? &h->cplan32 : nullptr;
+  return h->have_cplan64 ? &h->cplan64 : nullptr;
+}
+
+template <typename T>
 void coarse_solve(ddamg_handle* h, cplx<T>* x, const cplx<T>* b, int nrhs) {
   Level& C = h->lv[h->L - 1];
   Work<T>& w = work<T>(C);
   CoarseOp<T>& op = cop<T>(C);
   const size_t rs = C.vlen;
+  if (const CoarsestPlan* pl = cluster_plan<T>(h)) {
+    // the whole odd-even GMRES in one cluster-resident kernel per right-hand side
+    CK(coarsest_cluster_solve<T>(x, b, op, *pl, h->cgeo, nrhs, rs, h->p.coarse_restart, h->p.coarse_cycles,
+                                 h->p.coarse_tol, w.gs.ctl + 3, h->st));
+    return;
+  }
   cplx<T>*t1 = w.t[0], *bh = w.t[3], *xe = w.t[4];
   // bhat_e = b_e - D_eo D_oo^{-1} b_o
   coarse_schur_odd<T>(t1, nullptr, b, op, 1.0, 0.0, nrhs, rs, h->st);
@@ -944,6 +962,41 @@ void allocate_hierarchy(ddamg_handle* h) {
         CK(cudaMemcpy(d, odd.data(), sizeof(int) * odd.size(), cudaMemcpyHostToDevice));
         L.c64.odd_sites = L.c32.odd_sites = d;
         L.c64.n_odd = L.c32.n_odd = (int)odd.size();
+        // tables of the cluster solver: even/odd lists and the list index of each neighbour
+        std::vector<int> even, pos(L.g.V, -1);
+        for (int x = 0; x < L.g.V; ++x) {
+          int c[4];
+          geom_coords(L.g, x, c);
+          if (geom_parity(c) == 0) even.push_back(x);
+        }
+        for (size_t q = 0; q < even.size(); ++q) pos[even[q]] = (int)q;
+        for (size_t q = 0; q < odd.size(); ++q) pos[odd[q]] = (int)q;
+        auto nbr_table = [&](const std::vector<int>& from) {
+          std::vector<int> t(from.size() * 8);
+          for (size_t q = 0; q < from.size(); ++q) {
+            int c[4];
+            geom_coords(L.g, from[q], c);
+            for (int k = 0; k < 8; ++k) t[q * 8 + k] = pos[geom_neighbor(L.g, c, k % 4, k < 4 ? +1 : -1)];
+          }
+          return t;
+        };
+        const std::vector<int> eo = nbr_table(odd), oe = nbr_table(even);
+        int* de = dalloc<int>(h, even.size());
+        int* deo = dalloc<int>(h, eo.size());
+        int* doe = dalloc<int>(h, oe.size());
+        CK(cudaMemcpy(de, even.data(), sizeof(int) * even.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(deo, eo.data(), sizeof(int) * eo.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(doe, oe.data(), sizeof(int) * oe.size(), cudaMemcpyHostToDevice));
+        h->cgeo.even = de;
+        h->cgeo.odd = d;
+        h->cgeo.nbr_e_of_o = deo;
+        h->cgeo.nbr_o_of_e = doe;
+        h->cgeo.n_even = (int)even.size();
+        h->cgeo.n_odd = (int)odd.size();
+        CoarsestPlanIn in{(int)even.size(), (int)odd.size(), L.n, h->p.coarse_restart};
+        h->have_cplan32 = coarsest_cluster_plan<float>(in, &h->cplan32) != 0;
+        h->have_cplan64 = coarsest_cluster_plan<double>(in, &h->cplan64) != 0;
+        cudaGetLastError();
       }
     }
     if (!L.coarsest) {
@@ -1226,8 +1279,14 @@ int ddamg_set_option(ddamg_handle* h, int option, int value) {
   if (!h) return DDAMG_ERR_ARG;
   return guard([&] {
     sync(h);
-    if (option == DDAMG_OPT_GRAPHS) h->use_graphs = value != 0;
-    else fail(DDAMG_ERR_ARG, "unknown option");
+    if (option == DDAMG_OPT_GRAPHS) {
+      h->use_graphs = value != 0;
+    } else if (option == DDAMG_OPT_COARSEST_CLUSTER) {
+      h->use_cluster = value != 0;
+      free_graphs(h);   // captured graphs embed the previous choice
+    } else {
+      fail(DDAMG_ERR_ARG, "unknown option");
+    }
   });
 }
 

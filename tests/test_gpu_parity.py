@@ -149,10 +149,13 @@ def test_coarse_apply_and_sap(dd, spec):
                 assert rel(z, zref) <= tol, (l, prec, rel(z, zref))
 
 
+@pytest.mark.parametrize("cluster", [1, 0])
 @pytest.mark.parametrize("spec", [SMALL2, THREE])
-def test_coarsest_even_odd_gmres(dd, spec):
+def test_coarsest_even_odd_gmres(dd, spec, cluster):
+    """Coarsest odd-even GMRES: thread-block-cluster kernel and the host-driven loop, vs the oracle."""
     from oracle.krylov import coarsest_solve
     c, h, o = _pair(spec, max_rhs=2)
+    dd.ddamg_set_option(h, dd.DDAMG_OPT_COARSEST_CLUSTER, cluster)
     L = c.levels - 1
     dims, n, _ = h.level_info(L)
     b = _fields(2, dims, n, 60)
