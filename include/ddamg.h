@@ -113,10 +113,15 @@ int ddamg_set_stream(ddamg_handle* h, void* stream);
 enum {
   DDAMG_OPT_GRAPHS = 0,  /* 1 (default): each K-cycle runs as one captured CUDA graph whose inner
                             Krylov loops are device-driven conditional WHILE nodes; 0: host-driven */
-  DDAMG_OPT_COARSEST_CLUSTER = 1  /* 1 (default, where it fits): the coarsest odd-even GMRES runs as one
+  DDAMG_OPT_COARSEST_CLUSTER = 1, /* 1 (default, where it fits): the coarsest odd-even GMRES runs as one
                                      persistent thread-block-cluster kernel per right-hand side */
+  DDAMG_OPT_SAP_CLUSTER = 2       /* 1 (default, where it fits): coarse-level SAP sweeps run one
+                                     thread-block cluster per SAP block; 0: one CTA per block */
 };
 int ddamg_set_option(ddamg_handle* h, int option, int value);
+/* Effective setting: GRAPHS 0/1; COARSEST_CLUSTER and SAP_CLUSTER the cluster size in use on the
+ * coarsest level / on level 1 (FP32 path), 0 when the one-CTA kernels run. */
+int ddamg_get_option(ddamg_handle* h, int option, int* value);
 
 /* ---- measurement ----------------------------------------------------------- */
 

@@ -31,10 +31,11 @@ EXPORTED = (
     "ddamg_prolong", "ddamg_kcycle", "ddamg_coarse_solve", "ddamg_set_testvectors",
     "ddamg_get_testvectors", "ddamg_rebuild", "ddamg_get_interpolation", "ddamg_get_coarse_operator",
     "ddamg_profile", "ddamg_profile_read", "ddamg_launch_count", "ddamg_set_option",
-    "ddamg_krylov_steps", "ddamg_residual_norm_noalloc",
+    "ddamg_krylov_steps", "ddamg_residual_norm_noalloc", "ddamg_get_option",
 )
 DDAMG_OPT_GRAPHS = 0
 DDAMG_OPT_COARSEST_CLUSTER = 1
+DDAMG_OPT_SAP_CLUSTER = 2
 PROF_KINDS = {"fine_sap": 0, "fine_dslash": 1, "coarse_apply": 2, "coarse_sap": 3, "transfer": 4, "precond": 5,
               "outer_ortho": 6}
 
@@ -102,6 +103,7 @@ def _load():
     lib.ddamg_profile.argtypes = [vp, ip]
     lib.ddamg_profile_read.argtypes = [vp, ip, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
     lib.ddamg_set_option.argtypes = [vp, ip, ip]
+    lib.ddamg_get_option.argtypes = [vp, ip, C.POINTER(C.c_int)]
     lib.ddamg_krylov_steps.argtypes = [vp, ip, ip, C.POINTER(C.c_longlong)]
     lib.ddamg_residual_norm_noalloc.argtypes = [vp, vp, vp, ip, vp]
     lib.ddamg_launch_count.restype = C.c_longlong
@@ -292,3 +294,9 @@ def ddamg_krylov_steps(h, level, precision):
 def ddamg_residual_norm_noalloc(h, rhs, x, n, out):
     """||rhs_i - D x_i|| / ||rhs_i|| into out without any allocation (rhs, x on the device)."""
     _check(lib().ddamg_residual_norm_noalloc(h.raw, _ptr(rhs), _ptr(x), int(n), _ptr(out)))
+
+
+def ddamg_get_option(h, option):
+    v = C.c_int()
+    _check(lib().ddamg_get_option(h.raw, int(option), C.byref(v)))
+    return v.value

@@ -4,8 +4,12 @@
 // Blocks are stored column-major per (site, k) with k = 0 self, 1..4 forward,
 // 5..8 backward, so that the threads computing consecutive rows of one site
 // read consecutive words.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -266,6 +270,133 @@ __global__ void k_coarse_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict_
   }
 }
 
+// SAP colour sweep on a coarse level with one thread-block cluster per SAP
+// block.  CTA q of the cluster owns `spc` sites of the block (one thread per
+// (row, block k) of its sites).  Every CTA keeps a copy of the whole block
+// residual in shared memory; after each MR update each CTA writes its own rows
+// into all copies (distributed shared memory).  The MR dot products are summed
+// over the cluster from per-CTA partials in rank order, so every CTA computes
+// the same alpha.  Same arithmetic as k_coarse_sap: rho = (b - D z)_B, k MR
+// steps on D_B (hops leaving the block dropped), z_B += e_B.
+template <typename T>
+__global__ void k_coarse_sap_cluster(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
+                                     const cplx<T>* __restrict__ blk, Geom g, int n, size_t rstride,
+                                     const int* __restrict__ blocks, int k_mr, int spc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CLS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int vB = g.vB;
+  const int b = blocks[blockIdx.x / CLS];
+  const int rows = spc * n;
+  cplx<T>* rfull = reinterpret_cast<cplx<T>*>(smem_raw);   // [vB*n]
+  cplx<T>* part = rfull + (size_t)vB * n;                   // [9][rows]
+  T* red = reinterpret_cast<T*>(part + (size_t)9 * rows);   // [CLS][4] (read from rank 0)
+  T* sh = red + 4 * 16;                                      // [warps][3]
+  const size_t ro = (size_t)blockIdx.y * rstride;
+  const int k = threadIdx.x / rows;
+  const int rl = threadIdx.x - k * rows;
+  const int sl = rl / n, i = rl - (rl / n) * n;
+  const int site = b * vB + rank * spc + sl;
+  bool kin = false;   // this thread's block k couples to a site inside the SAP block
+  int nb = site, nloc = 0;
+  if (k < 9) {
+    int c[4];
+    geom_coords(g, site, c);
+    if (k == 0) {
+      kin = true;
+      nb = site;
+    } else {
+      const int mu = (k - 1) % 4, dir = k <= 4 ? +1 : -1;
+      nb = geom_neighbor(g, c, mu, dir);
+      kin = hop_internal(g, c, mu, dir, g.B);
+    }
+    nloc = nb - b * vB;
+  }
+  const cplx<T>* M = blk + (((size_t)site * 9 + (k < 9 ? k : 0)) * n) * n + i;
+  // rho = b - D z on the own rows (all 9 blocks, neighbours read from z)
+  {
+    cplx<T> acc = czero<T>();
+    if (k < 9) {
+      const cplx<T>* v = z + ro + (size_t)nb * n;
+#pragma unroll 8
+      for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], v[j]);
+      part[k * rows + rl] = acc;
+    }
+  }
+  __syncthreads();
+  cplx<T> r = czero<T>(), xs = czero<T>();
+  if (threadIdx.x < rows) {
+    cplx<T> d = czero<T>();
+#pragma unroll
+    for (int q = 0; q < 9; ++q) d = d + part[q * rows + threadIdx.x];
+    r = bsrc[ro + (size_t)(b * vB + rank * spc) * n + threadIdx.x] - d;
+    for (int q = 0; q < CLS; ++q) cluster.map_shared_rank(rfull, q)[(size_t)rank * rows + threadIdx.x] = r;
+  }
+  cluster.sync();
+  T* red0 = cluster.map_shared_rank(red, 0);
+  for (int it = 0; it < k_mr; ++it) {
+    // p = D_B r on the own rows
+    if (k < 9) {
+      cplx<T> acc = czero<T>();
+      if (kin) {
+        const cplx<T>* v = rfull + (size_t)nloc * n;
+#pragma unroll 8
+        for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], v[j]);
+      }
+      part[k * rows + rl] = acc;
+    }
+    __syncthreads();
+    cplx<T> p = czero<T>();
+    T nre = T(0), nim = T(0), den = T(0);
+    if (threadIdx.x < rows) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) p = p + part[q * rows + threadIdx.x];
+      const cplx<T> t = cdotc(p, r);
+      nre = t.re;
+      nim = t.im;
+      den = cnorm2(p);
+    }
+    // CTA reduction, then rank-ordered cluster reduction
+    for (int off = 16; off >= 1; off >>= 1) {
+      nre += __shfl_xor_sync(0xffffffffu, nre, off);
+      nim += __shfl_xor_sync(0xffffffffu, nim, off);
+      den += __shfl_xor_sync(0xffffffffu, den, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) { sh[3 * warp] = nre; sh[3 * warp + 1] = nim; sh[3 * warp + 2] = den; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T a = T(0), bb = T(0), cc = T(0);
+      for (int w = 0; w < nw; ++w) { a += sh[3 * w]; bb += sh[3 * w + 1]; cc += sh[3 * w + 2]; }
+      red0[rank * 4] = a;
+      red0[rank * 4 + 1] = bb;
+      red0[rank * 4 + 2] = cc;
+    }
+    cluster.sync();
+    if (threadIdx.x == 0) {   // one thread reads the remote partials, the CTA reads its copy
+      T a = T(0), bb = T(0), cc = T(0);
+      for (int q = 0; q < CLS; ++q) { a += red0[q * 4]; bb += red0[q * 4 + 1]; cc += red0[q * 4 + 2]; }
+      sh[96] = a;
+      sh[97] = bb;
+      sh[98] = cc;
+    }
+    __syncthreads();
+    const T a = sh[96], bb = sh[97], cc = sh[98];
+    const cplx<T> alpha = cc > T(0) ? cmk<T>(a / cc, bb / cc) : czero<T>();
+    if (threadIdx.x < rows) {
+      cfma(xs, alpha, r);
+      r = r - alpha * p;
+      for (int q = 0; q < CLS; ++q) cluster.map_shared_rank(rfull, q)[(size_t)rank * rows + threadIdx.x] = r;
+    }
+    cluster.sync();
+  }
+  if (threadIdx.x < rows) {
+    const size_t a = ro + (size_t)(b * vB + rank * spc) * n + threadIdx.x;
+    z[a] = z[a] + xs;
+  }
+}
+
 // Gauss-Jordan inversion with partial pivoting of every self block (FP64).
 __global__ void k_selfinv_build(cplx<double>* __restrict__ inv, const cplx<double>* __restrict__ blk, int n,
                                 int* err) {
@@ -396,6 +527,11 @@ __global__ void k_blocks_export(cplx<double>* __restrict__ dst, const cplx<doubl
 namespace dd {
 
 template <typename T>
+size_t coarse_sap_cluster_smem(int vB, int n, int spc) {
+  return (size_t)vB * n * sizeof(cplx<T>) + (size_t)9 * spc * n * sizeof(cplx<T>) + (4 * 16 + 32 * 3 + 4) * sizeof(T);
+}
+
+template <typename T>
 void coarse_apply(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const CoarseOp<T>& op, int nrhs, size_t rstride,
                   int sel, int sel_mu, int in_chir, cudaStream_t st) {
   const int threads = ((9 * op.n + 31) / 32) * 32;
@@ -408,9 +544,64 @@ void coarse_apply(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const Coars
     k_coarse_apply<T, false><<<grid, threads, sm, st>>>(out, in, b, op.blk, op.g, op.n, rstride, sel, sel_mu, in_chir);
 }
 
+// cluster plan of the coarse SAP: cluster size CLS and sites per CTA (0 if no plan fits)
+template <typename T>
+int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out) {
+  for (int CLS : {8, 16, 4, 2}) {
+    if (g.vB % CLS) continue;
+    const int spc = g.vB / CLS;
+    const int threads = ((9 * spc * n + 31) / 32) * 32;
+    if (threads > 1024) continue;
+    const size_t sm = coarse_sap_cluster_smem<T>(g.vB, n, spc);
+    if (CLS > 8) cudaFuncSetAttribute(k_coarse_sap_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CLS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CLS, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_sap_cluster<T>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (nclusters < 1) continue;
+    *CLS_out = CLS;
+    *spc_out = spc;
+    return 1;
+  }
+  return 0;
+}
+
 template <typename T>
 void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks, int nrhs,
                       size_t rstride, int k_mr, cudaStream_t st) {
+  if (op.sap_cls > 0) {
+    const int spc = op.g.vB / op.sap_cls;
+    const int threads = ((9 * spc * op.n + 31) / 32) * 32;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = op.sap_cls;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(nblocks * op.sap_cls, nrhs, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = coarse_sap_cluster_smem<T>(op.g.vB, op.n, spc);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launch();
+    if (cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T>, z, b, (const cplx<T>*)op.blk, op.g, op.n, rstride, blocks,
+                           k_mr, spc) == cudaSuccess)
+      return;
+    cudaGetLastError();   // cluster launch refused: run the one-CTA-per-block kernel instead
+  }
   const int threads = ((op.g.vB * op.n + 31) / 32) * 32;
   const size_t sm = (size_t)op.g.vB * op.n * sizeof(cplx<T>) + 32 * 3 * sizeof(T);
   static bool attr_set[2] = {false, false};
@@ -495,6 +686,7 @@ void coarse_blocks_export(cplx<double>* dst, const cplx<double>* blk, const Geom
                                     int, size_t, cudaStream_t);                                                   \
   template void coarse_schur_even<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const cplx<T>*, const CoarseOp<T>&, \
                                      double, double, double, int, size_t, cudaStream_t);                          \
+  template int coarse_sap_cluster_plan<T>(const Geom&, int, int*, int*);                                           \
   template void coarse_sap_sweep<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, const int*, int, int, size_t,   \
                                     int, cudaStream_t);                                                           \
   template void coarse_selfinv_apply<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, int, int, size_t,           \

@@ -249,9 +249,13 @@ __device__ T cluster_norm2(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group
   cta_sum_c(a, T(0), s, s.part);
   if (threadIdx.x == 0) red0[cx.rank * MAXM] = cmk<T>(s.scal[0], T(0));
   cluster.sync();
-  T t = T(0);
-  for (int q = 0; q < cx.CL; ++q) t += red0[q * MAXM].re;
-  return t;
+  if (threadIdx.x == 0) {   // one thread reads the remote partials, the CTA reads its copy
+    T t = T(0);
+    for (int q = 0; q < cx.CL; ++q) t += red0[q * MAXM].re;
+    s.scal[4] = t;
+  }
+  __syncthreads();
+  return s.scal[4];
 }
 
 template <typename T>

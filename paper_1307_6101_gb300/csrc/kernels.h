@@ -26,6 +26,7 @@ struct CoarseOp {
   cplx<T>* selfinv;     // [V][n][n] inverse of the self block (coarsest level), or null
   const int* odd_sites; // indices of the odd sites (coarsest level), or null
   int n_odd;
+  int sap_cls;          // cluster size of the cluster SAP kernel (0: one CTA per SAP block)
 };
 
 // ---- fine level -----------------------------------------------------------
@@ -57,6 +58,8 @@ template <typename T>
 void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks,
                       int nrhs, size_t rstride, int k_mr, cudaStream_t st);
 void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int n, int* err, cudaStream_t st);
+template <typename T>
+int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out);
 // t(A odd) = S^{-1}(a b + c D_oe x)     (even entries of t untouched)
 template <typename T>
 void coarse_schur_odd(cplx<T>* t, const cplx<T>* x, const cplx<T>* b, const CoarseOp<T>& op, double a, double c,

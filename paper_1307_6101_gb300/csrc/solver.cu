@@ -999,6 +999,12 @@ void allocate_hierarchy(ddamg_handle* h) {
         cudaGetLastError();
       }
     }
+    if (!L.fine && !L.coarsest) {
+      int cls = 0, spc = 0;
+      L.c32.sap_cls = coarse_sap_cluster_plan<float>(L.g, L.n, &cls, &spc) ? cls : 0;
+      L.c64.sap_cls = coarse_sap_cluster_plan<double>(L.g, L.n, &cls, &spc) ? cls : 0;
+      cudaGetLastError();
+    }
     if (!L.coarsest) {
       L.tv64 = dalloc<cplx<double>>(h, L.vlen * L.N);
       L.P64 = dalloc<cplx<double>>(h, L.vlen * L.N);
@@ -1284,6 +1290,30 @@ int ddamg_set_option(ddamg_handle* h, int option, int value) {
     } else if (option == DDAMG_OPT_COARSEST_CLUSTER) {
       h->use_cluster = value != 0;
       free_graphs(h);   // captured graphs embed the previous choice
+    } else if (option == DDAMG_OPT_SAP_CLUSTER) {
+      for (auto& L : h->lv) {
+        if (L.fine || L.coarsest) continue;
+        int cls = 0, spc = 0;
+        L.c32.sap_cls = (value && coarse_sap_cluster_plan<float>(L.g, L.n, &cls, &spc)) ? cls : 0;
+        L.c64.sap_cls = (value && coarse_sap_cluster_plan<double>(L.g, L.n, &cls, &spc)) ? cls : 0;
+      }
+      cudaGetLastError();
+      free_graphs(h);
+    } else {
+      fail(DDAMG_ERR_ARG, "unknown option");
+    }
+  });
+}
+
+int ddamg_get_option(ddamg_handle* h, int option, int* value) {
+  if (!h || !value) return DDAMG_ERR_ARG;
+  return guard([&] {
+    if (option == DDAMG_OPT_GRAPHS) {
+      *value = h->use_graphs ? 1 : 0;
+    } else if (option == DDAMG_OPT_COARSEST_CLUSTER) {
+      *value = (h->use_cluster && h->have_cplan32) ? h->cplan32.CL : 0;
+    } else if (option == DDAMG_OPT_SAP_CLUSTER) {
+      *value = h->L > 2 ? h->lv[1].c32.sap_cls : 0;
     } else {
       fail(DDAMG_ERR_ARG, "unknown option");
     }

@@ -128,9 +128,11 @@ def test_restrict_prolong(dd, spec):
             assert rel(out, pref) <= tol
 
 
+@pytest.mark.parametrize("cluster", [1, 0])
 @pytest.mark.parametrize("spec", [SMALL2, THREE])
-def test_coarse_apply_and_sap(dd, spec):
+def test_coarse_apply_and_sap(dd, spec, cluster):
     c, h, o = _pair(spec)
+    dd.ddamg_set_option(h, dd.DDAMG_OPT_SAP_CLUSTER, cluster)
     for l in range(1, c.levels):
         dims, n, _ = h.level_info(l)
         f = _fields(3, dims, n, 30 + l)
