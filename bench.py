@@ -173,7 +173,7 @@ def run_gpu(args, w):
     stream = torch.cuda.current_stream()
     setup_s = {}
     handles = {}
-    for name, prec in (("mixed", 1), ("fp64", 0)):
+    for name, prec in ((("mixed", 1),) if args.only_mixed else (("mixed", 1), ("fp64", 0))):
         t0 = time.perf_counter()
         h = dd.ddamg_setup(U, w["dims"], -1, m0, w["csw"], params(prec), tv)
         setup_s[name] = time.perf_counter() - t0
@@ -226,6 +226,13 @@ def run_gpu(args, w):
                                                tag="timed_mixed")
     steps1 = [dd.ddamg_krylov_steps(handles["mixed"], l, 1) for l in range(w["levels"])]
     clocks = clk.stop()
+    if args.only_mixed:
+        for h in handles.values():
+            h.free()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": nb * args.steps / (sum(ms_mixed) / 1e3), "unit": "RHS/s",
+                              "note": "profiling run (--only-mixed): not a bench line"}))
+        return
     ms_fp64, st_fp64, _, _ = timed(handles["fp64"], args.steps, max(1, min(args.warmup, 3)), tag="timed_fp64")
 
     for st in st_mixed + st_fp64:
@@ -393,6 +400,8 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="three_level_16c32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="time only the mixed-precision path (profiling runs)")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven inner solves instead of captured graphs (for kernel-level profiling)")
     args = ap.parse_args()
