@@ -65,7 +65,9 @@ typedef struct ddamg_params {
   double coarse_tol;                   /* coarsest relative tolerance (Table 1: 5e-2)    */
   int coarse_restart;                  /* coarsest GMRES restart length (<= 63)          */
   int coarse_cycles;                   /* coarsest GMRES cycles                          */
-  int precision;                       /* 0: preconditioner FP64; 1: FP32 (mixed)        */
+  int precision;                       /* preconditioner: 0 FP64; 1 FP32; 2 FP32 arithmetic
+                                          on FP16 storage (links, clover term, P, coarse
+                                          blocks; per-site / per-aggregate scales)        */
   int max_rhs;                         /* right-hand sides per batch                     */
 } ddamg_params;
 
@@ -96,7 +98,7 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
 
 /* Solves D x_i = rhs_i, i < n, with FGMRES(n_kv) in FP64 right-preconditioned
  * by one K-cycle (Alg. 2) per iteration (the preconditioner in FP32 when
- * precision = 1).  Batches of up to max_rhs right-hand sides share every
+ * precision = 1 or 2).  Batches of up to max_rhs right-hand sides share every
  * kernel launch; larger n is split into consecutive batches.  per_rhs may be
  * NULL.  Returns NOCONV (x holds the last iterate) if any rhs missed tol. */
 int ddamg_solve(ddamg_handle* h, const double* rhs, double* x, int n, double tol, ddamg_stats* per_rhs);
@@ -115,12 +117,19 @@ enum {
                             Krylov loops are device-driven conditional WHILE nodes; 0: host-driven */
   DDAMG_OPT_COARSEST_CLUSTER = 1, /* 1 (default, where it fits): the coarsest odd-even GMRES runs as one
                                      persistent thread-block-cluster kernel per right-hand side */
-  DDAMG_OPT_SAP_CLUSTER = 2       /* 1 (default, where it fits): coarse-level SAP sweeps run one
+  DDAMG_OPT_SAP_CLUSTER = 2,      /* 1 (default, where it fits): coarse-level SAP sweeps run one
                                      thread-block cluster per SAP block; 0: one CTA per block */
+  DDAMG_OPT_HALF_STORAGE = 3      /* 1: the FP32 kernels read FP16 copies of the fine links and
+                                     clover term (no scale), of P (one FP32 scale per aggregate
+                                     and chirality) and of the coarse blocks (one FP32 scale per
+                                     site): q = round-to-nearest-even(x / s), s = max |Re|, |Im|
+                                     of the group.  Default: 1 iff params.precision = 2.  The
+                                     paper keeps FP32 storage; this is a storage format only
+                                     (arithmetic stays FP32, the copies follow every rebuild). */
 };
 int ddamg_set_option(ddamg_handle* h, int option, int value);
 /* Effective setting: GRAPHS 0/1; COARSEST_CLUSTER and SAP_CLUSTER the cluster size in use on the
- * coarsest level / on level 1 (FP32 path), 0 when the one-CTA kernels run. */
+ * coarsest level / on level 1 (FP32 path), 0 when the one-CTA kernels run; HALF_STORAGE 0/1. */
 int ddamg_get_option(ddamg_handle* h, int option, int* value);
 
 /* ---- measurement ----------------------------------------------------------- */
@@ -179,7 +188,9 @@ int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double
  * (0 on the coarsest level). */
 int ddamg_level_info(ddamg_handle* h, int level, int dims[4], int* ndof, int* ntv);
 
-/* out = D_l in (n fields of level l). precision 0 = FP64, 1 = FP32 copy. */
+/* out = D_l in (n fields of level l). precision 0 = FP64, 1 = FP32 arithmetic on the
+ * FP32 path's storage (FP16 while DDAMG_OPT_HALF_STORAGE is on); the same for the
+ * precision argument of the calls below.  Other values: ARG. */
 int ddamg_apply(ddamg_handle* h, int level, int precision, const double* in, double* out, int n);
 
 /* iterations x { z <- z + M_SAP (b - D_l z) } on level l < L-1 (z in/out). */

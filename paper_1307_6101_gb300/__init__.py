@@ -36,6 +36,7 @@ EXPORTED = (
 DDAMG_OPT_GRAPHS = 0
 DDAMG_OPT_COARSEST_CLUSTER = 1
 DDAMG_OPT_SAP_CLUSTER = 2
+DDAMG_OPT_HALF_STORAGE = 3
 PROF_KINDS = {"fine_sap": 0, "fine_dslash": 1, "coarse_apply": 2, "coarse_sap": 3, "transfer": 4, "precond": 5,
               "outer_ortho": 6}
 

@@ -34,10 +34,11 @@ __device__ void cta_sum3(T& a, T& b, T& c, T* sh) {
 // neighbour vectors are staged in shared memory and the 9 partial rows are
 // summed in shared memory.  Blocks are column-major, so the threads of one k
 // read consecutive words for every column j.
-template <typename T, bool RESID>
+template <typename T, bool RESID, typename BS>
 __global__ void k_coarse_apply(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in,
-                               const cplx<T>* __restrict__ bsrc, const cplx<T>* __restrict__ blk, Geom g, int n,
-                               size_t rstride, int sel, int sel_mu, int in_chir) {
+                               const cplx<T>* __restrict__ bsrc, const BS* __restrict__ blk,
+                               const float* __restrict__ bscale, Geom g, int n, size_t rstride, int sel, int sel_mu,
+                               int in_chir) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);   // [9][n] neighbour vectors
   cplx<T>* part = xs + 9 * n;                           // [9][n] partial rows
@@ -76,10 +77,11 @@ __global__ void k_coarse_apply(cplx<T>* __restrict__ out, const cplx<T>* __restr
   if (k < 9) {
     cplx<T> acc = czero<T>();
     if (take[k]) {
-      const cplx<T>* M = blk + (((size_t)site * 9 + k) * n) * n + i;
+      const BS* M = blk + (((size_t)site * 9 + k) * n) * n + i;
       const cplx<T>* x = xs + k * n;
 #pragma unroll 8
-      for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], x[j]);
+      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), x[j]);
+      if (bscale) acc = T(bscale[site]) * acc;
     }
     part[k * n + i] = acc;
   }
@@ -99,9 +101,10 @@ __global__ void k_coarse_apply(cplx<T>* __restrict__ out, const cplx<T>* __restr
 //              (even entries of t are not written)
 // k_schur_even: on every even site A, y(A) = a*b(A) + s*S(A) x(A) + c*(D_eo t)(A);
 //              odd entries of y are set to zero.
-template <typename T>
+template <typename T, typename BS>
 __global__ void k_schur_odd(cplx<T>* __restrict__ t, const cplx<T>* __restrict__ x, const cplx<T>* __restrict__ b,
-                            const cplx<T>* __restrict__ blk, const cplx<T>* __restrict__ inv,
+                            const BS* __restrict__ blk, const float* __restrict__ bscale,
+                            const cplx<T>* __restrict__ inv,
                             const int* __restrict__ odd_sites, Geom g, int n, size_t rstride, double a, double c) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);   // [8][n]
@@ -124,10 +127,11 @@ __global__ void k_schur_odd(cplx<T>* __restrict__ t, const cplx<T>* __restrict__
   if (k < 8) {
     cplx<T> acc = czero<T>();
     if (x && c != 0.0) {
-      const cplx<T>* M = blk + (((size_t)site * 9 + 1 + k) * n) * n + i;
+      const BS* M = blk + (((size_t)site * 9 + 1 + k) * n) * n + i;
       const cplx<T>* xv = xs + k * n;
 #pragma unroll 8
-      for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], xv[j]);
+      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), xv[j]);
+      if (bscale) acc = T(bscale[site]) * acc;
     }
     part[k * n + i] = acc;
   }
@@ -150,10 +154,11 @@ __global__ void k_schur_odd(cplx<T>* __restrict__ t, const cplx<T>* __restrict__
   }
 }
 
-template <typename T>
+template <typename T, typename BS>
 __global__ void k_schur_even(cplx<T>* __restrict__ y, const cplx<T>* __restrict__ x, const cplx<T>* __restrict__ t,
-                             const cplx<T>* __restrict__ b, const cplx<T>* __restrict__ blk, Geom g, int n,
-                             size_t rstride, double a, double s, double c) {
+                             const cplx<T>* __restrict__ b, const BS* __restrict__ blk,
+                             const float* __restrict__ bscale, Geom g, int n, size_t rstride, double a, double s,
+                             double c) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);   // [9][n]
   cplx<T>* part = xs + 9 * n;                           // [9][n]
@@ -183,10 +188,11 @@ __global__ void k_schur_even(cplx<T>* __restrict__ y, const cplx<T>* __restrict_
     cplx<T> acc = czero<T>();
     const double w = k == 0 ? s : c;
     if (w != 0.0 && (k == 0 ? x : t)) {
-      const cplx<T>* M = blk + (((size_t)site * 9 + k) * n) * n + i;
+      const BS* M = blk + (((size_t)site * 9 + k) * n) * n + i;
       const cplx<T>* xv = xs + k * n;
 #pragma unroll 8
-      for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], xv[j]);
+      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), xv[j]);
+      if (bscale) acc = T(bscale[site]) * acc;
     }
     part[k * n + i] = T(w) * acc;
   }
@@ -203,10 +209,10 @@ __global__ void k_schur_even(cplx<T>* __restrict__ y, const cplx<T>* __restrict_
 
 // One colour sweep of SAP on a coarse level: one CTA per SAP block, one thread
 // per (site, row) of the block.  rho = (b - D z)_B, k MR steps on D_B, z_B += e_B.
-template <typename T>
+template <typename T, typename BS>
 __global__ void k_coarse_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
-                             const cplx<T>* __restrict__ blk, Geom g, int n, size_t rstride,
-                             const int* __restrict__ blocks, int k_mr) {
+                             const BS* __restrict__ blk, const float* __restrict__ bscale, Geom g, int n,
+                             size_t rstride, const int* __restrict__ blocks, int k_mr) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);        // [vB * n]
   T* sh = reinterpret_cast<T*>(rs + (size_t)g.vB * n);          // [warps][3]
@@ -218,18 +224,19 @@ __global__ void k_coarse_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict_
   cplx<T>* pz = z + ro;
   int c[4];
   geom_coords(g, site, c);
+  const T sc = bscale ? T(bscale[site]) : T(1);
   cplx<T> r = czero<T>(), xs = czero<T>();
   if (active) {
     cplx<T> acc = czero<T>();
     const cplx<T>* v = pz + (size_t)site * n;
-    for (int j = 0; j < n; ++j) cfma(acc, blk[bidx(site, 0, n, i, j)], v[j]);
+    for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(blk, bidx(site, 0, n, i, j)), v[j]);
     for (int mu = 0; mu < 4; ++mu) {
       v = pz + (size_t)geom_neighbor(g, c, mu, +1) * n;
-      for (int j = 0; j < n; ++j) cfma(acc, blk[bidx(site, 1 + mu, n, i, j)], v[j]);
+      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(blk, bidx(site, 1 + mu, n, i, j)), v[j]);
       v = pz + (size_t)geom_neighbor(g, c, mu, -1) * n;
-      for (int j = 0; j < n; ++j) cfma(acc, blk[bidx(site, 5 + mu, n, i, j)], v[j]);
+      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(blk, bidx(site, 5 + mu, n, i, j)), v[j]);
     }
-    r = bsrc[ro + (size_t)site * n + i] - acc;
+    r = bsrc[ro + (size_t)site * n + i] - sc * acc;
   }
   for (int it = 0; it < k_mr; ++it) {
     if (active) rs[threadIdx.x] = r;
@@ -239,21 +246,22 @@ __global__ void k_coarse_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict_
     if (active) {
       const cplx<T>* v = rs + (size_t)loc * n;
 #pragma unroll 8
-      for (int j = 0; j < n; ++j) cfma(p, blk[bidx(site, 0, n, i, j)], v[j]);
+      for (int j = 0; j < n; ++j) cfma(p, ld_cplx(blk, bidx(site, 0, n, i, j)), v[j]);
       for (int mu = 0; mu < 4; ++mu) {
         if (hop_internal(g, c, mu, +1, g.B)) {
           const int nl = geom_neighbor(g, c, mu, +1) - b * g.vB;
           v = rs + (size_t)nl * n;
 #pragma unroll 8
-          for (int j = 0; j < n; ++j) cfma(p, blk[bidx(site, 1 + mu, n, i, j)], v[j]);
+          for (int j = 0; j < n; ++j) cfma(p, ld_cplx(blk, bidx(site, 1 + mu, n, i, j)), v[j]);
         }
         if (hop_internal(g, c, mu, -1, g.B)) {
           const int nl = geom_neighbor(g, c, mu, -1) - b * g.vB;
           v = rs + (size_t)nl * n;
 #pragma unroll 8
-          for (int j = 0; j < n; ++j) cfma(p, blk[bidx(site, 5 + mu, n, i, j)], v[j]);
+          for (int j = 0; j < n; ++j) cfma(p, ld_cplx(blk, bidx(site, 5 + mu, n, i, j)), v[j]);
         }
       }
+      p = sc * p;
       const cplx<T> tt = cdotc(p, r);
       nre = tt.re;
       nim = tt.im;
@@ -278,10 +286,10 @@ __global__ void k_coarse_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict_
 // over the cluster from per-CTA partials in rank order, so every CTA computes
 // the same alpha.  Same arithmetic as k_coarse_sap: rho = (b - D z)_B, k MR
 // steps on D_B (hops leaving the block dropped), z_B += e_B.
-template <typename T>
+template <typename T, typename BS>
 __global__ void k_coarse_sap_cluster(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
-                                     const cplx<T>* __restrict__ blk, Geom g, int n, size_t rstride,
-                                     const int* __restrict__ blocks, int k_mr, int spc) {
+                                     const BS* __restrict__ blk, const float* __restrict__ bscale, Geom g, int n,
+                                     size_t rstride, const int* __restrict__ blocks, int k_mr, int spc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
   const int CLS = (int)cluster.num_blocks();
@@ -313,15 +321,16 @@ __global__ void k_coarse_sap_cluster(cplx<T>* __restrict__ z, const cplx<T>* __r
     }
     nloc = nb - b * vB;
   }
-  const cplx<T>* M = blk + (((size_t)site * 9 + (k < 9 ? k : 0)) * n) * n + i;
+  const BS* M = blk + (((size_t)site * 9 + (k < 9 ? k : 0)) * n) * n + i;
+  const T sc = bscale ? T(bscale[site]) : T(1);
   // rho = b - D z on the own rows (all 9 blocks, neighbours read from z)
   {
     cplx<T> acc = czero<T>();
     if (k < 9) {
       const cplx<T>* v = z + ro + (size_t)nb * n;
 #pragma unroll 8
-      for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], v[j]);
-      part[k * rows + rl] = acc;
+      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), v[j]);
+      part[k * rows + rl] = sc * acc;
     }
   }
   __syncthreads();
@@ -342,9 +351,9 @@ __global__ void k_coarse_sap_cluster(cplx<T>* __restrict__ z, const cplx<T>* __r
       if (kin) {
         const cplx<T>* v = rfull + (size_t)nloc * n;
 #pragma unroll 8
-        for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], v[j]);
+        for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), v[j]);
       }
-      part[k * rows + rl] = acc;
+      part[k * rows + rl] = sc * acc;
     }
     __syncthreads();
     cplx<T> p = czero<T>();
@@ -522,9 +531,39 @@ __global__ void k_blocks_export(cplx<double>* __restrict__ dst, const cplx<doubl
   dst[lex * per + (size_t)k * n * n + (size_t)i * n + j] = blk[bidx(site, k, n, i, j)];
 }
 
+// FP16 copy of one site's 9 blocks: s = float(max |re|, |im|), q = RNE_half(x / s)
+__global__ void k_blocks_to_half(__half2* __restrict__ dst, float* __restrict__ scale,
+                                 const cplx<double>* __restrict__ blk, int n) {
+  __shared__ double sh[32];
+  const size_t per = (size_t)9 * n * n;
+  const cplx<double>* src = blk + (size_t)blockIdx.x * per;
+  double mx = 0.0;
+  for (size_t e = threadIdx.x; e < per; e += blockDim.x) mx = fmax(mx, fmax(fabs(src[e].re), fabs(src[e].im)));
+  for (int off = 16; off >= 1; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    const float sf = m > 0.0 ? (float)m : 1.0f;
+    scale[blockIdx.x] = sf;
+    sh[0] = (double)sf;
+  }
+  __syncthreads();
+  const double sc = sh[0];
+  __half2* d = dst + (size_t)blockIdx.x * per;
+  for (size_t e = threadIdx.x; e < per; e += blockDim.x)
+    d[e] = __halves2half2(__double2half(src[e].re / sc), __double2half(src[e].im / sc));
+}
+
 }  // namespace
 
 namespace dd {
+
+void blocks_to_half(__half2* dst, float* scale, const cplx<double>* blk, int V, int n, cudaStream_t st) {
+  count_launch();
+  k_blocks_to_half<<<V, 256, 0, st>>>(dst, scale, blk, n);
+}
 
 template <typename T>
 size_t coarse_sap_cluster_smem(int vB, int n, int spc) {
@@ -538,10 +577,23 @@ void coarse_apply(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const Coars
   const size_t sm = (size_t)18 * op.n * sizeof(cplx<T>);
   dim3 grid(op.g.V, nrhs);
   count_launch();
+  if constexpr (sizeof(T) == 4) {
+    if (op.blkh) {
+      if (b)
+        k_coarse_apply<float, true, __half2><<<grid, threads, sm, st>>>(out, in, b, op.blkh, op.bscale, op.g, op.n,
+                                                                         rstride, sel, sel_mu, in_chir);
+      else
+        k_coarse_apply<float, false, __half2><<<grid, threads, sm, st>>>(out, in, b, op.blkh, op.bscale, op.g, op.n,
+                                                                          rstride, sel, sel_mu, in_chir);
+      return;
+    }
+  }
   if (b)
-    k_coarse_apply<T, true><<<grid, threads, sm, st>>>(out, in, b, op.blk, op.g, op.n, rstride, sel, sel_mu, in_chir);
+    k_coarse_apply<T, true, cplx<T>><<<grid, threads, sm, st>>>(out, in, b, op.blk, nullptr, op.g, op.n, rstride, sel,
+                                                                 sel_mu, in_chir);
   else
-    k_coarse_apply<T, false><<<grid, threads, sm, st>>>(out, in, b, op.blk, op.g, op.n, rstride, sel, sel_mu, in_chir);
+    k_coarse_apply<T, false, cplx<T>><<<grid, threads, sm, st>>>(out, in, b, op.blk, nullptr, op.g, op.n, rstride,
+                                                                  sel, sel_mu, in_chir);
 }
 
 // cluster plan of the coarse SAP: cluster size CLS and sites per CTA (0 if no plan fits)
@@ -553,7 +605,11 @@ int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out) {
     const int threads = ((9 * spc * n + 31) / 32) * 32;
     if (threads > 1024) continue;
     const size_t sm = coarse_sap_cluster_smem<T>(g.vB, n, spc);
-    if (CLS > 8) cudaFuncSetAttribute(k_coarse_sap_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (CLS > 8) {
+      cudaFuncSetAttribute(k_coarse_sap_cluster<T, cplx<T>>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if constexpr (sizeof(T) == 4)
+        cudaFuncSetAttribute(k_coarse_sap_cluster<float, __half2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -566,7 +622,7 @@ int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_sap_cluster<T>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_sap_cluster<T, cplx<T>>, &cfg) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -597,9 +653,19 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    if (cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T>, z, b, (const cplx<T>*)op.blk, op.g, op.n, rstride, blocks,
-                           k_mr, spc) == cudaSuccess)
-      return;
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+      if (op.blkh)
+        e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<float, __half2>, z, b, op.blkh, op.bscale, op.g, op.n,
+                               rstride, blocks, k_mr, spc);
+      else
+        e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
+                               (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc);
+    } else {
+      e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
+                             (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc);
+    }
+    if (e == cudaSuccess) return;
     cudaGetLastError();   // cluster launch refused: run the one-CTA-per-block kernel instead
   }
   const int threads = ((op.g.vB * op.n + 31) / 32) * 32;
@@ -607,11 +673,21 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
   static bool attr_set[2] = {false, false};
   bool& done = attr_set[sizeof(T) == 8];
   if (!done) {
-    cudaFuncSetAttribute(k_coarse_sap<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_coarse_sap<T, cplx<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if constexpr (sizeof(T) == 4)
+      cudaFuncSetAttribute(k_coarse_sap<float, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     done = true;
   }
   count_launch();
-  k_coarse_sap<T><<<dim3(nblocks, nrhs), threads, sm, st>>>(z, b, op.blk, op.g, op.n, rstride, blocks, k_mr);
+  if constexpr (sizeof(T) == 4) {
+    if (op.blkh) {
+      k_coarse_sap<float, __half2><<<dim3(nblocks, nrhs), threads, sm, st>>>(z, b, op.blkh, op.bscale, op.g, op.n,
+                                                                            rstride, blocks, k_mr);
+      return;
+    }
+  }
+  k_coarse_sap<T, cplx<T>><<<dim3(nblocks, nrhs), threads, sm, st>>>(z, b, op.blk, nullptr, op.g, op.n, rstride,
+                                                                      blocks, k_mr);
 }
 
 template <typename T>
@@ -620,8 +696,15 @@ void coarse_schur_odd(cplx<T>* t, const cplx<T>* x, const cplx<T>* b, const Coar
   const int threads = ((8 * op.n + 31) / 32) * 32;
   const size_t sm = (size_t)17 * op.n * sizeof(cplx<T>);
   count_launch();
-  k_schur_odd<T><<<dim3(op.n_odd, nrhs), threads, sm, st>>>(t, x, b, op.blk, op.selfinv, op.odd_sites, op.g, op.n,
-                                                            rstride, a, c);
+  if constexpr (sizeof(T) == 4) {
+    if (op.blkh) {
+      k_schur_odd<float, __half2><<<dim3(op.n_odd, nrhs), threads, sm, st>>>(t, x, b, op.blkh, op.bscale, op.selfinv,
+                                                                             op.odd_sites, op.g, op.n, rstride, a, c);
+      return;
+    }
+  }
+  k_schur_odd<T, cplx<T>><<<dim3(op.n_odd, nrhs), threads, sm, st>>>(t, x, b, op.blk, nullptr, op.selfinv,
+                                                                      op.odd_sites, op.g, op.n, rstride, a, c);
 }
 
 template <typename T>
@@ -630,7 +713,15 @@ void coarse_schur_even(cplx<T>* y, const cplx<T>* x, const cplx<T>* t, const cpl
   const int threads = ((9 * op.n + 31) / 32) * 32;
   const size_t sm = (size_t)18 * op.n * sizeof(cplx<T>);
   count_launch();
-  k_schur_even<T><<<dim3(op.g.V, nrhs), threads, sm, st>>>(y, x, t, b, op.blk, op.g, op.n, rstride, a, s, c);
+  if constexpr (sizeof(T) == 4) {
+    if (op.blkh) {
+      k_schur_even<float, __half2><<<dim3(op.g.V, nrhs), threads, sm, st>>>(y, x, t, b, op.blkh, op.bscale, op.g, op.n,
+                                                                            rstride, a, s, c);
+      return;
+    }
+  }
+  k_schur_even<T, cplx<T>><<<dim3(op.g.V, nrhs), threads, sm, st>>>(y, x, t, b, op.blk, nullptr, op.g, op.n, rstride,
+                                                                     a, s, c);
 }
 
 void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int n, int* err, cudaStream_t st) {

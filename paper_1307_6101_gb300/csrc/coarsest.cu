@@ -79,6 +79,8 @@ __device__ Smem<T> carve(unsigned char* base, int m, int nep, int nop, int n, in
 template <typename T>
 struct Ctx {
   const cplx<T>* blk;
+  const __half2* blkh;     // FP16 blocks (FP32 compute only) or null
+  const float* bscale;     // per-site scale of blkh
   const cplx<T>* inv;
   const int* even;
   const int* odd;
@@ -86,6 +88,25 @@ struct Ctx {
   const int* nbr_o_of_e;   // [n_e][8]
   int n_e, n_o, nep, nop, n, CL, rank;
 };
+
+// acc += sum_j M(site, k)[i][j] xv[j] from the compute-precision or the FP16 blocks
+template <typename T>
+__device__ __forceinline__ cplx<T> block_row(const Ctx<T>& cx, int site, int k, int i, const cplx<T>* xv) {
+  const int n = cx.n;
+  cplx<T> acc = czero<T>();
+  if constexpr (sizeof(T) == 4) {
+    if (cx.blkh) {
+      const __half2* M = cx.blkh + bidx(site, k, n, i, 0);
+#pragma unroll 8
+      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), xv[j]);
+      return T(cx.bscale[site]) * acc;
+    }
+  }
+  const cplx<T>* M = cx.blk + bidx(site, k, n, i, 0);
+#pragma unroll 8
+  for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], xv[j]);
+  return acc;
+}
 
 // t(own odd) = S^{-1} ( a*bo + c * sum_k D_k(o) v(even nbr_k) ), v read from the owners' array `src`
 template <typename T>
@@ -108,12 +129,7 @@ __device__ void odd_phase(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group&
       const int k = threadIdx.x / n, i = threadIdx.x - (threadIdx.x / n) * n;
       if (k < 8) {
         cplx<T> acc = czero<T>();
-        if (c != T(0)) {
-          const cplx<T>* M = cx.blk + bidx(site, 1 + k, n, i, 0);
-          const cplx<T>* xv = s.xs + k * n;
-#pragma unroll 8
-          for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], xv[j]);
-        }
+        if (c != T(0)) acc = block_row(cx, site, 1 + k, i, s.xs + k * n);
         s.part[k * n + i] = acc;
       }
     }
@@ -165,12 +181,7 @@ __device__ void even_phase(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group
       if (k < 9) {
         cplx<T> acc = czero<T>();
         const T w = k == 0 ? sc : c;
-        if (w != T(0)) {
-          const cplx<T>* M = cx.blk + bidx(site, k, n, i, 0);
-          const cplx<T>* xv = s.xs + k * n;
-#pragma unroll 8
-          for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], xv[j]);
-        }
+        if (w != T(0)) acc = block_row(cx, site, k, i, s.xs + k * n);
         s.part[k * n + i] = w * acc;
       }
     }
@@ -463,6 +474,8 @@ cudaError_t coarsest_cluster_solve(cplx<T>* x, const cplx<T>* b, const CoarseOp<
                                    int* iters, cudaStream_t st) {
   Ctx<T> cx;
   cx.blk = op.blk;
+  cx.blkh = op.blkh;
+  cx.bscale = op.bscale;
   cx.inv = op.selfinv;
   cx.even = geo.even;
   cx.odd = geo.odd;

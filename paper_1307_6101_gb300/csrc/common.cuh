@@ -15,6 +15,7 @@
 // contiguous index ranges.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -56,6 +57,16 @@ template <typename T> DD_HD T cnorm2(cplx<T> a) { return a.re * a.re + a.im * a.
 
 template <typename To, typename From> DD_HD cplx<To> ccast(cplx<From> a) {
   return cmk<To>(static_cast<To>(a.re), static_cast<To>(a.im));
+}
+
+// Storage loads: operator data is held in the compute precision, or in FP16
+// (__half / __half2 = one complex) and widened to FP32 on load.
+template <typename T> DD_HD T ld_real(const T* p, size_t i) { return p[i]; }
+__device__ __forceinline__ float ld_real(const __half* p, size_t i) { return __half2float(p[i]); }
+template <typename T> DD_HD cplx<T> ld_cplx(const cplx<T>* p, size_t i) { return p[i]; }
+__device__ __forceinline__ cplx<float> ld_cplx(const __half2* p, size_t i) {
+  const float2 f = __half22float2(p[i]);
+  return cmk<float>(f.x, f.y);
 }
 
 // ---------------------------------------------------------------------------

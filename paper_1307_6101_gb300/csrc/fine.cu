@@ -106,21 +106,23 @@ DD_HD void hop_accumulate(int mu, bool fwd, const cplx<T> u[9], const cplx<T> ps
 // packed Hermitian 6x6: 6 real diagonals, then the 15 upper off-diagonals (row-major) as re, im
 DD_HD int herm_off(int i, int j) { return i * 6 - (i * (i + 1)) / 2 + (j - i - 1); }
 
-template <typename T>
-DD_HD void clover_apply(const T* __restrict__ clov, int V, int x, const cplx<T> in[12], cplx<T> out[12]) {
+// out = (A + shift) in for the two packed Hermitian 6x6 blocks (shift on the diagonal)
+template <typename T, typename CS>
+DD_HD void clover_apply(const CS* __restrict__ clov, int V, int x, const cplx<T> in[12], cplx<T> out[12],
+                        T shift = T(0)) {
 #pragma unroll
   for (int ch = 0; ch < 2; ++ch) {
-    const T* a = clov + (size_t)ch * 36 * V + x;
+    const CS* a = clov + (size_t)ch * 36 * V + x;
     const cplx<T>* v = in + 6 * ch;
     cplx<T>* w = out + 6 * ch;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) w[i] = a[(size_t)i * V] * v[i];
+    for (int i = 0; i < 6; ++i) w[i] = (T(ld_real(a, (size_t)i * V)) + shift) * v[i];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
 #pragma unroll
       for (int j = i + 1; j < 6; ++j) {
         const int p = 6 + 2 * herm_off(i, j);
-        cplx<T> e = cmk<T>(a[(size_t)p * V], a[(size_t)(p + 1) * V]);
+        cplx<T> e = cmk<T>(T(ld_real(a, (size_t)p * V)), T(ld_real(a, (size_t)(p + 1) * V)));
         cfma(w[i], e, v[j]);
         cfmac(w[j], e, v[i]);
       }
@@ -128,10 +130,10 @@ DD_HD void clover_apply(const T* __restrict__ clov, int V, int x, const cplx<T> 
   }
 }
 
-template <typename T>
-DD_HD void load_link(const cplx<T>* __restrict__ U, int V, int mu, int x, cplx<T> u[9]) {
+template <typename T, typename LS>
+DD_HD void load_link(const LS* __restrict__ U, int V, int mu, int x, cplx<T> u[9]) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) u[k] = U[(size_t)(mu * 9 + k) * V + x];
+  for (int k = 0; k < 9; ++k) u[k] = ld_cplx(U, (size_t)(mu * 9 + k) * V + x);
 }
 
 template <typename T>
@@ -144,11 +146,11 @@ DD_HD void load_spinor(const cplx<T>* __restrict__ p, int V, int x, cplx<T> s[12
 }
 
 // ---------------------------------------------------------------------------
-template <typename T, bool RESID>
+template <typename T, bool RESID, typename LS, typename CS>
 __global__ void k_fine_dslash(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in,
-                              const cplx<T>* __restrict__ bsrc, const cplx<T>* __restrict__ U,
-                              const T* __restrict__ clov, Geom g, int bc_t, size_t rstride,
-                              int sel, int sel_mu, int in_chir) {
+                              const cplx<T>* __restrict__ bsrc, const LS* __restrict__ U,
+                              const CS* __restrict__ clov, Geom g, int bc_t, size_t rstride,
+                              int sel, int sel_mu, int in_chir, T shift) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.V) return;
   const size_t ro = (size_t)blockIdx.y * rstride;
@@ -186,7 +188,7 @@ __global__ void k_fine_dslash(cplx<T>* __restrict__ out, const cplx<T>* __restri
   cplx<T> d[12];
   if (sel == SEL_FULL || sel == SEL_AGG_SELF) {
     load_spinor(ps, V, x, nb, T(1), in_chir);
-    clover_apply(clov, V, x, nb, d);
+    clover_apply(clov, V, x, nb, d, shift);
   } else {
 #pragma unroll
     for (int k = 0; k < 12; ++k) d[k] = czero<T>();
@@ -235,11 +237,11 @@ __device__ void seg_sum3(T& a, T& b, T& c, int seg, T* scratch) {
 // terms of z: the black sweep's rho = b - D z sees the red update, which is the
 // same as r - D e with e the red correction.  One CTA segment of `seg` threads
 // per block, one thread per site; the block's residual lives in shared memory.
-template <typename T>
+template <typename T, typename LS, typename CS>
 __global__ void k_fine_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
-                           const cplx<T>* __restrict__ U, const T* __restrict__ clov, Geom g, int bc_t,
+                           const LS* __restrict__ U, const CS* __restrict__ clov, Geom g, int bc_t,
                            size_t rstride, const int* __restrict__ blocks, int nblocks, int seg,
-                           int k_mr) {
+                           int k_mr, T shift) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);            // [blockDim.x][12]
   T* scratch = reinterpret_cast<T*>(rs + (size_t)blockDim.x * 12);  // [warps][3]
@@ -275,7 +277,7 @@ __global__ void k_fine_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ 
       hop_accumulate(mu, false, u, nb, acc);
     }
     load_spinor(pz, V, x, nb, T(1), -1);
-    clover_apply(clov, V, x, nb, p);
+    clover_apply(clov, V, x, nb, p, shift);
     const cplx<T>* pb = bsrc + ro;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -316,7 +318,7 @@ __global__ void k_fine_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ 
           hop_accumulate(mu, false, u, nb, acc);
         }
       }
-      clover_apply(clov, V, x, r, p);
+      clover_apply(clov, V, x, r, p, shift);
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         p[k] = p[k] - T(0.5) * acc[k];
@@ -387,16 +389,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
   return true;
 }
 
-template <typename T>
+template <typename T, typename LS, typename CS>
 __global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
-                                                      const cplx<T>* __restrict__ U, const T* __restrict__ clov, Geom g,
+                                                      const LS* __restrict__ U, const CS* __restrict__ clov, Geom g,
                                                       int bc_t, size_t rstride, int nrhs, const int* __restrict__ blocks,
-                                                      int nblocks, int seg, int k_mr, int* err) {
+                                                      int nblocks, int seg, int k_mr, int* err, T shift) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int vB = g.vB;
   const int segs = blockDim.x / seg;
-  // per segment: links [36][vB] cplx, clover [72][vB] T, residual [12][vB] cplx
-  const size_t seg_bytes = (size_t)vB * (36 * sizeof(cplx<T>) + 72 * sizeof(T) + 12 * sizeof(cplx<T>));
+  // per segment: links [36][vB] LS, clover [72][vB] CS, residual [12][vB] cplx
+  const size_t seg_bytes = (size_t)vB * (36 * sizeof(LS) + 72 * sizeof(CS) + 12 * sizeof(cplx<T>));
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + (size_t)segs * seg_bytes);
   T* scratch = reinterpret_cast<T*>(bar + 2);
   const int s = threadIdx.x / seg;
@@ -405,8 +407,8 @@ __global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, c
   const bool active = (bi < nblocks) && (loc < vB);
   const int blk = (bi < nblocks) ? blocks[bi] : 0;
   unsigned char* sb = smem_raw + (size_t)s * seg_bytes;
-  cplx<T>* Ls = reinterpret_cast<cplx<T>*>(sb);
-  T* Cs = reinterpret_cast<T*>(Ls + 36 * vB);
+  LS* Ls = reinterpret_cast<LS*>(sb);
+  CS* Cs = reinterpret_cast<CS*>(Ls + 36 * vB);
   cplx<T>* Rs = reinterpret_cast<cplx<T>*>(Cs + 72 * vB);
   const int V = g.V;
   // stage the operator of every segment's block
@@ -415,20 +417,20 @@ __global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, c
   if (threadIdx.x < 32) {
     int nseg = 0;
     for (int q = 0; q < segs; ++q) nseg += (blockIdx.x * segs + q < nblocks) ? 1 : 0;
-    const unsigned bytes = (unsigned)(nseg * vB * (36 * sizeof(cplx<T>) + 72 * sizeof(T)));
+    const unsigned bytes = (unsigned)(nseg * vB * (36 * sizeof(LS) + 72 * sizeof(CS)));
     if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, bytes);
     __syncwarp();
     for (int q = 0; q < nseg; ++q) {
       const int bq = blocks[blockIdx.x * segs + q];
       unsigned char* sq = smem_raw + (size_t)q * seg_bytes;
-      cplx<T>* Lq = reinterpret_cast<cplx<T>*>(sq);
-      T* Cq = reinterpret_cast<T*>(Lq + 36 * vB);
+      LS* Lq = reinterpret_cast<LS*>(sq);
+      CS* Cq = reinterpret_cast<CS*>(Lq + 36 * vB);
       for (int cpy = threadIdx.x; cpy < 108; cpy += 32) {
         if (cpy < 36)
-          bulk_g2s(Lq + (size_t)cpy * vB, U + (size_t)cpy * V + (size_t)bq * vB, (unsigned)(vB * sizeof(cplx<T>)), bar);
+          bulk_g2s(Lq + (size_t)cpy * vB, U + (size_t)cpy * V + (size_t)bq * vB, (unsigned)(vB * sizeof(LS)), bar);
         else
           bulk_g2s(Cq + (size_t)(cpy - 36) * vB, clov + (size_t)(cpy - 36) * V + (size_t)bq * vB,
-                   (unsigned)(vB * sizeof(T)), bar);
+                   (unsigned)(vB * sizeof(CS)), bar);
       }
     }
   }
@@ -476,17 +478,17 @@ __global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, c
         load_spinor(pz, V, n, nb, nsign[k], -1);
         if (fwd) {
 #pragma unroll
-          for (int q = 0; q < 9; ++q) u[q] = Ls[(size_t)(mu * 9 + q) * vB + loc];
+          for (int q = 0; q < 9; ++q) u[q] = ld_cplx(Ls, (size_t)(mu * 9 + q) * vB + loc);
         } else if (nslot[k] >= 0) {
 #pragma unroll
-          for (int q = 0; q < 9; ++q) u[q] = Ls[(size_t)(mu * 9 + q) * vB + nslot[k]];
+          for (int q = 0; q < 9; ++q) u[q] = ld_cplx(Ls, (size_t)(mu * 9 + q) * vB + nslot[k]);
         } else {
           load_link(U, V, mu, n, u);
         }
         hop_accumulate(mu, fwd, u, nb, acc);
       }
       load_spinor(pz, V, x, nb, T(1), -1);
-      clover_apply(Cs, vB, loc, nb, p);
+      clover_apply(Cs, vB, loc, nb, p, shift);
       const cplx<T>* pb = bsrc + (size_t)rh * rstride;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
@@ -519,10 +521,10 @@ __global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, c
           for (int q = 0; q < 12; ++q) nb[q] = nsign[k] * Rs[(size_t)q * vB + sl];
           const int ls = fwd ? loc : sl;
 #pragma unroll
-          for (int q = 0; q < 9; ++q) u[q] = Ls[(size_t)(mu * 9 + q) * vB + ls];
+          for (int q = 0; q < 9; ++q) u[q] = ld_cplx(Ls, (size_t)(mu * 9 + q) * vB + ls);
           hop_accumulate(mu, fwd, u, nb, acc);
         }
-        clover_apply(Cs, vB, loc, r, p);
+        clover_apply(Cs, vB, loc, r, p, shift);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           p[k] = p[k] - T(0.5) * acc[k];
@@ -786,59 +788,118 @@ void fine_dslash(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const FineOp
                  size_t rstride, int sel, int sel_mu, int in_chir, cudaStream_t st) {
   dim3 grid(div_up(op.g.V, 128), nrhs);
   count_launch();
+  if constexpr (sizeof(T) == 4) {
+    if (op.Uh) {
+      const float sh = op.shift;
+      if (b)
+        k_fine_dslash<float, true, __half2, __half><<<grid, 128, 0, st>>>(out, in, b, op.Uh, op.clovh, op.g, op.bc_t,
+                                                                          rstride, sel, sel_mu, in_chir, sh);
+      else
+        k_fine_dslash<float, false, __half2, __half><<<grid, 128, 0, st>>>(out, in, b, op.Uh, op.clovh, op.g, op.bc_t,
+                                                                           rstride, sel, sel_mu, in_chir, sh);
+      return;
+    }
+  }
   if (b)
-    k_fine_dslash<T, true><<<grid, 128, 0, st>>>(out, in, b, op.U, op.clov, op.g, op.bc_t, rstride, sel, sel_mu,
-                                                  in_chir);
+    k_fine_dslash<T, true, cplx<T>, T><<<grid, 128, 0, st>>>(out, in, b, op.U, op.clov, op.g, op.bc_t, rstride, sel,
+                                                             sel_mu, in_chir, T(0));
   else
-    k_fine_dslash<T, false><<<grid, 128, 0, st>>>(out, in, b, op.U, op.clov, op.g, op.bc_t, rstride, sel,
-                                                   sel_mu, in_chir);
+    k_fine_dslash<T, false, cplx<T>, T><<<grid, 128, 0, st>>>(out, in, b, op.U, op.clov, op.g, op.bc_t, rstride,
+                                                              sel, sel_mu, in_chir, T(0));
 }
 
-// the staged kernel needs: FP32, the SAP block tiling the aggregate (inner tile),
-// 16-byte aligned component runs, and the staged block fitting in shared memory
+// the staged kernel needs: FP32 compute, the SAP block tiling the aggregate
+// (inner tile), 16-byte aligned component runs, and the staged block fitting in
+// shared memory
 template <typename T>
 bool sap_tma_ok(const FineOp<T>& op) {
   if (sizeof(T) != 4) return false;
   for (int d = 0; d < 4; ++d)
     if (op.g.I[d] != op.g.B[d]) return false;
-  if (op.g.vB % 4 || op.g.V % 4 || op.g.vB > 256) return false;
+  const int q = op.Uh ? 8 : 4;
+  if (op.g.vB % q || op.g.V % q || op.g.vB > 256) return false;
   return true;
 }
 
-template <typename T>
-void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int* blocks, int nblocks, int nrhs,
-                    size_t rstride, int k_mr, cudaStream_t st) {
-  if (sap_tma_ok(op) && op.err) {
-    int seg = 1;
-    while (seg < op.g.vB) seg <<= 1;
-    const int threads = 256;
-    const int segs = threads / seg;
-    const size_t seg_bytes = (size_t)op.g.vB * (36 * sizeof(cplx<T>) + 72 * sizeof(T) + 12 * sizeof(cplx<T>));
-    const size_t sm = segs * seg_bytes + 16 + (threads / 32) * 3 * sizeof(T) + 16;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_fine_sap_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      attr = true;
-    }
-    count_launch();
-    k_fine_sap_tma<T><<<div_up(nblocks, segs), threads, sm, st>>>(z, b, op.U, op.clov, op.g, op.bc_t, rstride, nrhs,
-                                                                   blocks, nblocks, seg, k_mr, op.err);
-    return;
+template <typename T, typename LS, typename CS>
+void launch_sap_tma(cplx<T>* z, const cplx<T>* b, const LS* U, const CS* clov, const FineOp<T>& op, const int* blocks,
+                    int nblocks, int nrhs, size_t rstride, int k_mr, T shift, cudaStream_t st) {
+  int seg = 1;
+  while (seg < op.g.vB) seg <<= 1;
+  const int threads = 256;
+  const int segs = threads / seg;
+  const size_t seg_bytes = (size_t)op.g.vB * (36 * sizeof(LS) + 72 * sizeof(CS) + 12 * sizeof(cplx<T>));
+  const size_t sm = segs * seg_bytes + 16 + (threads / 32) * 3 * sizeof(T) + 16;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fine_sap_tma<T, LS, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
   }
+  count_launch();
+  k_fine_sap_tma<T, LS, CS><<<div_up(nblocks, segs), threads, sm, st>>>(z, b, U, clov, op.g, op.bc_t, rstride, nrhs,
+                                                                       blocks, nblocks, seg, k_mr, op.err, shift);
+}
+
+template <typename T, typename LS, typename CS>
+void launch_sap_plain(cplx<T>* z, const cplx<T>* b, const LS* U, const CS* clov, const FineOp<T>& op,
+                      const int* blocks, int nblocks, int nrhs, size_t rstride, int k_mr, T shift, cudaStream_t st) {
   int seg = 1;
   while (seg < op.g.vB) seg <<= 1;
   const int threads = seg >= 256 ? seg : 256;
   const int segs = threads / seg;
   const size_t sm = (size_t)threads * 12 * sizeof(cplx<T>) + (size_t)(threads / 32) * 3 * sizeof(T);
-  static bool attr_set[2] = {false, false};
-  bool& done = attr_set[sizeof(T) == 8];
-  if (!done) {
-    cudaFuncSetAttribute(k_fine_sap<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    done = true;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fine_sap<T, LS, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
   }
   dim3 grid(div_up(nblocks, segs), nrhs);
   count_launch();
-  k_fine_sap<T><<<grid, threads, sm, st>>>(z, b, op.U, op.clov, op.g, op.bc_t, rstride, blocks, nblocks, seg, k_mr);
+  k_fine_sap<T, LS, CS><<<grid, threads, sm, st>>>(z, b, U, clov, op.g, op.bc_t, rstride, blocks, nblocks, seg, k_mr,
+                                                   shift);
+}
+
+template <typename T>
+void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int* blocks, int nblocks, int nrhs,
+                    size_t rstride, int k_mr, cudaStream_t st) {
+  const bool tma = sap_tma_ok(op) && op.err;
+  if constexpr (sizeof(T) == 4) {
+    if (op.Uh) {
+      if (tma)
+        launch_sap_tma<float, __half2, __half>(z, b, op.Uh, op.clovh, op, blocks, nblocks, nrhs, rstride, k_mr,
+                                               op.shift, st);
+      else
+        launch_sap_plain<float, __half2, __half>(z, b, op.Uh, op.clovh, op, blocks, nblocks, nrhs, rstride, k_mr,
+                                                 op.shift, st);
+      return;
+    }
+  }
+  if (tma)
+    launch_sap_tma<T, cplx<T>, T>(z, b, op.U, op.clov, op, blocks, nblocks, nrhs, rstride, k_mr, T(0), st);
+  else
+    launch_sap_plain<T, cplx<T>, T>(z, b, op.U, op.clov, op, blocks, nblocks, nrhs, rstride, k_mr, T(0), st);
+}
+
+__global__ void k_links_to_half(__half2* __restrict__ dst, const cplx<double>* __restrict__ U, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __halves2half2(__double2half(U[i].re), __double2half(U[i].im));
+}
+
+__global__ void k_clover_to_half(__half* __restrict__ dst, const double* __restrict__ A, int V, double shift) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)72 * V) return;
+  const int comp = (int)(i / V) % 36;   // 0..5: diagonal of the chirality block
+  dst[i] = __double2half(comp < 6 ? A[i] - shift : A[i]);
+}
+
+void links_to_half(__half2* dst, const cplx<double>* U, size_t n, cudaStream_t st) {
+  count_launch();
+  k_links_to_half<<<div_up(n, 256), 256, 0, st>>>(dst, U, n);
+}
+
+void clover_to_half(__half* dst, const double* A, int V, double shift, cudaStream_t st) {
+  count_launch();
+  k_clover_to_half<<<div_up((size_t)72 * V, 256), 256, 0, st>>>(dst, A, V, shift);
 }
 
 void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, double m0, double csw,

@@ -16,6 +16,10 @@ struct FineOp {
   cplx<T>* U;    // [4][9][V]
   T* clov;       // [2][36][V]  (m0 + 4) + clover, packed Hermitian
   int* err;      // device error flag (bounded waits), may be null
+  // FP16 storage (FP32 compute only): when Uh is set the kernels read these instead
+  const __half2* Uh = nullptr;   // [4][9][V] links
+  const __half* clovh = nullptr; // [2][36][V] clover term without the (m0 + 4) shift
+  float shift = 0.f;             // m0 + 4, added to the diagonal in FP32
 };
 
 template <typename T>
@@ -27,6 +31,9 @@ struct CoarseOp {
   const int* odd_sites; // indices of the odd sites (coarsest level), or null
   int n_odd;
   int sap_cls;          // cluster size of the cluster SAP kernel (0: one CTA per SAP block)
+  // FP16 storage (FP32 compute only): blocks and one scale per site
+  const __half2* blkh = nullptr;
+  const float* bscale = nullptr;
 };
 
 // ---- fine level -----------------------------------------------------------
@@ -43,6 +50,9 @@ int fine_residual_norm_noalloc(double* out, bool out_on_device, const cplx<doubl
                                const FineOp<double>& op, int nrhs, cudaStream_t st, const char** msg);
 void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, double m0, double csw,
                   cudaStream_t st);
+// FP16 copies: links (no scale, |U_ab| <= 1) and the clover term A - shift (no scale)
+void links_to_half(__half2* dst, const cplx<double>* U, size_t n, cudaStream_t st);
+void clover_to_half(__half* dst, const double* A, int V, double shift, cudaStream_t st);
 template <typename T>
 void links_import(cplx<T>* U, const cplx<double>* gauge_lex, const Geom& g, cudaStream_t st);
 template <typename T>
@@ -81,6 +91,8 @@ template <typename T>
 void coarse_export(cplx<double>* dst, const cplx<T>* src, const Geom& g, int n, int nrhs, size_t rstride,
                    cudaStream_t st);
 void coarse_blocks_export(cplx<double>* dst, const cplx<double>* blk, const Geom& g, int n, cudaStream_t st);
+// FP16 copy of the blocks with one scale per site: s = max |re|, |im| over the site's 9 blocks
+void blocks_to_half(__half2* dst, float* scale, const cplx<double>* blk, int V, int n, cudaStream_t st);
 
 // ---- coarsest level: cluster-resident odd-even GMRES ---------------------------
 struct CoarsestPlanIn {
@@ -106,14 +118,18 @@ cudaError_t coarsest_cluster_solve(cplx<T>* x, const cplx<T>* b, const CoarseOp<
 
 // ---- transfer ---------------------------------------------------------------
 // out(A)[s*N + j] = sum_{x in A, f in s} conj(P_j(x, f)) in(x, f)
+// (Ph, pscale): optional FP16 copy of P with per-(aggregate, chirality) scales (FP32 compute only)
 template <typename T>
 void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine,
                  int n, int N, int nrhs, size_t in_rstride, size_t out_rstride, size_t out_site_stride,
-                 cudaStream_t st);
+                 cudaStream_t st, const __half2* Ph = nullptr, const float* pscale = nullptr);
 // out(x, f) = [out +] sum_j P_j(x, f) in(A(x))[s(f)*N + j]
 template <typename T>
 void prolong_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine, int n,
-                int N, int nrhs, size_t out_rstride, size_t in_rstride, bool accumulate, cudaStream_t st);
+                int N, int nrhs, size_t out_rstride, size_t in_rstride, bool accumulate, cudaStream_t st,
+                const __half2* Ph = nullptr, const float* pscale = nullptr);
+void p_to_half(__half2* Ph, float* pscale, const cplx<double>* P, const Geom& g, bool fine, int n, int N,
+               cudaStream_t st);
 // in-place CGS2 per aggregate and chirality of N fields (FP64); err set on rank deficiency
 void orthonormalise(cplx<double>* P, const Geom& g, bool fine, int n, int N, int* err, cudaStream_t st);
 

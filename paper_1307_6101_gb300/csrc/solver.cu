@@ -68,6 +68,13 @@ struct Level {
   cplx<double>* tv64 = nullptr;
   cplx<double>* P64 = nullptr;
   cplx<float>* P32 = nullptr;
+  // FP16 storage copies read by the FP32 kernels when the handle stores FP16
+  __half2* Uh = nullptr;      // fine links
+  __half* clovh = nullptr;    // fine clover term without the (m0 + 4) shift
+  __half2* Ph = nullptr;      // P_l, one scale per (aggregate, chirality) in pscale
+  float* pscale = nullptr;
+  __half2* blkh = nullptr;    // coarse blocks, one scale per site in bscale
+  float* bscale = nullptr;
   int* blocks[2] = {nullptr, nullptr};
   int nblocks[2] = {0, 0};
   Work<double> w64;
@@ -146,6 +153,8 @@ struct ddamg_handle {
   GraphEntry* capturing = nullptr;
   cplx<double>* pin64 = nullptr;
   cplx<double>* pout64 = nullptr;
+  // FP16 storage of links, clover term, P and coarse blocks under FP32 arithmetic
+  bool half = false;
   // coarsest level on a thread-block cluster
   bool use_cluster = true;
   CoarsestGeo cgeo;
@@ -273,16 +282,20 @@ void apply_D(ddamg_handle* h, Level& L, cplx<T>* out, const cplx<T>* in, const c
 // and the operator once; per block the neighbour values across its faces (and
 // on the fine level the links of the backward hops entering the block)
 template <typename T>
-double sap_bytes(const Level& L, int c, int nrhs) {
+double sap_bytes(const Level& L, int c, int nrhs, bool half) {
   const double cs = 2.0 * sizeof(T);
+  const double os = half ? 4.0 : cs;                   // bytes of one stored operator complex
+  const double rs = half ? 2.0 : (double)sizeof(T);    // bytes of one stored operator real
   const double nsite = (double)L.nblocks[c] * L.g.vB;
   double faces = 0;
   for (int d = 0; d < 4; ++d) faces += (double)L.g.vB / L.g.B[d];
   if (L.fine)
-    return nsite * (nrhs * 36 * cs + 36 * cs + 72 * sizeof(T)) +
-           L.nblocks[c] * (nrhs * 2 * faces * 12 * cs + faces * 9 * cs);
-  return nsite * (nrhs * 3.0 * L.n * cs + 9.0 * L.n * L.n * cs) + L.nblocks[c] * nrhs * 2 * faces * L.n * cs;
+    return nsite * (nrhs * 36 * cs + 36 * os + 72 * rs) + L.nblocks[c] * (nrhs * 2 * faces * 12 * cs + faces * 9 * os);
+  return nsite * (nrhs * 3.0 * L.n * cs + 9.0 * L.n * L.n * os + (half ? 4.0 : 0.0)) +
+         L.nblocks[c] * nrhs * 2 * faces * L.n * cs;
 }
+
+template <typename T> bool half_on(const ddamg_handle* h) { return sizeof(T) == 4 && h->half; }
 
 // iterations x { z <- z + M_SAP (b - D z) }: each SAP application is a red then a black sweep
 template <typename T>
@@ -290,7 +303,7 @@ void sap(ddamg_handle* h, Level& L, cplx<T>* z, const cplx<T>* b, int nrhs, int 
   for (int it = 0; it < iterations; ++it)
     for (int c = 0; c < 2; ++c) {
       if (L.nblocks[c] == 0) continue;
-      Prof pr(h, L.fine ? DDAMG_PROF_FINE_SAP : DDAMG_PROF_COARSE_SAP, sap_bytes<T>(L, c, nrhs));
+      Prof pr(h, L.fine ? DDAMG_PROF_FINE_SAP : DDAMG_PROF_COARSE_SAP, sap_bytes<T>(L, c, nrhs, half_on<T>(h)));
       if (L.fine)
         fine_sap_sweep<T>(z, b, fop<T>(L), L.blocks[c], L.nblocks[c], nrhs, L.vlen, h->p.mr_steps, h->st);
       else
@@ -303,8 +316,11 @@ void restrict_lv(ddamg_handle* h, int l, cplx<T>* out, const cplx<T>* in, int nr
   Level& F = h->lv[l];
   Level& C = h->lv[l + 1];
   const double cs = 2.0 * sizeof(T);
-  Prof pr(h, DDAMG_PROF_TRANSFER, (double)F.vlen * cs * (nrhs + F.N) + (double)C.vlen * cs * nrhs);
-  restrict_op<T>(out, in, Pptr<T>(F), F.g, C.g, F.fine, F.n, F.N, nrhs, F.vlen, C.vlen, C.n, h->st);
+  const bool hf = half_on<T>(h);
+  const double ps = hf ? 4.0 : cs;
+  Prof pr(h, DDAMG_PROF_TRANSFER, (double)F.vlen * (cs * nrhs + ps * F.N) + (double)C.vlen * cs * nrhs);
+  restrict_op<T>(out, in, Pptr<T>(F), F.g, C.g, F.fine, F.n, F.N, nrhs, F.vlen, C.vlen, C.n, h->st,
+                 hf ? F.Ph : nullptr, hf ? F.pscale : nullptr);
 }
 
 template <typename T>
@@ -312,8 +328,12 @@ void prolong_lv(ddamg_handle* h, int l, cplx<T>* out, const cplx<T>* in, int nrh
   Level& F = h->lv[l];
   Level& C = h->lv[l + 1];
   const double cs = 2.0 * sizeof(T);
-  Prof pr(h, DDAMG_PROF_TRANSFER, (double)F.vlen * cs * (nrhs * (acc ? 2 : 1) + F.N) + (double)C.vlen * cs * nrhs);
-  prolong_op<T>(out, in, Pptr<T>(F), F.g, C.g, F.fine, F.n, F.N, nrhs, F.vlen, C.vlen, acc, h->st);
+  const bool hf = half_on<T>(h);
+  const double ps = hf ? 4.0 : cs;
+  Prof pr(h, DDAMG_PROF_TRANSFER,
+          (double)F.vlen * (cs * nrhs * (acc ? 2 : 1) + ps * F.N) + (double)C.vlen * cs * nrhs);
+  prolong_op<T>(out, in, Pptr<T>(F), F.g, C.g, F.fine, F.n, F.N, nrhs, F.vlen, C.vlen, acc, h->st,
+                hf ? F.Ph : nullptr, hf ? F.pscale : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -803,6 +823,53 @@ void check_err_flag(ddamg_handle* h, const char* what) {
   }
 }
 
+// FP16 storage copies: allocated on first use, filled from the FP64 data after
+// every change of it, and read by the FP32 kernels while h->half is set.
+void half_alloc(ddamg_handle* h) {
+  for (int l = 0; l < h->L; ++l) {
+    Level& L = h->lv[l];
+    if (L.fine && !L.Uh) {
+      L.Uh = dalloc<__half2>(h, (size_t)36 * L.g.V);
+      L.clovh = dalloc<__half>(h, (size_t)72 * L.g.V);
+    }
+    if (!L.fine && !L.blkh) {
+      L.blkh = dalloc<__half2>(h, (size_t)L.g.V * 9 * L.n * L.n);
+      L.bscale = dalloc<float>(h, (size_t)L.g.V);
+    }
+    if (!L.coarsest && !L.Ph) {
+      L.Ph = dalloc<__half2>(h, L.vlen * (size_t)L.N);
+      L.pscale = dalloc<float>(h, (size_t)L.g.nAgg * 2);
+    }
+  }
+}
+
+void half_refresh_fine(ddamg_handle* h) {
+  Level& F = h->lv[0];
+  links_to_half(F.Uh, F.f64.U, (size_t)36 * F.g.V, h->st);
+  clover_to_half(F.clovh, F.f64.clov, F.g.V, h->m0 + 4.0, h->st);
+}
+
+// P_l and D_{l+1}
+void half_refresh(ddamg_handle* h, int l) {
+  Level& F = h->lv[l];
+  Level& C = h->lv[l + 1];
+  p_to_half(F.Ph, F.pscale, F.P64, F.g, F.fine, F.n, F.N, h->st);
+  blocks_to_half(C.blkh, C.bscale, C.c64.blk, C.g.V, C.n, h->st);
+}
+
+void half_bind(ddamg_handle* h) {
+  for (auto& L : h->lv) {
+    if (L.fine) {
+      L.f32.Uh = h->half ? L.Uh : nullptr;
+      L.f32.clovh = h->half ? L.clovh : nullptr;
+      L.f32.shift = (float)(h->m0 + 4.0);
+    } else {
+      L.c32.blkh = h->half ? L.blkh : nullptr;
+      L.c32.bscale = h->half ? L.bscale : nullptr;
+    }
+  }
+}
+
 // P_l from the test vectors, D_{l+1} = P_l^+ D_l P_l (FP64), FP32 copies, coarsest self inverses
 void rebuild(ddamg_handle* h, int l) {
   Level& F = h->lv[l];
@@ -831,6 +898,7 @@ void rebuild(ddamg_handle* h, int l) {
     check_err_flag(h, "singular self block on the coarsest level");
     blas_convert<float, double>(C.c32.selfinv, C.c64.selfinv, (size_t)C.g.V * nc * nc, 1, 0, 0, st);
   }
+  if (F.Ph) half_refresh(h, l);
   sync(h);
 }
 
@@ -872,7 +940,7 @@ void initial_setup_phase(ddamg_handle* h, int l, const double* const* tv_random)
     }
   }
   sync(h);
-  if (h->p.precision == 1) setup_smooth<float>(h, l);
+  if (h->p.precision != 0) setup_smooth<float>(h, l);
   else setup_smooth<double>(h, l);
   rebuild(h, l);
   if (l < h->L - 2) initial_setup_phase(h, l + 1, tv_random);
@@ -1037,7 +1105,7 @@ void validate(const ddamg_params& p) {
     fail(DDAMG_ERR_ARG, "Krylov lengths must be 1..63");
   if (p.mr_steps < 0 || p.nu < 0 || p.mu < 0 || p.n_inv < 0 || p.eta_passes < 0) fail(DDAMG_ERR_ARG, "negative count");
   if (p.max_rhs < 1 || p.max_rhs > 64) fail(DDAMG_ERR_ARG, "max_rhs must be 1..64");
-  if (p.precision != 0 && p.precision != 1) fail(DDAMG_ERR_ARG, "precision must be 0 or 1");
+  if (p.precision < 0 || p.precision > 2) fail(DDAMG_ERR_ARG, "precision must be 0, 1 or 2");
 }
 
 template <typename T>
@@ -1113,6 +1181,17 @@ void hook(ddamg_handle* h, int l, const double* in, double* out, int n, bool out
 
 // ===========================================================================
 // C ABI
+namespace {
+
+// compute precision of the per-operation entry points: 0 FP64, 1 FP32 (on the
+// FP32 or FP16 storage the handle holds)
+bool fp32_compute(int precision) {
+  if (precision != 0 && precision != 1) fail(DDAMG_ERR_ARG, "precision must be 0 (FP64) or 1 (FP32)");
+  return precision == 1;
+}
+
+}  // namespace
+
 extern "C" {
 
 void ddamg_default_params(ddamg_params* p) {
@@ -1181,10 +1260,16 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
     links_import<float>(F.f32.U, gd, F.g, h->st);
     clover_build(F.f64.clov, gd, F.g, m0, csw, h->st);
     real_convert<float>(F.f32.clov, F.f64.clov, (size_t)72 * F.g.V, h->st);
+    if (h->p.precision == 2) {
+      h->half = true;
+      half_alloc(h);
+      half_refresh_fine(h);
+      half_bind(h);
+    }
     sync(h);
     initial_setup_phase(h, 0, tv_random);
     for (int i = 1; i <= h->p.n_inv; ++i) {
-      if (h->p.precision == 1) iterative_setup_phase<float>(h, 0, i);
+      if (h->p.precision != 0) iterative_setup_phase<float>(h, 0, i);
       else iterative_setup_phase<double>(h, 0, i);
     }
     sync(h);
@@ -1242,7 +1327,7 @@ int ddamg_solve(ddamg_handle* h, const double* rhs, double* x, int n, double tol
         apply_D<double>(h, F, o, in, bb, nb);
       };
       auto M = [&](cplx<double>* z, const cplx<double>* v) {
-        if (h->p.precision == 1) precond_outer<float>(h, z, v, nb);
+        if (h->p.precision != 0) precond_outer<float>(h, z, v, nb);
         else precond_outer<double>(h, z, v, nb);
       };
       KrylovResult res;
@@ -1299,6 +1384,16 @@ int ddamg_set_option(ddamg_handle* h, int option, int value) {
       }
       cudaGetLastError();
       free_graphs(h);
+    } else if (option == DDAMG_OPT_HALF_STORAGE) {
+      if (value && !h->lv[0].Uh) {
+        half_alloc(h);
+        half_refresh_fine(h);
+        for (int l = 0; l + 1 < h->L; ++l) half_refresh(h, l);
+        sync(h);
+      }
+      h->half = value != 0;
+      half_bind(h);
+      free_graphs(h);
     } else {
       fail(DDAMG_ERR_ARG, "unknown option");
     }
@@ -1314,6 +1409,8 @@ int ddamg_get_option(ddamg_handle* h, int option, int* value) {
       *value = (h->use_cluster && h->have_cplan32) ? h->cplan32.CL : 0;
     } else if (option == DDAMG_OPT_SAP_CLUSTER) {
       *value = h->L > 2 ? h->lv[1].c32.sap_cls : 0;
+    } else if (option == DDAMG_OPT_HALF_STORAGE) {
+      *value = h->half ? 1 : 0;
     } else {
       fail(DDAMG_ERR_ARG, "unknown option");
     }
@@ -1360,7 +1457,7 @@ int ddamg_krylov_steps(ddamg_handle* h, int level, int precision, long long* ste
     if (!steps) fail(DDAMG_ERR_ARG, "null output");
     int dev = 0;
     long long host = 0;
-    if (precision == 1) {
+    if (precision != 0) {
       CK(cudaMemcpy(&dev, L.w32.gs.ctl + 3, sizeof(int), cudaMemcpyDeviceToHost));
       host = L.w32.host_steps;
     } else {
@@ -1404,7 +1501,7 @@ int ddamg_apply(ddamg_handle* h, int level, int precision, const double* in, dou
   return guard([&] {
     Level& L = level_of(h, level);
     if (n < 1 || !in || !out) fail(DDAMG_ERR_ARG, "invalid fields");
-    if (precision == 1)
+    if (fp32_compute(precision))
       hook<float>(h, level, in, out, n, false, level,
                   [&](cplx<float>* o, cplx<float>* i) { apply_D<float>(h, L, o, i, nullptr, n); });
     else
@@ -1417,7 +1514,7 @@ int ddamg_smooth(ddamg_handle* h, int level, int precision, const double* b, dou
   return guard([&] {
     Level& L = level_of(h, level);
     if (L.coarsest || n < 1 || !b || !z) fail(DDAMG_ERR_ARG, "no smoother on this level");
-    if (precision == 1)
+    if (fp32_compute(precision))
       hook<float>(h, level, b, z, n, true, level,
                   [&](cplx<float>* o, cplx<float>* i) { sap<float>(h, L, o, i, n, iterations); });
     else
@@ -1430,7 +1527,7 @@ int ddamg_restrict(ddamg_handle* h, int level, int precision, const double* fine
   return guard([&] {
     Level& L = level_of(h, level);
     if (L.coarsest || n < 1) fail(DDAMG_ERR_ARG, "no restriction from the coarsest level");
-    if (precision == 1)
+    if (fp32_compute(precision))
       hook<float>(h, level, fine, coarse, n, false, level + 1,
                   [&](cplx<float>* o, cplx<float>* i) { restrict_lv<float>(h, level, o, i, n); });
     else
@@ -1443,7 +1540,7 @@ int ddamg_prolong(ddamg_handle* h, int level, int precision, const double* coars
   return guard([&] {
     Level& L = level_of(h, level);
     if (L.coarsest || n < 1) fail(DDAMG_ERR_ARG, "no prolongation to the coarsest level");
-    if (precision == 1)
+    if (fp32_compute(precision))
       hook<float>(h, level + 1, coarse, fine, n, false, level,
                   [&](cplx<float>* o, cplx<float>* i) { prolong_lv<float>(h, level, o, i, n, false); });
     else
@@ -1456,7 +1553,7 @@ int ddamg_kcycle(ddamg_handle* h, int level, int precision, const double* b, dou
   return guard([&] {
     Level& L = level_of(h, level);
     if (L.coarsest || n < 1 || n > h->max_batch) fail(DDAMG_ERR_ARG, "K-cycle needs a non-coarsest level, n <= max_rhs");
-    if (precision == 1)
+    if (fp32_compute(precision))
       hook<float>(h, level, b, z, n, false, level,
                   [&](cplx<float>* o, cplx<float>* i) { kcycle_run<float>(h, level, o, i, n); });
     else
@@ -1469,7 +1566,7 @@ int ddamg_coarse_solve(ddamg_handle* h, int precision, const double* b, double* 
   return guard([&] {
     if (!h || n < 1 || n > h->max_batch) fail(DDAMG_ERR_ARG, "n must be 1..max_rhs");
     const int l = h->L - 1;
-    if (precision == 1)
+    if (fp32_compute(precision))
       hook<float>(h, l, b, z, n, false, l, [&](cplx<float>* o, cplx<float>* i) { coarse_solve<float>(h, o, i, n); });
     else
       hook<double>(h, l, b, z, n, false, l,

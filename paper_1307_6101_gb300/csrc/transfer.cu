@@ -34,10 +34,10 @@ __device__ void block_sum(T* v, int cnt, T* sh) {
   __syncthreads();
 }
 
-template <typename T>
-__global__ void k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const cplx<T>* __restrict__ P,
-                           Geom gf, Geom gc, bool fine, int n, int N, size_t in_rstride, size_t pstride,
-                           size_t out_rstride, size_t out_site_stride) {
+template <typename T, typename PS>
+__global__ void k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const PS* __restrict__ P,
+                           const float* __restrict__ pscale, Geom gf, Geom gc, bool fine, int n, int N,
+                           size_t in_rstride, size_t pstride, size_t out_rstride, size_t out_site_stride) {
   __shared__ T sh[32 * 4 * JC];
   const int agg = blockIdx.x;
   const int V = gf.V;
@@ -59,7 +59,7 @@ __global__ void k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict_
 #pragma unroll
         for (int jj = 0; jj < JC; ++jj) {
           if (j0 + jj < N) {
-            const cplx<T> p = P[(size_t)(j0 + jj) * pstride + faddr(fine, V, n, x, f)];
+            const cplx<T> p = ld_cplx(P, (size_t)(j0 + jj) * pstride + faddr(fine, V, n, x, f));
             const cplx<T> t = cdotc(p, v);
             acc[(s * JC + jj) * 2] += t.re;
             acc[(s * JC + jj) * 2 + 1] += t.im;
@@ -70,15 +70,16 @@ __global__ void k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict_
     block_sum(acc, 4 * JC, sh);
     if (threadIdx.x < 2 * JC) {
       const int s = threadIdx.x / JC, jj = threadIdx.x % JC;
-      if (j0 + jj < N) po[s * N + j0 + jj] = cmk<T>(acc[(s * JC + jj) * 2], acc[(s * JC + jj) * 2 + 1]);
+      const T sc = pscale ? T(pscale[agg * 2 + s]) : T(1);
+      if (j0 + jj < N) po[s * N + j0 + jj] = cmk<T>(sc * acc[(s * JC + jj) * 2], sc * acc[(s * JC + jj) * 2 + 1]);
     }
   }
 }
 
-template <typename T>
-__global__ void k_prolong(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const cplx<T>* __restrict__ P,
-                          Geom gf, Geom gc, bool fine, int n, int N, size_t out_rstride, size_t in_rstride,
-                          size_t pstride, bool accumulate) {
+template <typename T, typename PS>
+__global__ void k_prolong(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const PS* __restrict__ P,
+                          const float* __restrict__ pscale, Geom gf, Geom gc, bool fine, int n, int N,
+                          size_t out_rstride, size_t in_rstride, size_t pstride, bool accumulate) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int V = gf.V;
   if (t >= (size_t)V * n) return;
@@ -92,7 +93,8 @@ __global__ void k_prolong(cplx<T>* __restrict__ out, const cplx<T>* __restrict__
   const cplx<T>* pc = in + (size_t)blockIdx.y * in_rstride + (size_t)cs * (2 * N) + s * N;
   cplx<T> acc = czero<T>();
   const size_t a = faddr(fine, V, n, x, f);
-  for (int j = 0; j < N; ++j) cfma(acc, P[(size_t)j * pstride + a], pc[j]);
+  for (int j = 0; j < N; ++j) cfma(acc, ld_cplx(P, (size_t)j * pstride + a), pc[j]);
+  if (pscale) acc = T(pscale[(x / gf.vA) * 2 + s]) * acc;
   cplx<T>* po = out + (size_t)blockIdx.y * out_rstride + a;
   *po = accumulate ? *po + acc : acc;
 }
@@ -159,28 +161,84 @@ __global__ void k_orthonormalise(cplx<double>* __restrict__ P, Geom g, bool fine
   }
 }
 
+// FP16 copy of P with one scale per (aggregate, chirality): s = float(max |re|, |im|)
+// over the N columns restricted to (A, s), q = RNE_half(x / s).
+__global__ void k_p_to_half(__half2* __restrict__ Ph, float* __restrict__ pscale, const cplx<double>* __restrict__ P,
+                            Geom g, bool fine, int n, int N, size_t pstride) {
+  __shared__ double sh[32];
+  const int agg = blockIdx.x, s = blockIdx.y, h = n / 2;
+  const int ne = g.vA * h;
+  const int V = g.V;
+  double mx = 0.0;
+  for (int j = 0; j < N; ++j)
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const cplx<double> v = P[(size_t)j * pstride + faddr(fine, V, n, agg * g.vA + e / h, s * h + e % h)];
+      mx = fmax(mx, fmax(fabs(v.re), fabs(v.im)));
+    }
+  for (int off = 16; off >= 1; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    const float sf = m > 0.0 ? (float)m : 1.0f;
+    pscale[agg * 2 + s] = sf;
+    sh[0] = (double)sf;
+  }
+  __syncthreads();
+  const double sc = sh[0];
+  for (int j = 0; j < N; ++j)
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const size_t a = (size_t)j * pstride + faddr(fine, V, n, agg * g.vA + e / h, s * h + e % h);
+      Ph[a] = __halves2half2(__double2half(P[a].re / sc), __double2half(P[a].im / sc));
+    }
+}
+
 }  // namespace
 
 namespace dd {
 
+void p_to_half(__half2* Ph, float* pscale, const cplx<double>* P, const Geom& g, bool fine, int n, int N,
+               cudaStream_t st) {
+  count_launch();
+  k_p_to_half<<<dim3(g.nAgg, 2), 256, 0, st>>>(Ph, pscale, P, g, fine, n, N, (size_t)g.V * n);
+}
+
 template <typename T>
 void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine, int n,
-                 int N, int nrhs, size_t in_rstride, size_t out_rstride, size_t out_site_stride, cudaStream_t st) {
+                 int N, int nrhs, size_t in_rstride, size_t out_rstride, size_t out_site_stride, cudaStream_t st,
+                 const __half2* Ph, const float* pscale) {
   const size_t pstride = (size_t)gf.V * n;
   const int threads = gf.vA >= 256 ? 256 : (gf.vA >= 128 ? 128 : (gf.vA >= 64 ? 64 : 32));
   count_launch();
-  k_restrict<T><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, P, gf, gc, fine, n, N, in_rstride, pstride,
-                                                          out_rstride, out_site_stride);
+  if constexpr (sizeof(T) == 4) {
+    if (Ph) {
+      k_restrict<float, __half2><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, Ph, pscale, gf, gc, fine, n, N,
+                                                                          in_rstride, pstride, out_rstride,
+                                                                          out_site_stride);
+      return;
+    }
+  }
+  k_restrict<T, cplx<T>><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, P, nullptr, gf, gc, fine, n, N,
+                                                                   in_rstride, pstride, out_rstride, out_site_stride);
 }
 
 template <typename T>
 void prolong_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine, int n,
-                int N, int nrhs, size_t out_rstride, size_t in_rstride, bool accumulate, cudaStream_t st) {
+                int N, int nrhs, size_t out_rstride, size_t in_rstride, bool accumulate, cudaStream_t st,
+                const __half2* Ph, const float* pscale) {
   const size_t pstride = (size_t)gf.V * n;
   const size_t tot = (size_t)gf.V * n;
   count_launch();
-  k_prolong<T><<<dim3(div_up(tot, 128), nrhs), 128, 0, st>>>(out, in, P, gf, gc, fine, n, N, out_rstride, in_rstride,
-                                                              pstride, accumulate);
+  if constexpr (sizeof(T) == 4) {
+    if (Ph) {
+      k_prolong<float, __half2><<<dim3(div_up(tot, 128), nrhs), 128, 0, st>>>(
+          out, in, Ph, pscale, gf, gc, fine, n, N, out_rstride, in_rstride, pstride, accumulate);
+      return;
+    }
+  }
+  k_prolong<T, cplx<T>><<<dim3(div_up(tot, 128), nrhs), 128, 0, st>>>(out, in, P, nullptr, gf, gc, fine, n, N,
+                                                                       out_rstride, in_rstride, pstride, accumulate);
 }
 
 void orthonormalise(cplx<double>* P, const Geom& g, bool fine, int n, int N, int* err, cudaStream_t st) {
@@ -191,9 +249,9 @@ void orthonormalise(cplx<double>* P, const Geom& g, bool fine, int n, int N, int
 
 #define INST(T)                                                                                                  \
   template void restrict_op<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const Geom&, const Geom&, bool, int, int, \
-                               int, size_t, size_t, size_t, cudaStream_t);                                      \
+                               int, size_t, size_t, size_t, cudaStream_t, const __half2*, const float*);        \
   template void prolong_op<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const Geom&, const Geom&, bool, int, int,  \
-                              int, size_t, size_t, bool, cudaStream_t);
+                              int, size_t, size_t, bool, cudaStream_t, const __half2*, const float*);
 INST(float)
 INST(double)
 #undef INST

@@ -31,3 +31,13 @@ def test_params_struct_matches_defaults_of_table1():
     assert p.n_tv[0] == 20 and p.n_inv == 6 and p.coarse_tol == pytest.approx(5e-2)
     assert p.outer_restart == 10 and p.mu == 0 and p.nu == 5 and list(p.sap_block[0]) == [2, 2, 2, 2]
     assert p.mr_steps == 3 and p.kcycle_len == 5 and p.kcycle_cycles == 2 and p.kcycle_tol == pytest.approx(0.1)
+
+
+def test_binding_constants_match_header():
+    import paper_1307_6101_gb300 as dd
+    src = open(os.path.join(ROOT, "include", "ddamg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(DDAMG_OPT_[A-Z_]+)\s*=\s*(-?\d+)", src))
+    assert "DDAMG_OPT_HALF_STORAGE" in consts
+    for k, v in consts.items():
+        assert getattr(dd, k) == v, k
