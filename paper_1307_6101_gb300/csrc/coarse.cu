@@ -8,6 +8,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -278,132 +279,195 @@ __global__ void k_coarse_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict_
   }
 }
 
+// shared-memory layout of k_coarse_sap_cluster (byte offsets, 16-byte aligned)
+struct SapSmem {
+  size_t rfull, pbuf, part, red, sh, slot, bar, total;
+};
+DD_HD size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+DD_HD SapSmem sap_smem_layout(int vB, int n, int spc, int nsl, size_t bs, size_t ts) {
+  SapSmem L;
+  size_t o = al16((size_t)spc * nsl * n * n * bs);
+  L.rfull = o;
+  o = al16(o + (size_t)vB * n * 2 * ts);
+  L.pbuf = o;
+  o = al16(o + (size_t)2 * vB * n * 2 * ts);
+  L.part = o;
+  o = al16(o + (size_t)9 * spc * n * 2 * ts);
+  L.red = o;
+  o = al16(o + (size_t)2 * 16 * 4 * ts);
+  L.sh = o;
+  o = al16(o + (size_t)(32 * 3 + 4) * ts);
+  L.slot = o;
+  o = al16(o + (size_t)spc * 9 * sizeof(int));
+  L.bar = o;
+  L.total = al16(o + 8);
+  return L;
+}
+
 // SAP colour sweep on a coarse level with one thread-block cluster per SAP
-// block.  CTA q of the cluster owns `spc` sites of the block (one thread per
-// (row, block k) of its sites).  Every CTA keeps a copy of the whole block
-// residual in shared memory; after each MR update each CTA writes its own rows
-// into all copies (distributed shared memory).  The MR dot products are summed
-// over the cluster from per-CTA partials in rank order, so every CTA computes
-// the same alpha.  Same arithmetic as k_coarse_sap: rho = (b - D z)_B, k MR
-// steps on D_B (hops leaving the block dropped), z_B += e_B.
+// block.  CTA q of the cluster owns `spc` sites of the block, one thread per
+// (row, block k) of its sites.  The blocks of its sites that couple inside the
+// SAP block (self block included) are staged once into shared memory by bulk
+// copies; the hops leaving the block are only needed for rho = b - D z and are
+// read from global memory.  Every CTA keeps the whole block residual r and the
+// whole MR direction p = D_B r in shared memory: after computing p on its own
+// rows a CTA writes them, with its partial dot products, into every CTA of the
+// cluster (distributed shared memory), so each MR step needs one cluster
+// barrier; p and the partials are double-buffered across steps.  The partial
+// dot products are summed in rank order, so every CTA computes the same alpha
+// and applies r <- r - alpha p to its whole copy.  Same arithmetic as
+// k_coarse_sap: rho = (b - D z)_B, k MR steps on D_B, z_B += e_B.
 template <typename T, typename BS>
 __global__ void k_coarse_sap_cluster(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
                                      const BS* __restrict__ blk, const float* __restrict__ bscale, Geom g, int n,
-                                     size_t rstride, const int* __restrict__ blocks, int k_mr, int spc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                                     size_t rstride, const int* __restrict__ blocks, int k_mr, int spc, int nsl,
+                                     int* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
   const int CLS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int vB = g.vB;
   const int b = blocks[blockIdx.x / CLS];
   const int rows = spc * n;
-  cplx<T>* rfull = reinterpret_cast<cplx<T>*>(smem_raw);   // [vB*n]
-  cplx<T>* part = rfull + (size_t)vB * n;                   // [9][rows]
-  T* red = reinterpret_cast<T*>(part + (size_t)9 * rows);   // [CLS][4] (read from rank 0)
-  T* sh = red + 4 * 16;                                      // [warps][3]
+  const size_t nn = (size_t)n * n;
+  const SapSmem L = sap_smem_layout(vB, n, spc, nsl, sizeof(BS), sizeof(T));
+  BS* stage = reinterpret_cast<BS*>(smem_raw);                                // [spc][nsl][n][n]
+  cplx<T>* rfull = reinterpret_cast<cplx<T>*>(smem_raw + L.rfull);            // [vB*n]
+  cplx<T>* pbuf = reinterpret_cast<cplx<T>*>(smem_raw + L.pbuf);              // [2][vB*n]
+  cplx<T>* part = reinterpret_cast<cplx<T>*>(smem_raw + L.part);              // [9][rows]
+  T* red = reinterpret_cast<T*>(smem_raw + L.red);                            // [2][16][4]
+  T* sh = reinterpret_cast<T*>(smem_raw + L.sh);                              // [32][3] + 3
+  int* slot = reinterpret_cast<int*>(smem_raw + L.slot);                      // [spc][9]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + L.bar);
   const size_t ro = (size_t)blockIdx.y * rstride;
+  const int site0 = b * vB + rank * spc;   // first own site
+  // slot of block k of own site sl in the staged array (-1: the hop leaves the SAP block)
+  if (threadIdx.x < spc) {
+    int c[4];
+    geom_coords(g, site0 + threadIdx.x, c);
+    int ns = 0;
+    for (int k = 0; k < 9; ++k) {
+      const bool in = k == 0 || hop_internal(g, c, (k - 1) % 4, k <= 4 ? +1 : -1, g.B);
+      slot[threadIdx.x * 9 + k] = in ? ns++ : -1;
+    }
+  }
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int cnt = 0;
+    for (int e = 0; e < spc * 9; ++e) cnt += slot[e] >= 0 ? 1 : 0;
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (unsigned)(cnt * nn * sizeof(BS)));
+    __syncwarp();
+    for (int e = threadIdx.x; e < spc * 9; e += 32) {
+      const int sl = e / 9, k = e % 9, q = slot[e];
+      if (q >= 0)
+        bulk_g2s(stage + ((size_t)sl * nsl + q) * nn, blk + ((size_t)(site0 + sl) * 9 + k) * nn,
+                 (unsigned)(nn * sizeof(BS)), bar);
+    }
+  }
   const int k = threadIdx.x / rows;
   const int rl = threadIdx.x - k * rows;
   const int sl = rl / n, i = rl - (rl / n) * n;
-  const int site = b * vB + rank * spc + sl;
-  bool kin = false;   // this thread's block k couples to a site inside the SAP block
-  int nb = site, nloc = 0;
+  const int site = site0 + sl;
+  const T sc = bscale ? T(bscale[site]) : T(1);
+  int q = -1, nb = site, nloc = 0;
   if (k < 9) {
-    int c[4];
-    geom_coords(g, site, c);
-    if (k == 0) {
-      kin = true;
-      nb = site;
-    } else {
-      const int mu = (k - 1) % 4, dir = k <= 4 ? +1 : -1;
-      nb = geom_neighbor(g, c, mu, dir);
-      kin = hop_internal(g, c, mu, dir, g.B);
+    q = slot[sl * 9 + k];
+    if (k > 0) {
+      int c[4];
+      geom_coords(g, site, c);
+      nb = geom_neighbor(g, c, (k - 1) % 4, k <= 4 ? +1 : -1);
     }
     nloc = nb - b * vB;
   }
-  const BS* M = blk + (((size_t)site * 9 + (k < 9 ? k : 0)) * n) * n + i;
-  const T sc = bscale ? T(bscale[site]) : T(1);
-  // rho = b - D z on the own rows (all 9 blocks, neighbours read from z)
-  {
-    cplx<T> acc = czero<T>();
-    if (k < 9) {
-      const cplx<T>* v = z + ro + (size_t)nb * n;
+  const BS* Ms = stage + ((size_t)sl * nsl + (q >= 0 ? q : 0)) * nn + i;   // staged row i (column-major)
+  // rho = b - D z on the own rows: hops leaving the block from global memory ...
+  cplx<T> acc = czero<T>();
+  if (k < 9 && q < 0) {
+    const BS* M = blk + ((size_t)site * 9 + k) * nn + i;
+    const cplx<T>* v = z + ro + (size_t)nb * n;
 #pragma unroll 8
-      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), v[j]);
-      part[k * rows + rl] = sc * acc;
-    }
+    for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), v[j]);
   }
+  const int ok = __syncthreads_and(mbar_wait_bounded(bar, 0) ? 1 : 0);
+  if (!ok && threadIdx.x == 0) atomicExch(err, 2);
+  // ... and the blocks inside it from shared memory
+  if (k < 9 && q >= 0) {
+    const cplx<T>* v = z + ro + (size_t)nb * n;
+#pragma unroll 8
+    for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(Ms, (size_t)j * n), v[j]);
+  }
+  if (k < 9) part[k * rows + rl] = sc * acc;
   __syncthreads();
   cplx<T> r = czero<T>(), xs = czero<T>();
   if (threadIdx.x < rows) {
     cplx<T> d = czero<T>();
 #pragma unroll
-    for (int q = 0; q < 9; ++q) d = d + part[q * rows + threadIdx.x];
-    r = bsrc[ro + (size_t)(b * vB + rank * spc) * n + threadIdx.x] - d;
-    for (int q = 0; q < CLS; ++q) cluster.map_shared_rank(rfull, q)[(size_t)rank * rows + threadIdx.x] = r;
+    for (int m = 0; m < 9; ++m) d = d + part[m * rows + threadIdx.x];
+    r = bsrc[ro + (size_t)site0 * n + threadIdx.x] - d;
+    for (int c = 0; c < CLS; ++c) cluster.map_shared_rank(rfull, c)[(size_t)rank * rows + threadIdx.x] = r;
   }
   cluster.sync();
-  T* red0 = cluster.map_shared_rank(red, 0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   for (int it = 0; it < k_mr; ++it) {
-    // p = D_B r on the own rows
+    const int buf = it & 1;
+    cplx<T>* pb = pbuf + (size_t)buf * vB * n;
+    T* rb = red + buf * 64;
+    // p = D_B r on the own rows, from the staged blocks and the local copy of r
     if (k < 9) {
-      cplx<T> acc = czero<T>();
-      if (kin) {
+      cplx<T> a = czero<T>();
+      if (q >= 0) {
         const cplx<T>* v = rfull + (size_t)nloc * n;
 #pragma unroll 8
-        for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), v[j]);
+        for (int j = 0; j < n; ++j) cfma(a, ld_cplx(Ms, (size_t)j * n), v[j]);
       }
-      part[k * rows + rl] = sc * acc;
+      part[k * rows + rl] = sc * a;
     }
     __syncthreads();
     cplx<T> p = czero<T>();
     T nre = T(0), nim = T(0), den = T(0);
     if (threadIdx.x < rows) {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) p = p + part[q * rows + threadIdx.x];
+      for (int m = 0; m < 9; ++m) p = p + part[m * rows + threadIdx.x];
       const cplx<T> t = cdotc(p, r);
       nre = t.re;
       nim = t.im;
       den = cnorm2(p);
+      for (int c = 0; c < CLS; ++c) cluster.map_shared_rank(pb, c)[(size_t)rank * rows + threadIdx.x] = p;
     }
-    // CTA reduction, then rank-ordered cluster reduction
     for (int off = 16; off >= 1; off >>= 1) {
       nre += __shfl_xor_sync(0xffffffffu, nre, off);
       nim += __shfl_xor_sync(0xffffffffu, nim, off);
       den += __shfl_xor_sync(0xffffffffu, den, off);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if (lane == 0) { sh[3 * warp] = nre; sh[3 * warp + 1] = nim; sh[3 * warp + 2] = den; }
     __syncthreads();
     if (threadIdx.x == 0) {
       T a = T(0), bb = T(0), cc = T(0);
       for (int w = 0; w < nw; ++w) { a += sh[3 * w]; bb += sh[3 * w + 1]; cc += sh[3 * w + 2]; }
-      red0[rank * 4] = a;
-      red0[rank * 4 + 1] = bb;
-      red0[rank * 4 + 2] = cc;
+      for (int c = 0; c < CLS; ++c) {
+        T* dst = cluster.map_shared_rank(rb, c) + rank * 4;
+        dst[0] = a;
+        dst[1] = bb;
+        dst[2] = cc;
+      }
     }
     cluster.sync();
-    if (threadIdx.x == 0) {   // one thread reads the remote partials, the CTA reads its copy
-      T a = T(0), bb = T(0), cc = T(0);
-      for (int q = 0; q < CLS; ++q) { a += red0[q * 4]; bb += red0[q * 4 + 1]; cc += red0[q * 4 + 2]; }
-      sh[96] = a;
-      sh[97] = bb;
-      sh[98] = cc;
-    }
-    __syncthreads();
-    const T a = sh[96], bb = sh[97], cc = sh[98];
+    T a = T(0), bb = T(0), cc = T(0);
+    for (int c = 0; c < CLS; ++c) { a += rb[c * 4]; bb += rb[c * 4 + 1]; cc += rb[c * 4 + 2]; }
     const cplx<T> alpha = cc > T(0) ? cmk<T>(a / cc, bb / cc) : czero<T>();
     if (threadIdx.x < rows) {
       cfma(xs, alpha, r);
       r = r - alpha * p;
-      for (int q = 0; q < CLS; ++q) cluster.map_shared_rank(rfull, q)[(size_t)rank * rows + threadIdx.x] = r;
     }
-    cluster.sync();
+    for (int e = threadIdx.x; e < vB * n; e += blockDim.x) rfull[e] = rfull[e] - alpha * pb[e];
+    __syncthreads();
   }
-  if (threadIdx.x < rows) {
-    const size_t a = ro + (size_t)(b * vB + rank * spc) * n + threadIdx.x;
+  if (ok && threadIdx.x < rows) {
+    const size_t a = ro + (size_t)site0 * n + threadIdx.x;
     z[a] = z[a] + xs;
   }
+  if (!ok && threadIdx.x == 0) mbar_wait_bounded(bar, 0);   // no copy may still be in flight at exit
 }
 
 // Gauss-Jordan inversion with partial pivoting of every self block (FP64).
@@ -566,11 +630,6 @@ void blocks_to_half(__half2* dst, float* scale, const cplx<double>* blk, int V, 
 }
 
 template <typename T>
-size_t coarse_sap_cluster_smem(int vB, int n, int spc) {
-  return (size_t)vB * n * sizeof(cplx<T>) + (size_t)9 * spc * n * sizeof(cplx<T>) + (4 * 16 + 32 * 3 + 4) * sizeof(T);
-}
-
-template <typename T>
 void coarse_apply(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const CoarseOp<T>& op, int nrhs, size_t rstride,
                   int sel, int sel_mu, int in_chir, cudaStream_t st) {
   const int threads = ((9 * op.n + 31) / 32) * 32;
@@ -596,20 +655,41 @@ void coarse_apply(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const Coars
                                                                   sel, sel_mu, in_chir);
 }
 
-// cluster plan of the coarse SAP: cluster size CLS and sites per CTA (0 if no plan fits)
+// staged blocks per site of the cluster SAP: the self block plus the hops that stay inside
+// the SAP block, maximised over the sites of a block (every block has the same shape)
+int coarse_sap_slots(const Geom& g) {
+  int best = 1;
+  for (int loc = 0; loc < g.vB; ++loc) {
+    int c[4];
+    geom_coords(g, loc, c);
+    int cnt = 1;
+    for (int k = 1; k < 9; ++k) cnt += hop_internal(g, c, (k - 1) % 4, k <= 4 ? +1 : -1, g.B) ? 1 : 0;
+    best = cnt > best ? cnt : best;
+  }
+  return best;
+}
+
+template <typename T, typename BS>
+void sap_cluster_attrs(size_t smem, int CLS) {
+  cudaFuncSetAttribute(k_coarse_sap_cluster<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (CLS > 8) cudaFuncSetAttribute(k_coarse_sap_cluster<T, BS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+// cluster plan of the coarse SAP: cluster size CLS, sites per CTA and staged blocks per
+// site (0 if no plan fits).  Sized for operator storage in the compute precision, which
+// also covers the FP16 storage.
 template <typename T>
-int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out) {
+int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out, int* nsl_out) {
+  const int nsl = coarse_sap_slots(g);
   for (int CLS : {8, 16, 4, 2}) {
     if (g.vB % CLS) continue;
     const int spc = g.vB / CLS;
     const int threads = ((9 * spc * n + 31) / 32) * 32;
     if (threads > 1024) continue;
-    const size_t sm = coarse_sap_cluster_smem<T>(g.vB, n, spc);
-    if (CLS > 8) {
-      cudaFuncSetAttribute(k_coarse_sap_cluster<T, cplx<T>>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if constexpr (sizeof(T) == 4)
-        cudaFuncSetAttribute(k_coarse_sap_cluster<float, __half2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    }
+    const size_t sm = sap_smem_layout(g.vB, n, spc, nsl, sizeof(cplx<T>), sizeof(T)).total;
+    if (sm > 227 * 1024) continue;
+    sap_cluster_attrs<T, cplx<T>>(sm, CLS);
+    if constexpr (sizeof(T) == 4) sap_cluster_attrs<float, __half2>(sm, CLS);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -629,6 +709,7 @@ int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out) {
     if (nclusters < 1) continue;
     *CLS_out = CLS;
     *spc_out = spc;
+    *nsl_out = nsl;
     return 1;
   }
   return 0;
@@ -640,6 +721,7 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
   if (op.sap_cls > 0) {
     const int spc = op.g.vB / op.sap_cls;
     const int threads = ((9 * spc * op.n + 31) / 32) * 32;
+    const bool half = sizeof(T) == 4 && op.blkh;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -648,22 +730,23 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(nblocks * op.sap_cls, nrhs, 1);
     cfg.blockDim = dim3(threads, 1, 1);
-    cfg.dynamicSmemBytes = coarse_sap_cluster_smem<T>(op.g.vB, op.n, spc);
+    cfg.dynamicSmemBytes =
+        sap_smem_layout(op.g.vB, op.n, spc, op.sap_nsl, half ? sizeof(__half2) : sizeof(cplx<T>), sizeof(T)).total;
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
     cudaError_t e;
     if constexpr (sizeof(T) == 4) {
-      if (op.blkh)
+      if (half)
         e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<float, __half2>, z, b, op.blkh, op.bscale, op.g, op.n,
-                               rstride, blocks, k_mr, spc);
+                               rstride, blocks, k_mr, spc, op.sap_nsl, op.err);
       else
         e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
-                               (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc);
+                               (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc, op.sap_nsl, op.err);
     } else {
       e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
-                             (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc);
+                             (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc, op.sap_nsl, op.err);
     }
     if (e == cudaSuccess) return;
     cudaGetLastError();   // cluster launch refused: run the one-CTA-per-block kernel instead
@@ -777,7 +860,7 @@ void coarse_blocks_export(cplx<double>* dst, const cplx<double>* blk, const Geom
                                     int, size_t, cudaStream_t);                                                   \
   template void coarse_schur_even<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const cplx<T>*, const CoarseOp<T>&, \
                                      double, double, double, int, size_t, cudaStream_t);                          \
-  template int coarse_sap_cluster_plan<T>(const Geom&, int, int*, int*);                                           \
+  template int coarse_sap_cluster_plan<T>(const Geom&, int, int*, int*, int*);                                     \
   template void coarse_sap_sweep<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, const int*, int, int, size_t,   \
                                     int, cudaStream_t);                                                           \
   template void coarse_selfinv_apply<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, int, int, size_t,           \

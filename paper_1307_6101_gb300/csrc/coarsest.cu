@@ -13,16 +13,25 @@
 // broadcast.  Cluster barriers separate the phases.  All loops are bounded by
 // max_cycles * m.  Stopping rules are those of the host-driven solver: |g_{j+1}|
 // <= tol ||bhat|| inside a cycle, the recomputed residual between cycles.
+//
+// Resident variant (NR > 0: FP32 arithmetic on FP16 blocks, one even and one odd
+// site per CTA): the operator does not change during the solve, so each CTA
+// loads it once -- the rows of its odd site's 8 hop blocks into registers (one
+// row per thread), its even site's 9 blocks and its odd site's self inverse into
+// shared memory by bulk copies -- and every GMRES step then reads the operator
+// from registers and shared memory instead of L2.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace {
 
 constexpr int MAXM = 64;
+constexpr int RES_NR = 56;   // largest coarse dof count of the resident variant (rows held in registers)
 
 DD_HD size_t bidx(int site, int k, int n, int i, int j) { return (((size_t)site * 9 + k) * n + j) * n + i; }
 
@@ -47,10 +56,15 @@ struct Smem {
   cplx<T>* htot;   // [MAXM] sum of both CGS passes
   T* cs;           // [m]
   T* scal;         // [8] broadcast scalars inside the CTA
+  // resident variant only
+  __half2* eblk;   // [9][n][n] blocks of the own even site
+  cplx<T>* oinv;   // [n][n] self inverse of the own odd site
+  unsigned long long* bar;
 };
 
 template <typename T>
 __device__ Smem<T> carve(unsigned char* base, int m, int nep, int nop, int n, int CL) {
+  // layout must match smem_bytes()
   Smem<T> s;
   cplx<T>* p = reinterpret_cast<cplx<T>*>(base);
   s.Vb = p; p += (size_t)(m + 1) * nep * n;
@@ -73,6 +87,13 @@ __device__ Smem<T> carve(unsigned char* base, int m, int nep, int nop, int n, in
   T* q = reinterpret_cast<T*>(p);
   s.cs = q; q += m;
   s.scal = q;
+  q += 8;
+  uintptr_t a = (reinterpret_cast<uintptr_t>(q) + 15) & ~uintptr_t(15);
+  s.eblk = reinterpret_cast<__half2*>(a);
+  a += (size_t)9 * n * n * sizeof(__half2);
+  s.oinv = reinterpret_cast<cplx<T>*>(a);
+  a += (size_t)n * n * sizeof(cplx<T>);
+  s.bar = reinterpret_cast<unsigned long long*>(a);
   return s;
 }
 
@@ -86,7 +107,14 @@ struct Ctx {
   const int* odd;
   const int* nbr_e_of_o;   // [n_o][8] even-list index of neighbour k (k<4: +mu, k>=4: -mu)
   const int* nbr_o_of_e;   // [n_e][8]
+  int* err;                // bounded-wait error flag
   int n_e, n_o, nep, nop, n, CL, rank;
+};
+
+// operator rows held by one thread of the resident variant
+template <int NR>
+struct RegRows {
+  __half2 r[NR > 0 ? NR : 1];
 };
 
 // acc += sum_j M(site, k)[i][j] xv[j] from the compute-precision or the FP16 blocks
@@ -109,9 +137,60 @@ __device__ __forceinline__ cplx<T> block_row(const Ctx<T>& cx, int site, int k, 
 }
 
 // t(own odd) = S^{-1} ( a*bo + c * sum_k D_k(o) v(even nbr_k) ), v read from the owners' array `src`
-template <typename T>
-__device__ void odd_phase(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group& cluster, cplx<T>* src, T a, T c) {
+template <typename T, int NR>
+__device__ void odd_phase(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group& cluster, cplx<T>* src, T a, T c,
+                          const RegRows<NR>& orow) {
   const int n = cx.n;
+  if constexpr (NR > 0) {
+    // one odd site per CTA; hop rows in registers, self inverse in shared memory
+    const int o = cx.rank;
+    if (o >= cx.n_o) return;   // uniform in the CTA
+    const int site = cx.odd[o];
+    if (c != T(0)) {
+      for (int t = threadIdx.x; t < 8 * n; t += blockDim.x) {
+        const int k = t / n, j = t - k * n;
+        const int nb = cx.nbr_e_of_o[o * 8 + k];
+        const cplx<T>* rem = cluster.map_shared_rank(src, nb / cx.nep);
+        s.xs[t] = rem[(nb % cx.nep) * n + j];
+      }
+    }
+    __syncthreads();
+    {
+      const int k = threadIdx.x / n, i = threadIdx.x - (threadIdx.x / n) * n;
+      if (k < 8) {
+        cplx<T> acc = czero<T>();
+        if (c != T(0)) {
+          const cplx<T>* xv = s.xs + k * n;
+#pragma unroll
+          for (int j = 0; j < NR; ++j)
+            if (j < n) {
+              const float2 f = __half22float2(orow.r[j]);
+              cfma(acc, cmk<T>(f.x, f.y), xv[j]);
+            }
+          acc = T(cx.bscale[site]) * acc;
+        }
+        s.part[k * n + i] = acc;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      cplx<T> u = czero<T>();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) u = u + s.part[q * n + i];
+      u = c * u;
+      if (a != T(0)) u = u + a * s.bo[i];
+      s.us[i] = u;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      cplx<T> acc = czero<T>();
+      const cplx<T>* Mi = s.oinv + i;
+#pragma unroll 8
+      for (int j = 0; j < n; ++j) cfma(acc, Mi[(size_t)j * n], s.us[j]);
+      s.tv[i] = acc;
+    }
+    __syncthreads();
+  } else {
   for (int so = 0; so < cx.nop; ++so) {
     const int o = cx.rank * cx.nop + so;
     if (o >= cx.n_o) break;   // uniform in the CTA
@@ -152,10 +231,11 @@ __device__ void odd_phase(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group&
     }
     __syncthreads();
   }
+  }
 }
 
 // dst(own even) = a*be + sc * S(e) xloc(e) + c * sum_k D_k(e) t(odd nbr_k)  (t read from the owners' tv)
-template <typename T>
+template <typename T, int NR>
 __device__ void even_phase(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group& cluster, const cplx<T>* xloc,
                            cplx<T>* dst, T a, T sc, T c) {
   const int n = cx.n;
@@ -181,7 +261,17 @@ __device__ void even_phase(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group
       if (k < 9) {
         cplx<T> acc = czero<T>();
         const T w = k == 0 ? sc : c;
-        if (w != T(0)) acc = block_row(cx, site, k, i, s.xs + k * n);
+        if (w != T(0)) {
+          if constexpr (NR > 0) {   // the own even site's blocks are in shared memory
+            const __half2* M = s.eblk + (size_t)k * n * n + i;
+            const cplx<T>* xv = s.xs + k * n;
+#pragma unroll 8
+            for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), xv[j]);
+            acc = T(cx.bscale[site]) * acc;
+          } else {
+            acc = block_row(cx, site, k, i, s.xs + k * n);
+          }
+        }
         s.part[k * n + i] = w * acc;
       }
     }
@@ -269,8 +359,8 @@ __device__ T cluster_norm2(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group
   return s.scal[4];
 }
 
-template <typename T>
-__global__ void k_coarsest_cluster(Ctx<T> cx0, const cplx<T>* __restrict__ b, cplx<T>* __restrict__ x, size_t rstride,
+template <typename T, int NR>
+__global__ void __launch_bounds__(512, 1) k_coarsest_cluster(Ctx<T> cx0, const cplx<T>* __restrict__ b, cplx<T>* __restrict__ x, size_t rstride,
                                    int m, int max_cycles, double tol, int* iters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
@@ -281,6 +371,30 @@ __global__ void k_coarsest_cluster(Ctx<T> cx0, const cplx<T>* __restrict__ b, cp
   Smem<T> s = carve<T>(smem_raw, m, cx.nep, cx.nop, n, cx.CL);
   const cplx<T>* pb = b + (size_t)blockIdx.y * rstride;
   cplx<T>* px = x + (size_t)blockIdx.y * rstride;
+  RegRows<NR> orow;
+  int staged = 1;
+  if constexpr (NR > 0) {
+    // stage the own sites' operator: even site's 9 blocks and odd site's self inverse
+    // (shared memory, bulk copies), odd site's 8 hop rows (registers)
+    const int e = cx.rank, o = cx.rank;
+    if (threadIdx.x == 0) {
+      mbar_init(s.bar, 1);
+      const unsigned be_bytes = (unsigned)(9 * n * n * sizeof(__half2));
+      const unsigned bi_bytes = (unsigned)(n * n * sizeof(cplx<T>));
+      mbar_arrive_expect_tx(s.bar, (e < cx.n_e ? be_bytes : 0u) + (o < cx.n_o ? bi_bytes : 0u));
+      if (e < cx.n_e) bulk_g2s(s.eblk, cx.blkh + (size_t)cx.even[e] * 9 * n * n, be_bytes, s.bar);
+      if (o < cx.n_o) bulk_g2s(s.oinv, cx.inv + (size_t)cx.odd[o] * n * n, bi_bytes, s.bar);
+    }
+    const int k = threadIdx.x / n, i = threadIdx.x - (threadIdx.x / n) * n;
+    if (k < 8 && o < cx.n_o) {
+      const __half2* M = cx.blkh + bidx(cx.odd[o], 1 + k, n, i, 0);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) orow.r[j] = j < n ? M[(size_t)j * n] : __half2();
+    }
+    __syncthreads();
+    staged = __syncthreads_and(mbar_wait_bounded(s.bar, 0) ? 1 : 0);
+    if (!staged && threadIdx.x == 0) atomicExch(cx.err, 2);
+  }
   // own b, zero x
   for (int t = threadIdx.x; t < len; t += blockDim.x) {
     const int e = cx.rank * cx.nep + t / n;
@@ -293,9 +407,9 @@ __global__ void k_coarsest_cluster(Ctx<T> cx0, const cplx<T>* __restrict__ b, cp
   }
   __syncthreads();
   // bhat_e = b_e - D_eo S_oo^{-1} b_o  -> rv
-  odd_phase<T>(cx, s, cluster, s.xv, T(1), T(0));
+  odd_phase<T, NR>(cx, s, cluster, s.xv, T(1), T(0), orow);
   cluster.sync();
-  even_phase<T>(cx, s, cluster, s.xv, s.rv, T(1), T(0), T(-1));
+  even_phase<T, NR>(cx, s, cluster, s.xv, s.rv, T(1), T(0), T(-1));
   const T bnorm = sqrt(cluster_norm2<T>(cx, s, cluster, s.rv, len));
   const T target = (T)tol * bnorm;
   // keep bhat: be <- rv (be is not needed any more)
@@ -316,9 +430,9 @@ __global__ void k_coarsest_cluster(Ctx<T> cx0, const cplx<T>* __restrict__ b, cp
     for (int j = 0; j < m; ++j) {
       cplx<T>* vj = s.Vb + (size_t)j * len;
       // w = Dhat v_j
-      odd_phase<T>(cx, s, cluster, vj, T(0), T(1));
+      odd_phase<T, NR>(cx, s, cluster, vj, T(0), T(1), orow);
       cluster.sync();
-      even_phase<T>(cx, s, cluster, vj, s.wv, T(0), T(1), T(-1));
+      even_phase<T, NR>(cx, s, cluster, vj, s.wv, T(0), T(1), T(-1));
       // CGS2
       for (int pass = 0; pass < 2; ++pass) {
         cluster_dots<T>(cx, s, cluster, s.wv, j, pass, len);
@@ -395,74 +509,95 @@ __global__ void k_coarsest_cluster(Ctx<T> cx0, const cplx<T>* __restrict__ b, cp
     cluster.sync();
     if (cycle + 1 == max_cycles) break;
     // true residual r = bhat - Dhat x
-    odd_phase<T>(cx, s, cluster, s.xv, T(0), T(1));
+    odd_phase<T, NR>(cx, s, cluster, s.xv, T(0), T(1), orow);
     cluster.sync();
-    even_phase<T>(cx, s, cluster, s.xv, s.rv, T(1), T(-1), T(1));   // uses be = bhat as b
+    even_phase<T, NR>(cx, s, cluster, s.xv, s.rv, T(1), T(-1), T(1));   // uses be = bhat as b
     beta = sqrt(cluster_norm2<T>(cx, s, cluster, s.rv, len));
   }
   // z_o = S_oo^{-1} (b_o - D_oe x_e); write x
   cluster.sync();
-  odd_phase<T>(cx, s, cluster, s.xv, T(1), T(-1));
-  for (int t = threadIdx.x; t < len; t += blockDim.x) {
+  odd_phase<T, NR>(cx, s, cluster, s.xv, T(1), T(-1), orow);
+  for (int t = threadIdx.x; staged && t < len; t += blockDim.x) {
     const int e = cx.rank * cx.nep + t / n;
     if (e < cx.n_e) px[(size_t)cx.even[e] * n + t % n] = s.xv[t];
   }
-  for (int t = threadIdx.x; t < cx.nop * n; t += blockDim.x) {
+  for (int t = threadIdx.x; staged && t < cx.nop * n; t += blockDim.x) {
     const int o = cx.rank * cx.nop + t / n;
     if (o < cx.n_o) px[(size_t)cx.odd[o] * n + t % n] = s.tv[t];
   }
+  if constexpr (NR > 0)
+    if (!staged && threadIdx.x == 0) mbar_wait_bounded(s.bar, 0);   // no copy in flight at exit
   if (cx.rank == 0 && threadIdx.x == 0 && iters) atomicAdd(iters, total);
   cluster.sync();   // no CTA exits while others may still read its shared memory
 }
 
 template <typename T>
-size_t smem_bytes(int m, int nep, int nop, int n, int CL) {
+size_t smem_bytes(int m, int nep, int nop, int n, int CL, bool resident) {
   size_t c = (size_t)(m + 1) * nep * n + 4 * (size_t)nep * n + 2 * (size_t)nop * n + 18 * (size_t)n + n +
              3 * (size_t)CL * MAXM + (size_t)(m + 1) * m + (m + 1) + 2 * (size_t)m + 2 * MAXM;
-  return c * sizeof(cplx<T>) + (m + 8) * sizeof(T) + 64;
+  size_t b = c * sizeof(cplx<T>) + (m + 8) * sizeof(T) + 16;
+  if (resident) b += (size_t)9 * n * n * sizeof(__half2) + (size_t)n * n * sizeof(cplx<T>) + 16;
+  return b + 64;
 }
 
 }  // namespace
 
 namespace dd {
 
+template <typename T, int NR>
+bool cluster_fits(int CL, int threads, size_t sm) {
+  cudaFuncSetAttribute(k_coarsest_cluster<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (CL > 8) cudaFuncSetAttribute(k_coarsest_cluster<T, NR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(CL, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarsest_cluster<T, NR>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return nclusters >= 1;
+}
+
 // Chooses the cluster size (16 if the device can co-schedule it, else 8, 4, 2)
 // and reports whether the cluster kernel can run this level (shared memory).
+// For FP32 it also records whether the resident variant (FP16 blocks, one even
+// and one odd site per CTA) fits.
 template <typename T>
 int coarsest_cluster_plan(const CoarsestPlanIn& in, CoarsestPlan* plan) {
   const int n_e = in.n_even, n_o = in.n_odd;
   for (int CL : {16, 8, 4, 2}) {
     if (CL > n_e || CL > n_o) continue;
     const int nep = (n_e + CL - 1) / CL, nop = (n_o + CL - 1) / CL;
-    const size_t sm = smem_bytes<T>(in.m, nep, nop, in.n, CL);
+    const size_t sm = smem_bytes<T>(in.m, nep, nop, in.n, CL, false);
     if (sm > 220 * 1024) continue;
     int threads = ((9 * in.n + 31) / 32) * 32;
     if (threads < 256) threads = 256;
     if (threads > 1024) return 0;
-    cudaFuncSetAttribute(k_coarsest_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (CL > 8) cudaFuncSetAttribute(k_coarsest_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(CL, 1, 1);
-    cfg.blockDim = dim3(threads, 1, 1);
-    cfg.dynamicSmemBytes = sm;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarsest_cluster<T>, &cfg) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    if (nclusters < 1) continue;
+    if (!cluster_fits<T, 0>(CL, threads, sm)) continue;
     plan->CL = CL;
     plan->nep = nep;
     plan->nop = nop;
     plan->threads = threads;
     plan->smem = sm;
+    plan->res_nr = 0;
+    plan->res_smem = 0;
+    if constexpr (sizeof(T) == 4) {
+      const size_t smr = smem_bytes<T>(in.m, nep, nop, in.n, CL, true);
+      if (nep == 1 && nop == 1 && in.n <= RES_NR && threads <= 512 && smr <= 227 * 1024 &&
+          cluster_fits<T, RES_NR>(CL, threads, smr)) {
+        plan->res_nr = RES_NR;
+        plan->res_smem = smr;
+      }
+    }
     return 1;
   }
   return 0;
@@ -481,6 +616,7 @@ cudaError_t coarsest_cluster_solve(cplx<T>* x, const cplx<T>* b, const CoarseOp<
   cx.odd = geo.odd;
   cx.nbr_e_of_o = geo.nbr_e_of_o;
   cx.nbr_o_of_e = geo.nbr_o_of_e;
+  cx.err = op.err;
   cx.n_e = geo.n_even;
   cx.n_o = geo.n_odd;
   cx.nep = plan.nep;
@@ -488,6 +624,7 @@ cudaError_t coarsest_cluster_solve(cplx<T>* x, const cplx<T>* b, const CoarseOp<
   cx.n = op.n;
   cx.CL = plan.CL;
   cx.rank = 0;
+  const bool resident = sizeof(T) == 4 && op.blkh && plan.res_nr > 0;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -496,12 +633,15 @@ cudaError_t coarsest_cluster_solve(cplx<T>* x, const cplx<T>* b, const CoarseOp<
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(plan.CL, nrhs, 1);
   cfg.blockDim = dim3(plan.threads, 1, 1);
-  cfg.dynamicSmemBytes = plan.smem;
+  cfg.dynamicSmemBytes = resident ? plan.res_smem : plan.smem;
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   count_launch();
-  return cudaLaunchKernelEx(&cfg, k_coarsest_cluster<T>, cx, b, x, rstride, m, max_cycles, tol, iters);
+  if constexpr (sizeof(T) == 4)
+    if (resident)
+      return cudaLaunchKernelEx(&cfg, k_coarsest_cluster<T, RES_NR>, cx, b, x, rstride, m, max_cycles, tol, iters);
+  return cudaLaunchKernelEx(&cfg, k_coarsest_cluster<T, 0>, cx, b, x, rstride, m, max_cycles, tol, iters);
 }
 
 #define INST(T)                                                                                                     \

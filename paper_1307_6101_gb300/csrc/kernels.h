@@ -31,6 +31,8 @@ struct CoarseOp {
   const int* odd_sites; // indices of the odd sites (coarsest level), or null
   int n_odd;
   int sap_cls;          // cluster size of the cluster SAP kernel (0: one CTA per SAP block)
+  int sap_nsl = 0;      // blocks per site staged in shared memory by the cluster SAP kernel
+  int* err = nullptr;   // device error flag (bounded waits)
   // FP16 storage (FP32 compute only): blocks and one scale per site
   const __half2* blkh = nullptr;
   const float* bscale = nullptr;
@@ -69,7 +71,7 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
                       int nrhs, size_t rstride, int k_mr, cudaStream_t st);
 void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int n, int* err, cudaStream_t st);
 template <typename T>
-int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out);
+int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out, int* nsl_out);
 // t(A odd) = S^{-1}(a b + c D_oe x)     (even entries of t untouched)
 template <typename T>
 void coarse_schur_odd(cplx<T>* t, const cplx<T>* x, const cplx<T>* b, const CoarseOp<T>& op, double a, double c,
@@ -101,6 +103,8 @@ struct CoarsestPlanIn {
 struct CoarsestPlan {
   int CL = 0, nep = 0, nop = 0, threads = 0;
   size_t smem = 0;
+  int res_nr = 0;        // > 0: the resident variant (FP32 on FP16 blocks) fits
+  size_t res_smem = 0;
 };
 struct CoarsestGeo {
   const int* even = nullptr;

@@ -1069,8 +1069,8 @@ void allocate_hierarchy(ddamg_handle* h) {
     }
     if (!L.fine && !L.coarsest) {
       int cls = 0, spc = 0;
-      L.c32.sap_cls = coarse_sap_cluster_plan<float>(L.g, L.n, &cls, &spc) ? cls : 0;
-      L.c64.sap_cls = coarse_sap_cluster_plan<double>(L.g, L.n, &cls, &spc) ? cls : 0;
+      L.c32.sap_cls = coarse_sap_cluster_plan<float>(L.g, L.n, &cls, &spc, &L.c32.sap_nsl) ? cls : 0;
+      L.c64.sap_cls = coarse_sap_cluster_plan<double>(L.g, L.n, &cls, &spc, &L.c64.sap_nsl) ? cls : 0;
       cudaGetLastError();
     }
     if (!L.coarsest) {
@@ -1250,6 +1250,7 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
     h->d_err = dalloc<int>(h, 1);
     CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
     h->lv[0].f64.err = h->lv[0].f32.err = h->d_err;
+    for (auto& L : h->lv) L.c64.err = L.c32.err = h->d_err;
     double gg[6 * 16 * 2];
     gamma_products(gg);
     set_gamma_products(gg);
@@ -1379,8 +1380,8 @@ int ddamg_set_option(ddamg_handle* h, int option, int value) {
       for (auto& L : h->lv) {
         if (L.fine || L.coarsest) continue;
         int cls = 0, spc = 0;
-        L.c32.sap_cls = (value && coarse_sap_cluster_plan<float>(L.g, L.n, &cls, &spc)) ? cls : 0;
-        L.c64.sap_cls = (value && coarse_sap_cluster_plan<double>(L.g, L.n, &cls, &spc)) ? cls : 0;
+        L.c32.sap_cls = (value && coarse_sap_cluster_plan<float>(L.g, L.n, &cls, &spc, &L.c32.sap_nsl)) ? cls : 0;
+        L.c64.sap_cls = (value && coarse_sap_cluster_plan<double>(L.g, L.n, &cls, &spc, &L.c64.sap_nsl)) ? cls : 0;
       }
       cudaGetLastError();
       free_graphs(h);

@@ -15,7 +15,6 @@ DD_HD size_t faddr(bool fine, int V, int n, int x, int f) {
   return fine ? (size_t)f * V + x : (size_t)x * n + f;
 }
 
-constexpr int JC = 4;   // coarse columns per chirality handled per pass
 
 template <typename T>
 __device__ void block_sum(T* v, int cnt, T* sh) {
@@ -34,11 +33,19 @@ __device__ void block_sum(T* v, int cnt, T* sh) {
   __syncthreads();
 }
 
+constexpr int RJ = 10;   // coarse columns j accumulated per thread by k_restrict
+
+// out(A)[s*N + j] = sum over x in A, f in s of conj(P_j(x, f)) in(x, f).
+// One CTA per aggregate (and right-hand side); thread (group g, lane l) owns the
+// columns j in [g*RJ, g*RJ + RJ) and the sites x = A*vA + l, l + S, ... of the
+// aggregate, so every input and every P entry is loaded once.  S is a power of
+// two; the per-thread partial sums are reduced over the S lanes of a group in a
+// fixed order (shuffles inside warps, then shared memory across warps).
 template <typename T, typename PS>
 __global__ void k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const PS* __restrict__ P,
-                           const float* __restrict__ pscale, Geom gf, Geom gc, bool fine, int n, int N,
+                           const float* __restrict__ pscale, Geom gf, Geom gc, bool fine, int n, int N, int S,
                            size_t in_rstride, size_t pstride, size_t out_rstride, size_t out_site_stride) {
-  __shared__ T sh[32 * 4 * JC];
+  __shared__ T red[32 * 2 * RJ];
   const int agg = blockIdx.x;
   const int V = gf.V;
   const cplx<T>* pin = in + (size_t)blockIdx.y * in_rstride;
@@ -47,31 +54,56 @@ __global__ void k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict_
   const int cs = coarse_site_of(gf, gc, c0);
   cplx<T>* po = out + (size_t)blockIdx.y * out_rstride + (size_t)cs * out_site_stride;
   const int h = n / 2;
-  for (int j0 = 0; j0 < N; j0 += JC) {
-    T acc[4 * JC];
+  const int seg = S < 32 ? S : 32;            // lanes of a group inside one warp
+  const int slots = S / seg;                  // partial sums per group after the warp stage
+  const int gpc = blockDim.x / S;             // groups per CTA
+  const int G = (N + RJ - 1) / RJ;            // column groups
+  const int lane = threadIdx.x % S;
+  for (int g0 = 0; g0 < G; g0 += gpc) {
+    const int g = g0 + threadIdx.x / S;
+    const int j0 = g * RJ;
+    for (int s = 0; s < 2; ++s) {
+      T acc[2 * RJ];
 #pragma unroll
-    for (int k = 0; k < 4 * JC; ++k) acc[k] = T(0);
-    for (int xl = threadIdx.x; xl < gf.vA; xl += blockDim.x) {
-      const int x = agg * gf.vA + xl;
-      for (int f = 0; f < n; ++f) {
-        const cplx<T> v = pin[faddr(fine, V, n, x, f)];
-        const int s = f < h ? 0 : 1;
+      for (int k = 0; k < 2 * RJ; ++k) acc[k] = T(0);
+      if (g < G) {
+        for (int xl = lane; xl < gf.vA; xl += S) {
+          const int x = agg * gf.vA + xl;
+          for (int f = s * h; f < (s + 1) * h; ++f) {
+            const size_t a = faddr(fine, V, n, x, f);
+            const cplx<T> v = pin[a];
 #pragma unroll
-        for (int jj = 0; jj < JC; ++jj) {
-          if (j0 + jj < N) {
-            const cplx<T> p = ld_cplx(P, (size_t)(j0 + jj) * pstride + faddr(fine, V, n, x, f));
-            const cplx<T> t = cdotc(p, v);
-            acc[(s * JC + jj) * 2] += t.re;
-            acc[(s * JC + jj) * 2 + 1] += t.im;
+            for (int jj = 0; jj < RJ; ++jj) {
+              if (j0 + jj < N) {
+                const cplx<T> t = cdotc(ld_cplx(P, (size_t)(j0 + jj) * pstride + a), v);
+                acc[2 * jj] += t.re;
+                acc[2 * jj + 1] += t.im;
+              }
+            }
           }
         }
       }
-    }
-    block_sum(acc, 4 * JC, sh);
-    if (threadIdx.x < 2 * JC) {
-      const int s = threadIdx.x / JC, jj = threadIdx.x % JC;
-      const T sc = pscale ? T(pscale[agg * 2 + s]) : T(1);
-      if (j0 + jj < N) po[s * N + j0 + jj] = cmk<T>(sc * acc[(s * JC + jj) * 2], sc * acc[(s * JC + jj) * 2 + 1]);
+      for (int off = seg / 2; off >= 1; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < 2 * RJ; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+      if (threadIdx.x % seg == 0)
+#pragma unroll
+        for (int k = 0; k < 2 * RJ; ++k) red[(threadIdx.x / seg) * 2 * RJ + k] = acc[k];
+      __syncthreads();
+      for (int t = threadIdx.x; t < gpc * RJ; t += blockDim.x) {
+        const int gl = t / RJ, jj = t % RJ;
+        const int j = (g0 + gl) * RJ + jj;
+        if (g0 + gl < G && j < N) {
+          T re = T(0), im = T(0);
+          for (int q = 0; q < slots; ++q) {
+            re += red[(gl * slots + q) * 2 * RJ + 2 * jj];
+            im += red[(gl * slots + q) * 2 * RJ + 2 * jj + 1];
+          }
+          const T sc = pscale ? T(pscale[agg * 2 + s]) : T(1);
+          po[s * N + j] = cmk<T>(sc * re, sc * im);
+        }
+      }
+      __syncthreads();
     }
   }
 }
@@ -209,17 +241,23 @@ void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& 
                  int N, int nrhs, size_t in_rstride, size_t out_rstride, size_t out_site_stride, cudaStream_t st,
                  const __half2* Ph, const float* pscale) {
   const size_t pstride = (size_t)gf.V * n;
-  const int threads = gf.vA >= 256 ? 256 : (gf.vA >= 128 ? 128 : (gf.vA >= 64 ? 64 : 32));
+  int S = 1;   // lanes per column group: a power of two >= the aggregate volume, at most 256
+  while (S < gf.vA && S < 256) S *= 2;
+  const int G = (N + RJ - 1) / RJ;
+  int gpc = 1024 / S < G ? 1024 / S : G;
+  while (gpc * S < 32) ++gpc;   // at least one full warp
+  if (S < 32 && gpc > 32) gpc = 32;   // partial-sum slots in shared memory
+  const int threads = gpc * S;
   count_launch();
   if constexpr (sizeof(T) == 4) {
     if (Ph) {
-      k_restrict<float, __half2><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, Ph, pscale, gf, gc, fine, n, N,
+      k_restrict<float, __half2><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, Ph, pscale, gf, gc, fine, n, N, S,
                                                                           in_rstride, pstride, out_rstride,
                                                                           out_site_stride);
       return;
     }
   }
-  k_restrict<T, cplx<T>><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, P, nullptr, gf, gc, fine, n, N,
+  k_restrict<T, cplx<T>><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, P, nullptr, gf, gc, fine, n, N, S,
                                                                    in_rstride, pstride, out_rstride, out_site_stride);
 }
 
