@@ -7,6 +7,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <stdexcept>
+
 #include <cstdio>
 #include <atomic>
 #include <mutex>
@@ -152,16 +154,24 @@ template <typename T>
 __global__ void k_multiaxpy(cplx<T>* __restrict__ y, const cplx<T>* __restrict__ V, size_t vstride, int m,
                             const cplx<double>* __restrict__ c, int cstride, double sign, size_t len,
                             size_t rstride) {
+  // coefficients sign * c_i of this right-hand side, computed once per CTA; a zero
+  // coefficient skips its vector (never touch unused, possibly unset vectors)
+  __shared__ cplx<T> cs[64];
+  __shared__ int use[64];
+  const int rhs = blockIdx.y;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const cplx<double> ci = c[(size_t)rhs * cstride + i];
+    use[i] = !(ci.re == 0.0 && ci.im == 0.0);
+    cs[i] = cmk<T>((T)(sign * ci.re), (T)(sign * ci.im));
+  }
+  __syncthreads();
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= len) return;
-  const int rhs = blockIdx.y;
   const size_t o = (size_t)rhs * rstride + e;
   cplx<T> acc = y[o];
   for (int i = 0; i < m; ++i) {
-    const cplx<double> ci = c[(size_t)rhs * cstride + i];
-    if (ci.re == 0.0 && ci.im == 0.0) continue;   // never touch unused (possibly unset) vectors
-    const cplx<T> cc = cmk<T>((T)(sign * ci.re), (T)(sign * ci.im));
-    cfma(acc, cc, V[(size_t)i * vstride + o]);
+    if (!use[i]) continue;
+    cfma(acc, cs[i], V[(size_t)i * vstride + o]);
   }
   y[o] = acc;
 }
@@ -329,6 +339,7 @@ template <typename T>
 void blas_multiaxpy(cplx<T>* y, const cplx<T>* V, size_t vstride, int m, const cplx<double>* c, int cstride,
                     double sign, size_t len, int nrhs, size_t rstride, cudaStream_t st) {
   if (m <= 0) return;
+  if (m > 64) throw std::runtime_error("blas_multiaxpy: at most 64 vectors");
   count_launch();
   k_multiaxpy<T><<<dim3(div_up(len, 256), nrhs), 256, 0, st>>>(y, V, vstride, m, c, cstride, sign, len, rstride);
 }

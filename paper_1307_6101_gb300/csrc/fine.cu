@@ -137,12 +137,24 @@ DD_HD void load_link(const LS* __restrict__ U, int V, int mu, int x, cplx<T> u[9
   for (int k = 0; k < 9; ++k) u[k] = ld_cplx(U, (size_t)(mu * 9 + k) * V + x);
 }
 
+// x * (+1 or -1) as a flip of the sign bit (integer operation: no FP64 pipe use; same bits as the product)
+__device__ __forceinline__ double sign_flip(double x, bool neg) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+}
+__device__ __forceinline__ float sign_flip(float x, bool neg) {
+  return __int_as_float(__float_as_int(x) ^ (neg ? (int)0x80000000u : 0));
+}
+
+// the 12 components of a spinor at x times sign (+1 / -1); chir >= 0 keeps one chirality
 template <typename T>
-DD_HD void load_spinor(const cplx<T>* __restrict__ p, int V, int x, cplx<T> s[12], T sign, int chir) {
+__device__ __forceinline__ void load_spinor(const cplx<T>* __restrict__ p, int V, int x, cplx<T> s[12], T sign,
+                                            int chir) {
+  const bool neg = sign < T(0);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const bool keep = chir < 0 || (k / 6) == chir;
-    s[k] = keep ? sign * p[(size_t)k * V + x] : czero<T>();
+    const cplx<T> v = p[(size_t)k * V + x];
+    s[k] = keep ? cmk<T>(sign_flip(v.re, neg), sign_flip(v.im, neg)) : czero<T>();
   }
 }
 
@@ -357,7 +369,7 @@ __global__ void k_fine_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ 
 // batch.  Waits are bounded: on a timeout the kernel records an error code,
 // waits (bounded) for its copies and returns without touching z.
 template <typename T, typename LS, typename CS>
-__global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
+__global__ void __launch_bounds__(256, 2) k_fine_sap_tma(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
                                                       const LS* __restrict__ U, const CS* __restrict__ clov, Geom g,
                                                       int bc_t, size_t rstride, int nrhs, const int* __restrict__ blocks,
                                                       int nblocks, int seg, int k_mr, int* err, T shift) {
@@ -429,7 +441,9 @@ __global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, c
     mbar_wait_bounded(bar, 0);
     return;
   }
-  cplx<T> r[12], xs[12], p[12], nb[12], u[9];
+  // The block residual lives only in shared memory (Rs); each thread keeps its
+  // site's share of the correction e_B (xs) and of p = D_B r in registers.
+  cplx<T> xs[12], p[12], nb[12], u[9];
   for (int rh = 0; rh < nrhs; ++rh) {
     cplx<T>* pz = z + (size_t)rh * rstride;
     if (active) {
@@ -459,20 +473,16 @@ __global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, c
       const cplx<T>* pb = bsrc + (size_t)rh * rstride;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        r[k] = pb[(size_t)k * V + x] - (p[k] - T(0.5) * acc[k]);
+        Rs[(size_t)k * vB + loc] = pb[(size_t)k * V + x] - (p[k] - T(0.5) * acc[k]);
         xs[k] = czero<T>();
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < 12; ++k) { r[k] = czero<T>(); xs[k] = czero<T>(); }
+      for (int k = 0; k < 12; ++k) xs[k] = czero<T>();
     }
+    __syncthreads();
 #pragma unroll 1
     for (int it = 0; it < k_mr; ++it) {
-      if (active) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) Rs[(size_t)k * vB + loc] = r[k];
-      }
-      __syncthreads();
       T nre = T(0), nim = T(0), den = T(0);
       if (active) {
         cplx<T> acc[12];
@@ -484,18 +494,24 @@ __global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, c
           if (sl < 0) continue;
           const int mu = k >> 1;
           const bool fwd = (k & 1) == 0;
+          const bool neg = nsign[k] < T(0);
 #pragma unroll
-          for (int q = 0; q < 12; ++q) nb[q] = nsign[k] * Rs[(size_t)q * vB + sl];
+          for (int q = 0; q < 12; ++q) {
+            const cplx<T> v = Rs[(size_t)q * vB + sl];
+            nb[q] = cmk<T>(sign_flip(v.re, neg), sign_flip(v.im, neg));
+          }
           const int ls = fwd ? loc : sl;
 #pragma unroll
           for (int q = 0; q < 9; ++q) u[q] = ld_cplx(Ls, (size_t)(mu * 9 + q) * vB + ls);
           hop_accumulate(mu, fwd, u, nb, acc);
         }
-        clover_apply(Cs, vB, loc, r, p, shift);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) nb[q] = Rs[(size_t)q * vB + loc];   // own residual
+        clover_apply(Cs, vB, loc, nb, p, shift);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           p[k] = p[k] - T(0.5) * acc[k];
-          const cplx<T> t = cdotc(p[k], r[k]);
+          const cplx<T> t = cdotc(p[k], nb[k]);
           nre += t.re;
           nim += t.im;
           den += cnorm2(p[k]);
@@ -503,10 +519,14 @@ __global__ void __launch_bounds__(256) k_fine_sap_tma(cplx<T>* __restrict__ z, c
       }
       seg_sum3(nre, nim, den, seg, scratch);
       const cplx<T> alpha = den > T(0) ? cmk<T>(nre / den, nim / den) : czero<T>();
+      __syncthreads();   // every read of Rs for p is done before Rs changes
+      if (active) {
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        cfma(xs[k], alpha, r[k]);
-        r[k] = r[k] - alpha * p[k];
+        for (int k = 0; k < 12; ++k) {
+          const cplx<T> r = Rs[(size_t)k * vB + loc];
+          cfma(xs[k], alpha, r);
+          Rs[(size_t)k * vB + loc] = r - alpha * p[k];
+        }
       }
       __syncthreads();
     }
@@ -841,10 +861,13 @@ void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int
       return;
     }
   }
-  if (tma)
-    launch_sap_tma<T, cplx<T>, T>(z, b, op.U, op.clov, op, blocks, nblocks, nrhs, rstride, k_mr, T(0), st);
-  else
-    launch_sap_plain<T, cplx<T>, T>(z, b, op.U, op.clov, op, blocks, nblocks, nrhs, rstride, k_mr, T(0), st);
+  if constexpr (sizeof(T) == 4) {   // the staged kernel is an FP32 kernel (sap_tma_ok)
+    if (tma) {
+      launch_sap_tma<T, cplx<T>, T>(z, b, op.U, op.clov, op, blocks, nblocks, nrhs, rstride, k_mr, T(0), st);
+      return;
+    }
+  }
+  launch_sap_plain<T, cplx<T>, T>(z, b, op.U, op.clov, op, blocks, nblocks, nrhs, rstride, k_mr, T(0), st);
 }
 
 __global__ void k_links_to_half(__half2* __restrict__ dst, const cplx<double>* __restrict__ U, size_t n) {
