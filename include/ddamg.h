@@ -118,7 +118,8 @@ enum {
   DDAMG_OPT_COARSEST_CLUSTER = 1, /* 1 (default, where it fits): the coarsest odd-even GMRES runs as one
                                      persistent thread-block-cluster kernel per right-hand side */
   DDAMG_OPT_SAP_CLUSTER = 2,      /* 1 (default, where it fits): coarse-level SAP sweeps run one
-                                     thread-block cluster per SAP block; 0: one CTA per block */
+                                     thread-block cluster per SAP block; 2, 4, 8 or 16: try that
+                                     cluster size first; 0: one CTA per block */
   DDAMG_OPT_HALF_STORAGE = 3      /* 1: the FP32 kernels read FP16 copies of the fine links and
                                      clover term (no scale), of P (one FP32 scale per aggregate
                                      and chirality) and of the coarse blocks (one FP32 scale per

@@ -94,8 +94,7 @@ __global__ void k_multidot1(double* __restrict__ part, const cplx<T>* __restrict
       for (int dd = 0; dd < 4; ++dd) {
         if (d0 + dd < m) {
           const cplx<T> v = V[(size_t)(d0 + dd) * vstride + (size_t)rhs * rstride + e];
-          at[2 * dd] += v.re * we.re + v.im * we.im;
-          at[2 * dd + 1] += v.re * we.im - v.im * we.re;
+          cdotc_acc(at[2 * dd], at[2 * dd + 1], v, we);
         }
       }
     }
@@ -134,7 +133,7 @@ __global__ void k_norm1(double* __restrict__ part, const cplx<T>* __restrict__ x
   T at = T(0);
   for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
     const cplx<T> v = px[e];
-    at += v.re * v.re + v.im * v.im;
+    cnorm2_acc(at, v);
   }
   double acc[1] = {(double)at};
   cta_sum(acc, 1, sh);

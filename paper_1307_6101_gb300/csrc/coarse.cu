@@ -318,7 +318,7 @@ DD_HD SapSmem sap_smem_layout(int vB, int n, int spc, int nsl, size_t bs, size_t
 // and applies r <- r - alpha p to its whole copy.  Same arithmetic as
 // k_coarse_sap: rho = (b - D z)_B, k MR steps on D_B, z_B += e_B.
 template <typename T, typename BS>
-__global__ void k_coarse_sap_cluster(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
+__global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
                                      const BS* __restrict__ blk, const float* __restrict__ bscale, Geom g, int n,
                                      size_t rstride, const int* __restrict__ blocks, int k_mr, int spc, int nsl,
                                      int* err) {
@@ -442,11 +442,17 @@ __global__ void k_coarse_sap_cluster(cplx<T>* __restrict__ z, const cplx<T>* __r
     }
     if (lane == 0) { sh[3 * warp] = nre; sh[3 * warp + 1] = nim; sh[3 * warp + 2] = den; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      T a = T(0), bb = T(0), cc = T(0);
-      for (int w = 0; w < nw; ++w) { a += sh[3 * w]; bb += sh[3 * w + 1]; cc += sh[3 * w + 2]; }
-      for (int c = 0; c < CLS; ++c) {
-        T* dst = cluster.map_shared_rank(rb, c) + rank * 4;
+    if (warp == 0) {   // warp partials summed by a shuffle tree (fixed order), then sent to every CTA
+      T a = lane < nw ? sh[3 * lane] : T(0);
+      T bb = lane < nw ? sh[3 * lane + 1] : T(0);
+      T cc = lane < nw ? sh[3 * lane + 2] : T(0);
+      for (int off = 16; off >= 1; off >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        bb += __shfl_xor_sync(0xffffffffu, bb, off);
+        cc += __shfl_xor_sync(0xffffffffu, cc, off);
+      }
+      if (lane < CLS) {
+        T* dst = cluster.map_shared_rank(rb, lane) + rank * 4;
         dst[0] = a;
         dst[1] = bb;
         dst[2] = cc;
@@ -679,13 +685,14 @@ void sap_cluster_attrs(size_t smem, int CLS) {
 // site (0 if no plan fits).  Sized for operator storage in the compute precision, which
 // also covers the FP16 storage.
 template <typename T>
-int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out, int* nsl_out) {
+int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out, int* nsl_out, int prefer) {
   const int nsl = coarse_sap_slots(g);
-  for (int CLS : {8, 16, 4, 2}) {
+  for (int CLS : {prefer, 16, 8, 4, 2}) {
+    if (CLS != 2 && CLS != 4 && CLS != 8 && CLS != 16) continue;
     if (g.vB % CLS) continue;
     const int spc = g.vB / CLS;
     const int threads = ((9 * spc * n + 31) / 32) * 32;
-    if (threads > 1024) continue;
+    if (threads > 768) continue;   // launch bounds of k_coarse_sap_cluster
     const size_t sm = sap_smem_layout(g.vB, n, spc, nsl, sizeof(cplx<T>), sizeof(T)).total;
     if (sm > 227 * 1024) continue;
     sap_cluster_attrs<T, cplx<T>>(sm, CLS);
@@ -860,7 +867,7 @@ void coarse_blocks_export(cplx<double>* dst, const cplx<double>* blk, const Geom
                                     int, size_t, cudaStream_t);                                                   \
   template void coarse_schur_even<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const cplx<T>*, const CoarseOp<T>&, \
                                      double, double, double, int, size_t, cudaStream_t);                          \
-  template int coarse_sap_cluster_plan<T>(const Geom&, int, int*, int*, int*);                                     \
+  template int coarse_sap_cluster_plan<T>(const Geom&, int, int*, int*, int*, int);                                \
   template void coarse_sap_sweep<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, const int*, int, int, size_t,   \
                                     int, cudaStream_t);                                                           \
   template void coarse_selfinv_apply<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, int, int, size_t,           \

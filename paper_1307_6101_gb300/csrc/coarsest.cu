@@ -182,12 +182,19 @@ __device__ void odd_phase(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group&
       s.us[i] = u;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    // t = S^{-1} u: 8 lanes per row, each a strided share of the columns, summed by shuffles
+    // (the loop runs to a multiple of 32 so that whole warps take part in the shuffles)
+    for (int t = threadIdx.x; t < ((8 * n + 31) & ~31); t += blockDim.x) {
+      const int i = t >> 3, q = t & 7;
       cplx<T> acc = czero<T>();
-      const cplx<T>* Mi = s.oinv + i;
-#pragma unroll 8
-      for (int j = 0; j < n; ++j) cfma(acc, Mi[(size_t)j * n], s.us[j]);
-      s.tv[i] = acc;
+      if (i < n)
+        for (int j = q; j < n; j += 8) cfma(acc, s.oinv[(size_t)j * n + i], s.us[j]);
+#pragma unroll
+      for (int off = 4; off >= 1; off >>= 1) {
+        acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
+        acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
+      }
+      if (q == 0 && i < n) s.tv[i] = acc;
     }
     __syncthreads();
   } else {
@@ -307,15 +314,18 @@ __device__ void cta_sum_c(T re, T im, const Smem<T>& s, cplx<T>* buf) {
   __syncthreads();
 }
 
-// h[d] = sum over all CTAs of conj(V_d) . w (d <= j), rank-ordered; slot selects the partial buffer.
-// Groups of 16 lanes own one d each and reduce with shuffles (fixed order).
+// h[d] = sum over all CTAs of conj(V_d) . w for d <= j and, with with_norm, h[j+1] = ||w||^2.
+// Groups of 16 lanes own one d each and reduce with shuffles (fixed order); lane q of the
+// group then writes the CTA's partial into CTA q's buffer `slot`, so after the barrier
+// every CTA sums its own copy in rank order (identical in every CTA, local reads only).
 template <typename T>
 __device__ void cluster_dots(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group& cluster, const cplx<T>* w,
-                             int j, int slot, int len) {
-  cplx<T>* red0 = cluster.map_shared_rank(s.red, 0) + (size_t)slot * cx.CL * MAXM;
+                             int j, int slot, int len, bool with_norm) {
+  cplx<T>* red = s.red + (size_t)slot * cx.CL * MAXM;
   const int G = 16;
   const int grp = threadIdx.x / G, l = threadIdx.x % G, ngrp = blockDim.x / G;
-  for (int d0 = 0; d0 <= j; d0 += ngrp) {
+  const int dmax = with_norm ? j + 1 : j;
+  for (int d0 = 0; d0 <= dmax; d0 += ngrp) {
     const int d = d0 + grp;
     T re = T(0), im = T(0);
     if (d <= j) {
@@ -325,34 +335,36 @@ __device__ void cluster_dots(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_gro
         re += t.re;
         im += t.im;
       }
+    } else if (d == dmax) {
+      for (int e = l; e < len; e += G) re += cnorm2(w[e]);
     }
     for (int off = G / 2; off >= 1; off >>= 1) {
       re += __shfl_xor_sync(0xffffffffu, re, off);
       im += __shfl_xor_sync(0xffffffffu, im, off);
     }
-    if (l == 0 && d <= j) red0[cx.rank * MAXM + d] = cmk<T>(re, im);
+    if (d <= dmax && l < cx.CL) cluster.map_shared_rank(red, l)[cx.rank * MAXM + d] = cmk<T>(re, im);
   }
   cluster.sync();
-  for (int d = threadIdx.x; d <= j; d += blockDim.x) {
+  for (int d = threadIdx.x; d <= dmax; d += blockDim.x) {
     cplx<T> t = czero<T>();
-    for (int q = 0; q < cx.CL; ++q) t = t + red0[q * MAXM + d];
+    for (int q = 0; q < cx.CL; ++q) t = t + red[q * MAXM + d];
     s.hsum[d] = t;
   }
   __syncthreads();
 }
 
-// ||w||^2 over the cluster (rank-ordered)
+// ||w||^2 over the cluster (rank-ordered; every CTA sums its own copy of the partials)
 template <typename T>
 __device__ T cluster_norm2(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group& cluster, const cplx<T>* w, int len) {
-  cplx<T>* red0 = cluster.map_shared_rank(s.red, 0) + (size_t)2 * cx.CL * MAXM;
+  cplx<T>* red = s.red + (size_t)2 * cx.CL * MAXM;
   T a = T(0);
   for (int e = threadIdx.x; e < len; e += blockDim.x) a += cnorm2(w[e]);
   cta_sum_c(a, T(0), s, s.part);
-  if (threadIdx.x == 0) red0[cx.rank * MAXM] = cmk<T>(s.scal[0], T(0));
+  if (threadIdx.x < cx.CL) cluster.map_shared_rank(red, threadIdx.x)[cx.rank * MAXM] = cmk<T>(s.scal[0], T(0));
   cluster.sync();
-  if (threadIdx.x == 0) {   // one thread reads the remote partials, the CTA reads its copy
+  if (threadIdx.x == 0) {
     T t = T(0);
-    for (int q = 0; q < cx.CL; ++q) t += red0[q * MAXM].re;
+    for (int q = 0; q < cx.CL; ++q) t += red[q * MAXM].re;
     s.scal[4] = t;
   }
   __syncthreads();
@@ -433,19 +445,35 @@ __global__ void __launch_bounds__(512, 1) k_coarsest_cluster(Ctx<T> cx0, const c
       odd_phase<T, NR>(cx, s, cluster, vj, T(0), T(1), orow);
       cluster.sync();
       even_phase<T, NR>(cx, s, cluster, vj, s.wv, T(0), T(1), T(-1));
-      // CGS2
+      // CGS2; the second pass also sums ||w'||^2, and ||w''||^2 = ||w'||^2 - sum_d |h2_d|^2
+      // (w'' = w' - V h2 with h2 = V^+ w' and V orthonormal), which saves a reduction
       for (int pass = 0; pass < 2; ++pass) {
-        cluster_dots<T>(cx, s, cluster, s.wv, j, pass, len);
-        if (threadIdx.x == 0)
-          for (int d = 0; d <= j; ++d) s.htot[d] = pass == 0 ? s.hsum[d] : s.htot[d] + s.hsum[d];
-        for (int e = threadIdx.x; e < len; e += blockDim.x) {
-          cplx<T> we = s.wv[e];
-          for (int d = 0; d <= j; ++d) we = we - s.hsum[d] * s.Vb[(size_t)d * len + e];
-          s.wv[e] = we;
+        cluster_dots<T>(cx, s, cluster, s.wv, j, pass, len, pass == 1);
+        if (threadIdx.x == 0) {
+          T h2 = T(0);
+          for (int d = 0; d <= j; ++d) {
+            s.htot[d] = pass == 0 ? s.hsum[d] : s.htot[d] + s.hsum[d];
+            h2 += cnorm2(s.hsum[d]);
+          }
+          if (pass == 1) s.scal[5] = s.hsum[j + 1].re - h2;
+        }
+        // w -= sum_d h_d V_d: 8 lanes per element, each a strided share of d, summed by shuffles
+        // (the loop runs to a multiple of 32 so that whole warps take part in the shuffles)
+        for (int t = threadIdx.x; t < ((8 * len + 31) & ~31); t += blockDim.x) {
+          const int e = t >> 3, q = t & 7;
+          cplx<T> acc = czero<T>();
+          if (e < len)
+            for (int d = q; d <= j; d += 8) cfma(acc, s.hsum[d], s.Vb[(size_t)d * len + e]);
+#pragma unroll
+          for (int off = 4; off >= 1; off >>= 1) {
+            acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
+            acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
+          }
+          if (q == 0 && e < len) s.wv[e] = s.wv[e] - acc;
         }
         __syncthreads();
       }
-      const T hn = sqrt(cluster_norm2<T>(cx, s, cluster, s.wv, len));
+      const T hn = sqrt(s.scal[5] > T(0) ? s.scal[5] : T(0));
       // Givens update, identical in every CTA
       if (threadIdx.x == 0) {
         cplx<T> h[MAXM + 1];

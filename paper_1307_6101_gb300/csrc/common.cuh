@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <cmath>
 
 #define DD_HD __host__ __device__ __forceinline__
 
@@ -41,15 +42,31 @@ template <typename T> DD_HD cplx<T> cconj(cplx<T> a) { return cmk<T>(a.re, -a.im
 template <typename T> DD_HD cplx<T> cdotc(cplx<T> a, cplx<T> b) {
   return cmk<T>(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
 }
-// acc += a * b
+// acc += a * b as four fused multiply-adds (no separate product and sum: on GB300
+// an FP64 multiply or add costs an FP64 pipe slot like an FMA)
 template <typename T> DD_HD void cfma(cplx<T>& acc, cplx<T> a, cplx<T> b) {
-  acc.re += a.re * b.re - a.im * b.im;
-  acc.im += a.re * b.im + a.im * b.re;
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
 }
 // acc += conj(a) * b
 template <typename T> DD_HD void cfmac(cplx<T>& acc, cplx<T> a, cplx<T> b) {
-  acc.re += a.re * b.re + a.im * b.im;
-  acc.im += a.re * b.im - a.im * b.re;
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+// (re, im) += conj(a) * b and n2 += |a|^2, fused
+template <typename T> DD_HD void cdotc_acc(T& re, T& im, cplx<T> a, cplx<T> b) {
+  re = fma(a.re, b.re, re);
+  re = fma(a.im, b.im, re);
+  im = fma(a.re, b.im, im);
+  im = fma(-a.im, b.re, im);
+}
+template <typename T> DD_HD void cnorm2_acc(T& n2, cplx<T> a) {
+  n2 = fma(a.re, a.re, n2);
+  n2 = fma(a.im, a.im, n2);
 }
 template <typename T> DD_HD cplx<T> times_i(cplx<T> a) { return cmk<T>(-a.im, a.re); }
 template <typename T> DD_HD cplx<T> times_mi(cplx<T> a) { return cmk<T>(a.im, -a.re); }

@@ -71,7 +71,8 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
                       int nrhs, size_t rstride, int k_mr, cudaStream_t st);
 void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int n, int* err, cudaStream_t st);
 template <typename T>
-int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out, int* nsl_out);
+// prefer: a cluster size (2, 4, 8, 16) to try first, anything else for the default order
+int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out, int* nsl_out, int prefer = 0);
 // t(A odd) = S^{-1}(a b + c D_oe x)     (even entries of t untouched)
 template <typename T>
 void coarse_schur_odd(cplx<T>* t, const cplx<T>* x, const cplx<T>* b, const CoarseOp<T>& op, double a, double c,

@@ -1380,8 +1380,10 @@ int ddamg_set_option(ddamg_handle* h, int option, int value) {
       for (auto& L : h->lv) {
         if (L.fine || L.coarsest) continue;
         int cls = 0, spc = 0;
-        L.c32.sap_cls = (value && coarse_sap_cluster_plan<float>(L.g, L.n, &cls, &spc, &L.c32.sap_nsl)) ? cls : 0;
-        L.c64.sap_cls = (value && coarse_sap_cluster_plan<double>(L.g, L.n, &cls, &spc, &L.c64.sap_nsl)) ? cls : 0;
+        L.c32.sap_cls =
+            (value && coarse_sap_cluster_plan<float>(L.g, L.n, &cls, &spc, &L.c32.sap_nsl, value)) ? cls : 0;
+        L.c64.sap_cls =
+            (value && coarse_sap_cluster_plan<double>(L.g, L.n, &cls, &spc, &L.c64.sap_nsl, value)) ? cls : 0;
       }
       cudaGetLastError();
       free_graphs(h);

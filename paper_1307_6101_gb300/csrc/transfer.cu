@@ -42,7 +42,7 @@ constexpr int RJ = 10;   // coarse columns j accumulated per thread by k_restric
 // two; the per-thread partial sums are reduced over the S lanes of a group in a
 // fixed order (shuffles inside warps, then shared memory across warps).
 template <typename T, typename PS>
-__global__ void k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const PS* __restrict__ P,
+__global__ void __launch_bounds__(512, 2) k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const PS* __restrict__ P,
                            const float* __restrict__ pscale, Geom gf, Geom gc, bool fine, int n, int N, int S,
                            size_t in_rstride, size_t pstride, size_t out_rstride, size_t out_site_stride) {
   __shared__ T red[32 * 2 * RJ];
@@ -244,9 +244,9 @@ void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& 
   int S = 1;   // lanes per column group: a power of two >= the aggregate volume, at most 256
   while (S < gf.vA && S < 256) S *= 2;
   const int G = (N + RJ - 1) / RJ;
-  int gpc = 1024 / S < G ? 1024 / S : G;
-  while (gpc * S < 32) ++gpc;   // at least one full warp
-  if (S < 32 && gpc > 32) gpc = 32;   // partial-sum slots in shared memory
+  int gpc = 512 / S < G ? 512 / S : G;   // at most 512 threads (launch bounds)
+  if (S < 32) gpc = ((gpc * S + 31) / 32) * (32 / S);   // whole warps (the shuffles use full masks)
+  if (S < 32 && gpc > 32) gpc = 32;                     // partial-sum slots in shared memory
   const int threads = gpc * S;
   count_launch();
   if constexpr (sizeof(T) == 4) {
