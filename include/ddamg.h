@@ -28,6 +28,7 @@
 #ifndef DDAMG_H
 #define DDAMG_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -40,7 +41,8 @@ enum {
   DDAMG_ERR_OOM = -2,       /* device allocation failed / admission refused    */
   DDAMG_ERR_NOCONV = -3,    /* outer FGMRES did not reach tol within its limit */
   DDAMG_ERR_CUDA = -4,      /* a CUDA call failed                              */
-  DDAMG_ERR_SINGULAR = -5   /* rank-deficient test vectors / singular block    */
+  DDAMG_ERR_SINGULAR = -5,  /* rank-deficient test vectors / singular block    */
+  DDAMG_ERR_ADMISSION = -6  /* serving: device footprint exceeds the budget    */
 };
 
 #define DDAMG_MAX_LEVELS 4
@@ -223,6 +225,48 @@ int ddamg_get_interpolation(ddamg_handle* h, int level, double* P);
 /* D_l (l >= 1) as blocks [coarse site lex][k][row][col] complex, k = 0 self,
  * 1..4 forward mu = t,z,y,x (couples to site + mu), 5..8 backward mu. */
 int ddamg_get_coarse_operator(ddamg_handle* h, int level, double* blocks);
+
+/* ---- Device footprint ------------------------------------------------------
+ * Bytes of the device memory the library allocated for this handle (operators,
+ * P, test vectors, Krylov workspaces, FP16 copies, staging buffers). */
+int ddamg_device_bytes(ddamg_handle* h, size_t* bytes);
+/* Estimate of ddamg_device_bytes for a hierarchy that is not built yet (host
+ * arithmetic only, no device call).  Errors: ARG. */
+int ddamg_estimate_bytes(const int dims[4], const ddamg_params* params, size_t* bytes);
+
+/* ---- Serving -------------------------------------------------------------------
+ * Not in the paper: a request loop over hierarchies that stay resident on the
+ * device.  Each registered hierarchy gets a worker thread that runs the outer
+ * FGMRES of Sec. 2 one restart cycle at a time on a batch of up to max_rhs
+ * right-hand sides (continuous batching): waiting right-hand sides enter free
+ * batch slots at every restart boundary, and a right-hand side leaves the batch
+ * once its true residual meets its tolerance (or after outer_max_cycles cycles).
+ * Every right-hand side is computed with batch-independent reductions, so its
+ * result does not depend on what else shares its batch.  Different hierarchies
+ * run on their handles' own streams and overlap on the device.  While a handle
+ * is registered, no other call may use it; ddamg_server_free returns it. */
+typedef struct ddamg_server ddamg_server;
+/* hbm_budget: device bytes the registered hierarchies may hold (0: 90% of the
+ * device memory). */
+int ddamg_server_create(size_t hbm_budget, ddamg_server** out);
+/* Registers a built hierarchy; *hid identifies it in submissions.  Errors:
+ * ADMISSION if its ddamg_device_bytes exceed the remaining budget, ARG. */
+int ddamg_server_add(ddamg_server* s, ddamg_handle* h, int* hid);
+/* Queues n right-hand sides (host memory, the ddamg_solve layout, copied before
+ * the call returns) at relative tolerance tol; *id names the request.  Returns
+ * at once. */
+int ddamg_server_submit(ddamg_server* s, int hid, const double* rhs, int n, double tol, long long* id);
+/* *done = 1 once the request has finished (its result can be taken by wait). */
+int ddamg_server_poll(ddamg_server* s, long long id, int* done);
+/* Blocks until request id has finished, copies its n solutions to x (host, the
+ * ddamg_solve layout) and per_rhs statistics (may be NULL), and releases it.
+ * times (may be NULL) receives 3 doubles in seconds: queueing before its first
+ * restart cycle, latency from submission to completion, time in the batch.
+ * Returns OK, NOCONV (x holds the last iterates) or the error of its batch. */
+int ddamg_server_wait(ddamg_server* s, long long id, double* x, ddamg_stats* per_rhs, double* times);
+/* Finishes the right-hand sides in the batches, fails the queued ones, joins
+ * the workers and frees the server (not the hierarchies). */
+int ddamg_server_free(ddamg_server* s);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@ DDAMG_ERR_OOM = -2
 DDAMG_ERR_NOCONV = -3
 DDAMG_ERR_CUDA = -4
 DDAMG_ERR_SINGULAR = -5
+DDAMG_ERR_ADMISSION = -6
 MAX_LEVELS = 4
 
 EXPORTED = (
@@ -32,6 +33,8 @@ EXPORTED = (
     "ddamg_get_testvectors", "ddamg_rebuild", "ddamg_get_interpolation", "ddamg_get_coarse_operator",
     "ddamg_profile", "ddamg_profile_read", "ddamg_launch_count", "ddamg_set_option",
     "ddamg_krylov_steps", "ddamg_residual_norm_noalloc", "ddamg_get_option",
+    "ddamg_device_bytes", "ddamg_estimate_bytes", "ddamg_server_create", "ddamg_server_add",
+    "ddamg_server_submit", "ddamg_server_poll", "ddamg_server_wait", "ddamg_server_free",
 )
 DDAMG_OPT_GRAPHS = 0
 DDAMG_OPT_COARSEST_CLUSTER = 1
@@ -109,6 +112,15 @@ def _load():
     lib.ddamg_residual_norm_noalloc.argtypes = [vp, vp, vp, ip, vp]
     lib.ddamg_launch_count.restype = C.c_longlong
     lib.ddamg_launch_count.argtypes = []
+    sp = C.POINTER(C.c_size_t)
+    lib.ddamg_device_bytes.argtypes = [vp, sp]
+    lib.ddamg_estimate_bytes.argtypes = [C.POINTER(C.c_int), C.POINTER(DdamgParams), sp]
+    lib.ddamg_server_create.argtypes = [C.c_size_t, C.POINTER(vp)]
+    lib.ddamg_server_add.argtypes = [vp, vp, C.POINTER(C.c_int)]
+    lib.ddamg_server_submit.argtypes = [vp, ip, vp, ip, C.c_double, C.POINTER(C.c_longlong)]
+    lib.ddamg_server_poll.argtypes = [vp, C.c_longlong, C.POINTER(C.c_int)]
+    lib.ddamg_server_wait.argtypes = [vp, C.c_longlong, vp, C.POINTER(DdamgStats), C.POINTER(C.c_double)]
+    lib.ddamg_server_free.argtypes = [vp]
     del dp
     return lib
 
@@ -301,3 +313,64 @@ def ddamg_get_option(h, option):
     v = C.c_int()
     _check(lib().ddamg_get_option(h.raw, int(option), C.byref(v)))
     return v.value
+
+
+def ddamg_device_bytes(h):
+    n = C.c_size_t()
+    _check(lib().ddamg_device_bytes(h.raw, C.byref(n)))
+    return n.value
+
+
+def ddamg_estimate_bytes(dims, params):
+    """Device bytes a hierarchy with these parameters would hold (host arithmetic, no device call)."""
+    d = (C.c_int * 4)(*[int(x) for x in dims])
+    n = C.c_size_t()
+    _check(lib().ddamg_estimate_bytes(d, C.byref(params), C.byref(n)))
+    return n.value
+
+
+class Server:
+    """Continuous-batching request loop over resident hierarchies (ddamg_server_*)."""
+
+    def __init__(self, hbm_budget=0):
+        self.raw = C.c_void_p()
+        _check(lib().ddamg_server_create(C.c_size_t(int(hbm_budget)), C.byref(self.raw)))
+        self._handles = []
+
+    def add(self, h):
+        hid = C.c_int()
+        _check(lib().ddamg_server_add(self.raw, h.raw, C.byref(hid)))
+        self._handles.append(h)
+        return hid.value
+
+    def submit(self, hid, rhs, n, tol):
+        rid = C.c_longlong()
+        _check(lib().ddamg_server_submit(self.raw, int(hid), _ptr(rhs), int(n), float(tol), C.byref(rid)))
+        return rid.value
+
+    def poll(self, rid):
+        d = C.c_int()
+        _check(lib().ddamg_server_poll(self.raw, C.c_longlong(rid), C.byref(d)))
+        return bool(d.value)
+
+    def wait(self, rid, x, n, check=True):
+        """Solutions into x; returns (per-rhs stats dicts, (queue_s, latency_s, batch_s), return code)."""
+        st = (DdamgStats * int(n))()
+        t = (C.c_double * 3)()
+        rc = lib().ddamg_server_wait(self.raw, C.c_longlong(rid), _ptr(x), st, t)
+        if check and rc not in (DDAMG_OK, DDAMG_ERR_NOCONV):
+            _check(rc)
+        stats = [dict(iterations=s.iterations, cycles=s.cycles, converged=bool(s.converged),
+                      true_residual=s.true_residual) for s in st]
+        return stats, (t[0], t[1], t[2]), rc
+
+    def free(self):
+        if self.raw:
+            lib().ddamg_server_free(self.raw)
+            self.raw = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -11,10 +11,17 @@
 #include "ddamg.h"
 #include "kernels.h"
 
+#include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace dd;
@@ -119,6 +126,8 @@ struct GraphEntry {
 
 struct ddamg_handle {
   ddamg_params p{};
+  int device = 0;
+  size_t dev_bytes = 0;   // bytes of the library's own device allocations for this handle
   int dims[4] = {0, 0, 0, 0};
   int bc_t = -1;
   double m0 = 0, csw = 0;
@@ -174,6 +183,7 @@ T* dalloc(ddamg_handle* h, size_t count) {
     fail(DDAMG_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
   }
   h->allocs.push_back(p);
+  h->dev_bytes += count * sizeof(T);
   return static_cast<T*>(p);
 }
 
@@ -184,12 +194,14 @@ void* scratch(ddamg_handle* h, int slot, size_t bytes) {
       CK(cudaStreamSynchronize(h->st));
       cudaFree(s.p);
       s.p = nullptr;
+      h->dev_bytes -= s.cap;
       s.cap = 0;
     }
     if (cudaMalloc(&s.p, bytes) != cudaSuccess) {
       cudaGetLastError();
       fail(DDAMG_ERR_OOM, "scratch allocation of " + std::to_string(bytes) + " bytes failed");
     }
+    h->dev_bytes += bytes;
     s.cap = bytes;
   }
   return s.p;
@@ -347,7 +359,10 @@ struct KrylovResult {
 
 template <typename T, class AOp, class MOp>
 void krylov_host(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>* b, int nrhs, int m, double tol,
-                 int max_cycles, bool final_residual, bool flexible, AOp A, MOp M, KrylovResult* res) {
+                 int max_cycles, bool final_residual, bool flexible, AOp A, MOp M, KrylovResult* res,
+                 bool resume = false, const double* tol_rhs = nullptr) {
+  // resume: x and ws.r already hold an iterate and its residual b - A x (continued
+  // restart cycles); tol_rhs: one relative tolerance per right-hand side
   cudaStream_t st = h->st;
   const size_t rs = vlen;
   const size_t vs = (size_t)h->max_batch * vlen;
@@ -359,10 +374,14 @@ void krylov_host(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cp
   CK(cudaMemcpyAsync(h->h_scal, s.beta, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
   sync(h);
   std::vector<double> bnorm(h->h_scal, h->h_scal + nrhs), target(nrhs);
-  for (int r = 0; r < nrhs; ++r) target[r] = tol * bnorm[r];
+  for (int r = 0; r < nrhs; ++r) target[r] = (tol_rhs ? tol_rhs[r] : tol) * bnorm[r];
   CK(cudaMemcpyAsync(s.target, target.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-  blas_zero<T>(x, vlen, nrhs, rs, st);
-  blas_convert<T, T>(ws.r, b, vlen, nrhs, rs, rs, st);
+  if (!resume) {
+    blas_zero<T>(x, vlen, nrhs, rs, st);
+    blas_convert<T, T>(ws.r, b, vlen, nrhs, rs, rs, st);
+  } else {
+    blas_norm2<T>(s.beta, ws.r, vlen, nrhs, rs, st);   // residual norms of the given iterates
+  }
   if (res) {
     res->iterations.assign(nrhs, 0);
     res->cycles.assign(nrhs, 0);
@@ -1183,6 +1202,244 @@ void hook(ddamg_handle* h, int l, const double* in, double* out, int n, bool out
 // C ABI
 namespace {
 
+// The outer FGMRES (FP64, flexible, preconditioned by one K-cycle) on the first
+// nb right-hand sides of h->ob, iterate in h->ox.  resume: continue from h->ox
+// and its residual in h->outer.r (one restart cycle at a time, as the serving
+// loop runs it).
+void outer_fgmres(ddamg_handle* h, int nb, double tol, int max_cycles, KrylovResult* res, bool resume = false,
+                  const double* tol_rhs = nullptr) {
+  Level& F = h->lv[0];
+  auto A = [&](cplx<double>* o, const cplx<double>* in, const cplx<double>* bb) {
+    apply_D<double>(h, F, o, in, bb, nb);
+  };
+  auto M = [&](cplx<double>* z, const cplx<double>* v) {
+    if (h->p.precision != 0) precond_outer<float>(h, z, v, nb);
+    else precond_outer<double>(h, z, v, nb);
+  };
+  krylov_host<double>(h, h->outer, F.vlen, h->ox, h->ob, nb, h->p.outer_restart, tol, max_cycles, true, true, A, M,
+                      res, resume, tol_rhs);
+}
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching of right-hand sides over resident hierarchies.
+//
+// Each registered hierarchy has a worker thread and keeps using the handle's
+// own stream, so the work of different hierarchies overlaps on the device.
+// Requests (1..n right-hand sides, one tolerance) are split into columns that
+// wait in a FIFO queue; a column enters a free batch slot at the next restart
+// boundary of the outer FGMRES, the batch runs one restart cycle, and slots
+// whose true residual meets their tolerance (or that used up the restart
+// budget) leave it; the remaining slots are compacted to the front.  Every
+// right-hand side is computed with batch-independent reductions, so its
+// iterate is the same whichever other columns share its batch.
+
+double now_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct SrvRequest {
+  int hid = 0, n = 0;
+  double tol = 0;
+  std::vector<double> b, x;   // n fields in the ABI layout
+  std::vector<ddamg_stats> st;
+  int remaining = 0;
+  int status = 1;             // 1: pending; 0: done; < 0: DDAMG_ERR_* of the request
+  double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+struct SrvSlot {
+  SrvRequest* rq = nullptr;
+  int col = 0, iterations = 0, cycles = 0;
+};
+
+struct SrvHier {
+  ddamg_handle* h = nullptr;
+  std::deque<std::pair<SrvRequest*, int>> queue;   // columns waiting for a slot
+  std::vector<SrvSlot> slots;                      // slots [0, active) are in the batch
+  int active = 0;
+  size_t bytes = 0;
+  std::thread worker;
+};
+
+}  // namespace
+
+struct ddamg_server {
+  std::mutex mu;
+  std::condition_variable work_cv, done_cv;
+  std::vector<SrvHier*> hs;
+  std::map<long long, SrvRequest*> reqs;
+  long long next_id = 1;
+  bool stop = false;
+  size_t budget = 0, used = 0;
+};
+
+namespace {
+
+void finish_column(ddamg_server* S, SrvRequest* rq, int col, const ddamg_stats& st, int err) {
+  rq->st[col] = st;
+  if (err) rq->status = err;
+  if (--rq->remaining == 0) {
+    if (rq->status == 1) {
+      bool ok = true;
+      for (const auto& q : rq->st) ok = ok && q.converged;
+      rq->status = ok ? DDAMG_OK : DDAMG_ERR_NOCONV;
+    }
+    rq->t_done = now_seconds();
+    S->done_cv.notify_all();
+  }
+}
+
+void server_worker(ddamg_server* S, SrvHier* H) {
+  ddamg_handle* h = H->h;
+  cudaSetDevice(h->device);
+  Level& F = h->lv[0];
+  const size_t vlen = F.vlen;
+  const size_t fb = sizeof(cplx<double>) * vlen;
+  const int cap = h->max_batch;
+  H->slots.assign(cap, SrvSlot{});
+  std::vector<double> tols(cap);
+  for (;;) {
+    std::vector<int> fresh;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->work_cv.wait(lk, [&] { return S->stop || !H->queue.empty() || H->active > 0; });
+      if (S->stop && H->active == 0) {
+        for (auto& qc : H->queue) finish_column(S, qc.first, qc.second, ddamg_stats{}, DDAMG_ERR_ARG);
+        H->queue.clear();
+        return;
+      }
+      while (!S->stop && H->active < cap && !H->queue.empty()) {
+        SrvSlot sl;
+        sl.rq = H->queue.front().first;
+        sl.col = H->queue.front().second;
+        H->queue.pop_front();
+        if (sl.rq->t_start == 0) sl.rq->t_start = now_seconds();
+        H->slots[H->active] = sl;
+        fresh.push_back(H->active++);
+      }
+    }
+    const int na = H->active;
+    std::vector<int> retire;
+    std::vector<ddamg_stats> rst;
+    const int rc = guard([&] {
+      for (int q : fresh) {   // new columns: b into the slot, x = 0, r = b
+        const SrvSlot& sl = H->slots[q];
+        const cplx<double>* din =
+            static_cast<const cplx<double>*>(dev_in(h, sl.rq->b.data() + (size_t)sl.col * vlen * 2, fb, 0));
+        fine_import<double>(h->ob + (size_t)q * vlen, din, F.g, 1, vlen, h->st);
+        blas_zero<double>(h->ox + (size_t)q * vlen, vlen, 1, vlen, h->st);
+        CK(cudaMemcpyAsync(h->outer.r + (size_t)q * vlen, h->ob + (size_t)q * vlen, fb, cudaMemcpyDeviceToDevice,
+                           h->st));
+      }
+      for (int q = 0; q < na; ++q) tols[q] = H->slots[q].rq->tol;
+      KrylovResult res;
+      outer_fgmres(h, na, 1.0, 1, &res, true, tols.data());
+      int e = 0;
+      CK(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      sync(h);
+      if (e == 2) {
+        CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
+        fail(DDAMG_ERR_CUDA, "a shared-memory staging wait of the SAP kernel timed out");
+      }
+      cplx<double>* dx = static_cast<cplx<double>*>(scratch(h, 1, fb));
+      for (int q = 0; q < na; ++q) {
+        SrvSlot& sl = H->slots[q];
+        sl.iterations += res.iterations[q];
+        sl.cycles += 1;
+        if (!(res.converged[q] || sl.cycles >= h->p.outer_max_cycles)) continue;
+        ddamg_stats st;
+        st.iterations = sl.iterations;
+        st.cycles = sl.cycles;
+        st.converged = res.converged[q];
+        st.true_residual = res.true_residual[q];
+        fine_export<double>(dx, h->ox + (size_t)q * vlen, F.g, 1, vlen, h->st);
+        CK(cudaMemcpyAsync(sl.rq->x.data() + (size_t)sl.col * vlen * 2, dx, fb, cudaMemcpyDeviceToHost, h->st));
+        sync(h);
+        retire.push_back(q);
+        rst.push_back(st);
+      }
+      // compact: the last slots move into the holes (b, x and the residual of the iterate)
+      int act = na;
+      for (int k = (int)retire.size() - 1; k >= 0; --k) {
+        const int q = retire[k], last = act - 1;
+        if (q != last) {
+          for (cplx<double>* base : {h->ob, h->ox, h->outer.r})
+            CK(cudaMemcpyAsync(base + (size_t)q * vlen, base + (size_t)last * vlen, fb, cudaMemcpyDeviceToDevice,
+                               h->st));
+        }
+        --act;
+      }
+      sync(h);
+    });
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (rc != DDAMG_OK) {   // the batch failed: every column in it fails
+      for (int q = 0; q < na; ++q) finish_column(S, H->slots[q].rq, H->slots[q].col, ddamg_stats{}, rc);
+      H->active = 0;
+      continue;
+    }
+    for (size_t k = 0; k < retire.size(); ++k) {
+      const SrvSlot& sl = H->slots[retire[k]];
+      finish_column(S, sl.rq, sl.col, rst[k], 0);
+    }
+    int act = na;
+    for (int k = (int)retire.size() - 1; k >= 0; --k) {
+      const int q = retire[k], last = act - 1;
+      if (q != last) H->slots[q] = H->slots[last];
+      --act;
+    }
+    H->active = act;
+  }
+}
+
+// Device bytes of a hierarchy with these parameters, before it is built: the
+// allocations of the setup (operators, P, test vectors, Krylov workspaces, FP16
+// copies) and the staging buffers of a full batch.
+size_t estimate_bytes(const int dims0[4], const ddamg_params& p) {
+  size_t tot = 0;
+  const size_t B = (size_t)p.max_rhs;
+  int dims[4] = {dims0[0], dims0[1], dims0[2], dims0[3]};
+  int nprev = 12, Nprev = 0;
+  size_t vlen0 = 0, maxtmp = 0;
+  for (int l = 0; l < p.levels; ++l) {
+    const bool fine = l == 0, coarsest = l == p.levels - 1;
+    const size_t V = (size_t)dims[0] * dims[1] * dims[2] * dims[3];
+    const int n = fine ? 12 : 2 * Nprev;
+    const size_t vlen = V * n;
+    const int N = coarsest ? 0 : p.n_tv[l];
+    if (fine) {
+      vlen0 = vlen;
+      tot += 36 * V * (16 + 8) + 72 * V * (8 + 4);
+      if (p.precision == 2) tot += 36 * V * 4 + 72 * V * 2;
+    } else {
+      const size_t nb = V * 9 * (size_t)n * n;
+      tot += nb * (16 + 8) + (p.precision == 2 ? nb * 4 + V * 4 : 0);
+      if (coarsest) tot += V * (size_t)n * n * (16 + 8) + 4 * V * sizeof(int) + 16 * V * sizeof(int);
+    }
+    if (!coarsest) {
+      tot += vlen * N * (16 + 16 + 8) + (p.precision == 2 ? vlen * N * 4 + V * 8 : 0);
+      tot += (size_t)(V + 1) * sizeof(int);   // SAP block lists
+      maxtmp = std::max(maxtmp, vlen * N * 16);
+    }
+    const int m = coarsest ? p.coarse_restart : (l >= 1 ? p.kcycle_len : 0);
+    const size_t vl = vlen * B;
+    const size_t nvec = 13 + (m > 0 ? (size_t)(m + 1) + (coarsest ? 0 : (size_t)m) : 0);
+    tot += nvec * vl * (8 + 16);
+    const size_t mm = m > 0 ? m : 1;
+    tot += 2 * B * ((mm + 1) * mm * 16 + mm * 8 + mm * 16 + 4 * (mm + 1) * 16 + 64);
+    if (!coarsest) {
+      for (int d = 0; d < 4; ++d) dims[d] /= p.agg[l][d];
+      nprev = n;
+      Nprev = N;
+    }
+  }
+  (void)nprev;
+  const size_t vl0 = vlen0 * B;
+  tot += (size_t)(2 * p.outer_restart + 1 + 13) * vl0 * 16;   // outer FGMRES V, Z and temporaries
+  tot += vl0 * (16 + 16 + 8 + 8);                              // ob, ox, pin32, pout32
+  tot += 2 * vl0 * 16 + maxtmp + 2 * maxtmp / 2;               // staging and setup scratch
+  return tot;
+}
+
 // compute precision of the per-operation entry points: 0 FP64, 1 FP32 (on the
 // FP32 or FP16 storage the handle holds)
 bool fp32_compute(int precision) {
@@ -1239,6 +1496,7 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
     h->m0 = m0;
     h->csw = csw;
     h->max_batch = params->max_rhs;
+    CK(cudaGetDevice(&h->device));
     CK(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
     h->st = h->own;
     for (int d = 0; d < 12; ++d) CK(cudaStreamCreateWithFlags(&h->cap.s[d], cudaStreamNonBlocking));
@@ -1324,16 +1582,8 @@ int ddamg_solve(ddamg_handle* h, const double* rhs, double* x, int n, double tol
       const cplx<double>* din =
           static_cast<const cplx<double>*>(dev_in(h, rhs + (size_t)s0 * F.vlen * 2, fbytes * nb, 0));
       fine_import<double>(h->ob, din, F.g, nb, F.vlen, h->st);
-      auto A = [&](cplx<double>* o, const cplx<double>* in, const cplx<double>* bb) {
-        apply_D<double>(h, F, o, in, bb, nb);
-      };
-      auto M = [&](cplx<double>* z, const cplx<double>* v) {
-        if (h->p.precision != 0) precond_outer<float>(h, z, v, nb);
-        else precond_outer<double>(h, z, v, nb);
-      };
       KrylovResult res;
-      krylov<double>(h, h->outer, F.vlen, h->ox, h->ob, nb, h->p.outer_restart, tol, h->p.outer_max_cycles, true,
-                     true, A, M, &res);
+      outer_fgmres(h, nb, tol, h->p.outer_max_cycles, &res);
       cplx<double>* dx = xdev ? reinterpret_cast<cplx<double>*>(x + (size_t)s0 * F.vlen * 2)
                               : static_cast<cplx<double>*>(scratch(h, 1, fbytes * nb));
       fine_export<double>(dx, h->ox, F.g, nb, F.vlen, h->st);
@@ -1625,6 +1875,173 @@ int ddamg_get_coarse_operator(ddamg_handle* h, int level, double* blocks) {
     if (!dev) CK(cudaMemcpyAsync(blocks, d, bytes, cudaMemcpyDeviceToHost, h->st));
     sync(h);
   });
+}
+
+int ddamg_device_bytes(ddamg_handle* h, size_t* bytes) {
+  if (!h || !bytes) {
+    g_err = "null argument";
+    return DDAMG_ERR_ARG;
+  }
+  *bytes = h->dev_bytes;
+  return DDAMG_OK;
+}
+
+int ddamg_estimate_bytes(const int dims[4], const ddamg_params* params, size_t* bytes) {
+  if (!dims || !params || !bytes) {
+    g_err = "null argument";
+    return DDAMG_ERR_ARG;
+  }
+  return guard([&] {
+    validate(*params);
+    for (int d = 0; d < 4; ++d)
+      if (dims[d] <= 0) fail(DDAMG_ERR_ARG, "lattice extents must be positive");
+    *bytes = estimate_bytes(dims, *params);
+  });
+}
+
+int ddamg_server_create(size_t hbm_budget, ddamg_server** out) {
+  if (!out) {
+    g_err = "null argument";
+    return DDAMG_ERR_ARG;
+  }
+  *out = nullptr;
+  ddamg_server* S = new ddamg_server();
+  const int rc = guard([&] {
+    if (hbm_budget == 0) {
+      size_t fr = 0, total = 0;
+      CK(cudaMemGetInfo(&fr, &total));
+      hbm_budget = total / 10 * 9;
+    }
+    S->budget = hbm_budget;
+  });
+  if (rc != DDAMG_OK) {
+    delete S;
+    return rc;
+  }
+  *out = S;
+  return DDAMG_OK;
+}
+
+int ddamg_server_add(ddamg_server* S, ddamg_handle* h, int* hid) {
+  if (!S || !h || !hid) {
+    g_err = "null argument";
+    return DDAMG_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (SrvHier* H : S->hs)
+    if (H->h == h) {
+      g_err = "hierarchy already registered";
+      return DDAMG_ERR_ARG;
+    }
+  if (S->used + h->dev_bytes > S->budget) {
+    g_err = "admission refused: the hierarchy's device footprint (" + std::to_string(h->dev_bytes) +
+            " bytes) exceeds the server's remaining HBM budget (" + std::to_string(S->budget - S->used) + " bytes)";
+    return DDAMG_ERR_ADMISSION;
+  }
+  SrvHier* H = new SrvHier();
+  H->h = h;
+  H->bytes = h->dev_bytes;
+  S->used += H->bytes;
+  S->hs.push_back(H);
+  *hid = (int)S->hs.size() - 1;
+  H->worker = std::thread(server_worker, S, H);
+  return DDAMG_OK;
+}
+
+int ddamg_server_submit(ddamg_server* S, int hid, const double* rhs, int n, double tol, long long* id) {
+  if (!S || !rhs || !id || n < 1 || !(tol > 0)) {
+    g_err = "invalid argument";
+    return DDAMG_ERR_ARG;
+  }
+  SrvHier* H = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (hid < 0 || hid >= (int)S->hs.size() || S->stop) {
+      g_err = "unknown hierarchy or server stopping";
+      return DDAMG_ERR_ARG;
+    }
+    H = S->hs[hid];   // SrvHier objects live until ddamg_server_free
+  }
+  SrvRequest* rq = new SrvRequest();
+  const size_t len = H->h->lv[0].vlen * 2 * (size_t)n;
+  if (is_device_ptr(rhs)) {
+    delete rq;
+    g_err = "serving takes right-hand sides in host memory";
+    return DDAMG_ERR_ARG;
+  }
+  rq->hid = hid;
+  rq->n = n;
+  rq->tol = tol;
+  rq->b.assign(rhs, rhs + len);
+  rq->x.assign(len, 0.0);
+  rq->st.assign(n, ddamg_stats{});
+  rq->remaining = n;
+  std::lock_guard<std::mutex> lk(S->mu);
+  rq->t_submit = now_seconds();
+  *id = S->next_id++;
+  S->reqs[*id] = rq;
+  for (int c = 0; c < n; ++c) H->queue.emplace_back(rq, c);
+  S->work_cv.notify_all();
+  return DDAMG_OK;
+}
+
+int ddamg_server_poll(ddamg_server* S, long long id, int* done) {
+  if (!S || !done) {
+    g_err = "null argument";
+    return DDAMG_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) {
+    g_err = "unknown request";
+    return DDAMG_ERR_ARG;
+  }
+  *done = it->second->status <= 0;
+  return DDAMG_OK;
+}
+
+int ddamg_server_wait(ddamg_server* S, long long id, double* x, ddamg_stats* per_rhs, double* times) {
+  if (!S || !x) {
+    g_err = "null argument";
+    return DDAMG_ERR_ARG;
+  }
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) {
+    g_err = "unknown request";
+    return DDAMG_ERR_ARG;
+  }
+  SrvRequest* rq = it->second;
+  S->done_cv.wait(lk, [&] { return rq->status <= 0; });
+  std::memcpy(x, rq->x.data(), sizeof(double) * rq->x.size());
+  if (per_rhs)
+    for (int c = 0; c < rq->n; ++c) per_rhs[c] = rq->st[c];
+  if (times) {
+    times[0] = rq->t_start - rq->t_submit;   // queueing before the first restart cycle
+    times[1] = rq->t_done - rq->t_submit;    // latency
+    times[2] = rq->t_done - rq->t_start;     // time in the batch
+  }
+  const int rc = rq->status;
+  S->reqs.erase(it);
+  delete rq;
+  if (rc != DDAMG_OK) g_err = rc == DDAMG_ERR_NOCONV ? "outer FGMRES did not reach the tolerance" : "request failed";
+  return rc;
+}
+
+int ddamg_server_free(ddamg_server* S) {
+  if (!S) return DDAMG_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->work_cv.notify_all();
+  }
+  for (SrvHier* H : S->hs) {
+    if (H->worker.joinable()) H->worker.join();
+    delete H;
+  }
+  for (auto& kv : S->reqs) delete kv.second;
+  delete S;
+  return DDAMG_OK;
 }
 
 }  // extern "C"

@@ -41,3 +41,19 @@ def test_binding_constants_match_header():
     assert "DDAMG_OPT_HALF_STORAGE" in consts
     for k, v in consts.items():
         assert getattr(dd, k) == v, k
+
+
+def test_footprint_estimate_is_host_only_and_consistent():
+    """ddamg_estimate_bytes needs no device: it grows with the lattice and with the batch."""
+    import paper_1307_6101_gb300 as dd
+    kw = dict(levels=3, agg=[(2, 2, 2, 2), (2, 2, 2, 2)], n_tv=[4, 6], sap_block=[(2, 2, 2, 2), (2, 2, 2, 2)])
+    p1 = dd.ddamg_default_params(**kw, max_rhs=1, precision=1)
+    p4 = dd.ddamg_default_params(**kw, max_rhs=4, precision=1)
+    p16 = dd.ddamg_default_params(**kw, max_rhs=1, precision=2)
+    small = dd.ddamg_estimate_bytes((8, 8, 8, 8), p1)
+    big = dd.ddamg_estimate_bytes((16, 8, 8, 8), p1)
+    assert 1.9 * small <= big <= 2.1 * small          # everything scales with the volume
+    assert dd.ddamg_estimate_bytes((8, 8, 8, 8), p4) > 2 * small
+    assert dd.ddamg_estimate_bytes((8, 8, 8, 8), p16) > small   # FP16 copies come on top
+    with pytest.raises(dd.DdamgError):
+        dd.ddamg_estimate_bytes((8, 8, 8, 8), dd.ddamg_default_params(**kw, max_rhs=0))
