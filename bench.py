@@ -53,6 +53,11 @@ WORKLOADS = {
         mr_steps=4, nu=3, n_inv=3, outer_restart=25, nrhs=1, seed=0, tv_seed=100, rhs_seed=1),
 }
 TOL = 1e-10
+SERVING = dict(
+    name="serving: Poisson requests over resident hierarchies 16^3x32, 24^3x48, 32^3x64 "
+         "(eps 0.4, csw 1.0, three levels as the 16^3x32 workload), 1-12 complex N(0,1) RHS per request",
+    lattices=[(32, 16, 16, 16), (48, 24, 24, 24), (64, 32, 32, 32)], rates=(5, 20, 80), seconds=10.0,
+    max_requests=1000, max_rhs_total=48, max_rhs=6, seed=3)
 PAPER_OUTER_ITERATIONS = 22   # three-level outer FGMRES iterations on P2 (Table 3 of the paper)
 
 
@@ -324,6 +329,12 @@ def run_gpu(args, w):
         "gpu_launches": int(launches),
         "krylov_steps_per_solve": [round((b - a) / args.steps, 1) for a, b in zip(steps0, steps1)],
     }
+    if rank == 0 and world == 1 and not args.no_serving and w is WORKLOADS["three_level_16c32"]:
+        # short serving run on this lattice: Poisson arrivals, 1-12 RHS per request, 6 batch slots
+        for h in handles.values():
+            h.free()
+        handles = {}
+        out["serving"] = serving_bench(dd, w, [tuple(w["dims"])], (20,), 5.0, 1000, 6, SERVING["seed"], 60)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, out["iterations"][0] if out["iterations"] else None)
     for h in handles.values():
@@ -398,6 +409,127 @@ def run_reference(args, w):
     print(json.dumps(out))
 
 
+# ---------------------------------------------------------------------------
+# Serving: continuous batching over resident hierarchies (library server)
+def serving_handle(dd, w, dims, max_rhs, seed):
+    import synth
+    U = synth.su3_field(dims, w["eps"], seed)
+    dims_l = [tuple(dims)]
+    for a in w["agg"]:
+        dims_l.append(tuple(d // x for d, x in zip(dims_l[-1], a)))
+    tv = synth.random_test_vectors(dims_l, w["n_tv"], seed + 100)
+    p = dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
+                                mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
+                                outer_restart=w["outer_restart"], precision=2, max_rhs=max_rhs)
+    return dd.ddamg_setup(U, dims, -1, mass(w["mass"]), w["csw"], p, tv)
+
+
+def serving_run(dd, srv, hids, pools, rate, seconds, max_requests, rng, max_rhs_total):
+    """Poisson arrivals at `rate` req/s for `seconds`; each request: a uniform hierarchy and 1-12 RHS.
+
+    Arrivals stop after `seconds` or once `max_rhs_total` right-hand sides were offered, so
+    that an offered load above capacity (the queue grows) still ends in bounded time.
+    """
+    import threading
+    sched, t, tot = [], 0.0, 0
+    while len(sched) < max_requests and tot < max_rhs_total:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        k = int(rng.integers(len(hids)))
+        n = int(rng.integers(1, 13))
+        cols = np.sort(rng.choice(pools[k].shape[0], size=n, replace=False))
+        sched.append((t, k, n, cols))
+        tot += n
+    subs = []
+    t0 = time.perf_counter()
+
+    def submitter():
+        for (ta, k, n, cols) in sched:
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            b = np.ascontiguousarray(pools[k][cols])
+            ts = time.perf_counter()
+            subs.append((srv.submit(hids[k], b, n, TOL), k, n, ts))
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    rec, i = [], 0
+    while True:
+        if i < len(subs):
+            rid, k, n, ts = subs[i]
+            x = np.zeros((n,) + pools[k].shape[1:], dtype=np.complex128)
+            st, times, rc = srv.wait(rid, x, n)
+            rec.append(dict(k=k, n=n, submit=ts - t0, latency=times[1], queue=times[0], rc=rc,
+                            res=max(q["true_residual"] for q in st), conv=all(q["converged"] for q in st)))
+            i += 1
+        elif not th.is_alive() and i >= len(subs):
+            break
+        else:
+            time.sleep(0.001)
+    th.join()
+    lat = sorted(r["latency"] for r in rec)
+    end = max(r["submit"] + r["latency"] for r in rec)
+    rhs = sum(r["n"] for r in rec)
+    p99 = lat[min(len(lat) - 1, int(np.ceil(0.99 * len(lat))) - 1)]
+    arrivals = sched[-1][0] if sched else 0.0
+    return {"rate_req_s": rate, "requests": len(rec), "rhs": rhs, "arrival_window_s": round(arrivals, 3),
+            "span_s": round(end, 3),
+            "rhs_per_s": round(rhs / end, 2), "offered_rhs_per_s": round(rate * 6.5, 1),
+            "p50_latency_s": round(statistics.median(lat), 4),
+            ("p99_latency_s" if len(lat) >= 100 else "p99_latency_s_is_max"): round(p99, 4),
+            "mean_queue_s": round(statistics.mean(r["queue"] for r in rec), 4),
+            "all_converged": all(r["conv"] and r["rc"] == 0 for r in rec),
+            "max_true_residual": max(r["res"] for r in rec)}
+
+
+def serving_bench(dd, w, lattices, rates, seconds, max_requests, max_rhs, seed, max_rhs_total):
+    import synth
+    t0 = time.perf_counter()
+    handles = [serving_handle(dd, w, dims, max_rhs, seed + 10 * k) for k, dims in enumerate(lattices)]
+    t_setup = time.perf_counter() - t0
+    pools = [np.ascontiguousarray(synth.random_spinors(12, dims, seed + 500 + k)) for k, dims in enumerate(lattices)]
+    srv = dd.Server()
+    hids = [srv.add(h) for h in handles]
+    footprint = sum(dd.ddamg_device_bytes(h) for h in handles)
+    rng = np.random.default_rng(seed)
+    # warm-up: one request per hierarchy (graph capture for the batch sizes happens on first use)
+    for k in range(len(hids)):
+        for n in range(1, max_rhs + 1):
+            b = np.ascontiguousarray(pools[k][:n])
+            x = np.zeros_like(b)
+            srv.wait(srv.submit(hids[k], b, n, TOL), x, n)
+    runs = [serving_run(dd, srv, hids, pools, r, seconds, max_requests, rng, max_rhs_total) for r in rates]
+    srv.free()
+    for h in handles:
+        h.free()
+    return {"lattices": ["x".join(str(d) for d in dims[::-1]) for dims in lattices], "batch_slots": max_rhs,
+            "setup_s": round(t_setup, 1), "device_bytes": int(footprint), "runs": runs}
+
+
+def run_serving(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1307_6101_gb300 as dd
+    w = WORKLOADS["three_level_16c32"]
+    S = SERVING
+    res = serving_bench(dd, w, S["lattices"], S["rates"], args.serve_seconds or S["seconds"], S["max_requests"],
+                        S["max_rhs"], S["seed"], S["max_rhs_total"])
+    tot_rhs = sum(r["rhs"] for r in res["runs"])
+    tot_t = sum(r["span_s"] for r in res["runs"])
+    out = {"metric": "serving: p50/p99 latency (s) and RHS/s under Poisson load, true rel. residual 1e-10",
+           "value": round(tot_rhs / tot_t, 3), "unit": "RHS/s", "n_gpus": 1, "higher_is_better": True,
+           "dtype": "f32 preconditioner on f16 storage / f64 outer FGMRES", "data": "synthetic",
+           "config": {"workload": S["name"], "rates_req_s": list(S["rates"]),
+                      "seconds_per_rate": args.serve_seconds or S["seconds"],
+                      "max_rhs_offered_per_rate": S["max_rhs_total"]},
+           "serving": res}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,10 +542,18 @@ def main():
                     help="time only the mixed-precision path (profiling runs)")
     ap.add_argument("--mixed-storage", choices=("fp16", "fp32"), default="fp16",
                     help="storage of the mixed path's operator data (default fp16, per-site scales)")
+    ap.add_argument("--serving", action="store_true",
+                    help="serving benchmark: Poisson request streams over three resident hierarchies")
+    ap.add_argument("--serve-seconds", type=float, default=0.0,
+                    help="seconds of arrivals per rate (serving benchmark; default 20)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the short serving run of the default bench")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven inner solves instead of captured graphs (for kernel-level profiling)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.serving:
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args, w)
     else:

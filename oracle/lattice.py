@@ -101,6 +101,23 @@ def from_blocks(g: np.ndarray, bs) -> np.ndarray:
     return h.reshape(*lead, Tb * b0, Zb * b1, Yb * b2, Xb * b3, n)
 
 
+def red_black_block(dims, bs):
+    """SAP block of a lattice whose block count must be even (or 1) in every direction.
+
+    The paper's SAP is red-black on a block grid; where the requested extent
+    gives an odd block count, the block is widened to the smallest extent
+    >= the requested one that divides the lattice into an even count (or one
+    block): 6 sites with 2-site blocks become 3-site blocks.
+    """
+    out = []
+    for L, b in zip(dims, bs):
+        c = b
+        while c < L and (L % c != 0 or (L // c) % 2 != 0):
+            c += 1
+        out.append(min(c, L))
+    return tuple(out)
+
+
 def check_blocking(dims, bs, what="block"):
     for mu in range(4):
         if bs[mu] <= 0 or dims[mu] % bs[mu] != 0:

@@ -12,7 +12,10 @@ K-cycle at level l (Alg. 2 = Alg. 1 with the recursion replaced):
     z += P_l z_{l+1};  nu times z += M_l (b - D_l z)
 Readings where the paper is silent: "maximal restarts 2" = at most two cycles
 of the inner FGMRES; the coarsest GMRES uses restart length 50 and at most 20
-cycles; the coarsest tolerance is on the Schur-complement residual.
+cycles; the coarsest tolerance is on the Schur-complement residual.  Lattices
+with odd extents: a SAP block grid with an odd count in some direction takes
+the smallest wider block that gives an even count (lattice.red_black_block),
+and a coarsest lattice with an odd extent is solved by plain GMRES on D_L.
 
 Outer solver: FGMRES in FP64 on D preconditioned by the K-cycle at level 0
 (restart n_kv = 10, tol 1e-10, Table 1).
@@ -35,11 +38,11 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .lattice import norm
+from .lattice import norm, red_black_block
 from .smoother import SAP
 from .stencil import EvenOdd
 from .transfer import build_interpolation, restrict, prolong, galerkin
-from .krylov import fgmres, coarsest_solve
+from .krylov import fgmres, gmres, coarsest_solve
 
 
 @dataclass
@@ -95,7 +98,7 @@ class Hierarchy:
     # --- construction of one level ------------------------------------------------
     def _make_sap(self, l):
         lev = self.levels[l]
-        lev.sap = SAP(lev.op, self.p.sap_block[l], self.p.mr_steps)
+        lev.sap = SAP(lev.op, red_black_block(lev.op.dims, self.p.sap_block[l]), self.p.mr_steps)
 
     def rebuild(self, l):
         """Construct P_l from the test vectors of level l and set D_{l+1} = P_l^+ D_l P_l."""
@@ -109,7 +112,9 @@ class Hierarchy:
         if self.trace is not None:
             self.trace.add("build", l)
         if l + 1 == self.L - 1:
-            self.levels[l + 1].eo = EvenOdd(Dc)
+            # odd-even GMRES needs even extents; a coarsest lattice with an odd extent
+            # is solved by plain GMRES on D_L (same length, cycles and tolerance)
+            self.levels[l + 1].eo = EvenOdd(Dc) if all(d % 2 == 0 for d in Dc.dims) else None
         else:
             self._make_sap(l + 1)
 
@@ -125,8 +130,12 @@ class Hierarchy:
             z = lev.sap.smooth(b, z, self.p.mu)
         bc = restrict(lev.P, self.p.agg[l], b - D(z))
         if l + 1 == self.L - 1:
-            zc, _ = coarsest_solve(self.levels[l + 1].eo, bc, self.p.coarse_tol,
-                                   self.p.coarse_restart, self.p.coarse_cycles)
+            eo = self.levels[l + 1].eo
+            if eo is not None:
+                zc, _ = coarsest_solve(eo, bc, self.p.coarse_tol, self.p.coarse_restart, self.p.coarse_cycles)
+            else:
+                zc, _ = gmres(self.levels[l + 1].op.apply, bc, m=self.p.coarse_restart, tol=self.p.coarse_tol,
+                              max_cycles=self.p.coarse_cycles, final_residual=True)
         else:
             zc, _ = fgmres(self.levels[l + 1].op.apply, bc, M=lambda v: self.kcycle(l + 1, v),
                            m=self.p.kcycle_len, tol=self.p.kcycle_tol,

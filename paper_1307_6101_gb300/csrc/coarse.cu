@@ -208,74 +208,108 @@ __global__ void k_schur_even(cplx<T>* __restrict__ y, const cplx<T>* __restrict_
   }
 }
 
-// One colour sweep of SAP on a coarse level: one CTA per SAP block, one thread
-// per (site, row) of the block.  rho = (b - D z)_B, k MR steps on D_B, z_B += e_B.
-template <typename T, typename BS>
+// One colour sweep of SAP on a coarse level: one CTA per SAP block; thread t owns
+// the rows t, t + blockDim.x, ... (at most RPT) of the block, row = (site, i) in
+// block-local order (bsite / bloc tables).  rho = (b - D z)_B, k MR steps on D_B
+// (hops leaving the block dropped), z_B += e_B; the operator is read from global
+// memory.
+template <typename T, typename BS, int RPT>
 __global__ void k_coarse_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
                              const BS* __restrict__ blk, const float* __restrict__ bscale, Geom g, int n,
-                             size_t rstride, const int* __restrict__ blocks, int k_mr) {
+                             size_t rstride, const int* __restrict__ blocks, int k_mr,
+                             const int* __restrict__ bsite, const int* __restrict__ bloc) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);        // [vB * n]
   T* sh = reinterpret_cast<T*>(rs + (size_t)g.vB * n);          // [warps][3]
   const int b = blocks[blockIdx.x];
-  const int loc = threadIdx.x / n, i = threadIdx.x % n;
-  const bool active = loc < g.vB;
-  const int site = b * g.vB + (active ? loc : 0);
+  const int rows = g.vB * n;
+  const int* bs = bsite + (size_t)b * g.vB;
   const size_t ro = (size_t)blockIdx.y * rstride;
   cplx<T>* pz = z + ro;
-  int c[4];
-  geom_coords(g, site, c);
-  const T sc = bscale ? T(bscale[site]) : T(1);
-  cplx<T> r = czero<T>(), xs = czero<T>();
-  if (active) {
-    cplx<T> acc = czero<T>();
-    const cplx<T>* v = pz + (size_t)site * n;
-    for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(blk, bidx(site, 0, n, i, j)), v[j]);
-    for (int mu = 0; mu < 4; ++mu) {
-      v = pz + (size_t)geom_neighbor(g, c, mu, +1) * n;
-      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(blk, bidx(site, 1 + mu, n, i, j)), v[j]);
-      v = pz + (size_t)geom_neighbor(g, c, mu, -1) * n;
-      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(blk, bidx(site, 5 + mu, n, i, j)), v[j]);
+  cplx<T> r[RPT], xs[RPT], p[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    r[q] = czero<T>();
+    xs[q] = czero<T>();
+    const int row = threadIdx.x + q * blockDim.x;
+    if (row < rows) {
+      const int loc = row / n, i = row - loc * n;
+      const int site = bs[loc];
+      int c[4];
+      geom_coords(g, site, c);
+      cplx<T> acc = czero<T>();
+      // self block, then the forward (1 + mu) and backward (5 + mu) blocks; written as
+      // explicit direction loops (a single 9-way loop over k was mis-executed here)
+      {
+        const cplx<T>* v = pz + (size_t)site * n;
+        for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(blk, bidx(site, 0, n, i, j)), v[j]);
+      }
+      for (int mu = 0; mu < 4; ++mu)
+        for (int sd = 0; sd < 2; ++sd) {
+          const int dir = sd ? -1 : +1, k = sd ? 5 + mu : 1 + mu;
+          const cplx<T>* v = pz + (size_t)geom_neighbor(g, c, mu, dir) * n;
+          for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(blk, bidx(site, k, n, i, j)), v[j]);
+        }
+      const T sc = bscale ? T(bscale[site]) : T(1);
+      r[q] = bsrc[ro + (size_t)site * n + i] - sc * acc;
     }
-    r = bsrc[ro + (size_t)site * n + i] - sc * acc;
   }
   for (int it = 0; it < k_mr; ++it) {
-    if (active) rs[threadIdx.x] = r;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int row = threadIdx.x + q * blockDim.x;
+      if (row < rows) rs[row] = r[q];
+    }
     __syncthreads();
     T nre = T(0), nim = T(0), den = T(0);
-    cplx<T> p = czero<T>();
-    if (active) {
-      const cplx<T>* v = rs + (size_t)loc * n;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      p[q] = czero<T>();
+      const int row = threadIdx.x + q * blockDim.x;
+      if (row < rows) {
+        const int loc = row / n, i = row - loc * n;
+        const int site = bs[loc];
+        int c[4];
+        geom_coords(g, site, c);
+        cplx<T> acc = czero<T>();
+        {
+          const cplx<T>* v = rs + (size_t)loc * n;
 #pragma unroll 8
-      for (int j = 0; j < n; ++j) cfma(p, ld_cplx(blk, bidx(site, 0, n, i, j)), v[j]);
-      for (int mu = 0; mu < 4; ++mu) {
-        if (hop_internal(g, c, mu, +1, g.B)) {
-          const int nl = geom_neighbor(g, c, mu, +1) - b * g.vB;
-          v = rs + (size_t)nl * n;
-#pragma unroll 8
-          for (int j = 0; j < n; ++j) cfma(p, ld_cplx(blk, bidx(site, 1 + mu, n, i, j)), v[j]);
+          for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(blk, bidx(site, 0, n, i, j)), v[j]);
         }
-        if (hop_internal(g, c, mu, -1, g.B)) {
-          const int nl = geom_neighbor(g, c, mu, -1) - b * g.vB;
-          v = rs + (size_t)nl * n;
+        for (int mu = 0; mu < 4; ++mu)
+          for (int sd = 0; sd < 2; ++sd) {
+            const int dir = sd ? -1 : +1, k = sd ? 5 + mu : 1 + mu;
+            if (!hop_internal(g, c, mu, dir, g.B)) continue;
+            const cplx<T>* v = rs + (size_t)bloc[geom_neighbor(g, c, mu, dir)] * n;
 #pragma unroll 8
-          for (int j = 0; j < n; ++j) cfma(p, ld_cplx(blk, bidx(site, 5 + mu, n, i, j)), v[j]);
-        }
+            for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(blk, bidx(site, k, n, i, j)), v[j]);
+          }
+        const T sc = bscale ? T(bscale[site]) : T(1);
+        p[q] = sc * acc;
+        const cplx<T> tt = cdotc(p[q], r[q]);
+        nre += tt.re;
+        nim += tt.im;
+        den += cnorm2(p[q]);
       }
-      p = sc * p;
-      const cplx<T> tt = cdotc(p, r);
-      nre = tt.re;
-      nim = tt.im;
-      den = cnorm2(p);
     }
     cta_sum3(nre, nim, den, sh);
     const cplx<T> alpha = den > T(0) ? cmk<T>(nre / den, nim / den) : czero<T>();
-    cfma(xs, alpha, r);
-    r = r - alpha * p;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      cfma(xs[q], alpha, r[q]);
+      r[q] = r[q] - alpha * p[q];
+    }
+    __syncthreads();
   }
-  if (active) {
-    const size_t a = ro + (size_t)site * n + i;
-    z[a] = z[a] + xs;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int row = threadIdx.x + q * blockDim.x;
+    if (row < rows) {
+      const int loc = row / n, i = row - loc * n;
+      const size_t a = ro + (size_t)bs[loc] * n + i;
+      z[a] = z[a] + xs[q];
+    }
   }
 }
 
@@ -321,7 +355,7 @@ template <typename T, typename BS>
 __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
                                      const BS* __restrict__ blk, const float* __restrict__ bscale, Geom g, int n,
                                      size_t rstride, const int* __restrict__ blocks, int k_mr, int spc, int nsl,
-                                     int* err) {
+                                     int* err, const int* __restrict__ bsite, const int* __restrict__ bloc) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
   const int CLS = (int)cluster.num_blocks();
@@ -340,16 +374,18 @@ __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restri
   int* slot = reinterpret_cast<int*>(smem_raw + L.slot);                      // [spc][9]
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + L.bar);
   const size_t ro = (size_t)blockIdx.y * rstride;
-  const int site0 = b * vB + rank * spc;   // first own site
+  const int* own = bsite + (size_t)b * vB + rank * spc;   // own sites, block-local order
   // slot of block k of own site sl in the staged array (-1: the hop leaves the SAP block)
   if (threadIdx.x < spc) {
     int c[4];
-    geom_coords(g, site0 + threadIdx.x, c);
+    geom_coords(g, own[threadIdx.x], c);
+    // slots in k order (self, forward mu = 0..3, backward mu = 0..3), explicit direction loops
+    int* sl9 = slot + threadIdx.x * 9;
     int ns = 0;
-    for (int k = 0; k < 9; ++k) {
-      const bool in = k == 0 || hop_internal(g, c, (k - 1) % 4, k <= 4 ? +1 : -1, g.B);
-      slot[threadIdx.x * 9 + k] = in ? ns++ : -1;
-    }
+    sl9[0] = ns++;
+    for (int sd = 0; sd < 2; ++sd)
+      for (int mu = 0; mu < 4; ++mu)
+        sl9[(sd ? 5 : 1) + mu] = hop_internal(g, c, mu, sd ? -1 : +1, g.B) ? ns++ : -1;
   }
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
@@ -361,14 +397,14 @@ __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restri
     for (int e = threadIdx.x; e < spc * 9; e += 32) {
       const int sl = e / 9, k = e % 9, q = slot[e];
       if (q >= 0)
-        bulk_g2s(stage + ((size_t)sl * nsl + q) * nn, blk + ((size_t)(site0 + sl) * 9 + k) * nn,
+        bulk_g2s(stage + ((size_t)sl * nsl + q) * nn, blk + ((size_t)own[sl] * 9 + k) * nn,
                  (unsigned)(nn * sizeof(BS)), bar);
     }
   }
   const int k = threadIdx.x / rows;
   const int rl = threadIdx.x - k * rows;
   const int sl = rl / n, i = rl - (rl / n) * n;
-  const int site = site0 + sl;
+  const int site = own[sl];
   const T sc = bscale ? T(bscale[site]) : T(1);
   int q = -1, nb = site, nloc = 0;
   if (k < 9) {
@@ -378,7 +414,7 @@ __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restri
       geom_coords(g, site, c);
       nb = geom_neighbor(g, c, (k - 1) % 4, k <= 4 ? +1 : -1);
     }
-    nloc = nb - b * vB;
+    nloc = q >= 0 ? bloc[nb] : 0;
   }
   const BS* Ms = stage + ((size_t)sl * nsl + (q >= 0 ? q : 0)) * nn + i;   // staged row i (column-major)
   // rho = b - D z on the own rows: hops leaving the block from global memory ...
@@ -404,7 +440,7 @@ __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restri
     cplx<T> d = czero<T>();
 #pragma unroll
     for (int m = 0; m < 9; ++m) d = d + part[m * rows + threadIdx.x];
-    r = bsrc[ro + (size_t)site0 * n + threadIdx.x] - d;
+    r = bsrc[ro + (size_t)own[threadIdx.x / n] * n + threadIdx.x % n] - d;
     for (int c = 0; c < CLS; ++c) cluster.map_shared_rank(rfull, c)[(size_t)rank * rows + threadIdx.x] = r;
   }
   cluster.sync();
@@ -470,7 +506,7 @@ __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restri
     __syncthreads();
   }
   if (ok && threadIdx.x < rows) {
-    const size_t a = ro + (size_t)site0 * n + threadIdx.x;
+    const size_t a = ro + (size_t)own[threadIdx.x / n] * n + threadIdx.x % n;
     z[a] = z[a] + xs;
   }
   if (!ok && threadIdx.x == 0) mbar_wait_bounded(bar, 0);   // no copy may still be in flight at exit
@@ -667,7 +703,7 @@ int coarse_sap_slots(const Geom& g) {
   int best = 1;
   for (int loc = 0; loc < g.vB; ++loc) {
     int c[4];
-    geom_coords(g, loc, c);
+    delin4(loc, g.B, c);   // the sites of the block at the origin
     int cnt = 1;
     for (int k = 1; k < 9; ++k) cnt += hop_internal(g, c, (k - 1) % 4, k <= 4 ? +1 : -1, g.B) ? 1 : 0;
     best = cnt > best ? cnt : best;
@@ -747,37 +783,54 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
     if constexpr (sizeof(T) == 4) {
       if (half)
         e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<float, __half2>, z, b, op.blkh, op.bscale, op.g, op.n,
-                               rstride, blocks, k_mr, spc, op.sap_nsl, op.err);
+                               rstride, blocks, k_mr, spc, op.sap_nsl, op.err, op.bsite, op.bloc);
       else
         e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
-                               (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc, op.sap_nsl, op.err);
+                               (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc, op.sap_nsl, op.err,
+                               op.bsite, op.bloc);
     } else {
       e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
-                             (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc, op.sap_nsl, op.err);
+                             (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc, op.sap_nsl, op.err,
+                             op.bsite, op.bloc);
     }
     if (e == cudaSuccess) return;
     cudaGetLastError();   // cluster launch refused: run the one-CTA-per-block kernel instead
   }
-  const int threads = ((op.g.vB * op.n + 31) / 32) * 32;
-  const size_t sm = (size_t)op.g.vB * op.n * sizeof(cplx<T>) + 32 * 3 * sizeof(T);
+  // one CTA per SAP block; up to 4 rows per thread for blocks of more than 1024 rows
+  const int rows = op.g.vB * op.n;
+  const int rpt = rows > 1024 ? 4 : 1;
+  const int threads = ((div_up(rows, rpt) + 31) / 32) * 32;
+  const size_t sm = (size_t)rows * sizeof(cplx<T>) + 32 * 3 * sizeof(T);
   static bool attr_set[2] = {false, false};
   bool& done = attr_set[sizeof(T) == 8];
   if (!done) {
-    cudaFuncSetAttribute(k_coarse_sap<T, cplx<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if constexpr (sizeof(T) == 4)
-      cudaFuncSetAttribute(k_coarse_sap<float, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_coarse_sap<T, cplx<T>, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_coarse_sap<T, cplx<T>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if constexpr (sizeof(T) == 4) {
+      cudaFuncSetAttribute(k_coarse_sap<float, __half2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(k_coarse_sap<float, __half2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    }
     done = true;
   }
   count_launch();
+  const dim3 grid(nblocks, nrhs);
   if constexpr (sizeof(T) == 4) {
     if (op.blkh) {
-      k_coarse_sap<float, __half2><<<dim3(nblocks, nrhs), threads, sm, st>>>(z, b, op.blkh, op.bscale, op.g, op.n,
-                                                                            rstride, blocks, k_mr);
+      if (rpt == 1)
+        k_coarse_sap<float, __half2, 1><<<grid, threads, sm, st>>>(z, b, op.blkh, op.bscale, op.g, op.n, rstride,
+                                                                    blocks, k_mr, op.bsite, op.bloc);
+      else
+        k_coarse_sap<float, __half2, 4><<<grid, threads, sm, st>>>(z, b, op.blkh, op.bscale, op.g, op.n, rstride,
+                                                                    blocks, k_mr, op.bsite, op.bloc);
       return;
     }
   }
-  k_coarse_sap<T, cplx<T>><<<dim3(nblocks, nrhs), threads, sm, st>>>(z, b, op.blk, nullptr, op.g, op.n, rstride,
-                                                                      blocks, k_mr);
+  if (rpt == 1)
+    k_coarse_sap<T, cplx<T>, 1><<<grid, threads, sm, st>>>(z, b, op.blk, nullptr, op.g, op.n, rstride, blocks, k_mr,
+                                                            op.bsite, op.bloc);
+  else
+    k_coarse_sap<T, cplx<T>, 4><<<grid, threads, sm, st>>>(z, b, op.blk, nullptr, op.g, op.n, rstride, blocks, k_mr,
+                                                            op.bsite, op.bloc);
 }
 
 template <typename T>

@@ -32,6 +32,8 @@ struct CoarseOp {
   int n_odd;
   int sap_cls;          // cluster size of the cluster SAP kernel (0: one CTA per SAP block)
   int sap_nsl = 0;      // blocks per site staged in shared memory by the cluster SAP kernel
+  const int* bsite = nullptr;   // [nBlk][vB] sites of each SAP block (block-local order)
+  const int* bloc = nullptr;    // [V] position of each site inside its SAP block
   int* err = nullptr;   // device error flag (bounded waits)
   // FP16 storage (FP32 compute only): blocks and one scale per site
   const __half2* blkh = nullptr;

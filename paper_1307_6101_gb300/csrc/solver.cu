@@ -84,6 +84,9 @@ struct Level {
   float* bscale = nullptr;
   int* blocks[2] = {nullptr, nullptr};
   int nblocks[2] = {0, 0};
+  int* bsite = nullptr;       // coarse levels: [nBlk][vB] site of each SAP block's sites (block-local order)
+  int* bloc = nullptr;        // coarse levels: [V] position of each site inside its SAP block
+  bool eo = true;             // coarsest level: odd-even solve possible (even extents)
   Work<double> w64;
   Work<float> w32;
 };
@@ -164,6 +167,7 @@ struct ddamg_handle {
   cplx<double>* pout64 = nullptr;
   // FP16 storage of links, clover term, P and coarse blocks under FP32 arithmetic
   bool half = false;
+  bool work_ready[2] = {false, false};   // Work<double>, Work<float> allocated on every level
   // coarsest level on a thread-block cluster
   bool use_cluster = true;
   CoarsestGeo cgeo;
@@ -551,6 +555,14 @@ void coarse_solve(ddamg_handle* h, cplx<T>* x, const cplx<T>* b, int nrhs) {
   Work<T>& w = work<T>(C);
   CoarseOp<T>& op = cop<T>(C);
   const size_t rs = C.vlen;
+  if (!C.eo) {
+    // odd extents: plain GMRES on D_L (same length, cycles and tolerance)
+    auto A = [&](cplx<T>* out, const cplx<T>* in, const cplx<T>* bb) { apply_D<T>(h, C, out, in, bb, nrhs); };
+    auto none = [](cplx<T>*, const cplx<T>*) {};
+    krylov<T>(h, w, C.vlen, x, b, nrhs, h->p.coarse_restart, h->p.coarse_tol, h->p.coarse_cycles, true, false, A,
+              none, nullptr);
+    return;
+  }
   if (const CoarsestPlan* pl = cluster_plan<T>(h)) {
     // the whole odd-even GMRES in one cluster-resident kernel per right-hand side
     CK(coarsest_cluster_solve<T>(x, b, op, *pl, h->cgeo, nrhs, rs, h->p.coarse_restart, h->p.coarse_cycles,
@@ -691,7 +703,9 @@ void free_graphs(ddamg_handle* h) {
 
 // ---------------------------------------------------------------------------
 // hierarchy construction
-void make_geom(Geom& g, const int L[4], const int A[4], const int B[4]) {
+// allow_loose: aggregates and SAP blocks need not nest (coarse levels); the sites are
+// then ordered by aggregate and the SAP blocks are addressed through site tables
+void make_geom(Geom& g, const int L[4], const int A[4], const int B[4], bool allow_loose = false) {
   bool b_in_a = true, a_in_b = true;
   for (int d = 0; d < 4; ++d) {
     if (L[d] <= 0 || A[d] <= 0 || B[d] <= 0 || L[d] % A[d] || L[d] % B[d])
@@ -701,9 +715,11 @@ void make_geom(Geom& g, const int L[4], const int A[4], const int B[4]) {
     b_in_a = b_in_a && (A[d] % B[d] == 0);
     a_in_b = a_in_b && (B[d] % A[d] == 0);
   }
-  if (!b_in_a && !a_in_b) fail(DDAMG_ERR_ARG, "aggregates and SAP blocks must nest (one must tile the other)");
-  const int* O = b_in_a ? A : B;
-  const int* I = b_in_a ? B : A;
+  const bool nest = b_in_a || a_in_b;
+  if (!nest && !allow_loose)
+    fail(DDAMG_ERR_ARG, "on the fine level aggregates and SAP blocks must nest (one must tile the other)");
+  const int* O = nest ? (b_in_a ? A : B) : A;
+  const int* I = nest ? (b_in_a ? B : A) : A;
   g.V = g.vA = g.vB = g.vI = g.nIO = g.nAgg = 1;
   for (int d = 0; d < 4; ++d) {
     g.L[d] = L[d];
@@ -731,13 +747,38 @@ void build_block_lists(ddamg_handle* h, Level& L) {
       fail(DDAMG_ERR_ARG, "red-black SAP needs an even number of blocks per direction on level " +
                               std::to_string(L.idx));
   }
-  if (L.fine ? g.vB > 1024 : g.vB * L.n > 1024)
-    fail(DDAMG_ERR_ARG, "SAP block too large for one CTA on level " + std::to_string(L.idx));
+  if (L.fine ? g.vB > 1024 : g.vB * L.n > 4 * 1024)
+    fail(DDAMG_ERR_ARG, "SAP block too large on level " + std::to_string(L.idx));
   std::vector<int> lists[2];
-  for (int b = 0; b < g.nBlk; ++b) {
-    int c[4];
-    geom_coords(g, b * g.vB, c);
-    lists[geom_block_colour(g, c)].push_back(b);
+  if (L.fine) {   // fine level: SAP blocks are contiguous index ranges
+    for (int b = 0; b < g.nBlk; ++b) {
+      int c[4];
+      geom_coords(g, b * g.vB, c);
+      lists[geom_block_colour(g, c)].push_back(b);
+    }
+  } else {        // coarse levels: blocks in lexicographic order, their sites through tables
+    int nb[4];
+    for (int d = 0; d < 4; ++d) nb[d] = g.L[d] / g.B[d];
+    std::vector<int> bsite((size_t)g.nBlk * g.vB), bloc(g.V);
+    for (int b = 0; b < g.nBlk; ++b) {
+      int bc[4], c[4], lc[4];
+      delin4(b, nb, bc);
+      for (int loc = 0; loc < g.vB; ++loc) {
+        delin4(loc, g.B, lc);
+        for (int d = 0; d < 4; ++d) c[d] = bc[d] * g.B[d] + lc[d];
+        const int site = geom_index(g, c);
+        bsite[(size_t)b * g.vB + loc] = site;
+        bloc[site] = loc;
+      }
+      for (int d = 0; d < 4; ++d) c[d] = bc[d] * g.B[d];
+      lists[geom_block_colour(g, c)].push_back(b);
+    }
+    L.bsite = dalloc<int>(h, bsite.size());
+    L.bloc = dalloc<int>(h, bloc.size());
+    CK(cudaMemcpy(L.bsite, bsite.data(), sizeof(int) * bsite.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.bloc, bloc.data(), sizeof(int) * bloc.size(), cudaMemcpyHostToDevice));
+    L.c64.bsite = L.c32.bsite = L.bsite;
+    L.c64.bloc = L.c32.bloc = L.bloc;
   }
   for (int c = 0; c < 2; ++c) {
     L.nblocks[c] = (int)lists[c].size();
@@ -747,19 +788,31 @@ void build_block_lists(ddamg_handle* h, Level& L) {
   }
 }
 
+// Workspaces by role: the fine level only needs the residual of the pre-smoother
+// and the fixed input/output of a captured K-cycle; the outer FGMRES only its
+// bases and residual; coarse levels the inner (F)GMRES and the restricted
+// right-hand side / coarse iterate; the coarsest also the odd-even temporaries.
+enum WorkRole { WORK_FINE, WORK_COARSE, WORK_COARSEST, WORK_OUTER };
+
 template <typename T>
-void alloc_work(ddamg_handle* h, Level& L, Work<T>& w, int m, bool flexible, int batch) {
+void alloc_work(ddamg_handle* h, Level& L, Work<T>& w, int m, WorkRole role, int batch) {
   const size_t vl = L.vlen * (size_t)batch;
+  const bool flexible = role != WORK_COARSEST;
   w.m = m;
-  w.bc = dalloc<cplx<T>>(h, vl);
-  w.xs = dalloc<cplx<T>>(h, vl);
   w.r = dalloc<cplx<T>>(h, vl);
-  for (int k = 0; k < 5; ++k) w.t[k] = dalloc<cplx<T>>(h, vl);
-  w.cur = dalloc<cplx<T>>(h, vl);
-  w.zc = dalloc<cplx<T>>(h, vl);
-  w.wv = dalloc<cplx<T>>(h, vl);
-  w.gin = dalloc<cplx<T>>(h, vl);
-  w.gout = dalloc<cplx<T>>(h, vl);
+  if (role != WORK_OUTER) {
+    w.gin = dalloc<cplx<T>>(h, vl);
+    w.gout = dalloc<cplx<T>>(h, vl);
+  }
+  if (role == WORK_COARSE || role == WORK_COARSEST) {
+    w.bc = dalloc<cplx<T>>(h, vl);
+    w.xs = dalloc<cplx<T>>(h, vl);
+    w.cur = dalloc<cplx<T>>(h, vl);
+    w.zc = dalloc<cplx<T>>(h, vl);
+    w.wv = dalloc<cplx<T>>(h, vl);
+  }
+  if (role == WORK_COARSEST)
+    for (int k = 0; k < 5; ++k) w.t[k] = dalloc<cplx<T>>(h, vl);
   if (m > 0) {
     w.V = dalloc<cplx<T>>(h, vl * (m + 1));
     if (flexible) w.Z = dalloc<cplx<T>>(h, vl * m);
@@ -912,7 +965,7 @@ void rebuild(ddamg_handle* h, int l) {
     }
   const size_t nb = (size_t)C.g.V * 9 * nc * nc;
   blas_convert<float, double>(C.c32.blk, C.c64.blk, nb, 1, 0, 0, st);
-  if (C.coarsest) {
+  if (C.coarsest && C.eo) {
     coarse_selfinv_build(C.c64.selfinv, C.c64.blk, C.g.V, nc, h->d_err, st);
     check_err_flag(h, "singular self block on the coarsest level");
     blas_convert<float, double>(C.c32.selfinv, C.c64.selfinv, (size_t)C.g.V * nc * nc, 1, 0, 0, st);
@@ -1008,15 +1061,41 @@ void build_hierarchy(ddamg_handle* h) {
     if (L.coarsest) {
       const int one[4] = {1, 1, 1, 1};
       make_geom(L.g, dims, dims, one);
-      for (int d = 0; d < 4; ++d)
-        if (dims[d] % 2) fail(DDAMG_ERR_ARG, "the coarsest lattice needs even extents for the odd-even solve");
+      // odd-even GMRES needs even extents; otherwise plain GMRES on D_L
+      L.eo = true;
+      for (int d = 0; d < 4; ++d) L.eo = L.eo && dims[d] % 2 == 0;
     } else {
-      make_geom(L.g, dims, p.agg[l], p.sap_block[l]);
+      // red-black SAP needs an even block count per direction (or one block): a
+      // block that gives an odd count is widened to the smallest extent that
+      // divides the lattice into an even count
+      int B[4];
+      for (int d = 0; d < 4; ++d) {
+        int c = p.sap_block[l][d];
+        while (c < dims[d] && (dims[d] % c != 0 || (dims[d] / c) % 2 != 0)) ++c;
+        B[d] = c < dims[d] ? c : dims[d];
+      }
+      make_geom(L.g, dims, p.agg[l], B, l > 0);
     }
     L.vlen = (size_t)L.g.V * L.n;
     if (!L.coarsest)
       for (int d = 0; d < 4; ++d) dims[d] /= p.agg[l][d];
   }
+}
+
+// workspaces of one precision on every level: inner FGMRES on levels 1..L-2,
+// GMRES on the coarsest, K-cycle input/output on level 0
+template <typename T>
+void ensure_work(ddamg_handle* h) {
+  bool& ready = h->work_ready[sizeof(T) == 4 ? 1 : 0];
+  if (ready) return;
+  if (h->cap.active) fail(DDAMG_ERR_ARG, "workspace allocation inside a graph capture");
+  for (int l = 0; l < h->L; ++l) {
+    Level& L = h->lv[l];
+    const int m = L.coarsest ? h->p.coarse_restart : (l >= 1 ? h->p.kcycle_len : 0);
+    const WorkRole role = L.fine ? WORK_FINE : (L.coarsest ? WORK_COARSEST : WORK_COARSE);
+    alloc_work<T>(h, L, work<T>(L), m, role, h->max_batch);
+  }
+  ready = true;
 }
 
 void allocate_hierarchy(ddamg_handle* h) {
@@ -1036,7 +1115,7 @@ void allocate_hierarchy(ddamg_handle* h) {
       const size_t nb = (size_t)L.g.V * 9 * L.n * L.n;
       L.c64.blk = dalloc<cplx<double>>(h, nb);
       L.c32.blk = dalloc<cplx<float>>(h, nb);
-      if (L.coarsest) {
+      if (L.coarsest && L.eo) {
         L.c64.selfinv = dalloc<cplx<double>>(h, (size_t)L.g.V * L.n * L.n);
         L.c32.selfinv = dalloc<cplx<float>>(h, (size_t)L.g.V * L.n * L.n);
         std::vector<int> odd;
@@ -1098,13 +1177,12 @@ void allocate_hierarchy(ddamg_handle* h) {
       L.P32 = dalloc<cplx<float>>(h, L.vlen * L.N);
       build_block_lists(h, L);
     }
-    // workspaces: inner FGMRES on levels 1..L-2, GMRES on the coarsest, temps on level 0
-    const int m = L.coarsest ? h->p.coarse_restart : (l >= 1 ? h->p.kcycle_len : 0);
-    const int batch = B;
-    alloc_work<float>(h, L, L.w32, m, !L.coarsest, batch);
-    alloc_work<double>(h, L, L.w64, m, !L.coarsest, batch);
   }
-  alloc_work<double>(h, h->lv[0], h->outer, h->p.outer_restart, true, B);
+  // workspaces of the configured preconditioner precision (the other precision's are
+  // allocated by the first per-operation call that uses them)
+  if (h->p.precision != 0) ensure_work<float>(h);
+  else ensure_work<double>(h);
+  alloc_work<double>(h, h->lv[0], h->outer, h->p.outer_restart, WORK_OUTER, B);
   h->ob = dalloc<cplx<double>>(h, h->lv[0].vlen * B);
   h->ox = dalloc<cplx<double>>(h, h->lv[0].vlen * B);
   h->pin32 = dalloc<cplx<float>>(h, h->lv[0].vlen * B);
@@ -1169,6 +1247,7 @@ Level& level_of(ddamg_handle* h, int level) {
 // run f on n fields of level l in chunks of the batch size; in/out are ABI (FP64 lex) buffers
 template <typename T, class F>
 void hook(ddamg_handle* h, int l, const double* in, double* out, int n, bool out_is_in_out, int out_level, F f) {
+  ensure_work<T>(h);
   Level& L = h->lv[l];
   Level& O = h->lv[out_level];
   const size_t in_bytes = sizeof(cplx<double>) * L.vlen * n;
@@ -1420,12 +1499,15 @@ size_t estimate_bytes(const int dims0[4], const ddamg_params& p) {
       tot += (size_t)(V + 1) * sizeof(int);   // SAP block lists
       maxtmp = std::max(maxtmp, vlen * N * 16);
     }
+    // workspaces of the configured precision (see alloc_work / ensure_work)
     const int m = coarsest ? p.coarse_restart : (l >= 1 ? p.kcycle_len : 0);
     const size_t vl = vlen * B;
-    const size_t nvec = 13 + (m > 0 ? (size_t)(m + 1) + (coarsest ? 0 : (size_t)m) : 0);
-    tot += nvec * vl * (8 + 16);
+    const size_t tb = p.precision == 0 ? 16 : 8;
+    size_t nvec = fine ? 3 : (coarsest ? 12 : 7);
+    if (m > 0) nvec += (size_t)(m + 1) + (coarsest ? 0 : (size_t)m);
+    tot += nvec * vl * tb;
     const size_t mm = m > 0 ? m : 1;
-    tot += 2 * B * ((mm + 1) * mm * 16 + mm * 8 + mm * 16 + 4 * (mm + 1) * 16 + 64);
+    tot += B * ((mm + 1) * mm * 16 + mm * 8 + mm * 16 + 4 * (mm + 1) * 16 + 64);
     if (!coarsest) {
       for (int d = 0; d < 4; ++d) dims[d] /= p.agg[l][d];
       nprev = n;
@@ -1434,7 +1516,7 @@ size_t estimate_bytes(const int dims0[4], const ddamg_params& p) {
   }
   (void)nprev;
   const size_t vl0 = vlen0 * B;
-  tot += (size_t)(2 * p.outer_restart + 1 + 13) * vl0 * 16;   // outer FGMRES V, Z and temporaries
+  tot += (size_t)(2 * p.outer_restart + 2) * vl0 * 16;        // outer FGMRES V, Z and residual
   tot += vl0 * (16 + 16 + 8 + 8);                              // ob, ox, pin32, pout32
   tot += 2 * vl0 * 16 + maxtmp + 2 * maxtmp / 2;               // staging and setup scratch
   return tot;
@@ -1711,10 +1793,10 @@ int ddamg_krylov_steps(ddamg_handle* h, int level, int precision, long long* ste
     int dev = 0;
     long long host = 0;
     if (precision != 0) {
-      CK(cudaMemcpy(&dev, L.w32.gs.ctl + 3, sizeof(int), cudaMemcpyDeviceToHost));
+      if (L.w32.gs.ctl) CK(cudaMemcpy(&dev, L.w32.gs.ctl + 3, sizeof(int), cudaMemcpyDeviceToHost));
       host = L.w32.host_steps;
     } else {
-      CK(cudaMemcpy(&dev, L.w64.gs.ctl + 3, sizeof(int), cudaMemcpyDeviceToHost));
+      if (L.w64.gs.ctl) CK(cudaMemcpy(&dev, L.w64.gs.ctl + 3, sizeof(int), cudaMemcpyDeviceToHost));
       host = L.w64.host_steps;
     }
     *steps = host + dev + (level == 0 ? h->outer.host_steps : 0);

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from cases import Case, rel, SMALL2, RAGGED2, THREE, C1, golden_mass
+from cases import Case, rel, SMALL2, RAGGED2, THREE, ODD3, C1, golden_mass
 
 pytestmark = pytest.mark.gpu
 
@@ -84,7 +84,7 @@ def test_fine_sap(dd, spec):
         assert rel(z, ref) <= tol, (prec, rel(z, ref))
 
 
-@pytest.mark.parametrize("spec", [SMALL2, RAGGED2, THREE])
+@pytest.mark.parametrize("spec", [SMALL2, RAGGED2, THREE, ODD3])
 def test_interpolation_and_coarse_operators(dd, spec):
     c, h, o = _pair(spec)
     for l in range(c.levels - 1):
@@ -108,7 +108,7 @@ def test_interpolation_and_coarse_operators(dd, spec):
             assert rel(lhs, rhs) <= 1e-12
 
 
-@pytest.mark.parametrize("spec", [SMALL2, RAGGED2, THREE])
+@pytest.mark.parametrize("spec", [SMALL2, RAGGED2, THREE, ODD3])
 def test_restrict_prolong(dd, spec):
     from oracle.transfer import restrict, prolong
     c, h, o = _pair(spec)
@@ -129,7 +129,7 @@ def test_restrict_prolong(dd, spec):
 
 
 @pytest.mark.parametrize("cluster", [1, 0])
-@pytest.mark.parametrize("spec", [SMALL2, THREE])
+@pytest.mark.parametrize("spec", [SMALL2, THREE, ODD3])
 def test_coarse_apply_and_sap(dd, spec, cluster):
     c, h, o = _pair(spec)
     dd.ddamg_set_option(h, dd.DDAMG_OPT_SAP_CLUSTER, cluster)
@@ -307,3 +307,26 @@ def test_device_pointers_through_torch(dd):
     out = torch.zeros_like(ft)
     dd.ddamg_apply(h, 0, 0, ft, out, 2)
     assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_odd_extents_plain_coarsest_gmres_and_solve(dd):
+    """Coarsest lattice with odd extents: plain GMRES on D_L, same as the oracle's; full solve to 1e-10."""
+    from oracle.krylov import gmres
+    c, h, o = _pair(ODD3, max_rhs=2)
+    assert o.levels[2].eo is None and o.levels[1].sap.block == (2, 3, 3, 3)
+    dims, n, _ = h.level_info(2)
+    b = _fields(2, dims, n, 61)
+    z = np.zeros_like(b)
+    dd.ddamg_coarse_solve(h, 0, b, z, 2)
+    for i in range(2):
+        zr, info = gmres(o.levels[2].op.apply, b[i], m=50, tol=5e-2, max_cycles=20)
+        assert rel(z[i], zr) <= 1e-9
+    z32 = np.zeros_like(b)
+    dd.ddamg_coarse_solve(h, 1, b, z32, 2)
+    for i in range(2):
+        assert np.linalg.norm(b[i] - o.levels[2].op.apply(z32[i])) <= 5e-2 * np.linalg.norm(b[i]) * 1.01
+    bb = np.ascontiguousarray(synth.random_spinors(1, c.dims, 62))
+    x = np.zeros_like(bb)
+    st = dd.ddamg_solve(h, bb, x, 1, 1e-10)
+    assert st[0]["converged"]
+    assert np.linalg.norm(bb[0] - o.levels[0].op.apply(x[0])) <= 1e-10 * np.linalg.norm(bb[0])

@@ -120,3 +120,41 @@ def test_three_level_solve_converges():
     b = synth.random_spinors(1, dims, 4)[0]
     x, info = h.solve(b, tol=1e-10)
     assert info.converged and norm(op.apply(x) - b) <= 1e-10 * norm(b)
+
+
+def test_red_black_block_reading():
+    from oracle.lattice import red_black_block
+    # the worked cases of the reading: 6-site extents with 2-site blocks -> 3-site blocks
+    assert red_black_block((12, 6, 6, 6), (2, 2, 2, 2)) == (2, 3, 3, 3)
+    assert red_black_block((12, 6, 6, 6), (3, 3, 3, 3)) == (3, 3, 3, 3)
+    assert red_black_block((8, 8, 8, 8), (2, 2, 2, 2)) == (2, 2, 2, 2)        # unchanged when even
+    assert red_black_block((4, 2, 2, 2), (2, 2, 2, 2)) == (2, 2, 2, 2)        # one block: no colouring needed
+    assert red_black_block((5, 3, 3, 6), (2, 2, 2, 2)) == (5, 3, 3, 3)        # falls back to one block
+    for dims in [(12, 6, 6, 6), (24, 12, 6, 10), (14, 14, 6, 6)]:
+        bs = red_black_block(dims, (2, 2, 2, 2))
+        for L, b in zip(dims, bs):
+            assert L % b == 0 and ((L // b) % 2 == 0 or L // b == 1)
+
+
+def test_odd_coarsest_uses_plain_gmres_and_solves():
+    """A three-level hierarchy whose coarsest lattice has odd extents (plain GMRES there)
+    and whose level-1 SAP blocks are widened to 3 sites: the K-cycle preconditioned
+    solve still reaches 1e-10 against the fine operator."""
+    import synth
+    from oracle.wilson import WilsonOp
+    from oracle.multigrid import Hierarchy, Params
+    dims = (8, 12, 12, 12)
+    U = synth.su3_field(dims, 0.3, 1)
+    op = WilsonOp.build(U, -0.2, 1.0)
+    p = Params(levels=3, agg=((2, 2, 2, 2), (2, 2, 2, 2)), n_tv=(4, 5),
+               sap_block=((2, 2, 2, 2), (2, 2, 2, 2), None), mr_steps=2, nu=2, n_inv=0, eta_passes=1,
+               outer_restart=10)
+    ld = [dims, (4, 6, 6, 6), (2, 3, 3, 3)]
+    tv = synth.random_test_vectors(ld, (4, 5), 3)
+    h = Hierarchy(op, p).setup(tv)
+    assert h.levels[2].eo is None
+    assert h.levels[1].sap.block == (2, 3, 3, 3)
+    b = synth.random_spinors(1, dims, 2)[0]
+    x, info = h.solve(b, tol=1e-10)
+    assert info.converged
+    assert np.linalg.norm(b - op.apply(x)) <= 1e-10 * np.linalg.norm(b)
