@@ -40,9 +40,11 @@ constexpr int RJ = 10;   // coarse columns j accumulated per thread by k_restric
 // columns j in [g*RJ, g*RJ + RJ) and the sites x = A*vA + l, l + S, ... of the
 // aggregate, so every input and every P entry is loaded once.  S is a power of
 // two; the per-thread partial sums are reduced over the S lanes of a group in a
-// fixed order (shuffles inside warps, then shared memory across warps).
-template <typename T, typename PS>
-__global__ void __launch_bounds__(512, 2) k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const PS* __restrict__ P,
+// fixed order (shuffles inside warps, then shared memory across warps).  HF > 0:
+// the fine level, whose HF = 6 dofs per chirality are unrolled so that all loads
+// of a chirality are in flight together.
+template <typename T, typename PS, int HF>
+__global__ void __launch_bounds__(512, HF > 0 ? 1 : 2) k_restrict(cplx<T>* __restrict__ out, const cplx<T>* __restrict__ in, const PS* __restrict__ P,
                            const float* __restrict__ pscale, Geom gf, Geom gc, bool fine, int n, int N, int S,
                            size_t in_rstride, size_t pstride, size_t out_rstride, size_t out_site_stride) {
   __shared__ T red[32 * 2 * RJ];
@@ -69,16 +71,24 @@ __global__ void __launch_bounds__(512, 2) k_restrict(cplx<T>* __restrict__ out, 
       if (g < G) {
         for (int xl = lane; xl < gf.vA; xl += S) {
           const int x = agg * gf.vA + xl;
-          for (int f = s * h; f < (s + 1) * h; ++f) {
-            const size_t a = faddr(fine, V, n, x, f);
-            const cplx<T> v = pin[a];
+          if constexpr (HF > 0) {
+            cplx<T> v[HF];
 #pragma unroll
-            for (int jj = 0; jj < RJ; ++jj) {
-              if (j0 + jj < N) {
-                const cplx<T> t = cdotc(ld_cplx(P, (size_t)(j0 + jj) * pstride + a), v);
-                acc[2 * jj] += t.re;
-                acc[2 * jj + 1] += t.im;
-              }
+            for (int f = 0; f < HF; ++f) v[f] = pin[(size_t)(s * HF + f) * V + x];
+#pragma unroll
+            for (int jj = 0; jj < RJ; ++jj)
+              if (j0 + jj < N)
+#pragma unroll
+                for (int f = 0; f < HF; ++f)
+                  cdotc_acc(acc[2 * jj], acc[2 * jj + 1],
+                            ld_cplx(P, (size_t)(j0 + jj) * pstride + (size_t)(s * HF + f) * V + x), v[f]);
+          } else {
+            for (int f = s * h; f < (s + 1) * h; ++f) {
+              const size_t a = faddr(fine, V, n, x, f);
+              const cplx<T> v = pin[a];
+#pragma unroll
+              for (int jj = 0; jj < RJ; ++jj)
+                if (j0 + jj < N) cdotc_acc(acc[2 * jj], acc[2 * jj + 1], ld_cplx(P, (size_t)(j0 + jj) * pstride + a), v);
             }
           }
         }
@@ -249,16 +259,24 @@ void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& 
   if (S < 32 && gpc > 32) gpc = 32;                     // partial-sum slots in shared memory
   const int threads = gpc * S;
   count_launch();
+  const dim3 grid(gf.nAgg, nrhs);
   if constexpr (sizeof(T) == 4) {
     if (Ph) {
-      k_restrict<float, __half2><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, Ph, pscale, gf, gc, fine, n, N, S,
-                                                                          in_rstride, pstride, out_rstride,
-                                                                          out_site_stride);
+      if (fine)
+        k_restrict<float, __half2, 6><<<grid, threads, 0, st>>>(out, in, Ph, pscale, gf, gc, fine, n, N, S, in_rstride,
+                                                                 pstride, out_rstride, out_site_stride);
+      else
+        k_restrict<float, __half2, 0><<<grid, threads, 0, st>>>(out, in, Ph, pscale, gf, gc, fine, n, N, S, in_rstride,
+                                                                 pstride, out_rstride, out_site_stride);
       return;
     }
   }
-  k_restrict<T, cplx<T>><<<dim3(gf.nAgg, nrhs), threads, 0, st>>>(out, in, P, nullptr, gf, gc, fine, n, N, S,
-                                                                   in_rstride, pstride, out_rstride, out_site_stride);
+  if (fine)
+    k_restrict<T, cplx<T>, 6><<<grid, threads, 0, st>>>(out, in, P, nullptr, gf, gc, fine, n, N, S, in_rstride,
+                                                          pstride, out_rstride, out_site_stride);
+  else
+    k_restrict<T, cplx<T>, 0><<<grid, threads, 0, st>>>(out, in, P, nullptr, gf, gc, fine, n, N, S, in_rstride,
+                                                          pstride, out_rstride, out_site_stride);
 }
 
 template <typename T>
