@@ -942,6 +942,8 @@ void half_bind(ddamg_handle* h) {
   }
 }
 
+constexpr int SETUP_CHUNK = 4;   // columns / test vectors per pass of the setup's batched operations
+
 // P_l from the test vectors, D_{l+1} = P_l^+ D_l P_l (FP64), FP32 copies, coarsest self inverses
 void rebuild(ddamg_handle* h, int l) {
   Level& F = h->lv[l];
@@ -952,16 +954,21 @@ void rebuild(ddamg_handle* h, int l) {
   orthonormalise(F.P64, F.g, F.fine, F.n, F.N, h->d_err, st);
   check_err_flag(h, "test vectors are linearly dependent on an aggregate");
   blas_convert<float, double>(F.P32, F.P64, tot, 1, 0, 0, st);
-  // Galerkin: column (s', j) of every block = P^+ (term of D applied to P_j restricted to chirality s')
-  cplx<double>* tmp = static_cast<cplx<double>*>(scratch(h, 4, sizeof(cplx<double>) * tot));
+  // Galerkin: column (s', j) of every block = P^+ (term of D applied to P_j restricted to chirality s'),
+  // in chunks of SETUP_CHUNK columns (bounded scratch)
+  const int jb_max = F.N < SETUP_CHUNK ? F.N : SETUP_CHUNK;
+  cplx<double>* tmp = static_cast<cplx<double>*>(scratch(h, 4, sizeof(cplx<double>) * F.vlen * jb_max));
   const int nc = C.n;
   for (int sp = 0; sp < 2; ++sp)
     for (int k = 0; k < 9; ++k) {
       const int sel = k == 0 ? SEL_AGG_SELF : (k <= 4 ? SEL_AGG_FWD : SEL_AGG_BWD);
       const int mu = k == 0 ? 0 : (k - 1) % 4;
-      apply_D<double>(h, F, tmp, F.P64, nullptr, F.N, sel, mu, sp);
-      restrict_op<double>(C.c64.blk + (size_t)k * nc * nc + (size_t)sp * F.N * nc, tmp, F.P64, F.g, C.g, F.fine, F.n,
-                          F.N, F.N, F.vlen, (size_t)nc, (size_t)9 * nc * nc, st);
+      for (int j0 = 0; j0 < F.N; j0 += jb_max) {
+        const int jb = F.N - j0 < jb_max ? F.N - j0 : jb_max;
+        apply_D<double>(h, F, tmp, F.P64 + (size_t)j0 * F.vlen, nullptr, jb, sel, mu, sp);
+        restrict_op<double>(C.c64.blk + (size_t)k * nc * nc + (size_t)(sp * F.N + j0) * nc, tmp, F.P64, F.g, C.g,
+                            F.fine, F.n, F.N, jb, F.vlen, (size_t)nc, (size_t)9 * nc * nc, st);
+      }
     }
   const size_t nb = (size_t)C.g.V * 9 * nc * nc;
   blas_convert<float, double>(C.c32.blk, C.c64.blk, nb, 1, 0, 0, st);
@@ -976,16 +983,21 @@ void rebuild(ddamg_handle* h, int l) {
 
 template <typename T>
 void setup_smooth(ddamg_handle* h, int l) {
+  // the test vectors in chunks of SETUP_CHUNK (bounded scratch; each vector is smoothed on its own)
   Level& L = h->lv[l];
-  const size_t tot = L.vlen * (size_t)L.N;
-  cplx<T>* bT = static_cast<cplx<T>*>(scratch(h, 5, sizeof(cplx<T>) * tot));
-  cplx<T>* xT = static_cast<cplx<T>*>(scratch(h, 6, sizeof(cplx<T>) * tot));
-  for (int eta = 1; eta <= h->p.eta_passes; ++eta) {
-    blas_convert<T, double>(bT, L.tv64, tot, 1, 0, 0, h->st);
-    blas_zero<T>(xT, tot, 1, 0, h->st);
-    sap<T>(h, L, xT, bT, L.N, eta);
-    blas_convert<double, T>(L.tv64, xT, tot, 1, 0, 0, h->st);
-  }
+  const int jb_max = L.N < SETUP_CHUNK ? L.N : SETUP_CHUNK;
+  cplx<T>* bT = static_cast<cplx<T>*>(scratch(h, 5, sizeof(cplx<T>) * L.vlen * jb_max));
+  cplx<T>* xT = static_cast<cplx<T>*>(scratch(h, 6, sizeof(cplx<T>) * L.vlen * jb_max));
+  for (int eta = 1; eta <= h->p.eta_passes; ++eta)
+    for (int j0 = 0; j0 < L.N; j0 += jb_max) {
+      const int jb = L.N - j0 < jb_max ? L.N - j0 : jb_max;
+      const size_t tot = L.vlen * (size_t)jb;
+      cplx<double>* tv = L.tv64 + (size_t)j0 * L.vlen;
+      blas_convert<T, double>(bT, tv, tot, 1, 0, 0, h->st);
+      blas_zero<T>(xT, tot, 1, 0, h->st);
+      sap<T>(h, L, xT, bT, jb, eta);
+      blas_convert<double, T>(tv, xT, tot, 1, 0, 0, h->st);
+    }
   sync(h);
 }
 
@@ -1497,7 +1509,7 @@ size_t estimate_bytes(const int dims0[4], const ddamg_params& p) {
     if (!coarsest) {
       tot += vlen * N * (16 + 16 + 8) + (p.precision == 2 ? vlen * N * 4 + V * 8 : 0);
       tot += (size_t)(V + 1) * sizeof(int);   // SAP block lists
-      maxtmp = std::max(maxtmp, vlen * N * 16);
+      maxtmp = std::max(maxtmp, vlen * (size_t)std::min(N, 4) * 16);
     }
     // workspaces of the configured precision (see alloc_work / ensure_work)
     const int m = coarsest ? p.coarse_restart : (l >= 1 ? p.kcycle_len : 0);

@@ -109,6 +109,10 @@ THREE = dict(dims=(8, 4, 4, 4), levels=3, agg=((2, 2, 2, 2), (2, 1, 1, 1)), n_tv
 # and the coarsest lattice (2, 3, 3, 3) is solved by plain GMRES
 ODD3 = dict(dims=(8, 12, 12, 12), levels=3, agg=((2, 2, 2, 2), (2, 2, 2, 2)), n_tv=(4, 5),
             sap=((2, 2, 2, 2), (2, 2, 2, 2)))
+# four levels (the structure of the 48^3x96 workload at a small size): aggregates 2^4 three
+# times; the coarsest lattice (2, 1, 1, 1) has odd extents and is solved by plain GMRES
+FOUR = dict(dims=(16, 8, 8, 8), levels=4, agg=((2, 2, 2, 2), (2, 2, 2, 2), (2, 2, 2, 2)), n_tv=(4, 5, 5),
+            sap=((2, 2, 2, 2), (2, 2, 2, 2), (2, 2, 2, 2)))
 # the two-level FP64 workload (8^4, eps 0.3, csw 0, aggregates 4^4, 8 test vectors, SAP 2^4)
 C1 = dict(dims=(8, 8, 8, 8), levels=2, agg=((4, 4, 4, 4),), n_tv=(8,), sap=((2, 2, 2, 2),), eps=0.3, csw=0.0,
           mr_steps=4, nu=3, n_inv=3, eta_passes=3, outer_restart=25)
