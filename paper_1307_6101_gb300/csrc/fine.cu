@@ -18,6 +18,7 @@
 #include "kernels.h"
 #include "tma.cuh"
 
+#include <cstdint>
 #include <mutex>
 
 namespace {
@@ -107,23 +108,44 @@ DD_HD void hop_accumulate(int mu, bool fwd, const cplx<T> u[9], const cplx<T> ps
 // packed Hermitian 6x6: 6 real diagonals, then the 15 upper off-diagonals (row-major) as re, im
 DD_HD int herm_off(int i, int j) { return i * 6 - (i * (i + 1)) / 2 + (j - i - 1); }
 
+// Clover storage: per chirality 36 packed reals, component-major with stride V.
+// FP32/FP64: one row per real ([2][36][V]); FP16: one __half2 row per pair of
+// consecutive reals ([2][18][V]), so a row load brings two reals.
+template <typename CS> struct ClovRows { static constexpr int per_chir = 36; };
+template <> struct ClovRows<__half2> { static constexpr int per_chir = 18; };
+
+template <typename T, typename CS>
+DD_HD void load_clover36(const CS* __restrict__ a, size_t stride, T c[36]) {
+#pragma unroll
+  for (int i = 0; i < 36; ++i) c[i] = T(ld_real(a, (size_t)i * stride));
+}
+__device__ __forceinline__ void load_clover36(const __half2* __restrict__ a, size_t stride, float c[36]) {
+#pragma unroll
+  for (int j = 0; j < 18; ++j) {
+    const float2 f = __half22float2(a[(size_t)j * stride]);
+    c[2 * j] = f.x;
+    c[2 * j + 1] = f.y;
+  }
+}
+
 // out = (A + shift) in for the two packed Hermitian 6x6 blocks (shift on the diagonal)
 template <typename T, typename CS>
 DD_HD void clover_apply(const CS* __restrict__ clov, int V, int x, const cplx<T> in[12], cplx<T> out[12],
                         T shift = T(0)) {
 #pragma unroll
   for (int ch = 0; ch < 2; ++ch) {
-    const CS* a = clov + (size_t)ch * 36 * V + x;
+    T a[36];
+    load_clover36(clov + (size_t)ch * ClovRows<CS>::per_chir * V + x, (size_t)V, a);
     const cplx<T>* v = in + 6 * ch;
     cplx<T>* w = out + 6 * ch;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) w[i] = (T(ld_real(a, (size_t)i * V)) + shift) * v[i];
+    for (int i = 0; i < 6; ++i) w[i] = (a[i] + shift) * v[i];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
 #pragma unroll
       for (int j = i + 1; j < 6; ++j) {
         const int p = 6 + 2 * herm_off(i, j);
-        cplx<T> e = cmk<T>(T(ld_real(a, (size_t)p * V)), T(ld_real(a, (size_t)(p + 1) * V)));
+        const cplx<T> e = cmk<T>(a[p], a[p + 1]);
         cfma(w[i], e, v[j]);
         cfmac(w[j], e, v[i]);
       }
@@ -376,8 +398,9 @@ __global__ void __launch_bounds__(256, 2) k_fine_sap_tma(cplx<T>* __restrict__ z
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int vB = g.vB;
   const int segs = blockDim.x / seg;
-  // per segment: links [36][vB] LS, clover [72][vB] CS, residual [12][vB] cplx
-  const size_t seg_bytes = (size_t)vB * (36 * sizeof(LS) + 72 * sizeof(CS) + 12 * sizeof(cplx<T>));
+  constexpr int CR = 2 * ClovRows<CS>::per_chir;
+  // per segment: links [36][vB] LS, clover [CR][vB] CS, residual [12][vB] cplx
+  const size_t seg_bytes = (size_t)vB * (36 * sizeof(LS) + CR * sizeof(CS) + 12 * sizeof(cplx<T>));
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + (size_t)segs * seg_bytes);
   T* scratch = reinterpret_cast<T*>(bar + 2);
   const int s = threadIdx.x / seg;
@@ -388,7 +411,7 @@ __global__ void __launch_bounds__(256, 2) k_fine_sap_tma(cplx<T>* __restrict__ z
   unsigned char* sb = smem_raw + (size_t)s * seg_bytes;
   LS* Ls = reinterpret_cast<LS*>(sb);
   CS* Cs = reinterpret_cast<CS*>(Ls + 36 * vB);
-  cplx<T>* Rs = reinterpret_cast<cplx<T>*>(Cs + 72 * vB);
+  cplx<T>* Rs = reinterpret_cast<cplx<T>*>(Cs + CR * vB);
   const int V = g.V;
   // stage the operator of every segment's block
   if (threadIdx.x == 0) mbar_init(bar, 1);
@@ -396,7 +419,7 @@ __global__ void __launch_bounds__(256, 2) k_fine_sap_tma(cplx<T>* __restrict__ z
   if (threadIdx.x < 32) {
     int nseg = 0;
     for (int q = 0; q < segs; ++q) nseg += (blockIdx.x * segs + q < nblocks) ? 1 : 0;
-    const unsigned bytes = (unsigned)(nseg * vB * (36 * sizeof(LS) + 72 * sizeof(CS)));
+    const unsigned bytes = (unsigned)(nseg * vB * (36 * sizeof(LS) + CR * sizeof(CS)));
     if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, bytes);
     __syncwarp();
     for (int q = 0; q < nseg; ++q) {
@@ -404,7 +427,7 @@ __global__ void __launch_bounds__(256, 2) k_fine_sap_tma(cplx<T>* __restrict__ z
       unsigned char* sq = smem_raw + (size_t)q * seg_bytes;
       LS* Lq = reinterpret_cast<LS*>(sq);
       CS* Cq = reinterpret_cast<CS*>(Lq + 36 * vB);
-      for (int cpy = threadIdx.x; cpy < 108; cpy += 32) {
+      for (int cpy = threadIdx.x; cpy < 36 + CR; cpy += 32) {
         if (cpy < 36)
           bulk_g2s(Lq + (size_t)cpy * vB, U + (size_t)cpy * V + (size_t)bq * vB, (unsigned)(vB * sizeof(LS)), bar);
         else
@@ -534,6 +557,215 @@ __global__ void __launch_bounds__(256, 2) k_fine_sap_tma(cplx<T>* __restrict__ z
 #pragma unroll
       for (int k = 0; k < 12; ++k) pz[(size_t)k * V + x] = pz[(size_t)k * V + x] + xs[k];
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SAP colour sweep for 4^4 blocks (the SAP block of the paper's fine level,
+// Table 1): one CTA of 256 threads per block, one thread per site.  The block
+// volume is a compile-time constant, so every shared-memory address below is
+// a thread base plus an immediate, and the eight hop directions are unrolled
+// with the spin projection of each direction fixed at compile time.
+//
+// Staging (cp.async.bulk on two mbarriers): the block's 36 link rows and its
+// clover rows (bar[0], once), and the block's own 12 rows of z (bar[1], once
+// per right-hand side) into the residual buffer Rs.  rho = b - D z then reads
+// internal neighbours from Rs and only the hops leaving the block from global
+// memory.  Each minimal-residual step takes two barriers: one after the warp
+// partials of <p, r> and |p|^2 are written (every read of Rs for p is done
+// by then), one after r is updated.  The partials are summed over the eight
+// warps in a fixed order by every thread, so all threads get the same alpha.
+// Waits are bounded: on a timeout the kernel sets *err, waits (bounded) for its
+// copies and returns without touching z.
+template <typename LS, typename CS>
+__global__ void __launch_bounds__(256, 2) k_fine_sap_b4(cplx<float>* __restrict__ z,
+                                                     const cplx<float>* __restrict__ bsrc, const LS* __restrict__ U,
+                                                     const CS* __restrict__ clov, Geom g, int bc_t, size_t rstride,
+                                                     int nrhs, const int* __restrict__ blocks, int k_mr, int* err,
+                                                     float shift) {
+  using C = cplx<float>;
+  constexpr int VB = 256;
+  constexpr int CR = 2 * ClovRows<CS>::per_chir;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LS* Ls = reinterpret_cast<LS*>(smem_raw);                       // [36][VB]
+  CS* Cs = reinterpret_cast<CS*>(Ls + 36 * VB);                   // [CR][VB]
+  C* Rs = reinterpret_cast<C*>(Cs + CR * VB);                     // [12][VB]: z of the block, then r
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(Rs + 12 * VB);
+  float* scratch = reinterpret_cast<float*>(bar + 2);             // [2][8 warps][3]
+  const int loc = threadIdx.x, lane = loc & 31, warp = loc >> 5;
+  const int blk = blocks[blockIdx.x];
+  const int V = g.V;
+  const int x = blk * VB + loc;
+  if (loc == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&bar[0], (unsigned)(VB * (36 * sizeof(LS) + CR * sizeof(CS))));
+      mbar_arrive_expect_tx(&bar[1], (unsigned)(12 * VB * sizeof(C)));
+    }
+    __syncwarp();
+    for (int cpy = lane; cpy < 36 + CR + 12; cpy += 32) {
+      if (cpy < 36)
+        bulk_g2s(Ls + (size_t)cpy * VB, U + (size_t)cpy * V + (size_t)blk * VB, VB * sizeof(LS), &bar[0]);
+      else if (cpy < 36 + CR)
+        bulk_g2s(Cs + (size_t)(cpy - 36) * VB, clov + (size_t)(cpy - 36) * V + (size_t)blk * VB, VB * sizeof(CS),
+                 &bar[0]);
+      else
+        bulk_g2s(Rs + (size_t)(cpy - 36 - CR) * VB, z + (size_t)(cpy - 36 - CR) * V + (size_t)blk * VB,
+                 VB * sizeof(C), &bar[1]);
+    }
+  }
+  // site geometry (overlaps the copies): local coordinates l_mu = (loc / st_mu) % 4,
+  // st = (64, 16, 4, 1); a hop is internal if it stays in the block, or wraps
+  // around a lattice direction of extent 4 that the block spans
+  int c[4];
+  geom_coords(g, x, c);
+  unsigned inmask = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int l = (loc >> (6 - 2 * mu)) & 3;
+    const bool wrap = g.L[mu] == 4;
+    if (l < 3 || wrap) inmask |= 1u << (2 * mu);
+    if (l > 0 || wrap) inmask |= 1u << (2 * mu + 1);
+  }
+  const bool neg_tf = bc_t < 0 && c[0] == g.L[0] - 1;   // forward time hop wraps the lattice
+  const bool neg_tb = bc_t < 0 && c[0] == 0;            // backward time hop wraps the lattice
+  auto slot = [&](int mu, bool fwd) {
+    const int st = 1 << (6 - 2 * mu);
+    const int l = (loc >> (6 - 2 * mu)) & 3;
+    return fwd ? (l < 3 ? loc + st : loc - 3 * st) : (l > 0 ? loc - st : loc + 3 * st);
+  };
+  bool ok = __syncthreads_and(mbar_wait_bounded(&bar[0], 0) ? 1 : 0);
+  C xs[12], p[12], nb[12], u[9];
+  int zphase = 0;   // phase of the last z copy issued on bar[1]
+  for (int rh = 0; rh < nrhs && ok; ++rh) {
+    C* pz = z + (size_t)rh * rstride;
+    zphase = rh & 1;
+    if (rh > 0 && warp == 0) {   // every access of Rs for the previous right-hand side is done (last barrier)
+      fence_proxy_async_shared();
+      if (lane == 0) mbar_arrive_expect_tx(&bar[1], (unsigned)(12 * VB * sizeof(C)));
+      __syncwarp();
+      if (lane < 12) bulk_g2s(Rs + (size_t)lane * VB, pz + (size_t)lane * V + (size_t)blk * VB, VB * sizeof(C), &bar[1]);
+    }
+    ok = __syncthreads_and(mbar_wait_bounded(&bar[1], zphase) ? 1 : 0);
+    if (!ok) break;
+    // rho = b - D z at x
+    {
+      C acc[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = czero<float>();
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int mu = k >> 1;
+        const bool fwd = (k & 1) == 0;
+        const bool neg = mu == 0 && (fwd ? neg_tf : neg_tb);
+        if (inmask & (1u << k)) {
+          const int sl = slot(mu, fwd);
+#pragma unroll
+          for (int q = 0; q < 12; ++q) {
+            const C v = Rs[q * VB + sl];
+            nb[q] = cmk<float>(sign_flip(v.re, neg), sign_flip(v.im, neg));
+          }
+          const int ls = fwd ? loc : sl;
+#pragma unroll
+          for (int q = 0; q < 9; ++q) u[q] = ld_cplx(Ls, (size_t)((mu * 9 + q) * VB + ls));
+        } else {
+          const int n = geom_neighbor(g, c, mu, fwd ? +1 : -1);
+          load_spinor(pz, V, n, nb, neg ? -1.f : 1.f, -1);
+          if (fwd) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) u[q] = ld_cplx(Ls, (size_t)((mu * 9 + q) * VB + loc));
+          } else {
+            load_link(U, V, mu, n, u);
+          }
+        }
+        hop_accumulate(mu, fwd, u, nb, acc);
+      }
+#pragma unroll
+      for (int q = 0; q < 12; ++q) nb[q] = Rs[q * VB + loc];
+      clover_apply(Cs, VB, loc, nb, p, shift);
+      const C* pb = bsrc + (size_t)rh * rstride;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        nb[k] = pb[(size_t)k * V + x] - (p[k] - 0.5f * acc[k]);
+        xs[k] = czero<float>();
+      }
+    }
+    __syncthreads();   // every read of the staged z is done
+#pragma unroll
+    for (int k = 0; k < 12; ++k) Rs[k * VB + loc] = nb[k];
+    __syncthreads();
+#pragma unroll 1
+    for (int it = 0; it < k_mr; ++it) {
+      C acc[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = czero<float>();
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int mu = k >> 1;
+        const bool fwd = (k & 1) == 0;
+        if (inmask & (1u << k)) {
+          const bool neg = mu == 0 && (fwd ? neg_tf : neg_tb);
+          const int sl = slot(mu, fwd);
+#pragma unroll
+          for (int q = 0; q < 12; ++q) {
+            const C v = Rs[q * VB + sl];
+            nb[q] = cmk<float>(sign_flip(v.re, neg), sign_flip(v.im, neg));
+          }
+          const int ls = fwd ? loc : sl;
+#pragma unroll
+          for (int q = 0; q < 9; ++q) u[q] = ld_cplx(Ls, (size_t)((mu * 9 + q) * VB + ls));
+          hop_accumulate(mu, fwd, u, nb, acc);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 12; ++q) nb[q] = Rs[q * VB + loc];   // own residual, kept for the update
+      clover_apply(Cs, VB, loc, nb, p, shift);
+      float nre = 0.f, nim = 0.f, den = 0.f;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        p[k] = p[k] - 0.5f * acc[k];
+        cdotc_acc(nre, nim, p[k], nb[k]);
+        cnorm2_acc(den, p[k]);
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        nre += __shfl_xor_sync(0xffffffffu, nre, off);
+        nim += __shfl_xor_sync(0xffffffffu, nim, off);
+        den += __shfl_xor_sync(0xffffffffu, den, off);
+      }
+      float* sc = scratch + (it & 1) * 24;
+      if (lane == 0) {
+        sc[3 * warp] = nre;
+        sc[3 * warp + 1] = nim;
+        sc[3 * warp + 2] = den;
+      }
+      __syncthreads();
+      nre = nim = den = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        nre += sc[3 * w];
+        nim += sc[3 * w + 1];
+        den += sc[3 * w + 2];
+      }
+      const C alpha = den > 0.f ? cmk<float>(nre / den, nim / den) : czero<float>();
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cfma(xs[k], alpha, nb[k]);
+        Rs[k * VB + loc] = nb[k] - alpha * p[k];
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) pz[(size_t)k * V + x] = pz[(size_t)k * V + x] + xs[k];
+  }
+  if (!ok) {   // uniform across the CTA
+    if (loc == 0) atomicExch(err, 2);
+    mbar_wait_bounded(&bar[0], 0);
+    mbar_wait_bounded(&bar[1], zphase);
   }
 }
 
@@ -779,10 +1011,10 @@ void fine_dslash(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const FineOp
     if (op.Uh) {
       const float sh = op.shift;
       if (b)
-        k_fine_dslash<float, true, __half2, __half><<<grid, 128, 0, st>>>(out, in, b, op.Uh, op.clovh, op.g, op.bc_t,
+        k_fine_dslash<float, true, __half2, __half2><<<grid, 128, 0, st>>>(out, in, b, op.Uh, op.clovh, op.g, op.bc_t,
                                                                           rstride, sel, sel_mu, in_chir, sh);
       else
-        k_fine_dslash<float, false, __half2, __half><<<grid, 128, 0, st>>>(out, in, b, op.Uh, op.clovh, op.g, op.bc_t,
+        k_fine_dslash<float, false, __half2, __half2><<<grid, 128, 0, st>>>(out, in, b, op.Uh, op.clovh, op.g, op.bc_t,
                                                                            rstride, sel, sel_mu, in_chir, sh);
       return;
     }
@@ -815,7 +1047,8 @@ void launch_sap_tma(cplx<T>* z, const cplx<T>* b, const LS* U, const CS* clov, c
   while (seg < op.g.vB) seg <<= 1;
   const int threads = 256;
   const int segs = threads / seg;
-  const size_t seg_bytes = (size_t)op.g.vB * (36 * sizeof(LS) + 72 * sizeof(CS) + 12 * sizeof(cplx<T>));
+  const size_t seg_bytes =
+      (size_t)op.g.vB * (36 * sizeof(LS) + 2 * ClovRows<CS>::per_chir * sizeof(CS) + 12 * sizeof(cplx<T>));
   const size_t sm = segs * seg_bytes + 16 + (threads / 32) * 3 * sizeof(T) + 16;
   static bool attr = false;
   if (!attr) {
@@ -825,6 +1058,32 @@ void launch_sap_tma(cplx<T>* z, const cplx<T>* b, const LS* U, const CS* clov, c
   count_launch();
   k_fine_sap_tma<T, LS, CS><<<div_up(nblocks, segs), threads, sm, st>>>(z, b, U, clov, op.g, op.bc_t, rstride, nrhs,
                                                                        blocks, nblocks, seg, k_mr, op.err, shift);
+}
+
+// the 4^4 kernel: FP32 compute, 4^4 SAP blocks that are the inner tile (contiguous
+// sites), and 16-byte aligned rows of z (bulk copies)
+template <typename T>
+bool sap_b4_ok(const FineOp<T>& op, const void* z, size_t rstride) {
+  if (sizeof(T) != 4) return false;
+  for (int d = 0; d < 4; ++d)
+    if (op.g.B[d] != 4 || op.g.I[d] != 4) return false;
+  return ((uintptr_t)z % 16) == 0 && rstride % 2 == 0 && op.g.V % 4 == 0;
+}
+
+template <typename LS, typename CS>
+void launch_sap_b4(cplx<float>* z, const cplx<float>* b, const LS* U, const CS* clov, const FineOp<float>& op,
+                   const int* blocks, int nblocks, int nrhs, size_t rstride, int k_mr, float shift, cudaStream_t st) {
+  constexpr int VB = 256;
+  const size_t sm = (size_t)VB * (36 * sizeof(LS) + 2 * ClovRows<CS>::per_chir * sizeof(CS) + 12 * sizeof(cplx<float>)) +
+                    16 + 2 * 24 * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fine_sap_b4<LS, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  count_launch();
+  k_fine_sap_b4<LS, CS><<<nblocks, VB, sm, st>>>(z, b, U, clov, op.g, op.bc_t, rstride, nrhs, blocks, k_mr, op.err,
+                                                 shift);
 }
 
 template <typename T, typename LS, typename CS>
@@ -851,12 +1110,19 @@ void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int
                     size_t rstride, int k_mr, cudaStream_t st) {
   const bool tma = sap_tma_ok(op) && op.err;
   if constexpr (sizeof(T) == 4) {
+    if (op.err && nblocks > 0 && sap_b4_ok(op, z, rstride)) {
+      if (op.Uh)
+        launch_sap_b4<__half2, __half2>(z, b, op.Uh, op.clovh, op, blocks, nblocks, nrhs, rstride, k_mr, op.shift, st);
+      else
+        launch_sap_b4<cplx<float>, float>(z, b, op.U, op.clov, op, blocks, nblocks, nrhs, rstride, k_mr, 0.f, st);
+      return;
+    }
     if (op.Uh) {
       if (tma)
-        launch_sap_tma<float, __half2, __half>(z, b, op.Uh, op.clovh, op, blocks, nblocks, nrhs, rstride, k_mr,
+        launch_sap_tma<float, __half2, __half2>(z, b, op.Uh, op.clovh, op, blocks, nblocks, nrhs, rstride, k_mr,
                                                op.shift, st);
       else
-        launch_sap_plain<float, __half2, __half>(z, b, op.Uh, op.clovh, op, blocks, nblocks, nrhs, rstride, k_mr,
+        launch_sap_plain<float, __half2, __half2>(z, b, op.Uh, op.clovh, op, blocks, nblocks, nrhs, rstride, k_mr,
                                                  op.shift, st);
       return;
     }
@@ -875,11 +1141,14 @@ __global__ void k_links_to_half(__half2* __restrict__ dst, const cplx<double>* _
   if (i < n) dst[i] = __halves2half2(__double2half(U[i].re), __double2half(U[i].im));
 }
 
-__global__ void k_clover_to_half(__half* __restrict__ dst, const double* __restrict__ A, int V, double shift) {
+__global__ void k_clover_to_half(__half2* __restrict__ dst, const double* __restrict__ A, int V, double shift) {
+  // row j of chirality ch holds the packed reals (2j, 2j+1); the diagonal (reals 0..5) loses the shift
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (size_t)72 * V) return;
-  const int comp = (int)(i / V) % 36;   // 0..5: diagonal of the chirality block
-  dst[i] = __double2half(comp < 6 ? A[i] - shift : A[i]);
+  if (i >= (size_t)36 * V) return;
+  const int row = (int)(i / V), site = (int)(i - (size_t)row * V);
+  const int ch = row / 18, p = 2 * (row - 18 * ch);
+  const double a0 = A[(size_t)(ch * 36 + p) * V + site], a1 = A[(size_t)(ch * 36 + p + 1) * V + site];
+  dst[i] = __halves2half2(__double2half(p < 6 ? a0 - shift : a0), __double2half(p + 1 < 6 ? a1 - shift : a1));
 }
 
 void links_to_half(__half2* dst, const cplx<double>* U, size_t n, cudaStream_t st) {
@@ -887,9 +1156,9 @@ void links_to_half(__half2* dst, const cplx<double>* U, size_t n, cudaStream_t s
   k_links_to_half<<<div_up(n, 256), 256, 0, st>>>(dst, U, n);
 }
 
-void clover_to_half(__half* dst, const double* A, int V, double shift, cudaStream_t st) {
+void clover_to_half(__half2* dst, const double* A, int V, double shift, cudaStream_t st) {
   count_launch();
-  k_clover_to_half<<<div_up((size_t)72 * V, 256), 256, 0, st>>>(dst, A, V, shift);
+  k_clover_to_half<<<div_up((size_t)36 * V, 256), 256, 0, st>>>(dst, A, V, shift);
 }
 
 void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, double m0, double csw,

@@ -18,7 +18,7 @@ struct FineOp {
   int* err;      // device error flag (bounded waits), may be null
   // FP16 storage (FP32 compute only): when Uh is set the kernels read these instead
   const __half2* Uh = nullptr;   // [4][9][V] links
-  const __half* clovh = nullptr; // [2][36][V] clover term without the (m0 + 4) shift
+  const __half2* clovh = nullptr; // [2][18][V] clover term without the (m0 + 4) shift, pairs of packed reals
   float shift = 0.f;             // m0 + 4, added to the diagonal in FP32
 };
 
@@ -56,7 +56,7 @@ void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, do
                   cudaStream_t st);
 // FP16 copies: links (no scale, |U_ab| <= 1) and the clover term A - shift (no scale)
 void links_to_half(__half2* dst, const cplx<double>* U, size_t n, cudaStream_t st);
-void clover_to_half(__half* dst, const double* A, int V, double shift, cudaStream_t st);
+void clover_to_half(__half2* dst, const double* A, int V, double shift, cudaStream_t st);
 template <typename T>
 void links_import(cplx<T>* U, const cplx<double>* gauge_lex, const Geom& g, cudaStream_t st);
 template <typename T>

@@ -77,7 +77,7 @@ struct Level {
   cplx<float>* P32 = nullptr;
   // FP16 storage copies read by the FP32 kernels when the handle stores FP16
   __half2* Uh = nullptr;      // fine links
-  __half* clovh = nullptr;    // fine clover term without the (m0 + 4) shift
+  __half2* clovh = nullptr;   // fine clover term without the (m0 + 4) shift (pairs of packed reals)
   __half2* Ph = nullptr;      // P_l, one scale per (aggregate, chirality) in pscale
   float* pscale = nullptr;
   __half2* blkh = nullptr;    // coarse blocks, one scale per site in bscale
@@ -902,7 +902,7 @@ void half_alloc(ddamg_handle* h) {
     Level& L = h->lv[l];
     if (L.fine && !L.Uh) {
       L.Uh = dalloc<__half2>(h, (size_t)36 * L.g.V);
-      L.clovh = dalloc<__half>(h, (size_t)72 * L.g.V);
+      L.clovh = dalloc<__half2>(h, (size_t)36 * L.g.V);
     }
     if (!L.fine && !L.blkh) {
       L.blkh = dalloc<__half2>(h, (size_t)L.g.V * 9 * L.n * L.n);
