@@ -16,7 +16,7 @@
 namespace {
 
 constexpr int RT = 256;         // threads per reduction CTA
-constexpr int MAXCHUNKS = 304;  // partials per rhs (and per dot in a multidot): two CTAs per SM of a GB300
+constexpr int MAXCHUNKS = 512;  // partials per rhs (and per dot in a multidot)
 
 // scratch for the partials, grown on demand (library-owned device memory).  A
 // buffer that was replaced is kept until the library is unloaded, because
@@ -40,7 +40,7 @@ double* partials(size_t count) {
 }
 
 int nchunks(size_t len) {
-  size_t c = (len + 8 * RT - 1) / (8 * RT);
+  size_t c = (len + 4 * RT - 1) / (4 * RT);
   if (c < 1) c = 1;
   if (c > MAXCHUNKS) c = MAXCHUNKS;
   return (int)c;
@@ -76,47 +76,38 @@ __device__ void chunk_range(size_t len, int nc, int c, size_t& lo, size_t& hi) {
   if (lo > len) lo = len;
 }
 
-// stage 1 of dot / norm: partial[(rhs * ndots + d) * nc + chunk] (re, im).
-// Dots in groups of eight: w is read once per group and only the group's
-// used accumulators are reduced over the CTA.
+// stage 1 of dot / norm: partial[(rhs * ndots + d) * nc + chunk] (re, im)
 template <typename T>
 __global__ void k_multidot1(double* __restrict__ part, const cplx<T>* __restrict__ V, size_t vstride, int m,
                             const cplx<T>* __restrict__ w, size_t len, size_t rstride, int nc) {
-  constexpr int G = 8;
-  __shared__ double sh[RT / 32][2 * G];
+  __shared__ double sh[32 * 8];
   const int chunk = blockIdx.x, rhs = blockIdx.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   size_t lo, hi;
   chunk_range(len, nc, chunk, lo, hi);
   const cplx<T>* pw = w + (size_t)rhs * rstride;
-  for (int d0 = 0; d0 < m; d0 += G) {
-    const int nd = m - d0 < G ? m - d0 : G;   // uniform across the CTA
+  for (int d0 = 0; d0 < m; d0 += 4) {
     // per-thread partials in the precision of the data (FP32 data: FP32 sums)
-    T at[2 * G];
-#pragma unroll
-    for (int k = 0; k < 2 * G; ++k) at[k] = T(0);
-    const cplx<T>* pv = V + (size_t)d0 * vstride + (size_t)rhs * rstride;
+    T at[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
       const cplx<T> we = pw[e];
 #pragma unroll
-      for (int dd = 0; dd < G; ++dd)
-        if (dd < nd) cdotc_acc(at[2 * dd], at[2 * dd + 1], pv[(size_t)dd * vstride + e], we);
-    }
-#pragma unroll
-    for (int k = 0; k < 2 * G; ++k) {
-      if (k < 2 * nd) {
-        double v = (double)at[k];
-        for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) sh[warp][k] = v;
+      for (int dd = 0; dd < 4; ++dd) {
+        if (d0 + dd < m) {
+          const cplx<T> v = V[(size_t)(d0 + dd) * vstride + (size_t)rhs * rstride + e];
+          cdotc_acc(at[2 * dd], at[2 * dd + 1], v, we);
+        }
       }
     }
-    __syncthreads();
-    if (threadIdx.x < 2 * nd) {
-      double acc = 0.0;
-      for (int q = 0; q < RT / 32; ++q) acc += sh[q][threadIdx.x];
-      part[(((size_t)rhs * m + d0 + (threadIdx.x >> 1)) * nc + chunk) * 2 + (threadIdx.x & 1)] = acc;
-    }
-    __syncthreads();
+    double acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = (double)at[k];
+    cta_sum(acc, 8, sh);
+    if (threadIdx.x == 0)
+      for (int dd = 0; dd < 4 && d0 + dd < m; ++dd) {
+        double* p = part + (((size_t)rhs * m + d0 + dd) * nc + chunk) * 2;
+        p[0] = acc[2 * dd];
+        p[1] = acc[2 * dd + 1];
+      }
   }
 }
 
