@@ -171,6 +171,37 @@ class WilsonOp:
         return Stencil(diag=self.diag.copy(), fwd=fwd, bwd=bwd)
 
 
+def apply_at_sites(build, U: np.ndarray, psi: np.ndarray, bc, sites) -> np.ndarray:
+    """(D psi)(x) at each site x of ``sites`` (a list of (t, z, y, x)), for lattices too large for ``apply``.
+
+    D psi(x) reads psi at x and x +/- mu_hat and links at most one hop from x (the
+    four clover leaves included), so it is the value at the centre of the operator
+    built on the 3^4 neighbourhood of x, taken periodic, applied to the same
+    neighbourhood of psi.  The boundary sign of a hop that wraps the lattice
+    multiplies the neighbourhood's psi on the far side instead of the hop.
+    ``build(U_patch)`` returns the operator of a patch with periodic boundaries
+    (e.g. ``lambda Up: WilsonOp.build(Up, m0, csw, 1)``).  Returns psi[..., nsites, 12].
+    """
+    dims = U.shape[:4]
+    out = []
+    for s in sites:
+        ix = np.ix_(*[(np.arange(-1, 2) + s[mu]) % dims[mu] for mu in range(4)])
+        Up = U[ix]
+        pp = psi[(Ellipsis,) + ix + (slice(None),)]
+        for mu in range(4):
+            if bc[mu] == 1:
+                continue
+            lo = [slice(None)] * pp.ndim
+            if s[mu] == 0:                      # the backward neighbour lies across the boundary
+                lo[mu - 5] = 0
+                pp[tuple(lo)] *= bc[mu]
+            if s[mu] == dims[mu] - 1:           # the forward neighbour lies across the boundary
+                lo[mu - 5] = 2
+                pp[tuple(lo)] *= bc[mu]
+        out.append(build(Up).apply(pp)[..., 1, 1, 1, 1, :])
+    return np.stack(out, axis=-2)
+
+
 def dense_matrix(op, dims=None) -> np.ndarray:
     """The operator as a dense matrix, by applying it to every unit vector (small lattices only).
 

@@ -336,19 +336,28 @@ __global__ void k_fine_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ 
       for (int k = 0; k < 12; ++k) acc[k] = czero<T>();
 #pragma unroll 1
       for (int mu = 0; mu < 4; ++mu) {
+        // a block that spans the whole time extent keeps the wrapping hop, with its boundary sign
         if (hop_internal(g, c, mu, +1, g.B)) {
           const int n = geom_neighbor(g, c, mu, +1);
           const int sl = base + (n - blk * g.vB);
+          const bool neg = mu == 0 && bc_t < 0 && c[0] == g.L[0] - 1;
 #pragma unroll
-          for (int k = 0; k < 12; ++k) nb[k] = rs[(size_t)sl * 12 + k];
+          for (int k = 0; k < 12; ++k) {
+            const cplx<T> v = rs[(size_t)sl * 12 + k];
+            nb[k] = cmk<T>(sign_flip(v.re, neg), sign_flip(v.im, neg));
+          }
           load_link(U, V, mu, x, u);
           hop_accumulate(mu, true, u, nb, acc);
         }
         if (hop_internal(g, c, mu, -1, g.B)) {
           const int n = geom_neighbor(g, c, mu, -1);
           const int sl = base + (n - blk * g.vB);
+          const bool neg = mu == 0 && bc_t < 0 && c[0] == 0;
 #pragma unroll
-          for (int k = 0; k < 12; ++k) nb[k] = rs[(size_t)sl * 12 + k];
+          for (int k = 0; k < 12; ++k) {
+            const cplx<T> v = rs[(size_t)sl * 12 + k];
+            nb[k] = cmk<T>(sign_flip(v.re, neg), sign_flip(v.im, neg));
+          }
           load_link(U, V, mu, n, u);
           hop_accumulate(mu, false, u, nb, acc);
         }

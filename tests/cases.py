@@ -113,6 +113,11 @@ ODD3 = dict(dims=(8, 12, 12, 12), levels=3, agg=((2, 2, 2, 2), (2, 2, 2, 2)), n_
 # times; the coarsest lattice (2, 1, 1, 1) has odd extents and is solved by plain GMRES
 FOUR = dict(dims=(16, 8, 8, 8), levels=4, agg=((2, 2, 2, 2), (2, 2, 2, 2), (2, 2, 2, 2)), n_tv=(4, 5, 5),
             sap=((2, 2, 2, 2), (2, 2, 2, 2), (2, 2, 2, 2)))
+# 4^4 SAP blocks on the fine level (the block of the three-level workloads), with 4^4 aggregates so
+# that the SAP block is the contiguous inner tile; SAP4W's blocks span the whole t and y extents, so
+# hops through those lattice boundaries (antiperiodic in t) wrap inside the block
+SAP4 = dict(dims=(8, 8, 8, 8), levels=2, agg=((4, 4, 4, 4),), n_tv=(3,), sap=((4, 4, 4, 4),))
+SAP4W = dict(dims=(4, 8, 4, 8), levels=2, agg=((4, 4, 4, 4),), n_tv=(3,), sap=((4, 4, 4, 4),))
 # the two-level FP64 workload (8^4, eps 0.3, csw 0, aggregates 4^4, 8 test vectors, SAP 2^4)
 C1 = dict(dims=(8, 8, 8, 8), levels=2, agg=((4, 4, 4, 4),), n_tv=(8,), sap=((2, 2, 2, 2),), eps=0.3, csw=0.0,
           mr_steps=4, nu=3, n_inv=3, eta_passes=3, outer_restart=25)

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from cases import Case, rel, SMALL2, RAGGED2, THREE, ODD3, FOUR, C1, golden_mass
+from cases import Case, rel, SMALL2, RAGGED2, THREE, ODD3, FOUR, C1, SAP4, SAP4W, golden_mass
 
 pytestmark = pytest.mark.gpu
 
@@ -82,6 +82,28 @@ def test_fine_sap(dd, spec):
         z = z0.copy()
         dd.ddamg_smooth(h, 0, prec, b, z, 2, it)
         assert rel(z, ref) <= tol, (prec, rel(z, ref))
+
+
+@pytest.mark.parametrize("spec", [SAP4, SAP4W])
+def test_fine_sap_4x4_blocks(dd, spec):
+    """The 4^4-block SAP sweep kernel: FP32 arithmetic on FP32 and on FP16 storage, three right-hand
+    sides in one sweep (the block's z is staged once per right-hand side)."""
+    from oracle.precision import fine_op_half
+    from oracle.smoother import SAP
+    c, h, o = _pair(spec, mr_steps=4)
+    b = _fields(3, c.dims, 12, 8)
+    z0 = _fields(3, c.dims, 12, 9)
+    for prec, tol, it in ((0, TOL64, 2), (1, TOL32, 1)):
+        ref = np.stack([o.levels[0].sap.smooth(b[i], z0[i], it) for i in range(3)])
+        z = z0.copy()
+        dd.ddamg_smooth(h, 0, prec, b, z, 3, it)
+        assert rel(z, ref) <= tol, (prec, rel(z, ref))
+    dd.ddamg_set_option(h, dd.DDAMG_OPT_HALF_STORAGE, 1)
+    sap = SAP(fine_op_half(c.gauge(), c.m0, c.csw, c.bc_t), c.sap[0], c.mr_steps)
+    ref = np.stack([sap.smooth(b[i], z0[i], 1) for i in range(3)])
+    z = z0.copy()
+    dd.ddamg_smooth(h, 0, 1, b, z, 3, 1)
+    assert rel(z, ref) <= TOL32, rel(z, ref)
 
 
 @pytest.mark.parametrize("spec", [SMALL2, RAGGED2, THREE, ODD3, FOUR])

@@ -5,7 +5,7 @@ import pytest
 import synth
 from oracle.gamma import GAMMA, GAMMA5, GAMMA_X, GAMMA_Y, GAMMA_Z, GAMMA_T, spin_colour
 from oracle.lattice import vdot, norm, internal_hop_masks
-from oracle.wilson import WilsonOp, clover_term, gauge_transform, colour_rotate, dense_matrix
+from oracle.wilson import WilsonOp, clover_term, gauge_transform, colour_rotate, dense_matrix, apply_at_sites
 from oracle.spectrum import sparse_matrix, leftmost_eigenvalues
 
 DIMS = (4, 4, 4, 4)
@@ -153,3 +153,35 @@ def test_dense_matrix_from_apply_matches_sparse_assembly():
     dims = (2, 2, 4, 2)
     op = WilsonOp.build(synth.su3_field(dims, 0.4, 41), -0.1, 1.0, -1)
     assert np.abs(dense_matrix(op) - sparse_matrix(op).toarray()).max() < 1e-14
+
+
+@pytest.mark.parametrize("dims,bc", [((4, 4, 4, 4), -1), ((2, 3, 4, 1), -1), ((3, 2, 1, 4), 1)])
+def test_apply_at_sites_matches_full_apply(dims, bc):
+    """Site-by-site evaluation on 3^4 neighbourhoods equals the whole-lattice operator, including
+    extents 1 and 2 (the neighbourhood repeats sites) and the antiperiodic time boundary."""
+    U = synth.su3_field(dims, 0.4, 3)
+    op = WilsonOp.build(U, -0.3, 1.2, bc)
+    f = synth.random_fields(2, dims, 12, 5)
+    sites = list(np.ndindex(*dims))
+    got = apply_at_sites(lambda Up: WilsonOp.build(Up, -0.3, 1.2, 1), U, f, op.bc, sites)
+    ref = op.apply(f).reshape(2, -1, 12)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_apply_at_sites_free_field_plane_wave_large_lattice():
+    """On a 16^3x32 unit-link lattice, sampled sites (time boundaries included) give the closed form
+    (m0 + sum_mu (1 - cos p_mu)) + i sum_mu gamma_mu sin p_mu of an antiperiodic plane wave."""
+    dims = (32, 16, 16, 16)
+    m0 = 0.13
+    U = synth.unit_gauge(dims)
+    p = np.array([5 * np.pi / 32, 2 * np.pi * 3 / 16, 2 * np.pi / 16, 0.0])
+    co = np.meshgrid(*[np.arange(d) for d in dims], indexing="ij")
+    u = np.random.default_rng(4).standard_normal(12) + 1j * np.random.default_rng(5).standard_normal(12)
+    psi = np.exp(1j * sum(p[m] * co[m] for m in range(4)))[..., None] * u
+    rng = np.random.default_rng(6)
+    sites = [(0, 3, 4, 5), (31, 15, 0, 7)] + [tuple(int(rng.integers(0, d)) for d in dims) for _ in range(10)]
+    got = apply_at_sites(lambda Up: WilsonOp.build(Up, m0, 1.0, 1), U, psi, (-1, 1, 1, 1), sites)
+    Dp = (m0 + np.sum(1 - np.cos(p))) * np.eye(4) + 1j * sum(GAMMA[m] * np.sin(p[m]) for m in range(4))
+    for k, s in enumerate(sites):
+        expect = (Dp @ psi[s].reshape(4, 3)).reshape(12)
+        assert np.abs(got[k] - expect).max() <= 1e-13
