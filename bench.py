@@ -144,14 +144,23 @@ def peaks():
         return 6800.0, "fallback"
 
 
+SAP_SRC = ("// SAP colour sweep for 4^4 blocks", "// Clover construction (FP64)")
+
+
+def kernel_sha(kernel_file, markers=SAP_SRC):
+    """sha256 of the source text of one kernel (from its leading comment to the next section)."""
+    s = open(kernel_file).read()
+    i = s.index(markers[0])
+    return hashlib.sha256(s[i:s.index(markers[1], i)].encode()).hexdigest()
+
+
 def ncu_traffic(kernel_file):
     """DRAM bytes per launch of the fine SAP sweep from the committed ncu summary, if the kernel is unchanged."""
     path = os.path.join(ROOT, "profiles", "fine_sap_sweep_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        h = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
-        if d.get("source_sha256") != h:
+        if d.get("source_sha256") != kernel_sha(kernel_file):
             return None
         return d.get("dram_bytes_per_launch_scaled")
     except (OSError, ValueError):
@@ -306,7 +315,7 @@ def run_gpu(args, w):
     avg_ms = p_ms / max(1, p_n)
     per_launch = p_bytes / max(1, p_n)
     achieved = per_launch / (avg_ms / 1e3) / 1e9
-    kname = ("k_fine_sap_tma<float, __half2, __half>" if mixed_prec == 2 else "k_fine_sap_tma<float, cplx<float>, float>")
+    kname = "k_fine_sap_b4<__half2, __half2>" if mixed_prec == 2 else "k_fine_sap_b4<cplx<float>, float>"
     roof = {"kernel": kname + " (one SAP colour sweep, 4 MR steps)", "bound": "hbm",
             "achieved": round(achieved, 1), "peak": pk, "unit": "GB/s", "frac": round(achieved / pk, 4),
             "peak_source": pk_src, "traffic": ncu_traffic(os.path.join(ROOT, "paper_1307_6101_gb300", "csrc",

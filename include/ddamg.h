@@ -226,6 +226,21 @@ int ddamg_get_interpolation(ddamg_handle* h, int level, double* P);
  * 1..4 forward mu = t,z,y,x (couples to site + mu), 5..8 backward mu. */
 int ddamg_get_coarse_operator(ddamg_handle* h, int level, double* blocks);
 
+/* ---- Setup timing ------------------------------------------------------------
+ * Wall-clock seconds the setup of this handle spent per level l and phase:
+ * seconds[l * DDAMG_SETUP_KINDS + kind] for n entries (levels beyond the
+ * hierarchy read 0).  SMOOTH: smoothing of the random test vectors (Alg. 3);
+ * KCYCLE: the K-cycle applied to each test vector (Alg. 4); REBUILD: P
+ * orthonormalisation and the Galerkin product of the next level (both
+ * algorithms), including ddamg_rebuild.  Errors: ARG. */
+enum {
+  DDAMG_SETUP_SMOOTH = 0,
+  DDAMG_SETUP_KCYCLE = 1,
+  DDAMG_SETUP_REBUILD = 2,
+  DDAMG_SETUP_KINDS = 3
+};
+int ddamg_setup_times(ddamg_handle* h, double* seconds, int n);
+
 /* ---- Device footprint ------------------------------------------------------
  * Bytes of the device memory the library allocated for this handle (operators,
  * P, test vectors, Krylov workspaces, FP16 copies, staging buffers). */

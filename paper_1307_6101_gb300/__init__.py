@@ -35,11 +35,13 @@ EXPORTED = (
     "ddamg_krylov_steps", "ddamg_residual_norm_noalloc", "ddamg_get_option",
     "ddamg_device_bytes", "ddamg_estimate_bytes", "ddamg_server_create", "ddamg_server_add",
     "ddamg_server_submit", "ddamg_server_poll", "ddamg_server_wait", "ddamg_server_free",
+    "ddamg_setup_times",
 )
 DDAMG_OPT_GRAPHS = 0
 DDAMG_OPT_COARSEST_CLUSTER = 1
 DDAMG_OPT_SAP_CLUSTER = 2
 DDAMG_OPT_HALF_STORAGE = 3
+SETUP_KINDS = ("smooth", "kcycle", "rebuild")   # DDAMG_SETUP_* order
 PROF_KINDS = {"fine_sap": 0, "fine_dslash": 1, "coarse_apply": 2, "coarse_sap": 3, "transfer": 4, "precond": 5,
               "outer_ortho": 6}
 
@@ -114,6 +116,7 @@ def _load():
     lib.ddamg_launch_count.argtypes = []
     sp = C.POINTER(C.c_size_t)
     lib.ddamg_device_bytes.argtypes = [vp, sp]
+    lib.ddamg_setup_times.argtypes = [vp, C.POINTER(C.c_double), ip]
     lib.ddamg_estimate_bytes.argtypes = [C.POINTER(C.c_int), C.POINTER(DdamgParams), sp]
     lib.ddamg_server_create.argtypes = [C.c_size_t, C.POINTER(vp)]
     lib.ddamg_server_add.argtypes = [vp, vp, C.POINTER(C.c_int)]
@@ -313,6 +316,14 @@ def ddamg_get_option(h, option):
     v = C.c_int()
     _check(lib().ddamg_get_option(h.raw, int(option), C.byref(v)))
     return v.value
+
+
+def ddamg_setup_times(h):
+    """Setup wall-clock seconds per level: [{"smooth": s, "kcycle": s, "rebuild": s}, ...]."""
+    n = MAX_LEVELS * len(SETUP_KINDS)
+    buf = (C.c_double * n)()
+    _check(lib().ddamg_setup_times(h.raw, buf, n))
+    return [dict(zip(SETUP_KINDS, buf[l * len(SETUP_KINDS):(l + 1) * len(SETUP_KINDS)])) for l in range(MAX_LEVELS)]
 
 
 def ddamg_device_bytes(h):

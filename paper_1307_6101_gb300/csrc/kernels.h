@@ -203,8 +203,10 @@ template <typename T>
 void kry_cycle_begin(const GmresState& s, cplx<T>* V0, cplx<T>* cur, const cplx<T>* r, size_t vlen, int nrhs,
                      cudaGraphConditionalHandle hinner, cudaStream_t st);
 template <typename T>
-void kry_arnoldi(const GmresState& s, cplx<T>* V, size_t vstride, cplx<T>* Z, const cplx<T>* zcur, cplx<T>* w,
-                 cplx<T>* cur, size_t vlen, int nrhs, cudaGraphConditionalHandle hinner, cudaStream_t st);
+cudaError_t kry_arnoldi(const GmresState& s, cplx<T>* V, size_t vstride, cplx<T>* Z, const cplx<T>* zcur, cplx<T>* w,
+                        cplx<T>* cur, size_t vlen, int nrhs, cudaGraphConditionalHandle hinner, cudaStream_t st);
+// queries (once, outside any stream capture) the cluster size the split Arnoldi step can use
+void kry_prepare();
 void kry_cycle_end(const GmresState& s, int nrhs, int max_cycles, cudaGraphConditionalHandle hcycle, cudaStream_t st);
 
 }  // namespace dd

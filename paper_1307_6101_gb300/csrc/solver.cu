@@ -131,6 +131,8 @@ struct ddamg_handle {
   ddamg_params p{};
   int device = 0;
   size_t dev_bytes = 0;   // bytes of the library's own device allocations for this handle
+  // wall-clock seconds of the setup per level and phase (DDAMG_SETUP_* order)
+  double setup_s[DDAMG_MAX_LEVELS][DDAMG_SETUP_KINDS] = {};
   int dims[4] = {0, 0, 0, 0};
   int bc_t = -1;
   double m0 = 0, csw = 0;
@@ -522,7 +524,7 @@ void krylov_dev(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cpl
       } else {
         A(ws.wv, ws.cur, nullptr);
       }
-      kry_arnoldi<T>(s, ws.V, vs, flexible ? ws.Z : nullptr, ws.zc, ws.wv, ws.cur, vlen, nrhs, hinner, h->st);
+      CK(kry_arnoldi<T>(s, ws.V, vs, flexible ? ws.Z : nullptr, ws.zc, ws.wv, ws.cur, vlen, nrhs, hinner, h->st));
     });
     gmres_solve_y(s, nrhs, h->st);
     blas_multiaxpy<T>(x, flexible ? ws.Z : ws.V, vs, m, s.y, m, 1.0, vlen, nrhs, vlen, h->st);
@@ -945,7 +947,18 @@ void half_bind(ddamg_handle* h) {
 constexpr int SETUP_CHUNK = 4;   // columns / test vectors per pass of the setup's batched operations
 
 // P_l from the test vectors, D_{l+1} = P_l^+ D_l P_l (FP64), FP32 copies, coarsest self inverses
+// adds the wall-clock time of its scope to h->setup_s[l][kind] (the phases end with a sync)
+struct SetupTimer {
+  ddamg_handle* h;
+  int l, kind;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  ~SetupTimer() {
+    h->setup_s[l][kind] += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
 void rebuild(ddamg_handle* h, int l) {
+  SetupTimer tm{h, l, DDAMG_SETUP_REBUILD};
   Level& F = h->lv[l];
   Level& C = h->lv[l + 1];
   cudaStream_t st = h->st;
@@ -983,6 +996,7 @@ void rebuild(ddamg_handle* h, int l) {
 
 template <typename T>
 void setup_smooth(ddamg_handle* h, int l) {
+  SetupTimer tm{h, l, DDAMG_SETUP_SMOOTH};
   // the test vectors in chunks of SETUP_CHUNK (bounded scratch; each vector is smoothed on its own)
   Level& L = h->lv[l];
   const int jb_max = L.N < SETUP_CHUNK ? L.N : SETUP_CHUNK;
@@ -1039,6 +1053,7 @@ void iterative_setup_phase(ddamg_handle* h, int l, int i) {
   cplx<T>* zT = static_cast<cplx<T>*>(scratch(h, 6, sizeof(cplx<T>) * L.vlen));
   double* nrm = static_cast<double*>(scratch(h, 7, sizeof(double) * 8));
   for (int j = 0; j < L.N; ++j) {
+    SetupTimer tm{h, l, DDAMG_SETUP_KCYCLE};
     blas_convert<T, double>(bT, L.tv64 + (size_t)j * L.vlen, L.vlen, 1, 0, 0, st);
     kcycle_run<T>(h, l, zT, bT, 1);
     for (int k = l; k < h->L - 1; ++k) {
@@ -1111,6 +1126,7 @@ void ensure_work(ddamg_handle* h) {
 }
 
 void allocate_hierarchy(ddamg_handle* h) {
+  kry_prepare();
   const int B = h->max_batch;
   for (int l = 0; l < h->L; ++l) {
     Level& L = h->lv[l];
@@ -1969,6 +1985,18 @@ int ddamg_get_coarse_operator(ddamg_handle* h, int level, double* blocks) {
     if (!dev) CK(cudaMemcpyAsync(blocks, d, bytes, cudaMemcpyDeviceToHost, h->st));
     sync(h);
   });
+}
+
+int ddamg_setup_times(ddamg_handle* h, double* seconds, int n) {
+  if (!h || !seconds || n < 0) {
+    g_err = "null argument";
+    return DDAMG_ERR_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    const int l = i / DDAMG_SETUP_KINDS, k = i % DDAMG_SETUP_KINDS;
+    seconds[i] = l < DDAMG_MAX_LEVELS ? h->setup_s[l][k] : 0.0;
+  }
+  return DDAMG_OK;
 }
 
 int ddamg_device_bytes(ddamg_handle* h, size_t* bytes) {

@@ -118,6 +118,11 @@ FOUR = dict(dims=(16, 8, 8, 8), levels=4, agg=((2, 2, 2, 2), (2, 2, 2, 2), (2, 2
 # hops through those lattice boundaries (antiperiodic in t) wrap inside the block
 SAP4 = dict(dims=(8, 8, 8, 8), levels=2, agg=((4, 4, 4, 4),), n_tv=(3,), sap=((4, 4, 4, 4),))
 SAP4W = dict(dims=(4, 8, 4, 8), levels=2, agg=((4, 4, 4, 4),), n_tv=(3,), sap=((4, 4, 4, 4),))
+# Krylov vectors long enough for the cluster-split Arnoldi step of the device-driven (F)GMRES:
+# BIG2's coarsest Schur vectors have 128 * 32 = 4096 entries, BIG3's level-1 vectors 256 * 16
+BIG2 = dict(dims=(8, 8, 8, 8), levels=2, agg=((2, 2, 2, 2),), n_tv=(16,), sap=((2, 2, 2, 2),))
+BIG3 = dict(dims=(8, 8, 8, 8), levels=3, agg=((2, 2, 2, 2), (2, 2, 2, 2)), n_tv=(8, 10),
+            sap=((2, 2, 2, 2), (2, 2, 2, 2)))
 # the two-level FP64 workload (8^4, eps 0.3, csw 0, aggregates 4^4, 8 test vectors, SAP 2^4)
 C1 = dict(dims=(8, 8, 8, 8), levels=2, agg=((4, 4, 4, 4),), n_tv=(8,), sap=((2, 2, 2, 2),), eps=0.3, csw=0.0,
           mr_steps=4, nu=3, n_inv=3, eta_passes=3, outer_restart=25)

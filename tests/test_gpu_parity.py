@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from cases import Case, rel, SMALL2, RAGGED2, THREE, ODD3, FOUR, C1, SAP4, SAP4W, golden_mass
+from cases import Case, rel, SMALL2, RAGGED2, THREE, ODD3, FOUR, C1, SAP4, SAP4W, BIG2, BIG3, golden_mass
 
 pytestmark = pytest.mark.gpu
 
@@ -215,6 +215,27 @@ def test_kcycle(dd, spec, graphs):
     z32 = np.zeros_like(b)
     dd.ddamg_kcycle(h, 0, 1, b, z32, 1)
     assert rel(z32[0], z[0]) <= 1e-3     # FP32 cycle vs FP64 cycle (inner stopping tolerances are 0.1 / 5e-2)
+
+
+@pytest.mark.parametrize("spec", [BIG2, BIG3])
+def test_kcycle_split_arnoldi(dd, spec):
+    """K-cycle through the captured graph with Krylov vectors long enough for the cluster-split Arnoldi
+    step (coarsest solve by the device-driven GMRES: coarsest cluster kernel off); two right-hand sides,
+    and one of them alone gives the same bits."""
+    c, h, o = _pair(spec, max_rhs=2)
+    dd.ddamg_set_option(h, dd.DDAMG_OPT_COARSEST_CLUSTER, 0)
+    dd.ddamg_set_option(h, dd.DDAMG_OPT_GRAPHS, 1)
+    b = _fields(2, c.dims, 12, 71)
+    z = np.zeros_like(b)
+    dd.ddamg_kcycle(h, 0, 0, b, z, 2)
+    for i in range(2):
+        assert rel(z[i], o.kcycle(0, b[i])) <= 1e-9, rel(z[i], o.kcycle(0, b[i]))
+    z1 = np.zeros_like(b[:1])
+    dd.ddamg_kcycle(h, 0, 0, np.ascontiguousarray(b[1:2]), z1, 1)
+    assert np.array_equal(z1[0], z[1])
+    z32 = np.zeros_like(b)
+    dd.ddamg_kcycle(h, 0, 1, b, z32, 2)
+    assert rel(z32, z) <= 1e-3
 
 
 def test_setup_initial_phase_alg3(dd):
