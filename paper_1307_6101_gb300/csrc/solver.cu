@@ -968,23 +968,49 @@ void rebuild(ddamg_handle* h, int l) {
   check_err_flag(h, "test vectors are linearly dependent on an aggregate");
   blas_convert<float, double>(F.P32, F.P64, tot, 1, 0, 0, st);
   // Galerkin: column (s', j) of every block = P^+ (term of D applied to P_j restricted to chirality s'),
-  // in chunks of SETUP_CHUNK columns (bounded scratch)
+  // in chunks of SETUP_CHUNK columns (bounded scratch).  A handle with the FP32 preconditioner forms
+  // the product in FP32 from the FP32 copies of the operator and P (the preconditioner's setup runs
+  // in single precision, Sec. 3); an FP64 handle in FP64.
   const int jb_max = F.N < SETUP_CHUNK ? F.N : SETUP_CHUNK;
-  cplx<double>* tmp = static_cast<cplx<double>*>(scratch(h, 4, sizeof(cplx<double>) * F.vlen * jb_max));
   const int nc = C.n;
-  for (int sp = 0; sp < 2; ++sp)
-    for (int k = 0; k < 9; ++k) {
-      const int sel = k == 0 ? SEL_AGG_SELF : (k <= 4 ? SEL_AGG_FWD : SEL_AGG_BWD);
-      const int mu = k == 0 ? 0 : (k - 1) % 4;
-      for (int j0 = 0; j0 < F.N; j0 += jb_max) {
-        const int jb = F.N - j0 < jb_max ? F.N - j0 : jb_max;
-        apply_D<double>(h, F, tmp, F.P64 + (size_t)j0 * F.vlen, nullptr, jb, sel, mu, sp);
-        restrict_op<double>(C.c64.blk + (size_t)k * nc * nc + (size_t)(sp * F.N + j0) * nc, tmp, F.P64, F.g, C.g,
-                            F.fine, F.n, F.N, jb, F.vlen, (size_t)nc, (size_t)9 * nc * nc, st);
-      }
-    }
   const size_t nb = (size_t)C.g.V * 9 * nc * nc;
-  blas_convert<float, double>(C.c32.blk, C.c64.blk, nb, 1, 0, 0, st);
+  if (h->p.precision != 0) {
+    cplx<float>* tmp = static_cast<cplx<float>*>(scratch(h, 4, sizeof(cplx<float>) * F.vlen * jb_max));
+    FineOp<float> fo = F.f32;   // FP32 storage, not the FP16 copies
+    fo.Uh = nullptr;
+    fo.clovh = nullptr;
+    CoarseOp<float> co = F.c32;
+    co.blkh = nullptr;
+    co.bscale = nullptr;
+    for (int sp = 0; sp < 2; ++sp)
+      for (int k = 0; k < 9; ++k) {
+        const int sel = k == 0 ? SEL_AGG_SELF : (k <= 4 ? SEL_AGG_FWD : SEL_AGG_BWD);
+        const int mu = k == 0 ? 0 : (k - 1) % 4;
+        for (int j0 = 0; j0 < F.N; j0 += jb_max) {
+          const int jb = F.N - j0 < jb_max ? F.N - j0 : jb_max;
+          const cplx<float>* pj = F.P32 + (size_t)j0 * F.vlen;
+          if (F.fine) fine_dslash<float>(tmp, pj, nullptr, fo, jb, F.vlen, sel, mu, sp, st);
+          else coarse_apply<float>(tmp, pj, nullptr, co, jb, F.vlen, sel, mu, sp, st);
+          restrict_op<float>(C.c32.blk + (size_t)k * nc * nc + (size_t)(sp * F.N + j0) * nc, tmp, F.P32, F.g, C.g,
+                             F.fine, F.n, F.N, jb, F.vlen, (size_t)nc, (size_t)9 * nc * nc, st);
+        }
+      }
+    blas_convert<double, float>(C.c64.blk, C.c32.blk, nb, 1, 0, 0, st);
+  } else {
+    cplx<double>* tmp = static_cast<cplx<double>*>(scratch(h, 4, sizeof(cplx<double>) * F.vlen * jb_max));
+    for (int sp = 0; sp < 2; ++sp)
+      for (int k = 0; k < 9; ++k) {
+        const int sel = k == 0 ? SEL_AGG_SELF : (k <= 4 ? SEL_AGG_FWD : SEL_AGG_BWD);
+        const int mu = k == 0 ? 0 : (k - 1) % 4;
+        for (int j0 = 0; j0 < F.N; j0 += jb_max) {
+          const int jb = F.N - j0 < jb_max ? F.N - j0 : jb_max;
+          apply_D<double>(h, F, tmp, F.P64 + (size_t)j0 * F.vlen, nullptr, jb, sel, mu, sp);
+          restrict_op<double>(C.c64.blk + (size_t)k * nc * nc + (size_t)(sp * F.N + j0) * nc, tmp, F.P64, F.g, C.g,
+                              F.fine, F.n, F.N, jb, F.vlen, (size_t)nc, (size_t)9 * nc * nc, st);
+        }
+      }
+    blas_convert<float, double>(C.c32.blk, C.c64.blk, nb, 1, 0, 0, st);
+  }
   if (C.coarsest && C.eo) {
     coarse_selfinv_build(C.c64.selfinv, C.c64.blk, C.g.V, nc, h->d_err, st);
     check_err_flag(h, "singular self block on the coarsest level");
