@@ -71,6 +71,32 @@ def mass(name):
         return json.load(f)["masses"][name]["m0"]
 
 
+def replica_env():
+    """(rank, world size, local rank) of this process; one process per GPU under torchrun."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rhs_seed(w, rank):
+    """Seed of a replica's right-hand sides: every rank solves its own (replicas, weak scaling)."""
+    return w["rhs_seed"] + 1000 * rank
+
+
+def reduce_max(x, dist, device):
+    """Maximum of a float over the ranks (the identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(rhs_per_rank_step, steps, world, max_seconds):
+    """Whole-job right-hand sides per second: every rank's solves over the slowest rank's time."""
+    return rhs_per_rank_step * steps * world / max_seconds
+
+
 def inputs(w, rank=0):
     import synth
     U = synth.su3_field(w["dims"], w["eps"], w["seed"])
@@ -78,7 +104,7 @@ def inputs(w, rank=0):
     for a in w["agg"]:
         dims_l.append(tuple(d // x for d, x in zip(dims_l[-1], a)))
     tv = synth.random_test_vectors(dims_l, w["n_tv"], w["tv_seed"])
-    rhs = synth.random_spinors(w["nrhs"], w["dims"], w["rhs_seed"] + 1000 * rank)
+    rhs = synth.random_spinors(w["nrhs"], w["dims"], rhs_seed(w, rank))
     return U, tv, np.ascontiguousarray(rhs)
 
 
@@ -170,9 +196,7 @@ def ncu_traffic(kernel_file):
 # ---------------------------------------------------------------------------
 def run_gpu(args, w):
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = replica_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -279,19 +303,10 @@ def run_gpu(args, w):
             if not (s["converged"] and s["true_residual"] <= TOL):
                 raise SystemExit(f"solve missed the tolerance: {s}")
 
-    def agg(ms):
-        tot = sum(ms)
-        if dist is not None:
-            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        return tot
-
-    tot_mixed = agg(ms_mixed)
-    tot_fp64 = agg(ms_fp64)
-    rhs_total = nb * args.steps * world
-    value = rhs_total / (tot_mixed / 1e3)
-    value_fp64 = rhs_total / (tot_fp64 / 1e3)
+    tot_mixed = reduce_max(sum(ms_mixed), dist, "cuda")   # the slowest rank's timed region
+    tot_fp64 = reduce_max(sum(ms_fp64), dist, "cuda")
+    value = whole_job_rate(nb, args.steps, world, tot_mixed / 1e3)
+    value_fp64 = whole_job_rate(nb, args.steps, world, tot_fp64 / 1e3)
 
     def pct(ms):
         s = sorted(ms)
@@ -302,11 +317,8 @@ def run_gpu(args, w):
     p50, p99 = pct(ms_mixed)
     q50, q99 = pct(ms_fp64)
 
-    if dist is not None:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": rhs_total / t_e2e, "unit": "RHS/s",
+    t_e2e = reduce_max(t_e2e, dist, "cuda")
+    e2e = {"value": whole_job_rate(nb, args.steps, world, t_e2e), "unit": "RHS/s",
            "h2d_bytes_per_step": int(rhs_np.nbytes), "d2h_bytes_per_step": int(x_np.nbytes)}
 
     # roofline of the dominant kernel: the fine SAP colour sweep
@@ -414,8 +426,8 @@ def cpu_baseline(w, its):
 
 
 def run_reference(args, w):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    rank = replica_env()[0]
+    if rank != 0:   # under torchrun only rank 0 times the oracle
         return
     s = oracle_sample(w, steps=args.steps, warmup=min(args.warmup, 1), iterations_per_solve=None)
     v = s["value"]
