@@ -51,6 +51,12 @@ WORKLOADS = {
         dims=(64, 32, 32, 32), eps=0.4, csw=1.0, mass="eps0.4_csw1", levels=3,
         agg=[(4, 4, 4, 4), (2, 2, 2, 2)], n_tv=[20, 28], sap=[(4, 4, 4, 4), (2, 2, 2, 2)],
         mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=12, seed=0, tv_seed=100, rhs_seed=1),
+    "four_level_48c96": dict(
+        name="four-level 48^3x96, eps 0.45, csw 1.0, 20/28/28 test vectors, SAP 4^4, 1 RHS",
+        dims=(96, 48, 48, 48), eps=0.45, csw=1.0, mass="eps0.45_csw1", levels=4,
+        agg=[(4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)], n_tv=[20, 28, 28],
+        sap=[(4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)],
+        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=1, seed=0, tv_seed=100, rhs_seed=1),
     "two_level_8c4": dict(
         name="two-level 8^4, eps 0.3, csw 0, 8 test vectors, SAP 2^4, 1 RHS",
         dims=(8, 8, 8, 8), eps=0.3, csw=0.0, mass="eps0.3_csw0", levels=2,

@@ -6,6 +6,7 @@ puts the left edge of the spectrum of D(m0) at Re = 1e-3.
 
   8^4, eps = 0.3, csw = 0, seed 0   -> m0 of the two-level FP64 workload
   8^4, eps = 0.4, csw = 1, seed 0   -> m0 reused on 16^3x32 and larger lattices
+  8^4, eps = 0.45, csw = 1, seed 0  -> m0 reused on the four-level 48^3x96 lattice
 
 Usage: python tests/golden/make_masses.py
 """
@@ -26,7 +27,7 @@ from oracle.wilson import WilsonOp  # noqa: E402
 def main():
     out = {"reading": "m0 = 1e-3 - min Re lambda(D(0)) on an 8^4 field (seed 0), antiperiodic time",
            "masses": {}}
-    for name, eps, csw in (("eps0.3_csw0", 0.3, 0.0), ("eps0.4_csw1", 0.4, 1.0)):
+    for name, eps, csw in (("eps0.3_csw0", 0.3, 0.0), ("eps0.4_csw1", 0.4, 1.0), ("eps0.45_csw1", 0.45, 1.0)):
         U = synth.su3_field((8, 8, 8, 8), eps, 0)
         m0, w = edge_mass(U, csw, -1, margin=1e-3)
         out["masses"][name] = {

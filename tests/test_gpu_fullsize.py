@@ -16,7 +16,13 @@ sample, and b - D x of every solution on the sample, which must lie below
 1e-10 |b| because the whole residual does.  The library's own FP64 true residual
 is <= 1e-10 for every column, and a column solved alone equals its batched
 result bit for bit.
+
+48^3x96, four levels, one right-hand side, mixed precision: only with
+DDAMG_TEST_LARGE=1 and enough memory (about 230 GB on the device, about 130 GB
+on the host while the inputs are generated); the solve's residual on sampled
+sites by the oracle and the library's FP64 true residual.
 """
+import os
 import time
 
 import numpy as np
@@ -136,3 +142,46 @@ def test_batched_workload_32c64(dd):
             dd.ddamg_solve(h, np.ascontiguousarray(b[k:k + 1]), xa, 1, TOL)
             assert np.array_equal(xa[0], x[k])
     h.free()
+
+
+def _host_available_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+@pytest.mark.skipif(os.environ.get("DDAMG_TEST_LARGE") != "1",
+                    reason="48^3x96 four levels: about 230 GB of device memory and minutes of setup (opt-in)")
+def test_four_level_workload_48c96(dd):
+    import torch
+    import bench
+    from oracle.wilson import WilsonOp, apply_at_sites
+    w = bench.WORKLOADS["four_level_48c96"]
+    p = _params(dd, w, 2, w["nrhs"])
+    need = dd.ddamg_estimate_bytes(w["dims"], p)
+    free = torch.cuda.mem_get_info()[0]
+    if need > 0.95 * free or _host_available_bytes() < 200e9:
+        pytest.skip(f"needs {need / 1e9:.0f} GB of {free / 1e9:.0f} GB free on the device and 200 GB on the host")
+    U, tv, rhs = bench.inputs(w)
+    m0 = bench.mass(w["mass"])
+    t0 = time.perf_counter()
+    h = dd.ddamg_setup(U, w["dims"], -1, m0, w["csw"], p, tv)
+    print(f"\n48^3x96 four-level mixed setup {time.perf_counter() - t0:.1f} s, device "
+          f"{dd.ddamg_device_bytes(h) / 1e9:.1f} GB, phases {dd.ddamg_setup_times(h)[:3]}")
+    del tv
+    x = np.zeros_like(rhs)
+    t0 = time.perf_counter()
+    st = dd.ddamg_solve(h, rhs, x, 1, TOL)
+    print(f"solve {time.perf_counter() - t0:.2f} s, {st}")
+    h.free()
+    assert st[0]["converged"] and st[0]["true_residual"] <= TOL, st
+    build = lambda Up: WilsonOp.build(Up, m0, w["csw"], 1)   # noqa: E731
+    sites = _sites(w["dims"], 24, 31)
+    dx = apply_at_sites(build, U, x, (-1, 1, 1, 1), sites)
+    rs = np.stack([rhs[0][s] for s in sites]) - dx[0]
+    assert np.linalg.norm(rs) <= TOL * np.linalg.norm(rhs[0])
