@@ -796,40 +796,67 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
     if (e == cudaSuccess) return;
     cudaGetLastError();   // cluster launch refused: run the one-CTA-per-block kernel instead
   }
-  // one CTA per SAP block; up to 4 rows per thread for blocks of more than 1024 rows
+  // one CTA per SAP block with rpt rows per thread: the fewest of 1, 4, 8 for which
+  // the CTA stays within the threads the kernel's registers allow
   const int rows = op.g.vB * op.n;
-  const int rpt = rows > 1024 ? 4 : 1;
-  const int threads = ((div_up(rows, rpt) + 31) / 32) * 32;
   const size_t sm = (size_t)rows * sizeof(cplx<T>) + 32 * 3 * sizeof(T);
-  static bool attr_set[2] = {false, false};
-  bool& done = attr_set[sizeof(T) == 8];
-  if (!done) {
-    cudaFuncSetAttribute(k_coarse_sap<T, cplx<T>, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_coarse_sap<T, cplx<T>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if constexpr (sizeof(T) == 4) {
-      cudaFuncSetAttribute(k_coarse_sap<float, __half2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      cudaFuncSetAttribute(k_coarse_sap<float, __half2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  const bool half = sizeof(T) == 4 && op.blkh;
+  static int maxthr[2][2][3] = {};   // [FP64][FP16 blocks][rpt 1, 4, 8]
+  int* mt = maxthr[sizeof(T) == 8][half ? 1 : 0];
+  auto query = [&](const void* fn, int q) {
+    if (mt[q] == 0) {
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncAttributes a;
+      mt[q] = cudaFuncGetAttributes(&a, fn) == cudaSuccess ? a.maxThreadsPerBlock : -1;
+      cudaGetLastError();
     }
-    done = true;
+    return mt[q];
+  };
+  const void* fns[3];
+  if constexpr (sizeof(T) == 4) {
+    if (half) {
+      fns[0] = (const void*)k_coarse_sap<float, __half2, 1>;
+      fns[1] = (const void*)k_coarse_sap<float, __half2, 4>;
+      fns[2] = (const void*)k_coarse_sap<float, __half2, 8>;
+    }
   }
+  if (!half) {
+    fns[0] = (const void*)k_coarse_sap<T, cplx<T>, 1>;
+    fns[1] = (const void*)k_coarse_sap<T, cplx<T>, 4>;
+    fns[2] = (const void*)k_coarse_sap<T, cplx<T>, 8>;
+  }
+  const int rpts[3] = {1, 4, 8};
+  int q = 2;
+  for (int c = 0; c < 3; ++c)
+    if (((div_up(rows, rpts[c]) + 31) / 32) * 32 <= query(fns[c], c)) {
+      q = c;
+      break;
+    }
+  const int threads = ((div_up(rows, rpts[q]) + 31) / 32) * 32;
   count_launch();
   const dim3 grid(nblocks, nrhs);
   if constexpr (sizeof(T) == 4) {
-    if (op.blkh) {
-      if (rpt == 1)
+    if (half) {
+      if (q == 0)
         k_coarse_sap<float, __half2, 1><<<grid, threads, sm, st>>>(z, b, op.blkh, op.bscale, op.g, op.n, rstride,
                                                                     blocks, k_mr, op.bsite, op.bloc);
-      else
+      else if (q == 1)
         k_coarse_sap<float, __half2, 4><<<grid, threads, sm, st>>>(z, b, op.blkh, op.bscale, op.g, op.n, rstride,
+                                                                    blocks, k_mr, op.bsite, op.bloc);
+      else
+        k_coarse_sap<float, __half2, 8><<<grid, threads, sm, st>>>(z, b, op.blkh, op.bscale, op.g, op.n, rstride,
                                                                     blocks, k_mr, op.bsite, op.bloc);
       return;
     }
   }
-  if (rpt == 1)
+  if (q == 0)
     k_coarse_sap<T, cplx<T>, 1><<<grid, threads, sm, st>>>(z, b, op.blk, nullptr, op.g, op.n, rstride, blocks, k_mr,
                                                             op.bsite, op.bloc);
-  else
+  else if (q == 1)
     k_coarse_sap<T, cplx<T>, 4><<<grid, threads, sm, st>>>(z, b, op.blk, nullptr, op.g, op.n, rstride, blocks, k_mr,
+                                                            op.bsite, op.bloc);
+  else
+    k_coarse_sap<T, cplx<T>, 8><<<grid, threads, sm, st>>>(z, b, op.blk, nullptr, op.g, op.n, rstride, blocks, k_mr,
                                                             op.bsite, op.bloc);
 }
 

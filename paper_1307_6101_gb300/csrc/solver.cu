@@ -1041,12 +1041,17 @@ void setup_smooth(ddamg_handle* h, int l) {
   sync(h);
 }
 
+// host fields -> device level layout, SETUP_CHUNK fields at a time through the staging
+// buffer (which stays allocated with the handle: chunks keep it near the gauge field's size)
 void import_fields(ddamg_handle* h, Level& L, cplx<double>* dst, const double* src, int n) {
-  if (n <= 0) return;
-  const size_t bytes = sizeof(cplx<double>) * L.vlen * n;
-  const cplx<double>* d = static_cast<const cplx<double>*>(dev_in(h, src, bytes, 0));
-  if (L.fine) fine_import<double>(dst, d, L.g, n, L.vlen, h->st);
-  else coarse_import<double>(dst, d, L.g, L.n, n, L.vlen, h->st);
+  for (int j0 = 0; j0 < n; j0 += SETUP_CHUNK) {
+    const int jb = n - j0 < SETUP_CHUNK ? n - j0 : SETUP_CHUNK;
+    const size_t bytes = sizeof(cplx<double>) * L.vlen * jb;
+    const cplx<double>* d =
+        static_cast<const cplx<double>*>(dev_in(h, src + (size_t)j0 * L.vlen * 2, bytes, 0));
+    if (L.fine) fine_import<double>(dst + (size_t)j0 * L.vlen, d, L.g, jb, L.vlen, h->st);
+    else coarse_import<double>(dst + (size_t)j0 * L.vlen, d, L.g, L.n, jb, L.vlen, h->st);
+  }
 }
 
 void initial_setup_phase(ddamg_handle* h, int l, const double* const* tv_random) {
@@ -1572,7 +1577,11 @@ size_t estimate_bytes(const int dims0[4], const ddamg_params& p) {
   const size_t vl0 = vlen0 * B;
   tot += (size_t)(2 * p.outer_restart + 2) * vl0 * 16;        // outer FGMRES V, Z and residual
   tot += vl0 * (16 + 16 + 8 + 8);                              // ob, ox, pin32, pout32
-  tot += 2 * vl0 * 16 + maxtmp + 2 * maxtmp / 2;               // staging and setup scratch
+  // staging: slot 0 holds the largest of the gauge field, a chunk of test vectors and a batch
+  // of right-hand sides; a second slot a batch of solutions; then the setup scratch
+  const size_t V0 = vlen0 / 12;
+  tot += std::max({V0 * 576, vlen0 * (size_t)std::min(p.n_tv[0], 4) * 16, vl0 * 16}) + vl0 * 16;
+  tot += maxtmp + 2 * maxtmp / 2;
   return tot;
 }
 

@@ -123,6 +123,10 @@ SAP4W = dict(dims=(4, 8, 4, 8), levels=2, agg=((4, 4, 4, 4),), n_tv=(3,), sap=((
 BIG2 = dict(dims=(8, 8, 8, 8), levels=2, agg=((2, 2, 2, 2),), n_tv=(16,), sap=((2, 2, 2, 2),))
 BIG3 = dict(dims=(8, 8, 8, 8), levels=3, agg=((2, 2, 2, 2), (2, 2, 2, 2)), n_tv=(8, 10),
             sap=((2, 2, 2, 2), (2, 2, 2, 2)))
+# level-1 SAP blocks widened to 2x3x3x3 sites of 56 dof (3024 rows, not nested in the 2^4
+# aggregates): the one-CTA-per-block coarse SAP kernel at eight rows per thread
+ODDBIG = dict(dims=(8, 12, 12, 12), levels=3, agg=((2, 2, 2, 2), (2, 2, 2, 2)), n_tv=(28, 28),
+              sap=((2, 2, 2, 2), (2, 2, 2, 2)))
 # the two-level FP64 workload (8^4, eps 0.3, csw 0, aggregates 4^4, 8 test vectors, SAP 2^4)
 C1 = dict(dims=(8, 8, 8, 8), levels=2, agg=((4, 4, 4, 4),), n_tv=(8,), sap=((2, 2, 2, 2),), eps=0.3, csw=0.0,
           mr_steps=4, nu=3, n_inv=3, eta_passes=3, outer_restart=25)

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from cases import Case, rel, SMALL2, RAGGED2, THREE, ODD3, FOUR, C1, SAP4, SAP4W, BIG2, BIG3, golden_mass
+from cases import Case, rel, SMALL2, RAGGED2, THREE, ODD3, FOUR, C1, SAP4, SAP4W, BIG2, BIG3, ODDBIG, golden_mass
 
 pytestmark = pytest.mark.gpu
 
@@ -174,6 +174,37 @@ def test_coarse_apply_and_sap(dd, spec, cluster):
                 z = z0.copy()
                 dd.ddamg_smooth(h, l, prec, b, z, 2, it)
                 assert rel(z, zref) <= tol, (l, prec, rel(z, zref))
+
+
+def test_coarse_sap_large_blocks(dd):
+    """Coarse SAP on 2x3x3x3-site blocks of 56 dof (3024 rows per block, not nested in the aggregates):
+    the one-CTA-per-block kernel takes eight rows per thread to stay within its register budget.  FP64,
+    FP32, and FP32 on FP16 blocks against the oracle."""
+    from oracle.precision import stencil_half
+    from oracle.smoother import SAP
+    c, h, o = _pair(ODDBIG, mr_steps=3)
+    dims, n, _ = h.level_info(1)
+    assert n == 56 and o.levels[1].sap.block == (2, 3, 3, 3)
+    f = _fields(2, dims, n, 31)
+    out = np.zeros_like(f)
+    dd.ddamg_apply(h, 1, 1, f, out, 2)                  # one FP32 application: the 2e-6 bound
+    assert rel(out, o.levels[1].op.apply(f)) <= TOL32
+    # one FP32 SAP iteration chains about eight such applications (two colours, each a residual and
+    # three MR steps; 9 * 56 = 504-term sums per row) and block reductions over 3024 rows: bound 1e-5
+    TOL_SAP32 = 1e-5
+    b = _fields(2, dims, n, 41)
+    z0 = _fields(2, dims, n, 51)
+    for prec, tol, it in ((0, TOL64, 2), (1, TOL_SAP32, 1)):
+        zref = np.stack([o.levels[1].sap.smooth(b[i], z0[i], it) for i in range(2)])
+        z = z0.copy()
+        dd.ddamg_smooth(h, 1, prec, b, z, 2, it)
+        assert rel(z, zref) <= tol, (prec, rel(z, zref))
+    dd.ddamg_set_option(h, dd.DDAMG_OPT_HALF_STORAGE, 1)
+    sap = SAP(stencil_half(o.levels[1].op), o.levels[1].sap.block, 3)
+    zref = np.stack([sap.smooth(b[i], z0[i], 1) for i in range(2)])
+    z = z0.copy()
+    dd.ddamg_smooth(h, 1, 1, b, z, 2, 1)
+    assert rel(z, zref) <= TOL_SAP32, rel(z, zref)
 
 
 @pytest.mark.parametrize("cluster", [1, 0])
