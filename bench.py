@@ -45,18 +45,21 @@ WORKLOADS = {
         name="three-level 16^3x32, eps 0.4, csw 1.0, 20/28 test vectors, SAP 4^4, 1 RHS",
         dims=(32, 16, 16, 16), eps=0.4, csw=1.0, mass="eps0.4_csw1", levels=3,
         agg=[(4, 4, 4, 4), (2, 2, 2, 2)], n_tv=[20, 28], sap=[(4, 4, 4, 4), (2, 2, 2, 2)],
-        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=1, seed=0, tv_seed=100, rhs_seed=1),
+        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=1, seed=0, tv_seed=100, rhs_seed=1,
+        outer_iterations=15),
     "batched_32c64": dict(
         name="three-level 32^3x64, eps 0.4, csw 1.0, 20/28 test vectors, SAP 4^4, 12 RHS per batched solve",
         dims=(64, 32, 32, 32), eps=0.4, csw=1.0, mass="eps0.4_csw1", levels=3,
         agg=[(4, 4, 4, 4), (2, 2, 2, 2)], n_tv=[20, 28], sap=[(4, 4, 4, 4), (2, 2, 2, 2)],
-        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=12, seed=0, tv_seed=100, rhs_seed=1),
+        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=12, seed=0, tv_seed=100, rhs_seed=1,
+        outer_iterations=15),
     "four_level_48c96": dict(
         name="four-level 48^3x96, eps 0.45, csw 1.0, 20/28/28 test vectors, SAP 4^4, 1 RHS",
         dims=(96, 48, 48, 48), eps=0.45, csw=1.0, mass="eps0.45_csw1", levels=4,
         agg=[(4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)], n_tv=[20, 28, 28],
         sap=[(4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)],
-        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=1, seed=0, tv_seed=100, rhs_seed=1),
+        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=1, seed=0, tv_seed=100, rhs_seed=1,
+        outer_iterations=15),
     "two_level_8c4": dict(
         name="two-level 8^4, eps 0.3, csw 0, 8 test vectors, SAP 2^4, 1 RHS",
         dims=(8, 8, 8, 8), eps=0.3, csw=0.0, mass="eps0.3_csw0", levels=2,
@@ -70,6 +73,9 @@ SERVING = dict(
     lattices=[(32, 16, 16, 16), (48, 24, 24, 24), (64, 32, 32, 32)], rates=(5, 20, 80), seconds=10.0,
     max_requests=1000, max_rhs_total=48, max_rhs=6, seed=3)
 PAPER_OUTER_ITERATIONS = 22   # three-level outer FGMRES iterations on P2 (Table 3 of the paper)
+# outer_iterations in a workload: the outer FGMRES iterations this method takes on it (measured with
+# the library's FP64 and mixed solves); the oracle's per-iteration time is scaled by it, else by the
+# paper's count
 
 
 def mass(name):
@@ -405,6 +411,7 @@ def oracle_sample(w, steps, warmup, iterations_per_solve):
     h = omg.Hierarchy(op, p).setup(tv)
     t_setup = time.perf_counter() - t0
     b = rhs[0]
+    per_op = oracle_operator_seconds(h, op, p, b)
     for _ in range(warmup):
         fgmres(op.apply, b, M=lambda v: h.kcycle(0, v), m=1, tol=TOL, max_cycles=1, final_residual=False)
     times = []
@@ -413,7 +420,7 @@ def oracle_sample(w, steps, warmup, iterations_per_solve):
         fgmres(op.apply, b, M=lambda v: h.kcycle(0, v), m=1, tol=TOL, max_cycles=1, final_residual=False)
         times.append(time.perf_counter() - t0)
     t_iter = statistics.mean(times)
-    its = iterations_per_solve or PAPER_OUTER_ITERATIONS
+    its = iterations_per_solve or w.get("outer_iterations") or PAPER_OUTER_ITERATIONS
     try:
         cores = len(os.sched_getaffinity(0))
     except AttributeError:
@@ -423,7 +430,25 @@ def oracle_sample(w, steps, warmup, iterations_per_solve):
             "sample": (f"{steps} outer FGMRES iteration(s) of the FP64 numpy oracle on the same workload "
                        f"(hierarchy from Alg. 3 without smoothing, built in {t_setup:.0f} s, untimed); "
                        f"{t_iter:.2f} s per iteration scaled by {its} iterations per solve"),
-            "seconds_per_iteration": t_iter, "iterations_per_solve": its}
+            "seconds_per_iteration": t_iter, "iterations_per_solve": its, "per_operator_s": per_op}
+
+
+def oracle_operator_seconds(h, op, p, b):
+    """Seconds of one oracle application of each operator of the path on this workload (one core)."""
+    from oracle.transfer import restrict, prolong
+
+    def tm(f):
+        t0 = time.perf_counter()
+        f()
+        return round(time.perf_counter() - t0, 4)
+
+    lev0, lev1 = h.levels[0], h.levels[1]
+    bc = restrict(lev0.P, p.agg[0], b)
+    return {"fine_D": tm(lambda: op.apply(b)),
+            "fine_SAP_one_application": tm(lambda: lev0.sap.smooth(b, np.zeros_like(b), 1)),
+            "restriction": tm(lambda: restrict(lev0.P, p.agg[0], b)),
+            "prolongation": tm(lambda: prolong(lev0.P, p.agg[0], bc)),
+            "level1_coarse_D": tm(lambda: lev1.op.apply(bc))}
 
 
 def cpu_baseline(w, its):
@@ -444,7 +469,8 @@ def run_reference(args, w):
            "config": {"workload": w["name"], "lattice": "x".join(str(d) for d in w["dims"][::-1]),
                       "levels": w["levels"], "rhs_per_step": w["nrhs"], "tol": TOL,
                       "step": "one outer FGMRES iteration of the oracle"},
-           "cpu_baseline": {"value": v, "unit": "RHS/s", "cores": 1, "kind": "oracle", "sample": s["sample"]},
+           "cpu_baseline": {"value": v, "unit": "RHS/s", "cores": 1, "kind": "oracle", "sample": s["sample"],
+                            "per_operator_s": s["per_operator_s"]},
            "e2e": {"value": v, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
