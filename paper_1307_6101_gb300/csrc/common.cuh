@@ -5,7 +5,8 @@
 //                                      32 consecutive sites read 32 consecutive words
 //   links        [mu][9][V]           complex, U_mu(x)_{ab} at (mu*9 + a*3 + b)*V + x
 //   clover       [2][36][V]           real, two packed Hermitian 6x6 blocks per site
-//                                      (chirality 0 = spins 0,1; 1 = spins 2,3)
+//                                      (chirality 0 = spins 0,1; 1 = spins 2,3);
+//                                      FP16 copy [2][18][V] half2, pairs of packed reals
 //   coarse field [rhs][V][n]          complex, dof-contiguous per coarse site
 //   coarse op    [V][9][n][n]         complex, column-major blocks: k = 0 self,
 //                                      1..4 forward mu, 5..8 backward mu
@@ -77,7 +78,8 @@ template <typename To, typename From> DD_HD cplx<To> ccast(cplx<From> a) {
 }
 
 // Storage loads: operator data is held in the compute precision, or in FP16
-// (__half / __half2 = one complex) and widened to FP32 on load.
+// (__half = one real, __half2 = one complex or a pair of reals) and widened to
+// FP32 on load.
 template <typename T> DD_HD T ld_real(const T* p, size_t i) { return p[i]; }
 __device__ __forceinline__ float ld_real(const __half* p, size_t i) { return __half2float(p[i]); }
 template <typename T> DD_HD cplx<T> ld_cplx(const cplx<T>* p, size_t i) { return p[i]; }

@@ -392,8 +392,9 @@ __global__ void k_fine_sap(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ 
 //
 // One CTA per SAP block (or several small blocks).  A single thread arms an
 // mbarrier and issues 1-D bulk copies (cp.async.bulk, global -> shared) of the
-// block's 36 link components and 72 clover components, each a contiguous run
-// of vB words in the component-major layout.  After the barrier completes,
+// block's 36 link rows and its clover rows (72 reals, or 36 half2 pairs for
+// FP16 storage), each a contiguous run of vB words in the component-major
+// layout.  (4^4 blocks use the specialised kernel below.)  After the barrier completes,
 // the k minimal-residual steps on D_B read links, clover and the residual only
 // from shared memory; the neighbour slots inside the block are computed once.
 // The CTA loops over the right-hand sides, so the operator is staged once per

@@ -5,8 +5,9 @@
 // Arithmetic is the same as the host-driven solver: Arnoldi with classical
 // Gram-Schmidt applied twice, Givens rotations, per-right-hand-side stopping
 // (|g_{j+1}| <= tol ||b|| inside a cycle, true residual between cycles).  Each
-// right-hand side is handled by its own CTA in the fused Arnoldi step, so the
-// reduction order of a right-hand side does not depend on the batch.  Loop
+// right-hand side is handled by its own CTA (or its own cluster, for long
+// vectors) in the fused Arnoldi step, so the reduction order of a right-hand
+// side does not depend on the batch.  Loop
 // conditions are set by the last CTA to finish (atomic arrival counter, no
 // waiting); every loop is bounded by its maximal iteration count.
 #include "common.cuh"
@@ -178,7 +179,8 @@ __device__ void arnoldi_advance(dd::GmresState& s, int nrhs, int nblocks, int j,
   }
 }
 
-// One Arnoldi step for every rhs (one CTA each): CGS2 of w against V_0..V_j,
+// One Arnoldi step for every rhs (one CTA each; long vectors use the cluster
+// variant k_arnoldi_cl below): CGS2 of w against V_0..V_j,
 // ||w||, Givens update of column j, V_{j+1} = w / ||w||, cur = V_{j+1},
 // Z_j = zcur (flexible).  The last CTA advances j and sets the loop condition.
 template <typename T>
