@@ -1,0 +1,63 @@
+"""Resource properties of the hot kernels, from ptxas's report of an sm_103a build (no GPU).
+
+The 4^4-block SAP sweep fits two 256-thread CTAs per SM only with at most 128
+registers per thread, and it is only fast without local memory (the generic
+staged kernel kept its direction tables there); the cluster-split Arnoldi step
+runs 512-thread CTAs.  A change that breaks one of these shows up here before it
+reaches a GPU."""
+import os
+import re
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1307_6101_gb300", "csrc")
+
+
+def _ptxas_report(src):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    with tempfile.TemporaryDirectory() as d:
+        cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "--expt-relaxed-constexpr",
+               "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-Xptxas", "-v", "-c",
+               os.path.join(CSRC, src), "-o", os.path.join(d, "k.o")]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = {}
+    name = None
+    for ln in r.stderr.splitlines():
+        m = re.search(r"Compiling entry function '([^']+)'", ln)
+        if m:
+            name = m.group(1)
+            out[name] = {}
+            continue
+        if name is None:
+            continue
+        m = re.search(r"(\d+) bytes stack frame, (\d+) bytes spill stores, (\d+) bytes spill loads", ln)
+        if m:
+            out[name].update(stack=int(m.group(1)), spill_st=int(m.group(2)), spill_ld=int(m.group(3)))
+        m = re.search(r"Used (\d+) registers", ln)
+        if m:
+            out[name]["regs"] = int(m.group(1))
+    return out
+
+
+def test_fine_sap_4x4_kernel_resources():
+    rep = _ptxas_report("fine.cu")
+    b4 = {k: v for k, v in rep.items() if "k_fine_sap_b4" in k}
+    assert len(b4) == 2                                  # FP16 and FP32 storage
+    for k, v in b4.items():
+        assert v["regs"] <= 128, (k, v)
+        assert v["stack"] == 0 and v["spill_st"] == 0 and v["spill_ld"] == 0, (k, v)
+
+
+def test_arnoldi_cluster_kernel_resources():
+    rep = _ptxas_report("krylov.cu")
+    cl = {k: v for k, v in rep.items() if "k_arnoldi_cl" in k}
+    assert len(cl) == 2                                  # FP32 and FP64 vectors
+    for k, v in cl.items():
+        assert v["regs"] * 512 <= 65536, (k, v)          # one 512-thread CTA fits an SM's registers
