@@ -61,3 +61,15 @@ def test_arnoldi_cluster_kernel_resources():
     assert len(cl) == 2                                  # FP32 and FP64 vectors
     for k, v in cl.items():
         assert v["regs"] * 512 <= 65536, (k, v)          # one 512-thread CTA fits an SM's registers
+
+
+def test_coarse_sap_eight_rows_per_thread_fits_3024_row_blocks():
+    """The 48^3x96 hierarchy's widened level-2 SAP blocks have 2*3*3*3 sites x 56 dof = 3024 rows: at
+    eight rows per thread, 378 threads (12 warps) of every variant must fit an SM's 65536 registers
+    (registers are allocated per warp in units of 8 per thread)."""
+    rep = _ptxas_report("coarse.cu")
+    r8 = {k: v for k, v in rep.items() if "k_coarse_sap" in k and "Li8E" in k}
+    assert len(r8) == 3                                  # FP64, FP32, FP32 on FP16 blocks
+    warps = (3024 // 8 + 31) // 32
+    for k, v in r8.items():
+        assert ((v["regs"] + 7) // 8 * 8) * 32 * warps <= 65536, (k, v)
