@@ -1118,9 +1118,10 @@ void launch_sap_plain(cplx<T>* z, const cplx<T>* b, const LS* U, const CS* clov,
 template <typename T>
 void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int* blocks, int nblocks, int nrhs,
                     size_t rstride, int k_mr, cudaStream_t st) {
+  if (nrhs < 1 || nblocks < 1) return;   // the staged kernels issue their copies before the rhs loop
   const bool tma = sap_tma_ok(op) && op.err;
   if constexpr (sizeof(T) == 4) {
-    if (op.err && nblocks > 0 && sap_b4_ok(op, z, rstride)) {
+    if (op.err && sap_b4_ok(op, z, rstride)) {
       if (op.Uh)
         launch_sap_b4<__half2, __half2>(z, b, op.Uh, op.clovh, op, blocks, nblocks, nrhs, rstride, k_mr, op.shift, st);
       else
