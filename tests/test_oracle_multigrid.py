@@ -158,3 +158,120 @@ def test_odd_coarsest_uses_plain_gmres_and_solves():
     x, info = h.solve(b, tol=1e-10)
     assert info.converged
     assert np.linalg.norm(b - op.apply(x)) <= 1e-10 * np.linalg.norm(b)
+
+
+# ---------------------------------------------------------------------------
+# The recursive K-cycle (Alg. 2 over Alg. 1): an inner FGMRES on level 1 whose
+# preconditioner is the K-cycle at level 1, which ends in the coarsest solve.
+# Exact SAP block solves and an exact coarsest solve make every cycle linear,
+# so each expected value below is written with dense matrices only.
+
+def _three_level_exact(nu, kcycle_len, kcycle_cycles, kcycle_tol):
+    """4^4 -> 2^4 (aggregates 2^4, N0 = 3) -> 1x1x2x2 (aggregates 2x2x1x1, N1 = 4)."""
+    op = WilsonOp.build(synth.su3_field(DIMS, 0.4, 5), -0.25, 1.0, -1)
+    p = Params(levels=3, agg=((2, 2, 2, 2), (2, 2, 1, 1)), n_tv=(3, 4),
+               sap_block=((2, 2, 2, 2), (1, 1, 2, 2), None), mr_steps=3, nu=nu, mu=0,
+               kcycle_len=kcycle_len, kcycle_cycles=kcycle_cycles, kcycle_tol=kcycle_tol,
+               coarse_tol=1e-15, coarse_restart=64, coarse_cycles=4)
+    h = Hierarchy(op, p)
+    h.levels[0].tv = synth.random_fields(3, DIMS, 12, 6)
+    h.rebuild(0)
+    h.levels[1].tv = synth.random_fields(4, coarse_dims(DIMS, (2, 2, 2, 2)), 6, 7)
+    h.rebuild(1)
+    h.levels[0].sap = SAP(op, (2, 2, 2, 2), 3, exact=True)
+    h.levels[1].sap = SAP(h.levels[1].op, (1, 1, 2, 2), 3, exact=True)
+    return op, h
+
+
+def _dense_op(f_apply, shape):
+    n = int(np.prod(shape))
+    return np.stack([f_apply(e.reshape(shape)).ravel() for e in np.eye(n, dtype=np.complex128)], axis=1)
+
+
+def _dense_levels(op, h):
+    """Dense D0, P0, D1 = P0^+ D0 P0, P1, D2 = P1^+ D1 P1, and the exact SAP maps M0 (as a
+    callable) and M1 (dense), all from the fine operator, the interpolations and SAP."""
+    D0 = sparse_matrix(op).toarray()
+    P0 = _dense_P(h.levels[0].P, (2, 2, 2, 2))
+    D1 = P0.conj().T @ D0 @ P0
+    P1 = _dense_P(h.levels[1].P, (2, 2, 1, 1))
+    D2 = P1.conj().T @ D1 @ P1
+    shape1 = coarse_dims(DIMS, (2, 2, 2, 2)) + (6,)
+    M1 = _dense_op(h.levels[1].sap, shape1)
+    return D0, P0, D1, P1, D2, M1
+
+
+def _smooth(M_apply, D_apply, b, z, nu):
+    for _ in range(nu):
+        z = z + M_apply(b - D_apply(z))
+    return z
+
+
+def _dense_cycle_level1(D1, P1, D2, M1, nu):
+    """The K-cycle at level 1 as a matrix: Z = P1 D2^{-1} P1^+, then nu times Z += M1 (I - D1 Z)."""
+    Z = P1 @ np.linalg.solve(D2, P1.conj().T)
+    for _ in range(nu):
+        Z = Z + M1 @ (np.eye(D1.shape[0]) - D1 @ Z)
+    return Z
+
+
+def test_recursive_kcycle_converged_inner_solve_is_exact_coarse_correction():
+    """kcycle_tol = 1e-14 with enough inner iterations: the level-1 FGMRES solves D1 y = P0^+ b
+    exactly, so the cycle from level 0 is z = P0 D1^{-1} P0^+ b followed by the nu level-0 SAP
+    iterations (Alg. 2; D1 = P0^+ D0 P0 of Sec. 1)."""
+    nu = 1
+    op, h = _three_level_exact(nu, kcycle_len=40, kcycle_cycles=6, kcycle_tol=1e-14)
+    D0, P0, D1, P1, D2, M1 = _dense_levels(op, h)
+    b = synth.random_spinors(1, DIMS, 8)[0]
+    z = h.kcycle(0, b)
+    y = P0 @ np.linalg.solve(D1, P0.conj().T @ b.ravel())
+    D0a = lambda v: (D0 @ v.ravel()).reshape(v.shape)
+    ref = _smooth(h.levels[0].sap, D0a, b, y.reshape(b.shape), nu)
+    assert norm(z - ref) <= 1e-10 * norm(ref)
+
+
+def test_recursive_kcycle_one_inner_step_is_scaled_level1_cycle():
+    """One inner FGMRES step (kcycle_len = kcycle_cycles = 1): with b1 = P0^+ b and K1 the dense
+    K-cycle at level 1 (coarsest solve plus nu SAP iterations there), the step's minimal-residual
+    coefficient is alpha = <D1 K1 b1, b1> / ||D1 K1 b1||^2 and z = P0 (alpha K1 b1), followed by
+    the nu level-0 SAP iterations.  This exercises the recursive preconditioner itself."""
+    nu = 2
+    op, h = _three_level_exact(nu, kcycle_len=1, kcycle_cycles=1, kcycle_tol=1e-14)
+    D0, P0, D1, P1, D2, M1 = _dense_levels(op, h)
+    K1 = _dense_cycle_level1(D1, P1, D2, M1, nu)
+    b = synth.random_spinors(1, DIMS, 9)[0]
+    b1 = P0.conj().T @ b.ravel()
+    y = K1 @ b1
+    w = D1 @ y
+    alpha = np.vdot(w, b1) / np.vdot(w, w).real
+    D0a = lambda v: (D0 @ v.ravel()).reshape(v.shape)
+    ref = _smooth(h.levels[0].sap, D0a, b, (P0 @ (alpha * y)).reshape(b.shape), nu)
+    z = h.kcycle(0, b)
+    assert norm(z - ref) <= 1e-10 * norm(ref)
+    # the level-1 iterate the setup reads (Alg. 4's z_l) is alpha K1 b1
+    assert norm(h.last_iterate[1].ravel() - alpha * y) <= 1e-10 * norm(alpha * y)
+
+
+def test_recursive_kcycle_two_inner_steps_minimise_over_two_directions():
+    """kcycle_len = 2, kcycle_cycles = 1: with a linear K-cycle at level 1 the inner FGMRES is
+    right-preconditioned GMRES(2), so y1 = K1 u with u minimising ||b1 - D1 K1 u|| over
+    span{b1, D1 K1 b1}.  Swapping the length and the number of cycles (two restarted one-step
+    cycles) gives a different vector, which this pin rejects."""
+    nu = 1
+    op, h = _three_level_exact(nu, kcycle_len=2, kcycle_cycles=1, kcycle_tol=1e-14)
+    D0, P0, D1, P1, D2, M1 = _dense_levels(op, h)
+    K1 = _dense_cycle_level1(D1, P1, D2, M1, nu)
+    A = D1 @ K1
+    b = synth.random_spinors(1, DIMS, 10)[0]
+    b1 = P0.conj().T @ b.ravel()
+    B = np.stack([b1, A @ b1], axis=1)
+    c, *_ = np.linalg.lstsq(A @ B, b1, rcond=None)
+    y1 = K1 @ (B @ c)
+    D0a = lambda v: (D0 @ v.ravel()).reshape(v.shape)
+    ref = _smooth(h.levels[0].sap, D0a, b, (P0 @ y1).reshape(b.shape), nu)
+    z = h.kcycle(0, b)
+    assert norm(z - ref) <= 1e-10 * norm(ref)
+    # two restarted one-step cycles differ from the two-step cycle by far more than rounding
+    _, h2 = _three_level_exact(nu, kcycle_len=1, kcycle_cycles=2, kcycle_tol=1e-14)
+    z2 = h2.kcycle(0, b)
+    assert norm(z2 - ref) > 1e-6 * norm(ref)
