@@ -191,39 +191,55 @@ int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double
  * (0 on the coarsest level). */
 int ddamg_level_info(ddamg_handle* h, int level, int dims[4], int* ndof, int* ntv);
 
-/* out = D_l in (n fields of level l). precision 0 = FP64, 1 = FP32 arithmetic on the
- * FP32 path's storage (FP16 while DDAMG_OPT_HALF_STORAGE is on); the same for the
- * precision argument of the calls below.  Other values: ARG. */
+/* out = D_l in (n fields of level l).  Level 0 is the Wilson-clover operator of
+ * Sec. 1 (the form of the two-level paper the text defers to); level l >= 1 is the
+ * Galerkin operator D_l = P_{l-1}^dagger D_{l-1} P_{l-1} of Sec. 1, applied as its
+ * 9-point stencil of dense blocks (Sec. 2).  precision 0 = FP64, 1 = FP32 arithmetic
+ * on the FP32 path's storage (FP16 while DDAMG_OPT_HALF_STORAGE is on); the same for
+ * the precision argument of the calls below.  Other values: ARG. */
 int ddamg_apply(ddamg_handle* h, int level, int precision, const double* in, double* out, int n);
 
-/* iterations x { z <- z + M_SAP (b - D_l z) } on level l < L-1 (z in/out). */
+/* iterations x { z <- z + M_SAP (b - D_l z) } on level l < L-1 (z in/out): the SAP
+ * smoother of Sec. 1 (red-black multiplicative Schwarz over lattice blocks, each
+ * block solved by mr_steps minimal-residual steps, Table 1), one iteration being
+ * the smoothing step of Alg. 1. */
 int ddamg_smooth(ddamg_handle* h, int level, int precision, const double* b, double* z, int n, int iterations);
 
-/* coarse = P_l^dagger fine (level l -> l+1). */
+/* coarse = P_l^dagger fine (level l -> l+1): the restriction of Sec. 1, P_l built
+ * from the aggregated test vectors (Sec. 2.2). */
 int ddamg_restrict(ddamg_handle* h, int level, int precision, const double* fine, double* coarse, int n);
 
-/* fine = P_l coarse (level l+1 -> l). */
+/* fine = P_l coarse (level l+1 -> l): the interpolation of Sec. 1. */
 int ddamg_prolong(ddamg_handle* h, int level, int precision, const double* coarse, double* fine, int n);
 
-/* z = K-cycle(l, b) (Alg. 2, one application, mu/nu from the parameters). */
+/* z = K-cycle(l, b): one application of Alg. 2 (Alg. 1 with the coarse solve replaced
+ * by FGMRES on D_{l+1} preconditioned by the K-cycle at l+1; coarsest level: the
+ * odd-even GMRES of Sec. 3), mu/nu and the inner solver's length, cycles and
+ * tolerance from the parameters (Table 1). */
 int ddamg_kcycle(ddamg_handle* h, int level, int precision, const double* b, double* z, int n);
 
-/* z = coarsest-level solve of b: even-odd preconditioned GMRES to coarse_tol. */
+/* z = coarsest-level solve of b: odd-even preconditioned GMRES to coarse_tol
+ * (Sec. 3; GMRES on the Schur complement, then the odd back-substitution; plain
+ * GMRES on a coarsest lattice with an odd extent). */
 int ddamg_coarse_solve(ddamg_handle* h, int precision, const double* b, double* z, int n);
 
-/* Test vectors of level l (N_l fields of level l). */
+/* Test vectors of level l (N_l fields of level l): the vectors Alg. 3 builds and
+ * Alg. 4 refines. */
 int ddamg_set_testvectors(ddamg_handle* h, int level, const double* tv, int n);
 int ddamg_get_testvectors(ddamg_handle* h, int level, double* tv, int n);
 
-/* Rebuilds P_l (CGS2 per aggregate and chirality) from the current test
- * vectors and D_{l+1} = P_l^dagger D_l P_l. */
+/* Rebuilds P_l (CGS2 per aggregate and chirality, Sec. 2.2: the test vectors are
+ * aggregated and orthonormalised per chirality) from the current test vectors and
+ * D_{l+1} = P_l^dagger D_l P_l (Sec. 1); the step that ends each level of Alg. 3
+ * and every pass of Alg. 4. */
 int ddamg_rebuild(ddamg_handle* h, int level);
 
-/* P_l as N_l fields of level l (the orthonormalised test vectors). */
+/* P_l as N_l fields of level l (the orthonormalised test vectors, Sec. 2.2). */
 int ddamg_get_interpolation(ddamg_handle* h, int level, double* P);
 
 /* D_l (l >= 1) as blocks [coarse site lex][k][row][col] complex, k = 0 self,
- * 1..4 forward mu = t,z,y,x (couples to site + mu), 5..8 backward mu. */
+ * 1..4 forward mu = t,z,y,x (couples to site + mu), 5..8 backward mu: the
+ * nearest-neighbour block structure of the Galerkin operator (Sec. 1, Sec. 2). */
 int ddamg_get_coarse_operator(ddamg_handle* h, int level, double* blocks);
 
 /* ---- Setup timing ------------------------------------------------------------

@@ -4,6 +4,7 @@
 // Blocks are stored column-major per (site, k) with k = 0 self, 1..4 forward,
 // 5..8 backward, so that the threads computing consecutive rows of one site
 // read consecutive words.
+#include <atomic>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -759,8 +760,8 @@ int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out, in
 }
 
 template <typename T>
-void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks, int nrhs,
-                      size_t rstride, int k_mr, cudaStream_t st) {
+cudaError_t coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks,
+                             int nrhs, size_t rstride, int k_mr, cudaStream_t st) {
   if (op.sap_cls > 0) {
     const int spc = op.g.vB / op.sap_cls;
     const int threads = ((9 * spc * op.n + 31) / 32) * 32;
@@ -793,7 +794,7 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
                              (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc, op.sap_nsl, op.err,
                              op.bsite, op.bloc);
     }
-    if (e == cudaSuccess) return;
+    if (e == cudaSuccess) return cudaSuccess;
     cudaGetLastError();   // cluster launch refused: run the one-CTA-per-block kernel instead
   }
   // one CTA per SAP block with rpt rows per thread: the fewest of 1, 4, 8 for which
@@ -801,16 +802,21 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
   const int rows = op.g.vB * op.n;
   const size_t sm = (size_t)rows * sizeof(cplx<T>) + 32 * 3 * sizeof(T);
   const bool half = sizeof(T) == 4 && op.blkh;
-  static int maxthr[2][2][3] = {};   // [FP64][FP16 blocks][rpt 1, 4, 8]
-  int* mt = maxthr[sizeof(T) == 8][half ? 1 : 0];
+  // threads per CTA the kernel's registers allow, queried once per variant (a property of the
+  // compiled kernel, the same on every device of this architecture); the entries are atomics
+  // because serving workers launch from several host threads
+  static std::atomic<int> maxthr[2][2][3];   // [FP64][FP16 blocks][rpt 1, 4, 8]; 0 = not queried
+  std::atomic<int>* mt = maxthr[sizeof(T) == 8][half ? 1 : 0];
   auto query = [&](const void* fn, int q) {
-    if (mt[q] == 0) {
+    int v = mt[q].load(std::memory_order_acquire);
+    if (v == 0) {
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncAttributes a;
-      mt[q] = cudaFuncGetAttributes(&a, fn) == cudaSuccess ? a.maxThreadsPerBlock : -1;
+      v = cudaFuncGetAttributes(&a, fn) == cudaSuccess ? a.maxThreadsPerBlock : -1;
       cudaGetLastError();
+      mt[q].store(v, std::memory_order_release);
     }
-    return mt[q];
+    return v;
   };
   const void* fns[3];
   if constexpr (sizeof(T) == 4) {
@@ -833,6 +839,7 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
       break;
     }
   const int threads = ((div_up(rows, rpts[q]) + 31) / 32) * 32;
+  if (threads > query(fns[q], q)) return cudaErrorInvalidConfiguration;   // block too large even at 8 rows
   count_launch();
   const dim3 grid(nblocks, nrhs);
   if constexpr (sizeof(T) == 4) {
@@ -846,7 +853,7 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
       else
         k_coarse_sap<float, __half2, 8><<<grid, threads, sm, st>>>(z, b, op.blkh, op.bscale, op.g, op.n, rstride,
                                                                     blocks, k_mr, op.bsite, op.bloc);
-      return;
+      return cudaPeekAtLastError();
     }
   }
   if (q == 0)
@@ -858,6 +865,7 @@ void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const
   else
     k_coarse_sap<T, cplx<T>, 8><<<grid, threads, sm, st>>>(z, b, op.blk, nullptr, op.g, op.n, rstride, blocks, k_mr,
                                                             op.bsite, op.bloc);
+  return cudaPeekAtLastError();
 }
 
 template <typename T>
@@ -948,7 +956,7 @@ void coarse_blocks_export(cplx<double>* dst, const cplx<double>* blk, const Geom
   template void coarse_schur_even<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const cplx<T>*, const CoarseOp<T>&, \
                                      double, double, double, int, size_t, cudaStream_t);                          \
   template int coarse_sap_cluster_plan<T>(const Geom&, int, int*, int*, int*, int);                                \
-  template void coarse_sap_sweep<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, const int*, int, int, size_t,   \
+  template cudaError_t coarse_sap_sweep<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, const int*, int, int, size_t,   \
                                     int, cudaStream_t);                                                           \
   template void coarse_selfinv_apply<T>(cplx<T>*, const cplx<T>*, const CoarseOp<T>&, int, int, size_t,           \
                                         cudaStream_t);                                                            \

@@ -1202,47 +1202,79 @@ static double* g_noalloc_part_addr[64] = {};
 static double* g_noalloc_out_addr[64] = {};
 
 int fine_residual_norm_noalloc(double* out, bool out_on_device, const cplx<double>* b, const cplx<double>* x,
-                               const FineOp<double>& op, int nrhs, cudaStream_t st, const char** msg) {
+                               const FineOp<double>& op, int device, int nrhs, cudaStream_t st, const char** msg) {
   if (nrhs < 1 || nrhs > NOALLOC_MAX_RHS) {
     *msg = "n must be between 1 and 64 (the size of the static scratch)";
     return -1;
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  if (device < 0 || device >= 64) {
+    *msg = "device index out of range";
+    return -1;
+  }
+  // an error left on this thread by an earlier, unrelated call must not be reported as ours
+  cudaGetLastError();
+  // the scratch address is per device: look it up with the handle's device current, then
+  // restore the caller's device
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
     *msg = "no usable current CUDA device";
     return -4;
   }
+  const bool switch_dev = prev != device;
+  if (switch_dev && cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    *msg = "cudaSetDevice to the handle's device failed";
+    return -4;
+  }
+  int rc = 0;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_part_addr[dev]) {
+    if (!g_noalloc_part_addr[device]) {
       double* p = nullptr;
       double* o = nullptr;
       if (cudaGetSymbolAddress((void**)&p, g_noalloc_partials) != cudaSuccess ||
           cudaGetSymbolAddress((void**)&o, g_noalloc_out) != cudaSuccess) {
         cudaGetLastError();
         *msg = "cudaGetSymbolAddress of the static scratch failed";
-        return -4;
+        rc = -4;
+      } else {
+        g_noalloc_part_addr[device] = p;
+        g_noalloc_out_addr[device] = o;
       }
-      g_noalloc_part_addr[dev] = p;
-      g_noalloc_out_addr[dev] = o;
     }
   }
-  int nchunks = (op.g.V + 255) / 256;
-  if (nchunks > NOALLOC_CHUNKS) nchunks = NOALLOC_CHUNKS;
-  double* dst = out_on_device ? out : g_noalloc_out_addr[dev];
-  count_launch(2);
-  k_resnorm_partials<<<dim3(nchunks, nrhs), 256, 0, st>>>(g_noalloc_part_addr[dev], b, x, op.U, op.clov, op.g,
-                                                          op.bc_t, nchunks);
-  k_resnorm_final<<<nrhs, 32, 0, st>>>(dst, g_noalloc_part_addr[dev], nchunks);
-  if (!out_on_device && cudaMemcpyAsync(out, dst, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
-    *msg = "copy of the result to the host failed";
-    return -4;
+  if (rc == 0) {
+    int nchunks = (op.g.V + 255) / 256;
+    if (nchunks > NOALLOC_CHUNKS) nchunks = NOALLOC_CHUNKS;
+    double* dst = out_on_device ? out : g_noalloc_out_addr[device];
+    count_launch(2);
+    k_resnorm_partials<<<dim3(nchunks, nrhs), 256, 0, st>>>(g_noalloc_part_addr[device], b, x, op.U, op.clov, op.g,
+                                                            op.bc_t, nchunks);
+    if (cudaPeekAtLastError() != cudaSuccess) {
+      *msg = "launch of the residual kernel failed";
+      rc = -4;
+    }
+    if (rc == 0) {
+      k_resnorm_final<<<nrhs, 32, 0, st>>>(dst, g_noalloc_part_addr[device], nchunks);
+      if (cudaPeekAtLastError() != cudaSuccess) {
+        *msg = "launch of the reduction kernel failed";
+        rc = -4;
+      }
+    }
+    if (rc == 0 && !out_on_device &&
+        cudaMemcpyAsync(out, dst, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+      *msg = "copy of the result to the host failed";
+      rc = -4;
+    }
+    if (rc == 0 && cudaStreamSynchronize(st) != cudaSuccess) {
+      *msg = "kernel failure";
+      rc = -4;
+    }
+    if (rc != 0) cudaGetLastError();
   }
-  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
-    *msg = "kernel failure";
-    return -4;
-  }
-  return 0;
+  if (switch_dev) cudaSetDevice(prev);
+  return rc;
 }
 
 #define INST(T)                                                                                              \

@@ -51,7 +51,7 @@ void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int
 // ||b_i - D x_i|| / ||b_i|| with FP64 b, x in the ABI layout (device memory), no
 // allocation (static scratch); returns 0 or a negative code with *msg set
 int fine_residual_norm_noalloc(double* out, bool out_on_device, const cplx<double>* b, const cplx<double>* x,
-                               const FineOp<double>& op, int nrhs, cudaStream_t st, const char** msg);
+                               const FineOp<double>& op, int device, int nrhs, cudaStream_t st, const char** msg);
 void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, double m0, double csw,
                   cudaStream_t st);
 // FP16 copies: links (no scale, |U_ab| <= 1) and the clover term A - shift (no scale)
@@ -68,8 +68,9 @@ void fine_export(cplx<double>* dst, const cplx<T>* src, const Geom& g, int nrhs,
 template <typename T>
 void coarse_apply(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const CoarseOp<T>& op, int nrhs,
                   size_t rstride, int sel, int sel_mu, int in_chir, cudaStream_t st);
+// cudaErrorInvalidConfiguration (nothing launched) when a SAP block exceeds what one CTA can hold
 template <typename T>
-void coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks,
+cudaError_t coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks,
                       int nrhs, size_t rstride, int k_mr, cudaStream_t st);
 void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int n, int* err, cudaStream_t st);
 template <typename T>

@@ -325,7 +325,7 @@ void sap(ddamg_handle* h, Level& L, cplx<T>* z, const cplx<T>* b, int nrhs, int 
       if (L.fine)
         fine_sap_sweep<T>(z, b, fop<T>(L), L.blocks[c], L.nblocks[c], nrhs, L.vlen, h->p.mr_steps, h->st);
       else
-        coarse_sap_sweep<T>(z, b, cop<T>(L), L.blocks[c], L.nblocks[c], nrhs, L.vlen, h->p.mr_steps, h->st);
+        CK(coarse_sap_sweep<T>(z, b, cop<T>(L), L.blocks[c], L.nblocks[c], nrhs, L.vlen, h->p.mr_steps, h->st));
     }
 }
 
@@ -1877,7 +1877,8 @@ int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double
   }
   const char* msg = "";
   const int rc = fine_residual_norm_noalloc(out, is_device_ptr(out), reinterpret_cast<const cplx<double>*>(rhs),
-                                            reinterpret_cast<const cplx<double>*>(x), h->lv[0].f64, n, h->st, &msg);
+                                            reinterpret_cast<const cplx<double>*>(x), h->lv[0].f64, h->device, n, h->st,
+                                            &msg);
   if (rc != 0) {
     g_err = msg;
     return rc == -1 ? DDAMG_ERR_ARG : DDAMG_ERR_CUDA;
