@@ -48,11 +48,12 @@ WORKLOADS = {
         mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=1, seed=0, tv_seed=100, rhs_seed=1,
         outer_iterations=15),
     "batched_32c64": dict(
-        name="three-level 32^3x64, eps 0.4, csw 1.0, 20/28 test vectors, SAP 4^4, 12 RHS per batched solve",
+        name="three-level 32^3x64, eps 0.4, csw 1.0, 20/28 test vectors, SAP 4^4, 24 RHS per step: "
+             "12 spin-colour point sources at a seeded site, then 12 complex N(0,1), 12 per batched launch",
         dims=(64, 32, 32, 32), eps=0.4, csw=1.0, mass="eps0.4_csw1", levels=3,
         agg=[(4, 4, 4, 4), (2, 2, 2, 2)], n_tv=[20, 28], sap=[(4, 4, 4, 4), (2, 2, 2, 2)],
-        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=12, seed=0, tv_seed=100, rhs_seed=1,
-        outer_iterations=15),
+        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=12, ncols=24, point_seed=4, seed=0, tv_seed=100,
+        rhs_seed=1, outer_iterations=15),
     "four_level_48c96": dict(
         name="four-level 48^3x96, eps 0.45, csw 1.0, 20/28/28 test vectors, SAP 4^4, 1 RHS",
         dims=(96, 48, 48, 48), eps=0.45, csw=1.0, mass="eps0.45_csw1", levels=4,
@@ -109,14 +110,21 @@ def whole_job_rate(rhs_per_rank_step, steps, world, max_seconds):
     return rhs_per_rank_step * steps * world / max_seconds
 
 
-def inputs(w, rank=0):
+def inputs(w, rank=0, with_rhs=True):
     import synth
     U = synth.su3_field(w["dims"], w["eps"], w["seed"])
     dims_l = [tuple(w["dims"])]
     for a in w["agg"]:
         dims_l.append(tuple(d // x for d, x in zip(dims_l[-1], a)))
     tv = synth.random_test_vectors(dims_l, w["n_tv"], w["tv_seed"])
-    rhs = synth.random_spinors(w["nrhs"], w["dims"], rhs_seed(w, rank))
+    if not with_rhs:
+        return U, tv, None
+    if "point_seed" in w:
+        # the spin-colour point sources at a seeded site, then N(0,1) fields: one batch each
+        rhs = np.concatenate([synth.point_sources(w["dims"], w["point_seed"]),
+                              synth.random_spinors(w["ncols"] - 12, w["dims"], rhs_seed(w, rank))])
+    else:
+        rhs = synth.random_spinors(w.get("ncols", w["nrhs"]), w["dims"], rhs_seed(w, rank))
     return U, tv, np.ascontiguousarray(rhs)
 
 
@@ -206,6 +214,89 @@ def ncu_traffic(kernel_file):
 
 
 # ---------------------------------------------------------------------------
+ROOF_KERNELS = {2: "k_fine_sap_b4<__half2, __half2>", 1: "k_fine_sap_b4<cplx<float>, float>"}
+
+
+def pct(ms):
+    s = sorted(ms)
+    p50 = statistics.median(s)
+    p99 = s[min(len(s) - 1, int(np.ceil(0.99 * len(s))) - 1)]
+    return p50, p99
+
+
+class Timer:
+    """Timed solves of one hierarchy: the device-timed region (CUDA events on the library's
+    stream, L2 flushed before every step), and a separate profiled region with per-launch
+    CUDA events for the roofline (the events are never recorded inside the region that
+    gives `value`)."""
+
+    def __init__(self, dd, torch, stream, rhs, x, nb, ncols, barrier):
+        self.dd, self.torch, self.stream = dd, torch, stream
+        self.rhs, self.x, self.nb, self.ncols = rhs, x, nb, ncols
+        self.barrier = barrier
+        self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (126 MB)
+
+    def solve(self, h):
+        return self.dd.ddamg_solve(h, self.rhs, self.x, self.ncols, TOL)
+
+    def timed(self, h, steps, warm, tag="timed"):
+        dd, torch = self.dd, self.torch
+        for _ in range(warm):
+            self.solve(h)
+        self.barrier()
+        ms, stats = [], []
+        launches0 = dd.ddamg_launch_count()
+        torch.cuda.nvtx.range_push(tag)   # lets a profiler select the timed solves
+        for _ in range(steps):
+            self.flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            st = self.solve(h)
+            e1.record(self.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            stats.append(st)
+        torch.cuda.nvtx.range_pop()
+        self.barrier()
+        return ms, stats, dd.ddamg_launch_count() - launches0
+
+    def profiled(self, h, steps, kind="fine_sap"):
+        """(total ms, launches, algorithmic bytes, solve ms) of one kernel class over `steps` solves."""
+        dd = self.dd
+        dd.ddamg_profile(h, 1 << dd.PROF_KINDS[kind])
+        self.solve(h)                      # captures the graphs of this profiling mask
+        dd.ddamg_profile(h, 1 << dd.PROF_KINDS[kind])   # restart the counters
+        ms = []
+        for _ in range(steps):
+            self.flush.fill_(1.0)
+            e0 = self.torch.cuda.Event(enable_timing=True)
+            e1 = self.torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            self.solve(h)
+            e1.record(self.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        out = dd.ddamg_profile_read(h, kind)
+        dd.ddamg_profile(h, 0)
+        return out + (sum(ms),)
+
+
+def roofline(prof, prec, kernel_file):
+    pk, pk_src = peaks()
+    p_ms, p_n, p_bytes, solve_ms = prof
+    avg_ms = p_ms / max(1, p_n)
+    per_launch = p_bytes / max(1, p_n)
+    achieved = per_launch / (avg_ms / 1e3) / 1e9
+    return {"kernel": ROOF_KERNELS[prec] + " (one SAP colour sweep, 4 MR steps)", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": pk, "unit": "GB/s", "frac": round(achieved / pk, 4),
+            "peak_source": pk_src, "traffic": ncu_traffic(kernel_file),
+            "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms, "launches": p_n,
+            "share_of_step": round(p_ms / max(1e-9, solve_ms), 4),
+            "timing": "CUDA events around every launch of this kernel on its stream, in a separate "
+                      "profiled region of the same solves (value comes from an uninstrumented region)"}
+
+
 def run_gpu(args, w):
     import torch
     rank, world, local = replica_env()
@@ -221,6 +312,7 @@ def run_gpu(args, w):
     U, tv, rhs_h = inputs(w, rank)
     m0 = mass(w["mass"])
     nb = w["nrhs"]
+    ncols = rhs_h.shape[0]
 
     def params(precision):
         return dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
@@ -242,60 +334,32 @@ def run_gpu(args, w):
         handles[name] = h
         return h
 
-    # one hierarchy on the device at a time: the mixed one is timed (and its e2e taken) and
-    # freed before the FP64 one is built (the 12-RHS 32^3x64 batch needs about 170 GB)
-    make("mixed", mixed_prec)
-
-    rhs = torch.from_numpy(rhs_h).cuda()
-    x = torch.zeros_like(rhs)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (126 MB)
-
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(h, steps, warm, profile_mask=0, tag="timed"):
-        for _ in range(warm):
-            dd.ddamg_solve(h, rhs, x, nb, TOL)
-        barrier()
-        ms, stats = [], []
-        launches0 = dd.ddamg_launch_count()
-        if profile_mask:
-            dd.ddamg_profile(h, profile_mask)
-        torch.cuda.nvtx.range_push(tag)
-        for _ in range(steps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = dd.ddamg_solve(h, rhs, x, nb, TOL)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-            stats.append(st)
-        torch.cuda.nvtx.range_pop()
-        barrier()
-        launches = dd.ddamg_launch_count() - launches0 - 0
-        prof = None
-        if profile_mask:
-            prof = dd.ddamg_profile_read(h, "fine_sap")
-            dd.ddamg_profile(h, 0)
-        return ms, stats, launches, prof
+    # one hierarchy on the device at a time: the mixed one is timed (and its e2e taken) and
+    # freed before the FP64 one is built (the 12-RHS 32^3x64 batch needs about 170 GB)
+    make("mixed", mixed_prec)
+    rhs = torch.from_numpy(rhs_h).cuda()
+    x = torch.zeros_like(rhs)
+    tm = Timer(dd, torch, stream, rhs, x, nb, ncols, barrier)
 
     clk = Clocks(local)
     clk.start()
     steps0 = [dd.ddamg_krylov_steps(handles["mixed"], l, 1) for l in range(w["levels"])]
-    ms_mixed, st_mixed, launches, prof = timed(handles["mixed"], args.steps, args.warmup, profile_mask=1,
-                                               tag="timed_mixed")
+    ms_mixed, st_mixed, launches = tm.timed(handles["mixed"], args.steps, args.warmup, tag="timed_mixed")
     steps1 = [dd.ddamg_krylov_steps(handles["mixed"], l, 1) for l in range(w["levels"])]
     clocks = clk.stop()
+    prof = tm.profiled(handles["mixed"], args.steps)
     if args.only_mixed:
         for h in handles.values():
             h.free()
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": nb * args.steps / (sum(ms_mixed) / 1e3), "unit": "RHS/s",
-                              "note": "profiling run (--only-mixed): not a bench line"}))
+            print(json.dumps({"metric": METRIC, "value": ncols * args.steps / (sum(ms_mixed) / 1e3), "unit": "RHS/s",
+                              "note": "profiling run (--only-mixed): not a bench line",
+                              "roofline": roofline(prof, mixed_prec, KERNEL_FILE)}))
         return
     # end to end through the C ABI with host buffers in pinned memory (H2D of the rhs and D2H of x
     # inside every step; L2 flushed before every step, as in the device-timed loop)
@@ -308,16 +372,16 @@ def run_gpu(args, w):
         x_t = torch.zeros_like(rhs_t)
         host_mem = "pageable"
     rhs_np, x_np = rhs_t.numpy(), x_t.numpy()
-    dd.ddamg_solve(handles["mixed"], rhs_np, x_np, nb, TOL)
+    dd.ddamg_solve(handles["mixed"], rhs_np, x_np, ncols, TOL)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        flush.fill_(1.0)
-        dd.ddamg_solve(handles["mixed"], rhs_np, x_np, nb, TOL)
+        tm.flush.fill_(1.0)
+        dd.ddamg_solve(handles["mixed"], rhs_np, x_np, ncols, TOL)
     t_e2e = time.perf_counter() - t0
     handles.pop("mixed").free()
     make("fp64", 0)
-    ms_fp64, st_fp64, _, _ = timed(handles["fp64"], args.steps, max(1, min(args.warmup, 3)), tag="timed_fp64")
+    ms_fp64, st_fp64, _ = tm.timed(handles["fp64"], args.steps, max(1, min(args.warmup, 3)), tag="timed_fp64")
 
     for st in st_mixed + st_fp64:
         for s in st:
@@ -326,36 +390,15 @@ def run_gpu(args, w):
 
     tot_mixed = reduce_max(sum(ms_mixed), dist, "cuda")   # the slowest rank's timed region
     tot_fp64 = reduce_max(sum(ms_fp64), dist, "cuda")
-    value = whole_job_rate(nb, args.steps, world, tot_mixed / 1e3)
-    value_fp64 = whole_job_rate(nb, args.steps, world, tot_fp64 / 1e3)
-
-    def pct(ms):
-        s = sorted(ms)
-        p50 = statistics.median(s)
-        p99 = s[min(len(s) - 1, int(np.ceil(0.99 * len(s))) - 1)]
-        return p50, p99
-
+    value = whole_job_rate(ncols, args.steps, world, tot_mixed / 1e3)
+    value_fp64 = whole_job_rate(ncols, args.steps, world, tot_fp64 / 1e3)
     p50, p99 = pct(ms_mixed)
     q50, q99 = pct(ms_fp64)
 
     t_e2e = reduce_max(t_e2e, dist, "cuda")
-    e2e = {"value": whole_job_rate(nb, args.steps, world, t_e2e), "unit": "RHS/s",
+    e2e = {"value": whole_job_rate(ncols, args.steps, world, t_e2e), "unit": "RHS/s",
            "h2d_bytes_per_step": int(rhs_np.nbytes), "d2h_bytes_per_step": int(x_np.nbytes),
            "host_memory": host_mem, "l2": "flushed before every step"}
-
-    # roofline of the dominant kernel: the fine SAP colour sweep
-    pk, pk_src = peaks()
-    p_ms, p_n, p_bytes = prof
-    avg_ms = p_ms / max(1, p_n)
-    per_launch = p_bytes / max(1, p_n)
-    achieved = per_launch / (avg_ms / 1e3) / 1e9
-    kname = "k_fine_sap_b4<__half2, __half2>" if mixed_prec == 2 else "k_fine_sap_b4<cplx<float>, float>"
-    roof = {"kernel": kname + " (one SAP colour sweep, 4 MR steps)", "bound": "hbm",
-            "achieved": round(achieved, 1), "peak": pk, "unit": "GB/s", "frac": round(achieved / pk, 4),
-            "peak_source": pk_src, "traffic": ncu_traffic(os.path.join(ROOT, "paper_1307_6101_gb300", "csrc",
-                                                                        "fine.cu")),
-            "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms, "launches": p_n,
-            "share_of_step": round(p_ms / max(1e-9, sum(ms_mixed)), 4)}
 
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
@@ -365,54 +408,97 @@ def run_gpu(args, w):
                  " / f64 outer FGMRES",
         "data": "synthetic (seeded SU(3) links, complex N(0,1) rhs)",
         "config": {"workload": w["name"], "lattice": "x".join(str(d) for d in w["dims"][::-1]),
-                   "levels": w["levels"], "rhs_per_step": nb, "global_batch": nb * world,
+                   "levels": w["levels"], "rhs_per_step": ncols, "rhs_per_launch": nb, "global_batch": ncols * world,
                    "tol": TOL, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
-        "s_per_rhs": round(tot_mixed / 1e3 / (nb * args.steps), 6),
+        "s_per_rhs": round(tot_mixed / 1e3 / (ncols * args.steps), 6),
         "p50_ms": round(p50, 3), ("p99_ms" if len(ms_mixed) >= 100 else "p99_ms_is_max_of_steps"): round(p99, 3),
         "iterations": [s["iterations"] for st in st_mixed[:1] for s in st],
         "true_residual": max(s["true_residual"] for st in st_mixed for s in st),
         "plain_fp64": {"value": round(value_fp64, 4), "unit": "RHS/s",
-                       "s_per_rhs": round(tot_fp64 / 1e3 / (nb * args.steps), 6),
+                       "s_per_rhs": round(tot_fp64 / 1e3 / (ncols * args.steps), 6),
                        "p50_ms": round(q50, 3), "p99_ms_is_max_of_steps": round(q99, 3),
                        "iterations": [s["iterations"] for st in st_fp64[:1] for s in st],
                        "true_residual": max(s["true_residual"] for st in st_fp64 for s in st)},
         "mixed_over_fp64": round(value / value_fp64, 3),
         "setup_s": {k: round(v, 2) for k, v in setup_s.items()},
-        "roofline": roof,
+        "roofline": roofline(prof, mixed_prec, KERNEL_FILE),
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "krylov_steps_per_solve": [round((b - a) / args.steps, 1) for a, b in zip(steps0, steps1)],
     }
-    if rank == 0 and world == 1 and not args.no_serving and w is WORKLOADS["three_level_16c32"]:
-        # short serving run on this lattice: Poisson arrivals, 1-12 RHS per request, 6 batch slots
-        for h in handles.values():
-            h.free()
-        handles = {}
-        out["serving"] = serving_bench(dd, w, [tuple(w["dims"])], (20,), 5.0, 1000, 6, SERVING["seed"], 60)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and w is WORKLOADS["three_level_16c32"]:
-        out["cpu_baseline"] = cpu_baseline(w, out["iterations"][0] if out["iterations"] else None)
-    for h in handles.values():
+    for h in list(handles.values()):
         h.free()
+    handles = {}
+    default = w is WORKLOADS["three_level_16c32"]
+    if rank == 0 and world == 1 and default and not args.no_large:
+        # the batched 32^3x64 workload (two 12-column launches per step) with its own roofline
+        del rhs, x, tm
+        torch.cuda.empty_cache()
+        out["batched_32c64"] = large_workload(dd, torch, stream, WORKLOADS["batched_32c64"], mixed_prec,
+                                              args.large_steps, barrier)
+    if rank == 0 and world == 1 and not args.no_serving and default:
+        # short serving run on this lattice: Poisson arrivals, 1-12 RHS per request, 6 batch slots
+        out["serving"] = serving_bench(dd, w, [tuple(w["dims"])], (20,), 5.0, 1000, 6, SERVING["seed"], 60)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and default:
+        out["cpu_baseline"] = cpu_baseline(w, out["iterations"][0] if out["iterations"] else None)
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
 
 
-# ---------------------------------------------------------------------------
-def oracle_sample(w, steps, warmup, iterations_per_solve):
-    """Oracle timing: one outer FGMRES iteration (K-cycle + D + CGS2) per step on the same workload.
+KERNEL_FILE = os.path.join(ROOT, "paper_1307_6101_gb300", "csrc", "fine.cu")
 
-    The oracle hierarchy is built by Alg. 3 without smoothing passes (random test
-    vectors orthonormalised, Galerkin operators) so that its construction stays
-    bounded; the per-iteration cost does not depend on the test vectors.
-    """
+
+def large_workload(dd, torch, stream, w, prec, steps, barrier):
+    """Mixed-precision solves of a workload that leaves L2: device-timed value and the fine SAP roofline."""
+    U, tv, rhs_h = inputs(w)
+    p = dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
+                                mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
+                                outer_restart=w["outer_restart"], precision=prec, max_rhs=w["nrhs"])
+    t0 = time.perf_counter()
+    h = dd.ddamg_setup(U, w["dims"], -1, mass(w["mass"]), w["csw"], p, tv)
+    t_setup = time.perf_counter() - t0
+    del U, tv
+    dd.ddamg_set_stream(h, stream.cuda_stream)
+    ncols = rhs_h.shape[0]
+    rhs = torch.from_numpy(rhs_h).cuda()
+    del rhs_h
+    x = torch.zeros_like(rhs)
+    tm = Timer(dd, torch, stream, rhs, x, w["nrhs"], ncols, barrier)
+    clk = Clocks(torch.cuda.current_device())
+    clk.start()
+    ms, stats, launches = tm.timed(h, steps, 1)
+    clocks = clk.stop()
+    prof = tm.profiled(h, 1)
+    res = max(s["true_residual"] for st in stats for s in st)
+    conv = all(s["converged"] for st in stats for s in st)
+    dev = dd.ddamg_device_bytes(h)
+    h.free()
+    del rhs, x, tm
+    torch.cuda.empty_cache()
+    tot = sum(ms)
+    return {"workload": w["name"], "lattice": "x".join(str(d) for d in w["dims"][::-1]),
+            "rhs_per_step": ncols, "rhs_per_launch": w["nrhs"], "steps": steps, "warmup": 1,
+            "value": round(ncols * steps / (tot / 1e3), 4), "unit": "RHS/s",
+            "s_per_rhs": round(tot / 1e3 / (ncols * steps), 5), "ms_per_step": round(tot / steps, 1),
+            "iterations": [s["iterations"] for s in stats[0]], "true_residual": res, "all_converged": conv,
+            "setup_s": round(t_setup, 1), "device_bytes": int(dev), "gpu_launches": int(launches),
+            "clocks": clocks, "roofline": roofline(prof, prec, KERNEL_FILE)}
+
+
+# ---------------------------------------------------------------------------
+def _oracle_worker(job):
+    """One oracle process: build the hierarchy (untimed), then time `steps` outer FGMRES iterations
+    (K-cycle + D + CGS2) on this worker's own right-hand side.  Returns per-iteration seconds."""
+    name, worker, steps, warmup, with_ops = job
     import oracle.multigrid as omg
     from oracle.krylov import fgmres
     from oracle.wilson import WilsonOp
-    U, tv, rhs = inputs(w)
+    w = WORKLOADS[name]
+    U, tv, rhs = inputs(w, rank=worker)
     op = WilsonOp.build(U, mass(w["mass"]), w["csw"], -1)
     p = omg.Params(levels=w["levels"], agg=tuple(w["agg"]), n_tv=tuple(w["n_tv"]),
                    sap_block=tuple(w["sap"]) + (None,), mr_steps=w["mr_steps"], nu=w["nu"], n_inv=0,
@@ -421,7 +507,7 @@ def oracle_sample(w, steps, warmup, iterations_per_solve):
     h = omg.Hierarchy(op, p).setup(tv)
     t_setup = time.perf_counter() - t0
     b = rhs[0]
-    per_op = oracle_operator_seconds(h, op, p, b)
+    per_op = oracle_operator_seconds(h, op, p, b) if with_ops else None
     for _ in range(warmup):
         fgmres(op.apply, b, M=lambda v: h.kcycle(0, v), m=1, tol=TOL, max_cycles=1, final_residual=False)
     times = []
@@ -430,21 +516,53 @@ def oracle_sample(w, steps, warmup, iterations_per_solve):
         t0 = time.perf_counter()
         fgmres(op.apply, b, M=lambda v: h.kcycle(0, v), m=1, tol=TOL, max_cycles=1, final_residual=False)
         times.append(time.perf_counter() - t0)
-    # threads actually used: CPU seconds of the process (all threads) over wall seconds
     used = (time.process_time() - c0) / max(1e-9, sum(times))
-    t_iter = statistics.mean(times)
-    its = iterations_per_solve or w.get("outer_iterations") or PAPER_OUTER_ITERATIONS
+    return {"times": times, "setup_s": t_setup, "cpu_per_wall": used, "per_op": per_op}
+
+
+def _single_thread_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def host_cores():
     try:
-        cores = len(os.sched_getaffinity(0))
+        return len(os.sched_getaffinity(0))
     except AttributeError:
-        cores = os.cpu_count()
-    return {"value": 1.0 / (t_iter * its), "unit": "RHS/s", "cores": max(1, round(used)),
-            "cpu_seconds_per_wall_second": round(used, 2), "host_cores_available": cores,
+        return os.cpu_count() or 1
+
+
+def oracle_sample(w, steps, warmup, iterations_per_solve, workers=1):
+    """Oracle timing on `workers` host cores: one process per core, each solving its own right-hand
+    side, all timed together; one step = one outer FGMRES iteration on every worker.
+
+    The oracle hierarchy is built by the oracle itself, by Alg. 3 without smoothing passes (random
+    test vectors orthonormalised, Galerkin operators), so that its construction stays bounded: the
+    oracle's inputs never come from the CUDA library, and its full setup would take hours here.  The
+    per-iteration cost does not depend on the test vectors.
+    """
+    import multiprocessing as mp
+    _single_thread_env()
+    name = next(k for k, v in WORKLOADS.items() if v is w)
+    jobs = [(name, q, steps, warmup, q == 0) for q in range(workers)]
+    if workers == 1:
+        res = [_oracle_worker(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    # the slowest worker's iteration time bounds the concurrent throughput
+    t_iter = max(statistics.mean(r["times"]) for r in res)
+    its = iterations_per_solve or w.get("outer_iterations") or PAPER_OUTER_ITERATIONS
+    used = sum(r["cpu_per_wall"] for r in res)
+    ncols = 1
+    return {"value": workers * ncols / (t_iter * its), "unit": "RHS/s", "cores": workers,
+            "cpu_seconds_per_wall_second": round(used, 2), "host_cores_available": host_cores(),
             "kind": "oracle",
-            "sample": (f"{steps} outer FGMRES iteration(s) of the FP64 numpy oracle on the same workload "
-                       f"(hierarchy from Alg. 3 without smoothing, built in {t_setup:.0f} s, untimed); "
-                       f"{t_iter:.2f} s per iteration scaled by {its} iterations per solve"),
-            "seconds_per_iteration": t_iter, "iterations_per_solve": its, "per_operator_s": per_op}
+            "sample": (f"{steps} outer FGMRES iteration(s) of the FP64 numpy oracle on the same workload, "
+                       f"{workers} single-threaded process(es) each on its own right-hand side "
+                       f"(hierarchy from Alg. 3 without smoothing, built in {max(r['setup_s'] for r in res):.0f} s, "
+                       f"untimed); {t_iter:.2f} s per iteration scaled by {its} iterations per solve"),
+            "seconds_per_iteration": t_iter, "iterations_per_solve": its, "per_operator_s": res[0]["per_op"]}
 
 
 def oracle_operator_seconds(h, op, p, b):
@@ -466,25 +584,38 @@ def oracle_operator_seconds(h, op, p, b):
 
 
 def cpu_baseline(w, its):
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    return oracle_sample(w, steps=1, warmup=0, iterations_per_solve=its)
+    """The oracle on all host cores (the headline baseline) and on one core."""
+    allc = oracle_sample(w, steps=1, warmup=0, iterations_per_solve=its, workers=host_cores())
+    one = oracle_sample(w, steps=1, warmup=0, iterations_per_solve=its, workers=1)
+    allc["one_core"] = {k: one[k] for k in ("value", "unit", "cores", "seconds_per_iteration", "sample")}
+    return allc
+
+
+REFERENCE_BUDGET_S = 150.0   # timed seconds of the reference arm (its steps are capped to fit)
 
 
 def run_reference(args, w):
     rank = replica_env()[0]
     if rank != 0:   # under torchrun only rank 0 times the oracle
         return
-    s = oracle_sample(w, steps=args.steps, warmup=min(args.warmup, 1), iterations_per_solve=None)
+    workers = host_cores()
+    probe = oracle_sample(w, steps=1, warmup=0, iterations_per_solve=None, workers=1)
+    steps = max(1, min(args.steps, int(REFERENCE_BUDGET_S // max(1e-9, probe["seconds_per_iteration"]))))
+    s = oracle_sample(w, steps=steps, warmup=0, iterations_per_solve=None, workers=workers)
     v = s["value"]
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "RHS/s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": s["seconds_per_iteration"] * 1e3,
+           "steps": steps, "steps_requested": args.steps, "warmup": args.warmup,
+           "ms_per_step": s["seconds_per_iteration"] * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded SU(3) links, complex N(0,1) rhs)",
            "config": {"workload": w["name"], "lattice": "x".join(str(d) for d in w["dims"][::-1]),
-                      "levels": w["levels"], "rhs_per_step": w["nrhs"], "tol": TOL,
-                      "step": "one outer FGMRES iteration of the oracle"},
+                      "levels": w["levels"], "rhs_per_step": workers, "tol": TOL,
+                      "step": f"one outer FGMRES iteration of the oracle on each of {workers} cores "
+                              f"(own right-hand side per core); steps capped at {REFERENCE_BUDGET_S:.0f} s"},
            "cpu_baseline": {"value": v, "unit": "RHS/s", "cores": s["cores"], "kind": "oracle", "sample": s["sample"],
-                            "per_operator_s": s["per_operator_s"]},
+                            "per_operator_s": probe["per_operator_s"],
+                            "one_core": {"value": probe["value"], "cores": 1,
+                                         "seconds_per_iteration": probe["seconds_per_iteration"]}},
            "e2e": {"value": v, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -627,6 +758,10 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=0.0,
                     help="seconds of arrivals per rate (serving benchmark; default 20)")
     ap.add_argument("--no-serving", action="store_true", help="skip the short serving run of the default bench")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the batched 32^3x64 sub-measurement of the default bench")
+    ap.add_argument("--large-steps", type=int, default=2,
+                    help="timed steps (24 right-hand sides each) of the 32^3x64 sub-measurement")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven inner solves instead of captured graphs (for kernel-level profiling)")
     args = ap.parse_args()

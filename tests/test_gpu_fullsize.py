@@ -102,7 +102,7 @@ def test_batched_workload_32c64(dd):
     from oracle.wilson import WilsonOp, apply_at_sites
     w = bench.WORKLOADS["batched_32c64"]
     nb = w["nrhs"]
-    U, tv, _ = bench.inputs(w)
+    U, tv, _ = bench.inputs(w, with_rhs=False)
     m0 = bench.mass(w["mass"])
     csw = w["csw"]
     bc = (-1, 1, 1, 1)
