@@ -110,13 +110,19 @@ def whole_job_rate(rhs_per_rank_step, steps, world, max_seconds):
     return rhs_per_rank_step * steps * world / max_seconds
 
 
-def inputs(w, rank=0, with_rhs=True):
+def inputs(w, rank=0, with_rhs=True, host_tv=False):
+    """Gauge field, setup start vectors and right-hand sides of a workload.
+
+    The library draws the setup's random start vectors itself from the workload's tv_seed
+    (tv is None then, and the params carry the seed); host_tv=True returns the same fields
+    as host arrays, drawn by synth's implementation of the same generator (for the oracle).
+    """
     import synth
     U = synth.su3_field(w["dims"], w["eps"], w["seed"])
     dims_l = [tuple(w["dims"])]
     for a in w["agg"]:
         dims_l.append(tuple(d // x for d, x in zip(dims_l[-1], a)))
-    tv = synth.random_test_vectors(dims_l, w["n_tv"], w["tv_seed"])
+    tv = synth.philox_test_vectors(dims_l, w["n_tv"], w["tv_seed"]) if host_tv else None
     if not with_rhs:
         return U, tv, None
     if "point_seed" in w:
@@ -317,7 +323,8 @@ def run_gpu(args, w):
     def params(precision):
         return dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
                                        mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
-                                       outer_restart=w["outer_restart"], precision=precision, max_rhs=nb)
+                                       outer_restart=w["outer_restart"], precision=precision, max_rhs=nb,
+                                       seed=w["tv_seed"])
 
     stream = torch.cuda.current_stream()
     setup_s = {}
@@ -457,11 +464,12 @@ def large_workload(dd, torch, stream, w, prec, steps, barrier):
     U, tv, rhs_h = inputs(w)
     p = dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
                                 mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
-                                outer_restart=w["outer_restart"], precision=prec, max_rhs=w["nrhs"])
+                                outer_restart=w["outer_restart"], precision=prec, max_rhs=w["nrhs"],
+                                seed=w["tv_seed"])
     t0 = time.perf_counter()
     h = dd.ddamg_setup(U, w["dims"], -1, mass(w["mass"]), w["csw"], p, tv)
     t_setup = time.perf_counter() - t0
-    del U, tv
+    del U
     dd.ddamg_set_stream(h, stream.cuda_stream)
     ncols = rhs_h.shape[0]
     rhs = torch.from_numpy(rhs_h).cuda()
@@ -498,7 +506,7 @@ def _oracle_worker(job):
     from oracle.krylov import fgmres
     from oracle.wilson import WilsonOp
     w = WORKLOADS[name]
-    U, tv, rhs = inputs(w, rank=worker)
+    U, tv, rhs = inputs(w, rank=worker, host_tv=True)
     op = WilsonOp.build(U, mass(w["mass"]), w["csw"], -1)
     p = omg.Params(levels=w["levels"], agg=tuple(w["agg"]), n_tv=tuple(w["n_tv"]),
                    sap_block=tuple(w["sap"]) + (None,), mr_steps=w["mr_steps"], nu=w["nu"], n_inv=0,
@@ -625,14 +633,10 @@ def run_reference(args, w):
 def serving_handle(dd, w, dims, max_rhs, seed):
     import synth
     U = synth.su3_field(dims, w["eps"], seed)
-    dims_l = [tuple(dims)]
-    for a in w["agg"]:
-        dims_l.append(tuple(d // x for d, x in zip(dims_l[-1], a)))
-    tv = synth.random_test_vectors(dims_l, w["n_tv"], seed + 100)
     p = dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
                                 mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
-                                outer_restart=w["outer_restart"], precision=2, max_rhs=max_rhs)
-    return dd.ddamg_setup(U, dims, -1, mass(w["mass"]), w["csw"], p, tv)
+                                outer_restart=w["outer_restart"], precision=2, max_rhs=max_rhs, seed=seed + 100)
+    return dd.ddamg_setup(U, dims, -1, mass(w["mass"]), w["csw"], p, None)
 
 
 def serving_run(dd, srv, hids, pools, rate, seconds, max_requests, rng, max_rhs_total):

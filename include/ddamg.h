@@ -71,6 +71,8 @@ typedef struct ddamg_params {
                                           on FP16 storage (links, clover term, P, coarse
                                           blocks; per-site / per-aggregate scales)        */
   int max_rhs;                         /* right-hand sides per batch                     */
+  uint64_t seed;                       /* seed of the random start vectors of Alg. 3 when
+                                          ddamg_setup draws them (tv_random = NULL)       */
 } ddamg_params;
 
 typedef struct ddamg_stats {
@@ -89,9 +91,18 @@ void ddamg_default_params(ddamg_params* p);
 
 /* Builds the hierarchy: imports the gauge field, builds the clover term
  * (c_sw), runs the initial setup (Alg. 3) and n_inv iterative setup phases
- * (Alg. 4).  tv_random[l] are the random start vectors of the setup:
- * tv_random[0] holds n_tv[0] fine fields; tv_random[l] (l >= 1) holds
- * max(0, n_tv[l] - n_tv[l-1]) level-l fields (may be NULL when that is 0).
+ * (Alg. 4).  Alg. 3 starts from random test vectors:
+ *   tv_random = NULL: the library draws them on the device from params.seed
+ *     (complex N(0,1) entries, independent real and imaginary parts): entry
+ *     (field j, lexicographic site x, dof k) of level l comes from Philox4x32-10
+ *     (Salmon et al., SC 2011) on counter (x, k, j, l) with key (seed mod 2^32,
+ *     seed div 2^32) and the Box-Muller transform of its two 53-bit uniforms;
+ *     level 0 draws fields j = 0..n_tv[0]-1, a level l >= 1 the fields
+ *     j = 0..n_tv[l]-n_tv[l-1]-1 that restriction does not provide.  Nothing is
+ *     staged through host memory.
+ *   otherwise tv_random[0] holds n_tv[0] fine fields (host or device) and
+ *     tv_random[l] (l >= 1) holds max(0, n_tv[l] - n_tv[l-1]) level-l fields
+ *     (may be NULL when that count is 0).
  * On success *out is a new handle.  Errors: ARG (geometry: extents must be
  * divisible by aggregates and SAP blocks, SAP block counts even or 1, coarsest
  * extents even), OOM, SINGULAR, CUDA. */

@@ -67,6 +67,7 @@ class DdamgParams(C.Structure):
         ("coarse_cycles", C.c_int),
         ("precision", C.c_int),
         ("max_rhs", C.c_int),
+        ("seed", C.c_uint64),
     ]
 
 
@@ -210,10 +211,14 @@ class Handle:
         return tuple(d), n.value, t.value
 
 
-def ddamg_setup(gauge, dims, bc_t, m0, csw, params: DdamgParams, tv_random) -> Handle:
+def ddamg_setup(gauge, dims, bc_t, m0, csw, params: DdamgParams, tv_random=None) -> Handle:
+    """tv_random = None: the library draws the setup's random vectors from params.seed."""
     d = (C.c_int * 4)(*[int(x) for x in dims])
-    ptrs = (C.c_void_p * MAX_LEVELS)(*[_ptr(t) if t is not None else None for t in tv_random] +
-                                     [None] * (MAX_LEVELS - len(tv_random)))
+    if tv_random is None:
+        ptrs = None
+    else:
+        ptrs = (C.c_void_p * MAX_LEVELS)(*[_ptr(t) if t is not None else None for t in tv_random] +
+                                         [None] * (MAX_LEVELS - len(tv_random)))
     out = C.c_void_p()
     _check(lib().ddamg_setup(_ptr(gauge), d, int(bc_t), float(m0), float(csw), C.byref(params), ptrs,
                             C.byref(out)))

@@ -141,6 +141,13 @@ void p_to_half(__half2* Ph, float* pscale, const cplx<double>* P, const Geom& g,
 // in-place CGS2 per aggregate and chirality of N fields (FP64); err set on rank deficiency
 void orthonormalise(cplx<double>* P, const Geom& g, bool fine, int n, int N, int* err, cudaStream_t st);
 
+// ---- random fields (setup) -----------------------------------------------------
+// nfields complex N(0,1) fields j0 .. j0+nfields-1 of `level` in that level's layout
+// (fine: [12][V], coarse: [V][n]), rstride complex elements apart: Philox4x32-10 on the
+// counter (lexicographic site, dof, field, level) under the 64-bit seed, then Box-Muller
+void draw_fields(cplx<double>* dst, const Geom& g, bool fine, int n, int nfields, int j0, int level, uint64_t seed,
+                 size_t rstride, cudaStream_t st);
+
 // ---- BLAS-1 (batched over rhs, rstride complex elements between rhs) ----------
 template <typename T>
 void blas_dot(cplx<double>* res, const cplx<T>* x, const cplx<T>* y, size_t len, int nrhs, size_t rstride,

@@ -1054,18 +1054,29 @@ void import_fields(ddamg_handle* h, Level& L, cplx<double>* dst, const double* s
   }
 }
 
+// Alg. 3 on level l and below.  tv_random = NULL: the random start vectors are drawn on the
+// device from params.seed (level 0: fields 0..N_0-1; level l: the fields beyond those that
+// restriction provides); otherwise they are the caller's host or device fields.
 void initial_setup_phase(ddamg_handle* h, int l, const double* const* tv_random) {
   Level& L = h->lv[l];
   if (l == 0) {
-    if (!tv_random || !tv_random[0]) fail(DDAMG_ERR_ARG, "random test vectors of level 0 missing");
-    import_fields(h, L, L.tv64, tv_random[0], L.N);
+    if (!tv_random) {
+      draw_fields(L.tv64, L.g, true, L.n, L.N, 0, 0, h->p.seed, L.vlen, h->st);
+    } else {
+      if (!tv_random[0]) fail(DDAMG_ERR_ARG, "random test vectors of level 0 missing");
+      import_fields(h, L, L.tv64, tv_random[0], L.N);
+    }
   } else {
     Level& U = h->lv[l - 1];
     const int take = L.N < U.N ? L.N : U.N;
     restrict_op<double>(L.tv64, U.tv64, U.P64, U.g, L.g, U.fine, U.n, U.N, take, U.vlen, L.vlen, L.n, h->st);
     if (L.N > take) {
-      if (!tv_random || !tv_random[l]) fail(DDAMG_ERR_ARG, "random test vectors of a coarse level missing");
-      import_fields(h, L, L.tv64 + (size_t)take * L.vlen, tv_random[l], L.N - take);
+      if (!tv_random) {
+        draw_fields(L.tv64 + (size_t)take * L.vlen, L.g, false, L.n, L.N - take, 0, l, h->p.seed, L.vlen, h->st);
+      } else {
+        if (!tv_random[l]) fail(DDAMG_ERR_ARG, "random test vectors of a coarse level missing");
+        import_fields(h, L, L.tv64 + (size_t)take * L.vlen, tv_random[l], L.N - take);
+      }
     }
   }
   sync(h);
@@ -1621,6 +1632,7 @@ void ddamg_default_params(ddamg_params* p) {
   p->coarse_cycles = 20;
   p->precision = 1;
   p->max_rhs = 1;
+  p->seed = 0;
 }
 
 const char* ddamg_last_error(void) { return g_err.c_str(); }

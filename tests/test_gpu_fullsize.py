@@ -49,7 +49,8 @@ def dd():
 def _params(dd, w, precision, max_rhs):
     return dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
                                    mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
-                                   outer_restart=w["outer_restart"], precision=precision, max_rhs=max_rhs)
+                                   outer_restart=w["outer_restart"], precision=precision, max_rhs=max_rhs,
+                                   seed=w["tv_seed"])
 
 
 def _sites(dims, n, seed, extra=()):
@@ -165,8 +166,8 @@ def test_four_level_workload_48c96(dd):
     p = _params(dd, w, 2, w["nrhs"])
     need = dd.ddamg_estimate_bytes(w["dims"], p)
     free = torch.cuda.mem_get_info()[0]
-    if need > 0.95 * free or _host_available_bytes() < 200e9:
-        pytest.skip(f"needs {need / 1e9:.0f} GB of {free / 1e9:.0f} GB free on the device and 200 GB on the host")
+    if need > 0.95 * free or _host_available_bytes() < 40e9:
+        pytest.skip(f"needs {need / 1e9:.0f} GB of {free / 1e9:.0f} GB free on the device and 40 GB on the host")
     U, tv, rhs = bench.inputs(w)
     m0 = bench.mass(w["mass"])
     t0 = time.perf_counter()
