@@ -133,17 +133,24 @@ enum {
   DDAMG_OPT_SAP_CLUSTER = 2,      /* 1 (default, where it fits): coarse-level SAP sweeps run one
                                      thread-block cluster per SAP block; 2, 4, 8 or 16: try that
                                      cluster size first; 0: one CTA per block */
-  DDAMG_OPT_HALF_STORAGE = 3      /* 1: the FP32 kernels read FP16 copies of the fine links and
+  DDAMG_OPT_HALF_STORAGE = 3,     /* 1: the FP32 kernels read FP16 copies of the fine links and
                                      clover term (no scale), of P (one FP32 scale per aggregate
                                      and chirality) and of the coarse blocks (one FP32 scale per
                                      site): q = round-to-nearest-even(x / s), s = max |Re|, |Im|
                                      of the group.  Default: 1 iff params.precision = 2.  The
                                      paper keeps FP32 storage; this is a storage format only
                                      (arithmetic stays FP32, the copies follow every rebuild). */
+  DDAMG_OPT_COARSE_TC = 4         /* batch kernels on FP16 storage (coarse stencil, restriction,
+                                     prolongation): -1 (default): autotuned per level (see
+                                     ddamg_autotune_times); 0: the per-right-hand-side / CUDA-core
+                                     kernels; 1..4: the tensor-core kernels with the k dimension
+                                     split over that many warp groups (and the batch
+                                     prolongation), where they fit */
 };
 int ddamg_set_option(ddamg_handle* h, int option, int value);
 /* Effective setting: GRAPHS 0/1; COARSEST_CLUSTER and SAP_CLUSTER the cluster size in use on the
- * coarsest level / on level 1 (FP32 path), 0 when the one-CTA kernels run; HALF_STORAGE 0/1. */
+ * coarsest level / on level 1 (FP32 path), 0 when the one-CTA kernels run; HALF_STORAGE 0/1;
+ * COARSE_TC the kernel in use on level 1 (0 CUDA cores, k >= 1 tensor cores with k-split k). */
 int ddamg_get_option(ddamg_handle* h, int option, int* value);
 
 /* ---- measurement ----------------------------------------------------------- */
@@ -195,6 +202,20 @@ int ddamg_krylov_steps(ddamg_handle* h, int level, int precision, long long* ste
  * clearing, but calls that overlap on the GPU (other streams or threads) race
  * on it. */
 int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double* x, int n, double* out);
+
+/* Autotuner of the kernels that read FP16 operator data for a whole batch (FP16 storage).
+ * kind DDAMG_TUNE_COARSE (levels >= 1): one coarse stencil application by the CUDA-core kernel (0)
+ *   and by the tensor-core kernel with k-split 1..4;
+ * kind DDAMG_TUNE_RESTRICT (level l -> l+1, l < L-1): the per-right-hand-side kernel (0) and the
+ *   tensor-core kernel with k-split 1..4 (P read once per batch);
+ * kind DDAMG_TUNE_PROLONG (level l+1 -> l): the per-right-hand-side kernel (0) and the kernel that
+ *   reads P once for the batch (1).
+ * ms[0..4] = milliseconds of one application of the handle's batch size per candidate (-1 where
+ * the candidate does not fit or was not timed); *chosen = the candidate in use.  The tuner runs at
+ * setup and when DDAMG_OPT_HALF_STORAGE or DDAMG_OPT_COARSE_TC is set; its choice holds for every
+ * batch size.  Errors: ARG. */
+enum { DDAMG_TUNE_COARSE = 0, DDAMG_TUNE_RESTRICT = 1, DDAMG_TUNE_PROLONG = 2 };
+int ddamg_autotune_times(ddamg_handle* h, int kind, int level, double* ms, int* chosen);
 
 /* ---- building blocks of the method, exposed for parity tests ------------ */
 

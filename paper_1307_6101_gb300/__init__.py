@@ -35,12 +35,13 @@ EXPORTED = (
     "ddamg_krylov_steps", "ddamg_residual_norm_noalloc", "ddamg_get_option",
     "ddamg_device_bytes", "ddamg_estimate_bytes", "ddamg_server_create", "ddamg_server_add",
     "ddamg_server_submit", "ddamg_server_poll", "ddamg_server_wait", "ddamg_server_free",
-    "ddamg_setup_times",
+    "ddamg_setup_times", "ddamg_autotune_times",
 )
 DDAMG_OPT_GRAPHS = 0
 DDAMG_OPT_COARSEST_CLUSTER = 1
 DDAMG_OPT_SAP_CLUSTER = 2
 DDAMG_OPT_HALF_STORAGE = 3
+DDAMG_OPT_COARSE_TC = 4
 SETUP_KINDS = ("smooth", "kcycle", "rebuild")   # DDAMG_SETUP_* order
 PROF_KINDS = {"fine_sap": 0, "fine_dslash": 1, "coarse_apply": 2, "coarse_sap": 3, "transfer": 4, "precond": 5,
               "outer_ortho": 6}
@@ -118,6 +119,7 @@ def _load():
     sp = C.POINTER(C.c_size_t)
     lib.ddamg_device_bytes.argtypes = [vp, sp]
     lib.ddamg_setup_times.argtypes = [vp, C.POINTER(C.c_double), ip]
+    lib.ddamg_autotune_times.argtypes = [vp, ip, ip, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.ddamg_estimate_bytes.argtypes = [C.POINTER(C.c_int), C.POINTER(DdamgParams), sp]
     lib.ddamg_server_create.argtypes = [C.c_size_t, C.POINTER(vp)]
     lib.ddamg_server_add.argtypes = [vp, vp, C.POINTER(C.c_int)]
@@ -329,6 +331,18 @@ def ddamg_setup_times(h):
     buf = (C.c_double * n)()
     _check(lib().ddamg_setup_times(h.raw, buf, n))
     return [dict(zip(SETUP_KINDS, buf[l * len(SETUP_KINDS):(l + 1) * len(SETUP_KINDS)])) for l in range(MAX_LEVELS)]
+
+
+TUNE_KINDS = {"coarse": 0, "restrict": 1, "prolong": 2}
+
+
+def ddamg_autotune_times(h, kind, level):
+    """(ms per candidate, -1 where not timed; the candidate in use) of an autotuned kernel class."""
+    ms = (C.c_double * 5)()
+    ch = C.c_int()
+    k = TUNE_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().ddamg_autotune_times(h.raw, k, int(level), ms, C.byref(ch)))
+    return list(ms), ch.value
 
 
 def ddamg_device_bytes(h):

@@ -678,6 +678,13 @@ void coarse_apply(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const Coars
   const int threads = ((9 * op.n + 31) / 32) * 32;
   const size_t sm = (size_t)18 * op.n * sizeof(cplx<T>);
   dim3 grid(op.g.V, nrhs);
+  if constexpr (sizeof(T) == 4) {
+    // the whole operator on FP16 storage: the tensor-core kernel where the autotuner chose it
+    if (op.blkh && op.tc_ks > 0 && sel == SEL_FULL && in_chir < 0) {
+      if (coarse_apply_tc(out, in, b, op, nrhs, rstride, op.tc_ks, st) == cudaSuccess) return;
+      cudaGetLastError();
+    }
+  }
   count_launch();
   if constexpr (sizeof(T) == 4) {
     if (op.blkh) {

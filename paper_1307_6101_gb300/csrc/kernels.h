@@ -38,6 +38,9 @@ struct CoarseOp {
   // FP16 storage (FP32 compute only): blocks and one scale per site
   const __half2* blkh = nullptr;
   const float* bscale = nullptr;
+  // full applications on FP16 storage: 0 = CUDA-core kernel, k >= 1 = tensor-core kernel with the
+  // k-dimension split over k warp groups (chosen per level by the autotuner)
+  int tc_ks = 0;
 };
 
 // ---- fine level -----------------------------------------------------------
@@ -68,6 +71,12 @@ void fine_export(cplx<double>* dst, const cplx<T>* src, const Geom& g, int nrhs,
 template <typename T>
 void coarse_apply(cplx<T>* out, const cplx<T>* in, const cplx<T>* b, const CoarseOp<T>& op, int nrhs,
                   size_t rstride, int sel, int sel_mu, int in_chir, cudaStream_t st);
+// tensor-core coarse stencil on FP16 blocks (whole operator, any batch; see coarse_tc.cu):
+// cudaErrorInvalidValue (nothing launched) when the configuration does not fit
+cudaError_t coarse_apply_tc(cplx<float>* out, const cplx<float>* in, const cplx<float>* b, const CoarseOp<float>& op,
+                            int nrhs, size_t rstride, int ks, cudaStream_t st);
+bool coarse_tc_fits(int n, int ks);
+size_t coarse_tc_smem(int n, int ks);
 // cudaErrorInvalidConfiguration (nothing launched) when a SAP block exceeds what one CTA can hold
 template <typename T>
 cudaError_t coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks,
@@ -127,15 +136,25 @@ cudaError_t coarsest_cluster_solve(cplx<T>* x, const cplx<T>* b, const CoarseOp<
 // ---- transfer ---------------------------------------------------------------
 // out(A)[s*N + j] = sum_{x in A, f in s} conj(P_j(x, f)) in(x, f)
 // (Ph, pscale): optional FP16 copy of P with per-(aggregate, chirality) scales (FP32 compute only)
+// tc_ks >= 1 (FP32 compute on FP16 P only): the tensor-core kernel with that k-split, P read once
+// per batch (transfer_tc.cu)
 template <typename T>
 void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine,
                  int n, int N, int nrhs, size_t in_rstride, size_t out_rstride, size_t out_site_stride,
-                 cudaStream_t st, const __half2* Ph = nullptr, const float* pscale = nullptr);
+                 cudaStream_t st, const __half2* Ph = nullptr, const float* pscale = nullptr, int tc_ks = 0);
 // out(x, f) = [out +] sum_j P_j(x, f) in(A(x))[s(f)*N + j]
+// batch != 0 (FP32 compute on FP16 P only): one CTA per aggregate for the whole batch (P read once)
 template <typename T>
 void prolong_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine, int n,
                 int N, int nrhs, size_t out_rstride, size_t in_rstride, bool accumulate, cudaStream_t st,
-                const __half2* Ph = nullptr, const float* pscale = nullptr);
+                const __half2* Ph = nullptr, const float* pscale = nullptr, int batch = 0);
+cudaError_t restrict_tc(cplx<float>* out, const cplx<float>* in, const __half2* Ph, const float* pscale,
+                        const Geom& gf, const Geom& gc, bool fine, int n, int N, int nrhs, size_t in_rstride,
+                        size_t out_rstride, size_t out_site_stride, int ks, cudaStream_t st);
+bool restrict_tc_fits(int N, int ks);
+cudaError_t prolong_batch(cplx<float>* out, const cplx<float>* in, const __half2* Ph, const float* pscale,
+                          const Geom& gf, const Geom& gc, bool fine, int n, int N, int nrhs, size_t out_rstride,
+                          size_t in_rstride, bool accumulate, cudaStream_t st);
 void p_to_half(__half2* Ph, float* pscale, const cplx<double>* P, const Geom& g, bool fine, int n, int N,
                cudaStream_t st);
 // in-place CGS2 per aggregate and chirality of N fields (FP64); err set on rank deficiency

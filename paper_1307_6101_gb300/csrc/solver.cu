@@ -87,6 +87,8 @@ struct Level {
   int* bsite = nullptr;       // coarse levels: [nBlk][vB] site of each SAP block's sites (block-local order)
   int* bloc = nullptr;        // coarse levels: [V] position of each site inside its SAP block
   bool eo = true;             // coarsest level: odd-even solve possible (even extents)
+  int tr_ks = 0;              // restriction to l+1 on FP16 P: 0 per-rhs kernel, k tensor cores with k-split k
+  int pr_batch = 0;           // prolongation from l+1 on FP16 P: 1 = the batch kernel (P read once)
   Work<double> w64;
   Work<float> w32;
 };
@@ -170,6 +172,10 @@ struct ddamg_handle {
   // FP16 storage of links, clover term, P and coarse blocks under FP32 arithmetic
   bool half = false;
   bool work_ready[2] = {false, false};   // Work<double>, Work<float> allocated on every level
+  // autotuner of the coarse stencil kernels: milliseconds per application at the batch size for
+  // [level][candidate] (candidate 0 = CUDA-core kernel, k = tensor cores with k-split k; -1 = not run)
+  double tune_ms[3][DDAMG_MAX_LEVELS][5] = {};   // [DDAMG_TUNE_*][level][candidate]
+  int tc_force = -1;   // DDAMG_OPT_COARSE_TC: -1 autotune, 0 CUDA cores, k >= 1 that split
   // coarsest level on a thread-block cluster
   bool use_cluster = true;
   CoarsestGeo cgeo;
@@ -338,7 +344,7 @@ void restrict_lv(ddamg_handle* h, int l, cplx<T>* out, const cplx<T>* in, int nr
   const double ps = hf ? 4.0 : cs;
   Prof pr(h, DDAMG_PROF_TRANSFER, (double)F.vlen * (cs * nrhs + ps * F.N) + (double)C.vlen * cs * nrhs);
   restrict_op<T>(out, in, Pptr<T>(F), F.g, C.g, F.fine, F.n, F.N, nrhs, F.vlen, C.vlen, C.n, h->st,
-                 hf ? F.Ph : nullptr, hf ? F.pscale : nullptr);
+                 hf ? F.Ph : nullptr, hf ? F.pscale : nullptr, hf ? F.tr_ks : 0);
 }
 
 template <typename T>
@@ -351,7 +357,7 @@ void prolong_lv(ddamg_handle* h, int l, cplx<T>* out, const cplx<T>* in, int nrh
   Prof pr(h, DDAMG_PROF_TRANSFER,
           (double)F.vlen * (cs * nrhs * (acc ? 2 : 1) + ps * F.N) + (double)C.vlen * cs * nrhs);
   prolong_op<T>(out, in, Pptr<T>(F), F.g, C.g, F.fine, F.n, F.N, nrhs, F.vlen, C.vlen, acc, h->st,
-                hf ? F.Ph : nullptr, hf ? F.pscale : nullptr);
+                hf ? F.Ph : nullptr, hf ? F.pscale : nullptr, hf ? F.pr_batch : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -940,6 +946,92 @@ void half_bind(ddamg_handle* h) {
     } else {
       L.c32.blkh = h->half ? L.blkh : nullptr;
       L.c32.bscale = h->half ? L.bscale : nullptr;
+    }
+  }
+}
+
+// Autotuner of the kernels that read FP16 operator data for a whole batch: on every level, time
+// each candidate kernel for one application of the handle's batch size (after a warm-up, CUDA
+// events on the library stream) and keep the fastest:
+//   coarse stencil (levels >= 1): CUDA-core kernel (0), tensor cores with k-split 1..4;
+//   restriction l -> l+1: per-right-hand-side kernel (0), tensor cores with k-split 1..4;
+//   prolongation l+1 -> l: per-right-hand-side kernel (0), one CTA per aggregate for the batch (1).
+// The choice is made once per level and used for every batch size, so a right-hand side keeps the
+// same bits alone and inside a batch.  Timing does not depend on the operand values.
+template <class Run>
+int time_candidates(ddamg_handle* h, double* ms_out, int ncand, Run run) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 0;
+  double best_ms = 1e300;
+  for (int k = 0; k < ncand; ++k) {
+    ms_out[k] = -1.0;
+    if (!run(k, true)) continue;   // warm-up; false: the candidate does not fit
+    constexpr int reps = 5;
+    CK(cudaEventRecord(e0, h->st));
+    for (int q = 0; q < reps; ++q) run(k, false);
+    CK(cudaEventRecord(e1, h->st));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaGetLastError());
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms_out[k] = ms / reps;
+    if (ms / reps < best_ms) {
+      best_ms = ms / reps;
+      best = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+void tune_kernels(ddamg_handle* h) {
+  const int B = h->max_batch;
+  for (int l = 0; l < h->L; ++l) {
+    Level& L = h->lv[l];
+    for (int t = 0; t < 3; ++t)
+      for (int k = 0; k < 5; ++k) h->tune_ms[t][l][k] = -1.0;
+    L.c32.tc_ks = 0;
+    L.tr_ks = 0;
+    L.pr_batch = 0;
+    if (!h->half) continue;
+    if (h->tc_force >= 0) {
+      const int f = h->tc_force;
+      if (!L.fine) L.c32.tc_ks = (f > 0 && coarse_tc_fits(L.n, f)) ? f : 0;
+      if (!L.coarsest) {
+        L.tr_ks = (f > 0 && restrict_tc_fits(L.N, f)) ? f : 0;
+        L.pr_batch = f > 0 ? 1 : 0;
+      }
+      continue;
+    }
+    Work<float>& w = work<float>(L);
+    blas_zero<float>(w.gin, L.vlen, B, L.vlen, h->st);
+    if (!L.fine) {
+      CoarseOp<float>& op = L.c32;
+      op.tc_ks = time_candidates(h, h->tune_ms[DDAMG_TUNE_COARSE][l], 5, [&](int k, bool) {
+        if (k > 0 && !coarse_tc_fits(L.n, k)) return false;
+        op.tc_ks = k;
+        coarse_apply<float>(w.gout, w.gin, nullptr, op, B, L.vlen, SEL_FULL, 0, -1, h->st);
+        return true;
+      });
+    }
+    if (!L.coarsest) {
+      Level& C = h->lv[l + 1];
+      Work<float>& wc = work<float>(C);
+      L.tr_ks = time_candidates(h, h->tune_ms[DDAMG_TUNE_RESTRICT][l], 5, [&](int k, bool) {
+        if (k > 0 && !restrict_tc_fits(L.N, k)) return false;
+        restrict_op<float>(wc.bc, w.gin, L.P32, L.g, C.g, L.fine, L.n, L.N, B, L.vlen, C.vlen, C.n, h->st, L.Ph,
+                           L.pscale, k);
+        return true;
+      });
+      blas_zero<float>(wc.bc, C.vlen, B, C.vlen, h->st);
+      L.pr_batch = time_candidates(h, h->tune_ms[DDAMG_TUNE_PROLONG][l], 2, [&](int k, bool) {
+        prolong_op<float>(w.gout, wc.bc, L.P32, L.g, C.g, L.fine, L.n, L.N, B, L.vlen, C.vlen, false, h->st, L.Ph,
+                          L.pscale, k);
+        return true;
+      });
     }
   }
 }
@@ -1681,6 +1773,7 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
       half_alloc(h);
       half_refresh_fine(h);
       half_bind(h);
+      tune_kernels(h);
     }
     sync(h);
     initial_setup_phase(h, 0, tv_random);
@@ -1803,6 +1896,14 @@ int ddamg_set_option(ddamg_handle* h, int option, int value) {
       }
       h->half = value != 0;
       half_bind(h);
+      ensure_work<float>(h);
+      tune_kernels(h);
+      free_graphs(h);
+    } else if (option == DDAMG_OPT_COARSE_TC) {
+      if (value < -1 || value > 4) fail(DDAMG_ERR_ARG, "coarse tensor-core option must be -1..4");
+      h->tc_force = value;
+      ensure_work<float>(h);
+      tune_kernels(h);
       free_graphs(h);
     } else {
       fail(DDAMG_ERR_ARG, "unknown option");
@@ -1821,6 +1922,8 @@ int ddamg_get_option(ddamg_handle* h, int option, int* value) {
       *value = h->L > 2 ? h->lv[1].c32.sap_cls : 0;
     } else if (option == DDAMG_OPT_HALF_STORAGE) {
       *value = h->half ? 1 : 0;
+    } else if (option == DDAMG_OPT_COARSE_TC) {
+      *value = h->L > 1 ? h->lv[1].c32.tc_ks : 0;
     } else {
       fail(DDAMG_ERR_ARG, "unknown option");
     }
@@ -1896,6 +1999,18 @@ int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double
     return rc == -1 ? DDAMG_ERR_ARG : DDAMG_ERR_CUDA;
   }
   return DDAMG_OK;
+}
+
+int ddamg_autotune_times(ddamg_handle* h, int kind, int level, double* ms, int* chosen) {
+  return guard([&] {
+    Level& L = level_of(h, level);
+    if (kind < 0 || kind > 2) fail(DDAMG_ERR_ARG, "unknown autotuned kernel");
+    if (kind == DDAMG_TUNE_COARSE && L.fine) fail(DDAMG_ERR_ARG, "the coarse stencil runs on levels >= 1");
+    if (kind != DDAMG_TUNE_COARSE && L.coarsest) fail(DDAMG_ERR_ARG, "no transfer below the coarsest level");
+    if (ms)
+      for (int k = 0; k < 5; ++k) ms[k] = h->tune_ms[kind][level][k];
+    if (chosen) *chosen = kind == DDAMG_TUNE_COARSE ? L.c32.tc_ks : (kind == DDAMG_TUNE_RESTRICT ? L.tr_ks : L.pr_batch);
+  });
 }
 
 int ddamg_level_info(ddamg_handle* h, int level, int dims[4], int* ndof, int* ntv) {

@@ -249,7 +249,16 @@ void p_to_half(__half2* Ph, float* pscale, const cplx<double>* P, const Geom& g,
 template <typename T>
 void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine, int n,
                  int N, int nrhs, size_t in_rstride, size_t out_rstride, size_t out_site_stride, cudaStream_t st,
-                 const __half2* Ph, const float* pscale) {
+                 const __half2* Ph, const float* pscale, int tc_ks) {
+  if constexpr (sizeof(T) == 4) {
+    // FP16 P: the tensor-core kernel (P read once per batch) where the autotuner chose it
+    if (Ph && tc_ks > 0) {
+      if (restrict_tc(out, in, Ph, pscale, gf, gc, fine, n, N, nrhs, in_rstride, out_rstride, out_site_stride, tc_ks,
+                      st) == cudaSuccess)
+        return;
+      cudaGetLastError();
+    }
+  }
   const size_t pstride = (size_t)gf.V * n;
   int S = 1;   // lanes per column group: a power of two >= the aggregate volume, at most 256
   while (S < gf.vA && S < 256) S *= 2;
@@ -282,7 +291,16 @@ void restrict_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& 
 template <typename T>
 void prolong_op(cplx<T>* out, const cplx<T>* in, const cplx<T>* P, const Geom& gf, const Geom& gc, bool fine, int n,
                 int N, int nrhs, size_t out_rstride, size_t in_rstride, bool accumulate, cudaStream_t st,
-                const __half2* Ph, const float* pscale) {
+                const __half2* Ph, const float* pscale, int batch) {
+  if constexpr (sizeof(T) == 4) {
+    // FP16 P: one CTA per aggregate for the whole batch (P read once) where the autotuner chose it
+    if (Ph && batch) {
+      if (prolong_batch(out, in, Ph, pscale, gf, gc, fine, n, N, nrhs, out_rstride, in_rstride, accumulate, st) ==
+          cudaSuccess)
+        return;
+      cudaGetLastError();
+    }
+  }
   const size_t pstride = (size_t)gf.V * n;
   const size_t tot = (size_t)gf.V * n;
   count_launch();
@@ -305,9 +323,9 @@ void orthonormalise(cplx<double>* P, const Geom& g, bool fine, int n, int N, int
 
 #define INST(T)                                                                                                  \
   template void restrict_op<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const Geom&, const Geom&, bool, int, int, \
-                               int, size_t, size_t, size_t, cudaStream_t, const __half2*, const float*);        \
+                               int, size_t, size_t, size_t, cudaStream_t, const __half2*, const float*, int);   \
   template void prolong_op<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const Geom&, const Geom&, bool, int, int,  \
-                              int, size_t, size_t, bool, cudaStream_t, const __half2*, const float*);
+                              int, size_t, size_t, bool, cudaStream_t, const __half2*, const float*, int);
 INST(float)
 INST(double)
 #undef INST
