@@ -64,6 +64,7 @@ class Params:
     coarse_tol: float = 5e-2
     coarse_restart: int = 50
     coarse_cycles: int = 20
+    fine_sap_schur: bool = False   # fine-level SAP blocks solved on their even-odd Schur complement
 
 
 @dataclass
@@ -98,7 +99,8 @@ class Hierarchy:
     # --- construction of one level ------------------------------------------------
     def _make_sap(self, l):
         lev = self.levels[l]
-        lev.sap = SAP(lev.op, red_black_block(lev.op.dims, self.p.sap_block[l]), self.p.mr_steps)
+        lev.sap = SAP(lev.op, red_black_block(lev.op.dims, self.p.sap_block[l]), self.p.mr_steps,
+                      schur=(l == 0 and self.p.fine_sap_schur))
 
     def rebuild(self, l):
         """Construct P_l from the test vectors of level l and set D_{l+1} = P_l^+ D_l P_l."""
