@@ -73,6 +73,11 @@ typedef struct ddamg_params {
   int max_rhs;                         /* right-hand sides per batch                     */
   uint64_t seed;                       /* seed of the random start vectors of Alg. 3 when
                                           ddamg_setup draws them (tv_random = NULL)       */
+  int sap_schur;                       /* 1: the FP32 preconditioner's fine-level SAP solves
+                                          each block on its even-odd Schur complement (MR on
+                                          Dhat_B = D_ee - D_eo D_oo^-1 D_oe, then the odd
+                                          back-substitution; needs 4^4 SAP blocks); 0: MR on
+                                          D_B (the paper does not say which)              */
 } ddamg_params;
 
 typedef struct ddamg_stats {
@@ -140,12 +145,14 @@ enum {
                                      of the group.  Default: 1 iff params.precision = 2.  The
                                      paper keeps FP32 storage; this is a storage format only
                                      (arithmetic stays FP32, the copies follow every rebuild). */
-  DDAMG_OPT_COARSE_TC = 4         /* batch kernels on FP16 storage (coarse stencil, restriction,
+  DDAMG_OPT_COARSE_TC = 4,        /* batch kernels on FP16 storage (coarse stencil, restriction,
                                      prolongation): -1 (default): autotuned per level (see
                                      ddamg_autotune_times); 0: the per-right-hand-side / CUDA-core
                                      kernels; 1..4: the tensor-core kernels with the k dimension
                                      split over that many warp groups (and the batch
                                      prolongation), where they fit */
+  DDAMG_OPT_SAP_SCHUR = 5         /* 0/1: params.sap_schur switched after setup (the per-site
+                                     inverse tables are built on first use)            */
 };
 int ddamg_set_option(ddamg_handle* h, int option, int value);
 /* Effective setting: GRAPHS 0/1; COARSEST_CLUSTER and SAP_CLUSTER the cluster size in use on the

@@ -42,6 +42,7 @@ DDAMG_OPT_COARSEST_CLUSTER = 1
 DDAMG_OPT_SAP_CLUSTER = 2
 DDAMG_OPT_HALF_STORAGE = 3
 DDAMG_OPT_COARSE_TC = 4
+DDAMG_OPT_SAP_SCHUR = 5
 SETUP_KINDS = ("smooth", "kcycle", "rebuild")   # DDAMG_SETUP_* order
 PROF_KINDS = {"fine_sap": 0, "fine_dslash": 1, "coarse_apply": 2, "coarse_sap": 3, "transfer": 4, "precond": 5,
               "outer_ortho": 6}
@@ -69,6 +70,7 @@ class DdamgParams(C.Structure):
         ("precision", C.c_int),
         ("max_rhs", C.c_int),
         ("seed", C.c_uint64),
+        ("sap_schur", C.c_int),
     ]
 
 

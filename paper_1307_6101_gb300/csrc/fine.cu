@@ -881,6 +881,335 @@ __global__ void k_clover_build(double* __restrict__ clov, const cd* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Inverse of the site-diagonal part A(x) = (m0 + 4) + C(x) on the fine level: per site and
+// chirality a Hermitian 6x6 block, factored A = L D L^+ (L unit lower triangular, D real) in
+// FP64 and inverted column by column (forward and back substitution).  Output in the packed
+// Hermitian layout of the clover term.  A vanishing or non-finite pivot sets *err.
+__global__ void k_clover_inverse(double* __restrict__ inv, const double* __restrict__ clov, int V, int* err) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)2 * V) return;
+  const int ch = (int)(t / V), x = (int)(t - (size_t)ch * V);
+  const double* a = clov + (size_t)ch * 36 * V + x;
+  cd A[6][6];
+  for (int i = 0; i < 6; ++i) A[i][i] = cmk(a[(size_t)i * V], 0.0);
+  for (int i = 0; i < 6; ++i)
+    for (int j = i + 1; j < 6; ++j) {
+      const int p = 6 + 2 * herm_off(i, j);
+      A[i][j] = cmk(a[(size_t)p * V], a[(size_t)(p + 1) * V]);
+      A[j][i] = cconj(A[i][j]);
+    }
+  // L D L^+ : column j of L below the diagonal and D_j
+  cd L[6][6];
+  double Dg[6];
+  for (int j = 0; j < 6; ++j) {
+    double d = A[j][j].re;
+    for (int k = 0; k < j; ++k) d -= Dg[k] * cnorm2(L[j][k]);
+    if (!(fabs(d) > 1e-300) || !isfinite(d)) {
+      atomicExch(err, 1);
+      return;
+    }
+    Dg[j] = d;
+    for (int i = j + 1; i < 6; ++i) {
+      cd s = A[i][j];
+      for (int k = 0; k < j; ++k) s = s - Dg[k] * (L[i][k] * cconj(L[j][k]));
+      L[i][j] = (1.0 / d) * s;
+    }
+  }
+  // X = A^{-1}: solve L y = e_c, then D, then L^+ x = y, for each column c
+  cd X[6][6];
+  for (int c = 0; c < 6; ++c) {
+    cd y[6];
+    for (int i = 0; i < 6; ++i) {
+      cd s = cmk(i == c ? 1.0 : 0.0, 0.0);
+      for (int k = 0; k < i; ++k) s = s - L[i][k] * y[k];
+      y[i] = s;
+    }
+    for (int i = 0; i < 6; ++i) y[i] = (1.0 / Dg[i]) * y[i];
+    for (int i = 5; i >= 0; --i) {
+      cd s = y[i];
+      for (int k = i + 1; k < 6; ++k) s = s - cconj(L[k][i]) * X[k][c];
+      X[i][c] = s;
+    }
+  }
+  double* o = inv + (size_t)ch * 36 * V + x;
+  for (int i = 0; i < 6; ++i) o[(size_t)i * V] = X[i][i].re;
+  for (int i = 0; i < 6; ++i)
+    for (int j = i + 1; j < 6; ++j) {
+      const int p = 6 + 2 * herm_off(i, j);
+      o[(size_t)p * V] = X[i][j].re;
+      o[(size_t)(p + 1) * V] = X[i][j].im;
+    }
+}
+
+// Per-site tables read by the Schur SAP kernel: the clover term on even sites, the inverse of
+// A(x) on odd sites.  FP32: [2][36][V] reals (even sites with the (m0 + 4) shift, as the FP32
+// clover); FP16: [2][18][V] pairs of reals (even sites without the shift, as the FP16 clover).
+__global__ void k_clover_mix32(float* __restrict__ mix, const double* __restrict__ clov,
+                               const double* __restrict__ inv, Geom g) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)72 * g.V) return;
+  const int x = (int)(i % g.V);
+  int c[4];
+  geom_coords(g, x, c);
+  mix[i] = (float)(geom_parity(c) ? inv[i] : clov[i]);
+}
+
+__global__ void k_clover_mix_half(__half2* __restrict__ mix, const double* __restrict__ clov,
+                                  const double* __restrict__ inv, Geom g, double shift) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)36 * g.V) return;
+  const int row = (int)(i / g.V), x = (int)(i - (size_t)row * g.V);
+  const int ch = row / 18, p = 2 * (row - 18 * ch);
+  int c[4];
+  geom_coords(g, x, c);
+  const bool odd = geom_parity(c) != 0;
+  const double* src = odd ? inv : clov;
+  const double sh = odd ? 0.0 : shift;
+  const double a0 = src[(size_t)(ch * 36 + p) * g.V + x], a1 = src[(size_t)(ch * 36 + p + 1) * g.V + x];
+  mix[i] = __halves2half2(__double2half(p < 6 ? a0 - sh : a0), __double2half(p + 1 < 6 ? a1 - sh : a1));
+}
+
+// ---------------------------------------------------------------------------
+// SAP colour sweep for 4^4 blocks with each block solved on its even-odd Schur complement
+// (the block solve of the oracle's schur reading): with D = A - H/2 (A the site-diagonal part,
+// H the hop sum) and H^B the hops that stay inside the block,
+//   t_o   = A_o^{-1} rho_o = A_o^{-1} (b_o + H z / 2) - z_o
+//   r_e   = rhohat_e = rho_e + H^B t_o / 2
+//   k MR steps on  Dhat r = A_e r - H^B A_o^{-1} H^B r / 4   (alpha per block over even sites)
+//   x_o   = t_o + A_o^{-1} H^B x_e / 2
+// so no step needs A on odd sites: the staged per-site table holds A's clover term on even
+// sites and A^{-1} on odd sites.  One CTA of 128 threads per block; thread t owns the two
+// x-neighbours 2t, 2t+1 of the block (one even, one odd site), so every warp works on one parity
+// at a time.  Staging and bounded waits as in the kernel above; the residual buffer Rs holds z,
+// then r on even and the odd-site temporaries on odd sites; Ts holds t_o.
+template <typename LS, typename CS>
+__global__ void __launch_bounds__(128, 2) k_fine_sap_b4_eo(cplx<float>* __restrict__ z,
+                                                        const cplx<float>* __restrict__ bsrc,
+                                                        const LS* __restrict__ U, const CS* __restrict__ mix,
+                                                        Geom g, int bc_t, size_t rstride, int nrhs,
+                                                        const int* __restrict__ blocks, int k_mr, int* err,
+                                                        float shift) {
+  using C = cplx<float>;
+  constexpr int VB = 256;
+  constexpr int CR = 2 * ClovRows<CS>::per_chir;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LS* Ls = reinterpret_cast<LS*>(smem_raw);                       // [36][VB]
+  CS* Cs = reinterpret_cast<CS*>(Ls + 36 * VB);                   // [CR][VB]
+  C* Rs = reinterpret_cast<C*>(Cs + CR * VB);                     // [12][VB]
+  C* Ts = Rs + 12 * VB;                                           // [12][128]: t_o of thread t
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(Ts + 12 * 128);
+  float* scratch = reinterpret_cast<float*>(bar + 2);             // [2][4 warps][3]
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int blk = blocks[blockIdx.x];
+  const int V = g.V;
+  const int la = 2 * t;
+  const int pa = (((la >> 6) & 3) + ((la >> 4) & 3) + ((la >> 2) & 3)) & 1;   // la & 3 is 0 or 2
+  const int le = la + pa, lo = la + 1 - pa;                                     // even, odd site
+  const int xe = blk * VB + le, xo = blk * VB + lo;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&bar[0], (unsigned)(VB * (36 * sizeof(LS) + CR * sizeof(CS))));
+      mbar_arrive_expect_tx(&bar[1], (unsigned)(12 * VB * sizeof(C)));
+    }
+    __syncwarp();
+    for (int cpy = lane; cpy < 36 + CR + 12; cpy += 32) {
+      if (cpy < 36)
+        bulk_g2s(Ls + (size_t)cpy * VB, U + (size_t)cpy * V + (size_t)blk * VB, VB * sizeof(LS), &bar[0]);
+      else if (cpy < 36 + CR)
+        bulk_g2s(Cs + (size_t)(cpy - 36) * VB, mix + (size_t)(cpy - 36) * V + (size_t)blk * VB, VB * sizeof(CS),
+                 &bar[0]);
+      else
+        bulk_g2s(Rs + (size_t)(cpy - 36 - CR) * VB, z + (size_t)(cpy - 36 - CR) * V + (size_t)blk * VB,
+                 VB * sizeof(C), &bar[1]);
+    }
+  }
+  // geometry of the two sites: internal-hop masks and the time-boundary signs
+  int ce[4], co[4];
+  geom_coords(g, xe, ce);
+  geom_coords(g, xo, co);
+  auto inmask_of = [&](int l) {
+    unsigned m = 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const int q = (l >> (6 - 2 * mu)) & 3;
+      const bool wrap = g.L[mu] == 4;
+      if (q < 3 || wrap) m |= 1u << (2 * mu);
+      if (q > 0 || wrap) m |= 1u << (2 * mu + 1);
+    }
+    return m;
+  };
+  const unsigned im_e = inmask_of(le), im_o = inmask_of(lo);
+  const bool ntf_e = bc_t < 0 && ce[0] == g.L[0] - 1, ntb_e = bc_t < 0 && ce[0] == 0;
+  const bool ntf_o = bc_t < 0 && co[0] == g.L[0] - 1, ntb_o = bc_t < 0 && co[0] == 0;
+  auto slot = [](int l, int mu, bool fwd) {
+    const int st = 1 << (6 - 2 * mu);
+    const int q = (l >> (6 - 2 * mu)) & 3;
+    return fwd ? (q < 3 ? l + st : l - 3 * st) : (q > 0 ? l - st : l + 3 * st);
+  };
+  C nb[12], u[9];
+  // acc = sum of the hops of site l (at x, coordinates c) that stay in the block, from Rs
+  auto hops_in = [&](int l, unsigned inm, bool ntf, bool ntb, C acc[12]) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = czero<float>();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int mu = k >> 1;
+      const bool fwd = (k & 1) == 0;
+      if (inm & (1u << k)) {
+        const bool neg = mu == 0 && (fwd ? ntf : ntb);
+        const int sl = slot(l, mu, fwd);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          const C v = Rs[q * VB + sl];
+          nb[q] = cmk<float>(sign_flip(v.re, neg), sign_flip(v.im, neg));
+        }
+        const int ls = fwd ? l : sl;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) u[q] = ld_cplx(Ls, (size_t)((mu * 9 + q) * VB + ls));
+        hop_accumulate(mu, fwd, u, nb, acc);
+      }
+    }
+  };
+  // acc = H z at site l: internal hops from Rs, the others from global z and links
+  auto hops_all = [&](const C* pz, int l, int x, const int* c, unsigned inm, bool ntf, bool ntb, C acc[12]) {
+    hops_in(l, inm, ntf, ntb, acc);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int mu = k >> 1;
+      const bool fwd = (k & 1) == 0;
+      if (!(inm & (1u << k))) {
+        const bool neg = mu == 0 && (fwd ? ntf : ntb);
+        const int n = geom_neighbor(g, c, mu, fwd ? +1 : -1);
+        load_spinor(pz, V, n, nb, neg ? -1.f : 1.f, -1);
+        if (fwd) {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) u[q] = ld_cplx(Ls, (size_t)((mu * 9 + q) * VB + l));
+        } else {
+          load_link(U, V, mu, n, u);
+        }
+        hop_accumulate(mu, fwd, u, nb, acc);
+      }
+    }
+  };
+  bool ok = __syncthreads_and(mbar_wait_bounded(&bar[0], 0) ? 1 : 0);
+  C re[12], xe_[12], p[12], acc[12];
+  int zphase = 0;
+  for (int rh = 0; rh < nrhs && ok; ++rh) {
+    C* pz = z + (size_t)rh * rstride;
+    const C* pb = bsrc + (size_t)rh * rstride;
+    zphase = rh & 1;
+    if (rh > 0 && warp == 0) {   // every access of Rs for the previous right-hand side is done
+      fence_proxy_async_shared();
+      if (lane == 0) mbar_arrive_expect_tx(&bar[1], (unsigned)(12 * VB * sizeof(C)));
+      __syncwarp();
+      if (lane < 12) bulk_g2s(Rs + (size_t)lane * VB, pz + (size_t)lane * V + (size_t)blk * VB, VB * sizeof(C), &bar[1]);
+    }
+    ok = __syncthreads_and(mbar_wait_bounded(&bar[1], zphase) ? 1 : 0);
+    if (!ok) break;
+    // rho_e = b_e - A_e z_e + H z / 2 (even site); t_o = A_o^{-1} (b_o + H z / 2) - z_o (odd site)
+    hops_all(pz, le, xe, ce, im_e, ntf_e, ntb_e, acc);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) nb[q] = Rs[q * VB + le];
+    clover_apply(Cs, VB, le, nb, p, shift);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) re[k] = pb[(size_t)k * V + xe] - (p[k] - 0.5f * acc[k]);
+    hops_all(pz, lo, xo, co, im_o, ntf_o, ntb_o, acc);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) nb[k] = pb[(size_t)k * V + xo] + 0.5f * acc[k];
+    clover_apply(Cs, VB, lo, nb, p, 0.f);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      p[k] = p[k] - Rs[k * VB + lo];
+      Ts[k * 128 + t] = p[k];
+    }
+    __syncthreads();   // every read of the staged z is done
+#pragma unroll
+    for (int k = 0; k < 12; ++k) Rs[k * VB + lo] = p[k];
+    __syncthreads();
+    // r_e = rhohat_e = rho_e + H^B t_o / 2
+    hops_in(le, im_e, ntf_e, ntb_e, acc);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      re[k] = re[k] + 0.5f * acc[k];
+      xe_[k] = czero<float>();
+      Rs[k * VB + le] = re[k];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int it = 0; it < k_mr; ++it) {
+      // odd stage: s_o = A_o^{-1} H^B r
+      hops_in(lo, im_o, ntf_o, ntb_o, acc);
+      clover_apply(Cs, VB, lo, acc, p, 0.f);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) Rs[k * VB + lo] = p[k];
+      __syncthreads();
+      // even stage: p = A_e r - H^B s_o / 4
+      hops_in(le, im_e, ntf_e, ntb_e, acc);
+      clover_apply(Cs, VB, le, re, p, shift);
+      float nre = 0.f, nim = 0.f, den = 0.f;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        p[k] = p[k] - 0.25f * acc[k];
+        cdotc_acc(nre, nim, p[k], re[k]);
+        cnorm2_acc(den, p[k]);
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        nre += __shfl_xor_sync(0xffffffffu, nre, off);
+        nim += __shfl_xor_sync(0xffffffffu, nim, off);
+        den += __shfl_xor_sync(0xffffffffu, den, off);
+      }
+      float* sc = scratch + (it & 1) * 12;
+      if (lane == 0) {
+        sc[3 * warp] = nre;
+        sc[3 * warp + 1] = nim;
+        sc[3 * warp + 2] = den;
+      }
+      __syncthreads();
+      nre = nim = den = 0.f;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        nre += sc[3 * w];
+        nim += sc[3 * w + 1];
+        den += sc[3 * w + 2];
+      }
+      const C alpha = den > 0.f ? cmk<float>(nre / den, nim / den) : czero<float>();
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cfma(xe_[k], alpha, re[k]);
+        re[k] = re[k] - alpha * p[k];
+        Rs[k * VB + le] = re[k];
+      }
+      __syncthreads();
+    }
+    // x_o = t_o + A_o^{-1} H^B x_e / 2;  z += x
+#pragma unroll
+    for (int k = 0; k < 12; ++k) Rs[k * VB + le] = xe_[k];
+    __syncthreads();
+    hops_in(lo, im_o, ntf_o, ntb_o, acc);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0.5f * acc[k];
+    clover_apply(Cs, VB, lo, acc, p, 0.f);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      pz[(size_t)k * V + xo] = pz[(size_t)k * V + xo] + (Ts[k * 128 + t] + p[k]);
+      pz[(size_t)k * V + xe] = pz[(size_t)k * V + xe] + xe_[k];
+    }
+    __syncthreads();   // Rs is read no more before the next right-hand side's copy
+  }
+  if (!ok) {   // uniform across the CTA
+    if (t == 0) atomicExch(err, 2);
+    mbar_wait_bounded(&bar[0], 0);
+    mbar_wait_bounded(&bar[1], zphase);
+  }
+}
+
 // gauge field from the ABI layout [lex site][mu][3][3] (FP64) to [mu][9][V]
 template <typename T>
 __global__ void k_links_import(cplx<T>* __restrict__ U, const cd* __restrict__ gl, Geom g) {
@@ -1096,6 +1425,22 @@ void launch_sap_b4(cplx<float>* z, const cplx<float>* b, const LS* U, const CS* 
                                                  shift);
 }
 
+template <typename LS, typename CS>
+void launch_sap_b4_eo(cplx<float>* z, const cplx<float>* b, const LS* U, const CS* mix, const FineOp<float>& op,
+                      const int* blocks, int nblocks, int nrhs, size_t rstride, int k_mr, float shift,
+                      cudaStream_t st) {
+  constexpr int VB = 256;
+  const size_t sm = (size_t)VB * (36 * sizeof(LS) + 2 * ClovRows<CS>::per_chir * sizeof(CS) + 12 * sizeof(cplx<float>)) +
+                    (size_t)12 * 128 * sizeof(cplx<float>) + 16 + 2 * 12 * sizeof(float);
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
+    cudaFuncSetAttribute(k_fine_sap_b4_eo<LS, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  });
+  count_launch();
+  k_fine_sap_b4_eo<LS, CS><<<nblocks, 128, sm, st>>>(z, b, U, mix, op.g, op.bc_t, rstride, nrhs, blocks, k_mr, op.err,
+                                                     shift);
+}
+
 template <typename T, typename LS, typename CS>
 void launch_sap_plain(cplx<T>* z, const cplx<T>* b, const LS* U, const CS* clov, const FineOp<T>& op,
                       const int* blocks, int nblocks, int nrhs, size_t rstride, int k_mr, T shift, cudaStream_t st) {
@@ -1121,6 +1466,15 @@ void fine_sap_sweep(cplx<T>* z, const cplx<T>* b, const FineOp<T>& op, const int
   if (nrhs < 1 || nblocks < 1) return;   // the staged kernels issue their copies before the rhs loop
   const bool tma = sap_tma_ok(op) && op.err;
   if constexpr (sizeof(T) == 4) {
+    if (op.schur && op.err && sap_b4_ok(op, z, rstride)) {
+      // block solves on the even-odd Schur complement (per-site clover / inverse tables)
+      if (op.Uh)
+        launch_sap_b4_eo<__half2, __half2>(z, b, op.Uh, op.mixh, op, blocks, nblocks, nrhs, rstride, k_mr, op.shift,
+                                           st);
+      else
+        launch_sap_b4_eo<cplx<float>, float>(z, b, op.U, op.mix32, op, blocks, nblocks, nrhs, rstride, k_mr, 0.f, st);
+      return;
+    }
     if (op.err && sap_b4_ok(op, z, rstride)) {
       if (op.Uh)
         launch_sap_b4<__half2, __half2>(z, b, op.Uh, op.clovh, op, blocks, nblocks, nrhs, rstride, k_mr, op.shift, st);
@@ -1160,6 +1514,23 @@ __global__ void k_clover_to_half(__half2* __restrict__ dst, const double* __rest
   const int ch = row / 18, p = 2 * (row - 18 * ch);
   const double a0 = A[(size_t)(ch * 36 + p) * V + site], a1 = A[(size_t)(ch * 36 + p + 1) * V + site];
   dst[i] = __halves2half2(__double2half(p < 6 ? a0 - shift : a0), __double2half(p + 1 < 6 ? a1 - shift : a1));
+}
+
+void clover_inverse(double* inv, const double* clov, int V, int* err, cudaStream_t st) {
+  count_launch();
+  k_clover_inverse<<<div_up((size_t)2 * V, 128), 128, 0, st>>>(inv, clov, V, err);
+}
+
+void clover_mix(float* mix32, __half2* mixh, const double* clov, const double* inv, const Geom& g, double shift,
+                cudaStream_t st) {
+  if (mix32) {
+    count_launch();
+    k_clover_mix32<<<div_up((size_t)72 * g.V, 256), 256, 0, st>>>(mix32, clov, inv, g);
+  }
+  if (mixh) {
+    count_launch();
+    k_clover_mix_half<<<div_up((size_t)36 * g.V, 256), 256, 0, st>>>(mixh, clov, inv, g, shift);
+  }
 }
 
 void links_to_half(__half2* dst, const cplx<double>* U, size_t n, cudaStream_t st) {

@@ -20,6 +20,11 @@ struct FineOp {
   const __half2* Uh = nullptr;   // [4][9][V] links
   const __half2* clovh = nullptr; // [2][18][V] clover term without the (m0 + 4) shift, pairs of packed reals
   float shift = 0.f;             // m0 + 4, added to the diagonal in FP32
+  // SAP block solves on the even-odd Schur complement (FP32 compute, 4^4 blocks): per-site tables
+  // with the clover term on even sites and the inverse of (m0 + 4) + clover on odd sites
+  bool schur = false;
+  const float* mix32 = nullptr;    // [2][36][V] (even sites with the shift)
+  const __half2* mixh = nullptr;   // [2][18][V] (even sites without the shift)
 };
 
 template <typename T>
@@ -57,6 +62,11 @@ int fine_residual_norm_noalloc(double* out, bool out_on_device, const cplx<doubl
                                const FineOp<double>& op, int device, int nrhs, cudaStream_t st, const char** msg);
 void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, double m0, double csw,
                   cudaStream_t st);
+// per-site inverse of the packed Hermitian 6x6 blocks (LDL^+ in FP64); *err = 1 on a zero pivot
+void clover_inverse(double* inv, const double* clov, int V, int* err, cudaStream_t st);
+// the Schur SAP tables (either pointer may be null)
+void clover_mix(float* mix32, __half2* mixh, const double* clov, const double* inv, const Geom& g, double shift,
+                cudaStream_t st);
 // FP16 copies: links (no scale, |U_ab| <= 1) and the clover term A - shift (no scale)
 void links_to_half(__half2* dst, const cplx<double>* U, size_t n, cudaStream_t st);
 void clover_to_half(__half2* dst, const double* A, int V, double shift, cudaStream_t st);

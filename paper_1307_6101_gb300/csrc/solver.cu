@@ -82,6 +82,8 @@ struct Level {
   float* pscale = nullptr;
   __half2* blkh = nullptr;    // coarse blocks, one scale per site in bscale
   float* bscale = nullptr;
+  float* mix32 = nullptr;     // fine level, Schur SAP: clover (even sites) / inverse (odd sites), FP32
+  __half2* mixh = nullptr;    // the same tables in FP16
   int* blocks[2] = {nullptr, nullptr};
   int nblocks[2] = {0, 0};
   int* bsite = nullptr;       // coarse levels: [nBlk][vB] site of each SAP block's sites (block-local order)
@@ -176,6 +178,7 @@ struct ddamg_handle {
   // [level][candidate] (candidate 0 = CUDA-core kernel, k = tensor cores with k-split k; -1 = not run)
   double tune_ms[3][DDAMG_MAX_LEVELS][5] = {};   // [DDAMG_TUNE_*][level][candidate]
   int tc_force = -1;   // DDAMG_OPT_COARSE_TC: -1 autotune, 0 CUDA cores, k >= 1 that split
+  bool sap_schur = false;   // fine-level FP32 SAP block solves on the even-odd Schur complement
   // coarsest level on a thread-block cluster
   bool use_cluster = true;
   CoarsestGeo cgeo;
@@ -948,6 +951,40 @@ void half_bind(ddamg_handle* h) {
       L.c32.bscale = h->half ? L.bscale : nullptr;
     }
   }
+}
+
+// Schur SAP tables of the fine level: A(x)^{-1} per site in FP64 (temporary), then the tables with
+// the clover term on even and the inverse on odd sites, in FP32 and FP16.  A zero pivot is an error.
+void schur_tables(ddamg_handle* h) {
+  Level& F = h->lv[0];
+  if (!F.mix32) F.mix32 = dalloc<float>(h, (size_t)72 * F.g.V);
+  if (!F.mixh) F.mixh = dalloc<__half2>(h, (size_t)36 * F.g.V);
+  double* inv = nullptr;
+  if (cudaMalloc(&inv, sizeof(double) * 72 * (size_t)F.g.V) != cudaSuccess) {
+    cudaGetLastError();
+    fail(DDAMG_ERR_OOM, "temporary for the clover inverse");
+  }
+  clover_inverse(inv, F.f64.clov, F.g.V, h->d_err, h->st);
+  clover_mix(F.mix32, F.mixh, F.f64.clov, inv, F.g, h->m0 + 4.0, h->st);
+  const cudaError_t e = cudaStreamSynchronize(h->st);
+  cudaFree(inv);
+  CK(e);
+  check_err_flag(h, "singular site-diagonal block (clover inverse)");
+}
+
+// the 4^4 Schur kernel's conditions: FP32 preconditioner, fine SAP blocks 4^4 and the inner tile
+void schur_check(ddamg_handle* h) {
+  const Geom& g = h->lv[0].g;
+  for (int d = 0; d < 4; ++d)
+    if (g.B[d] != 4 || g.I[d] != 4)
+      fail(DDAMG_ERR_ARG, "Schur SAP block solves need 4^4 fine SAP blocks that tile the aggregates");
+}
+
+void schur_bind(ddamg_handle* h) {
+  Level& F = h->lv[0];
+  F.f32.schur = h->sap_schur;
+  F.f32.mix32 = h->sap_schur ? F.mix32 : nullptr;
+  F.f32.mixh = h->sap_schur && h->half ? F.mixh : nullptr;
 }
 
 // Autotuner of the kernels that read FP16 operator data for a whole batch: on every level, time
@@ -1725,6 +1762,7 @@ void ddamg_default_params(ddamg_params* p) {
   p->precision = 1;
   p->max_rhs = 1;
   p->seed = 0;
+  p->sap_schur = 0;
 }
 
 const char* ddamg_last_error(void) { return g_err.c_str(); }
@@ -1774,6 +1812,13 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
       half_refresh_fine(h);
       half_bind(h);
       tune_kernels(h);
+    }
+    if (h->p.sap_schur) {
+      if (h->p.precision == 0) fail(DDAMG_ERR_ARG, "Schur SAP block solves are an option of the FP32 preconditioner");
+      schur_check(h);
+      schur_tables(h);
+      h->sap_schur = true;
+      schur_bind(h);
     }
     sync(h);
     initial_setup_phase(h, 0, tv_random);
@@ -1896,8 +1941,17 @@ int ddamg_set_option(ddamg_handle* h, int option, int value) {
       }
       h->half = value != 0;
       half_bind(h);
+      schur_bind(h);
       ensure_work<float>(h);
       tune_kernels(h);
+      free_graphs(h);
+    } else if (option == DDAMG_OPT_SAP_SCHUR) {
+      if (value) {
+        schur_check(h);
+        if (!h->lv[0].mix32) schur_tables(h);
+      }
+      h->sap_schur = value != 0;
+      schur_bind(h);
       free_graphs(h);
     } else if (option == DDAMG_OPT_COARSE_TC) {
       if (value < -1 || value > 4) fail(DDAMG_ERR_ARG, "coarse tensor-core option must be -1..4");
@@ -1924,6 +1978,8 @@ int ddamg_get_option(ddamg_handle* h, int option, int* value) {
       *value = h->half ? 1 : 0;
     } else if (option == DDAMG_OPT_COARSE_TC) {
       *value = h->L > 1 ? h->lv[1].c32.tc_ks : 0;
+    } else if (option == DDAMG_OPT_SAP_SCHUR) {
+      *value = h->sap_schur ? 1 : 0;
     } else {
       fail(DDAMG_ERR_ARG, "unknown option");
     }
