@@ -123,6 +123,24 @@ int ddamg_solve(ddamg_handle* h, const double* rhs, double* x, int n, double tol
 
 void ddamg_free(ddamg_handle* h);
 
+/* The plain Krylov solver the paper compares the method with (Sec. 3.3, Table 5): CGNR on the
+ * fine operator of the handle, in FP64, in its least-squares form (CG on D^+ D x = D^+ b that
+ * updates s = b - D x), with D^+ = Gamma_5 D Gamma_5 (gamma_5-symmetry, Sec. 1).  Same layout and
+ * batching as ddamg_solve (max_rhs per batch, each column with its own coefficients); a column
+ * stops when ||s|| <= tol ||b|| or after max_iter iterations, and its true residual is recomputed
+ * at the end (per_rhs: iterations, converged on the true residual, true_residual).  Returns
+ * NOCONV if a column missed tol (x holds its last iterate). */
+int ddamg_cgnr(ddamg_handle* h, const double* rhs, double* x, int n, double tol, int max_iter, ddamg_stats* per_rhs);
+
+/* Extreme singular values of the fine operator (the quantity the paper's masses are tuned by,
+ * Sec. 3): `steps` CG iterations on D^+ D from a random field drawn from `seed` (as the setup
+ * draws its vectors, field 0 of level 7), then the smallest and largest eigenvalues of the CG
+ * Lanczos matrix (diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal sqrt(beta_j)/alpha_j)
+ * by Sturm bisection; sigma = sqrt(lambda).  The estimates approach the extreme singular values
+ * from inside as steps grows.  sigma_max and steps_taken may be NULL.  Errors: ARG. */
+int ddamg_sigma_extremes(ddamg_handle* h, int steps, uint64_t seed, double* sigma_min, double* sigma_max,
+                         int* steps_taken);
+
 const char* ddamg_last_error(void);
 
 /* Runs the library's kernels on this CUDA stream from now on (cudaStream_t;

@@ -125,3 +125,73 @@ def coarsest_solve(eo, b, tol: float, m: int, max_cycles: int):
     bh = eo.schur_rhs(b)
     xe, info = gmres(eo.schur_apply, bh, m=m, tol=tol, max_cycles=max_cycles, final_residual=True)
     return eo.back_substitute(xe, b), info
+
+
+def cgls(A, AH, b, tol: float = 1e-10, max_iter: int = 100000):
+    """CGNR in its least-squares form (CG on A^+ A x = A^+ b that updates s = b - A x; Saad, Iterative
+    Methods for Sparse Linear Systems, Sec. 8.3): the plain Krylov solver the method is compared
+    with (Sec. 3.3 of the paper).  Stops when ||s|| <= tol ||b||; returns (x, KrylovInfo) with
+    the true residual recomputed at the end.
+
+        x = 0, s = b, r = A^+ s, p = r, gamma = |r|^2
+        repeat: q = A p; alpha = gamma / |q|^2; x += alpha p; s -= alpha q;
+                r = A^+ s; gamma' = |r|^2; p = r + (gamma'/gamma) p
+    """
+    info = KrylovInfo()
+    bnorm = norm(b)
+    x = np.zeros_like(b)
+    if bnorm == 0.0:
+        info.converged, info.true_residual = True, 0.0
+        return x, info
+    s = b.copy()
+    r = AH(s)
+    p = r.copy()
+    gamma = norm(r) ** 2
+    for it in range(max_iter):
+        q = A(p)
+        alpha = gamma / norm(q) ** 2
+        x = x + alpha * p
+        s = s - alpha * q
+        info.iterations = it + 1
+        if norm(s) <= tol * bnorm:
+            break
+        r = AH(s)
+        g2 = norm(r) ** 2
+        p = r + (g2 / gamma) * p
+        gamma = g2
+    info.true_residual = norm(b - A(x)) / bnorm
+    info.converged = info.true_residual <= tol
+    return x, info
+
+
+def cg_lanczos_coefficients(Aop, v, steps: int):
+    """CG on a Hermitian positive definite operator from the start vector v: the step lengths alpha_j
+    and the ratios beta_j = |r_{j+1}|^2 / |r_j|^2 (stopping early when the residual vanishes)."""
+    r = v.copy()
+    p = r.copy()
+    gamma = norm(r) ** 2
+    alphas, betas = [], []
+    for _ in range(steps):
+        q = Aop(p)
+        alpha = gamma / vdot(p, q).real
+        r = r - alpha * q
+        g2 = norm(r) ** 2
+        alphas.append(alpha)
+        betas.append(g2 / gamma)
+        if g2 == 0.0:
+            break
+        p = r + (g2 / gamma) * p
+        gamma = g2
+    return np.array(alphas), np.array(betas)
+
+
+def lanczos_tridiagonal(alphas, betas) -> np.ndarray:
+    """The Lanczos matrix T_k of CG (Saad, Sec. 6.7.3): diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1},
+    off-diagonal sqrt(beta_j)/alpha_j; its eigenvalues (Ritz values) approximate the operator's."""
+    k = len(alphas)
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(betas[j]) / alphas[j]
+    return T

@@ -35,7 +35,7 @@ EXPORTED = (
     "ddamg_krylov_steps", "ddamg_residual_norm_noalloc", "ddamg_get_option",
     "ddamg_device_bytes", "ddamg_estimate_bytes", "ddamg_server_create", "ddamg_server_add",
     "ddamg_server_submit", "ddamg_server_poll", "ddamg_server_wait", "ddamg_server_free",
-    "ddamg_setup_times", "ddamg_autotune_times",
+    "ddamg_setup_times", "ddamg_autotune_times", "ddamg_cgnr", "ddamg_sigma_extremes",
 )
 DDAMG_OPT_GRAPHS = 0
 DDAMG_OPT_COARSEST_CLUSTER = 1
@@ -97,6 +97,9 @@ def _load():
                                 C.POINTER(C.c_void_p), C.POINTER(vp)]
     lib.ddamg_solve.argtypes = [vp, vp, vp, ip, C.c_double, C.POINTER(DdamgStats)]
     lib.ddamg_free.argtypes = [vp]
+    lib.ddamg_cgnr.argtypes = [vp, vp, vp, ip, C.c_double, ip, C.POINTER(DdamgStats)]
+    lib.ddamg_sigma_extremes.argtypes = [vp, ip, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_int)]
     lib.ddamg_free.restype = None
     lib.ddamg_last_error.restype = C.c_char_p
     lib.ddamg_set_stream.argtypes = [vp, vp]
@@ -236,6 +239,24 @@ def ddamg_solve(h: Handle, rhs, x, n, tol, with_stats=True, raise_noconv=False):
         _check(rc)
     return [dict(iterations=s.iterations, cycles=s.cycles, converged=bool(s.converged),
                  true_residual=s.true_residual) for s in stats[:n]]
+
+
+def ddamg_cgnr(h: Handle, rhs, x, n, tol, max_iter=100000):
+    """FP64 CGNR on the handle's fine operator; per-rhs stats (iterations, converged, true residual)."""
+    stats = (DdamgStats * max(1, n))()
+    rc = lib().ddamg_cgnr(h.raw, _ptr(rhs), _ptr(x), int(n), float(tol), int(max_iter), stats)
+    if rc not in (DDAMG_OK, DDAMG_ERR_NOCONV):
+        _check(rc)
+    return [dict(iterations=s.iterations, converged=bool(s.converged), true_residual=s.true_residual)
+            for s in stats[:n]]
+
+
+def ddamg_sigma_extremes(h: Handle, steps, seed=0):
+    """(sigma_min, sigma_max, steps taken) of the fine operator from the CG Lanczos matrix of D^+ D."""
+    a, b, k = C.c_double(), C.c_double(), C.c_int()
+    _check(lib().ddamg_sigma_extremes(h.raw, int(steps), C.c_uint64(int(seed)), C.byref(a), C.byref(b),
+                                      C.byref(k)))
+    return a.value, b.value, k.value
 
 
 def ddamg_free(h: Handle):

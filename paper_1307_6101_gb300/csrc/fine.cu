@@ -1516,6 +1516,20 @@ __global__ void k_clover_to_half(__half2* __restrict__ dst, const double* __rest
   dst[i] = __halves2half2(__double2half(p < 6 ? a0 - shift : a0), __double2half(p + 1 < 6 ? a1 - shift : a1));
 }
 
+// out = Gamma_5 in (spins 2, 3 negated), component-major fine fields
+__global__ void k_gamma5(cplx<double>* __restrict__ out, const cplx<double>* __restrict__ in, int V, size_t rstride) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)12 * V) return;
+  const size_t a = (size_t)blockIdx.y * rstride + t;
+  const cplx<double> v = in[a];
+  out[a] = t < (size_t)6 * V ? v : cmk(-v.re, -v.im);
+}
+
+void fine_gamma5(cplx<double>* out, const cplx<double>* in, int V, int nrhs, size_t rstride, cudaStream_t st) {
+  count_launch();
+  k_gamma5<<<dim3(div_up((size_t)12 * V, 256), nrhs), 256, 0, st>>>(out, in, V, rstride);
+}
+
 void clover_inverse(double* inv, const double* clov, int V, int* err, cudaStream_t st) {
   count_launch();
   k_clover_inverse<<<div_up((size_t)2 * V, 128), 128, 0, st>>>(inv, clov, V, err);

@@ -62,6 +62,8 @@ int fine_residual_norm_noalloc(double* out, bool out_on_device, const cplx<doubl
                                const FineOp<double>& op, int device, int nrhs, cudaStream_t st, const char** msg);
 void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, double m0, double csw,
                   cudaStream_t st);
+// out = Gamma_5 in on nrhs fine FP64 fields (may be in place)
+void fine_gamma5(cplx<double>* out, const cplx<double>* in, int V, int nrhs, size_t rstride, cudaStream_t st);
 // per-site inverse of the packed Hermitian 6x6 blocks (LDL^+ in FP64); *err = 1 on a zero pivot
 void clover_inverse(double* inv, const double* clov, int V, int* err, cudaStream_t st);
 // the Schur SAP tables (either pointer may be null)

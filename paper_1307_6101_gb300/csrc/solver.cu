@@ -179,6 +179,12 @@ struct ddamg_handle {
   double tune_ms[3][DDAMG_MAX_LEVELS][5] = {};   // [DDAMG_TUNE_*][level][candidate]
   int tc_force = -1;   // DDAMG_OPT_COARSE_TC: -1 autotune, 0 CUDA cores, k >= 1 that split
   bool sap_schur = false;   // fine-level FP32 SAP block solves on the even-odd Schur complement
+  // plain Krylov solver (CGNR) and sigma_min: four FP64 fine vectors per batch column, per-column
+  // coefficients on the device, pinned host scalars
+  cplx<double>* cg_vec = nullptr;
+  cplx<double>* cg_coef = nullptr;
+  double* cg_dcoef = nullptr;
+  double* cg_host = nullptr;
   // coarsest level on a thread-block cluster
   bool use_cluster = true;
   CoarsestGeo cgeo;
@@ -1422,6 +1428,189 @@ void precond_outer<float>(ddamg_handle* h, cplx<double>* z, const cplx<double>* 
   blas_convert<double, float>(z, h->pout32, vl, nrhs, vl, vl, h->st);
 }
 
+// ---------------------------------------------------------------------------
+// The plain Krylov solver the paper compares with (Sec. 3.3): CGNR, here in its least-squares
+// form (CG on D^+ D x = D^+ b that updates s = b - D x), in FP64 on the fine operator, with
+// D^+ = Gamma_5 D Gamma_5 (gamma_5-symmetry, Sec. 1).  Batched over right-hand sides, each with
+// its own coefficients; a column stops when ||s|| <= tol ||b|| and its true residual is
+// recomputed at the end.
+void cg_alloc(ddamg_handle* h) {
+  if (h->cg_vec) return;
+  h->cg_vec = dalloc<cplx<double>>(h, (size_t)4 * h->max_batch * h->lv[0].vlen);
+  h->cg_coef = dalloc<cplx<double>>(h, 64);
+  h->cg_dcoef = dalloc<double>(h, 64);
+  CK(cudaMallocHost(&h->cg_host, sizeof(double) * 4 * 64));
+}
+
+void cg_norms(ddamg_handle* h, const cplx<double>* v, int nb, double* host) {
+  Level& F = h->lv[0];
+  double* d = h->cg_dcoef;
+  blas_norm2<double>(d, v, F.vlen, nb, F.vlen, h->st);
+  CK(cudaMemcpyAsync(host, d, sizeof(double) * nb, cudaMemcpyDeviceToHost, h->st));
+  sync(h);
+}
+
+void cgnr_batch(ddamg_handle* h, int nb, double tol, int max_iter, KrylovResult* res) {
+  cg_alloc(h);
+  Level& F = h->lv[0];
+  const size_t vl = F.vlen, vs = (size_t)h->max_batch * vl;
+  cplx<double>*s = h->cg_vec, *r = s + vs, *p = r + vs, *q = p + vs;
+  cplx<double>* x = h->ox;
+  const cplx<double>* b = h->ob;
+  cudaStream_t st = h->st;
+  auto D = [&](cplx<double>* o, const cplx<double>* i) { apply_D<double>(h, F, o, i, nullptr, nb); };
+  auto DH = [&](cplx<double>* o, const cplx<double>* i, cplx<double>* tmp) {   // o = Gamma_5 D Gamma_5 i
+    fine_gamma5(tmp, i, F.g.V, nb, vl, st);
+    D(o, tmp);
+    fine_gamma5(o, o, F.g.V, nb, vl, st);
+  };
+  double* hv = h->cg_host;   // [0, 64): per-column scalars read back; [64, 128): coefficients
+  std::vector<double> bn(nb), gam(nb);
+  std::vector<int> done(nb, 0), its(nb, 0);
+  cg_norms(h, b, nb, hv);
+  for (int c = 0; c < nb; ++c) {
+    bn[c] = hv[c];
+    done[c] = bn[c] == 0.0;
+  }
+  blas_zero<double>(x, vl, nb, vl, st);
+  blas_convert<double, double>(s, b, vl, nb, vl, vl, st);
+  DH(r, s, q);
+  blas_convert<double, double>(p, r, vl, nb, vl, vl, st);
+  cg_norms(h, r, nb, hv);
+  for (int c = 0; c < nb; ++c) gam[c] = hv[c] * hv[c];
+  auto upload_axpy = [&](const std::vector<double>& a) {
+    for (int c = 0; c < nb; ++c) {
+      hv[64 + 2 * c] = a[c];
+      hv[64 + 2 * c + 1] = 0.0;
+    }
+    CK(cudaMemcpyAsync(h->cg_coef, hv + 64, sizeof(cplx<double>) * nb, cudaMemcpyHostToDevice, st));
+  };
+  std::vector<double> coef(nb);
+  for (int it = 0; it < max_iter; ++it) {
+    bool all = true;
+    for (int c = 0; c < nb; ++c) all = all && done[c];
+    if (all) break;
+    D(q, p);
+    cg_norms(h, q, nb, hv);
+    for (int c = 0; c < nb; ++c) coef[c] = (done[c] || hv[c] == 0.0) ? 0.0 : gam[c] / (hv[c] * hv[c]);
+    upload_axpy(coef);
+    blas_multiaxpy<double>(x, p, 0, 1, h->cg_coef, 1, 1.0, vl, nb, vl, st);
+    blas_multiaxpy<double>(s, q, 0, 1, h->cg_coef, 1, -1.0, vl, nb, vl, st);
+    cg_norms(h, s, nb, hv);
+    for (int c = 0; c < nb; ++c)
+      if (!done[c]) {
+        its[c] = it + 1;
+        if (hv[c] <= tol * bn[c]) done[c] = 1;
+      }
+    DH(r, s, q);
+    cg_norms(h, r, nb, hv);
+    for (int c = 0; c < nb; ++c) {
+      const double g2 = hv[c] * hv[c];
+      coef[c] = (done[c] || gam[c] == 0.0) ? 0.0 : g2 / gam[c];
+      gam[c] = g2;
+    }
+    for (int c = 0; c < nb; ++c) hv[128 + c] = coef[c];
+    CK(cudaMemcpyAsync(h->cg_dcoef, hv + 128, sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+    blas_scale_to<double>(p, p, h->cg_dcoef, vl, nb, vl, st);
+    blas_axpy<double>(p, r, 1.0, vl, nb, vl, st);
+  }
+  // true residuals b - D x
+  apply_D<double>(h, F, s, x, b, nb);
+  cg_norms(h, s, nb, hv);
+  res->iterations.assign(nb, 0);
+  res->cycles.assign(nb, 1);
+  res->converged.assign(nb, 0);
+  res->true_residual.assign(nb, 0.0);
+  for (int c = 0; c < nb; ++c) {
+    res->iterations[c] = its[c];
+    res->true_residual[c] = bn[c] > 0 ? hv[c] / bn[c] : 0.0;
+    res->converged[c] = res->true_residual[c] <= tol;
+  }
+}
+
+// number of eigenvalues below x of the symmetric tridiagonal matrix (d, off-diagonal squares e2)
+int sturm_count(const std::vector<double>& d, const std::vector<double>& e2, double x) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (q < 0) ++cnt;
+  for (size_t i = 1; i < d.size(); ++i) {
+    if (q == 0.0) q = 1e-300;
+    q = d[i] - x - e2[i - 1] / q;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+// the k-th smallest eigenvalue (k = 0..n-1) by bisection on the Sturm count
+double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e2, int k) {
+  const size_t n = d.size();
+  double lo = 1e300, hi = -1e300;
+  for (size_t i = 0; i < n; ++i) {
+    double rad = 0;
+    if (i > 0) rad += std::sqrt(e2[i - 1]);
+    if (i + 1 < n) rad += std::sqrt(e2[i]);
+    lo = std::min(lo, d[i] - rad);
+    hi = std::max(hi, d[i] + rad);
+  }
+  for (int it = 0; it < 300 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(d, e2, mid) > k) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Smallest and largest singular value of D from the Lanczos matrix of CG on D^+ D (Saad, Sec. 6.7.3:
+// diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal sqrt(beta_j)/alpha_j), started from a
+// seeded random field; the extreme Ritz values approach lambda_min and lambda_max of D^+ D.
+void sigma_extremes(ddamg_handle* h, int steps, uint64_t seed, double* smin, double* smax, int* used) {
+  cg_alloc(h);
+  Level& F = h->lv[0];
+  const size_t vl = F.vlen, vs = (size_t)h->max_batch * vl;
+  cplx<double>*s = h->cg_vec, *r = s + vs, *p = r + vs, *q = p + vs;
+  cudaStream_t st = h->st;
+  double* hv = h->cg_host;
+  draw_fields(r, F.g, true, F.n, 1, 0, 7, seed, vl, st);
+  blas_convert<double, double>(p, r, vl, 1, vl, vl, st);
+  cg_norms(h, r, 1, hv);
+  double gam = hv[0] * hv[0];
+  const double gam0 = gam;
+  std::vector<double> al, be;
+  for (int j = 0; j < steps; ++j) {
+    apply_D<double>(h, F, q, p, nullptr, 1);      // q = D p, <p, D^+ D p> = |q|^2
+    cg_norms(h, q, 1, hv);
+    if (!(hv[0] > 0.0)) break;
+    const double alpha = gam / (hv[0] * hv[0]);
+    fine_gamma5(s, q, F.g.V, 1, vl, st);           // s = D^+ q = Gamma_5 D Gamma_5 q
+    apply_D<double>(h, F, q, s, nullptr, 1);
+    fine_gamma5(s, q, F.g.V, 1, vl, st);
+    hv[64] = -alpha;
+    hv[65] = 0.0;
+    CK(cudaMemcpyAsync(h->cg_coef, hv + 64, sizeof(cplx<double>), cudaMemcpyHostToDevice, st));
+    blas_multiaxpy<double>(r, s, 0, 1, h->cg_coef, 1, 1.0, vl, 1, vl, st);   // r -= alpha D^+ D p
+    cg_norms(h, r, 1, hv);
+    const double g2 = hv[0] * hv[0];
+    al.push_back(alpha);
+    be.push_back(g2 / gam);
+    if (g2 <= 1e-28 * gam0) break;
+    hv[128] = g2 / gam;
+    CK(cudaMemcpyAsync(h->cg_dcoef, hv + 128, sizeof(double), cudaMemcpyHostToDevice, st));
+    blas_scale_to<double>(p, p, h->cg_dcoef, vl, 1, vl, st);
+    blas_axpy<double>(p, r, 1.0, vl, 1, vl, st);
+    gam = g2;
+  }
+  const size_t k = al.size();
+  if (k == 0) fail(DDAMG_ERR_ARG, "no Lanczos step could be taken");
+  std::vector<double> d(k), e2(k > 1 ? k - 1 : 1, 0.0);
+  for (size_t j = 0; j < k; ++j) {
+    d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    if (j + 1 < k) e2[j] = be[j] / (al[j] * al[j]);
+  }
+  *smin = std::sqrt(std::max(0.0, tridiag_eig(d, e2, 0)));
+  *smax = std::sqrt(std::max(0.0, tridiag_eig(d, e2, (int)k - 1)));
+  if (used) *used = (int)k;
+}
+
 }  // namespace
 
 namespace {
@@ -1848,6 +2037,7 @@ void ddamg_free(ddamg_handle* h) {
   if (h->h_done) cudaFreeHost(h->h_done);
   if (h->h_kr) cudaFreeHost(h->h_kr);
   if (h->h_scal) cudaFreeHost(h->h_scal);
+  if (h->cg_host) cudaFreeHost(h->cg_host);
   for (auto& v : h->ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
   if (h->own) cudaStreamDestroy(h->own);
@@ -1910,6 +2100,60 @@ int ddamg_solve(ddamg_handle* h, const double* rhs, double* x, int n, double tol
     return DDAMG_ERR_NOCONV;
   }
   return DDAMG_OK;
+}
+
+int ddamg_cgnr(ddamg_handle* h, const double* rhs, double* x, int n, double tol, int max_iter, ddamg_stats* per_rhs) {
+  if (!h || !rhs || !x || n < 0 || !(tol > 0) || max_iter < 1) {
+    g_err = "invalid argument";
+    return DDAMG_ERR_ARG;
+  }
+  bool all_conv = true;
+  const int rc = guard([&] {
+    Level& F = h->lv[0];
+    const size_t fbytes = sizeof(cplx<double>) * F.vlen;
+    const bool xdev = is_device_ptr(x);
+    for (int s0 = 0; s0 < n; s0 += h->max_batch) {
+      const int nb = (n - s0) < h->max_batch ? (n - s0) : h->max_batch;
+      const cplx<double>* din =
+          static_cast<const cplx<double>*>(dev_in(h, rhs + (size_t)s0 * F.vlen * 2, fbytes * nb, 0));
+      fine_import<double>(h->ob, din, F.g, nb, F.vlen, h->st);
+      KrylovResult res;
+      cgnr_batch(h, nb, tol, max_iter, &res);
+      cplx<double>* dx = xdev ? reinterpret_cast<cplx<double>*>(x + (size_t)s0 * F.vlen * 2)
+                              : static_cast<cplx<double>*>(scratch(h, 1, fbytes * nb));
+      fine_export<double>(dx, h->ox, F.g, nb, F.vlen, h->st);
+      if (!xdev) CK(cudaMemcpyAsync(x + (size_t)s0 * F.vlen * 2, dx, fbytes * nb, cudaMemcpyDeviceToHost, h->st));
+      sync(h);
+      for (int r = 0; r < nb; ++r) {
+        if (per_rhs) {
+          per_rhs[s0 + r].iterations = res.iterations[r];
+          per_rhs[s0 + r].cycles = 1;
+          per_rhs[s0 + r].converged = res.converged[r];
+          per_rhs[s0 + r].true_residual = res.true_residual[r];
+        }
+        all_conv = all_conv && res.converged[r];
+      }
+    }
+  });
+  if (rc != DDAMG_OK) return rc;
+  if (!all_conv) {
+    g_err = "CGNR did not reach the tolerance";
+    return DDAMG_ERR_NOCONV;
+  }
+  return DDAMG_OK;
+}
+
+int ddamg_sigma_extremes(ddamg_handle* h, int steps, uint64_t seed, double* sigma_min, double* sigma_max,
+                         int* steps_taken) {
+  if (!h || steps < 1 || !sigma_min) {
+    g_err = "invalid argument";
+    return DDAMG_ERR_ARG;
+  }
+  return guard([&] {
+    double smax = 0.0;
+    sigma_extremes(h, steps, seed, sigma_min, &smax, steps_taken);
+    if (sigma_max) *sigma_max = smax;
+  });
 }
 
 int ddamg_set_option(ddamg_handle* h, int option, int value) {

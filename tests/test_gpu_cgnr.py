@@ -1,0 +1,62 @@
+"""The plain Krylov comparison solver (CGNR, FP64) and the singular-value estimate on the GPU against
+the oracle: CGNR reaches the true residual measured with the oracle's D, in the oracle's iteration
+count up to rounding; sigma_min and sigma_max from the CG Lanczos matrix match the oracle's dense /
+shift-invert values on a 4^4 lattice."""
+import numpy as np
+import pytest
+
+import synth
+from cases import Case, SMALL2, C1, golden_mass
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dd():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1307_6101_gb300 as m
+    return m
+
+
+def test_cgnr_matches_oracle(dd):
+    from oracle.wilson import WilsonOp
+    from oracle.krylov import cgls
+    c = Case(**SMALL2, m0=-0.2, n_inv=0, eta_passes=0, max_rhs=3)
+    U = c.gauge()
+    h = c.gpu(1, U)
+    op = WilsonOp.build(U, c.m0, c.csw, c.bc_t)
+    b = np.ascontiguousarray(synth.random_spinors(3, c.dims, 5))
+    b[2] = synth.point_sources(c.dims, 4)[1]
+    x = np.zeros_like(b)
+    st = dd.ddamg_cgnr(h, b, x, 3, 1e-10)
+    g5 = op.gamma5
+    for i in range(3):
+        assert st[i]["converged"]
+        assert np.linalg.norm(b[i] - op.apply(x[i])) <= 1e-10 * np.linalg.norm(b[i])
+        _, info = cgls(op.apply, lambda v: g5 * op.apply(g5 * v), b[i], tol=1e-10)
+        assert abs(st[i]["iterations"] - info.iterations) <= max(2, 0.02 * info.iterations), (st[i], info.iterations)
+    # one column alone takes the same iterations as inside the batch
+    x1 = np.zeros_like(b[:1])
+    s1 = dd.ddamg_cgnr(h, np.ascontiguousarray(b[1:2]), x1, 1, 1e-10)
+    assert s1[0]["iterations"] == st[1]["iterations"]
+    h.free()
+
+
+def test_sigma_extremes_match_oracle(dd):
+    from oracle.wilson import WilsonOp
+    from oracle.spectrum import sparse_matrix, sigma_min
+    c = Case(**SMALL2, m0=-0.35, csw=1.0, n_inv=0, eta_passes=0)
+    U = c.gauge()
+    h = c.gpu(1, U)
+    op = WilsonOp.build(U, c.m0, c.csw, c.bc_t)
+    smin_ref = sigma_min(op)
+    s = np.linalg.svd(sparse_matrix(op).toarray(), compute_uv=False)
+    smin, smax, k = dd.ddamg_sigma_extremes(h, 800, seed=3)
+    assert abs(smin - smin_ref) <= 1e-6 * smin_ref, (smin, smin_ref, k)
+    assert abs(smin - s[-1]) <= 1e-6 * s[-1]
+    assert abs(smax - s[0]) <= 1e-6 * s[0], (smax, s[0])
+    # few steps: inside the spectrum
+    a, b_, _ = dd.ddamg_sigma_extremes(h, 20, seed=3)
+    assert s[-1] * (1 - 1e-12) <= a and b_ <= s[0] * (1 + 1e-12)
+    h.free()

@@ -236,3 +236,46 @@ def test_sap_schur_application_uses_schur_block_solves():
     e = sap.mr_schur(r * red) * red
     e = e + sap.mr_schur((r - op.apply(e)) * ~red) * ~red
     assert norm(sap(r) - e) <= 1e-13 * norm(e)
+
+
+def test_cgls_solves_dense_system():
+    """CGNR (CGLS form) on a small complex system: the solution of the dense solve, and finite
+    termination within the dimension on a 24 x 24 matrix."""
+    from oracle.krylov import cgls
+    rng = np.random.default_rng(11)
+    A = np.eye(24) * 2 + 0.4 * (rng.standard_normal((24, 24)) + 1j * rng.standard_normal((24, 24)))
+    b = rng.standard_normal(24) + 1j * rng.standard_normal(24)
+    x, info = cgls(lambda v: A @ v, lambda v: A.conj().T @ v, b, tol=1e-12, max_iter=200)
+    assert info.converged and info.iterations <= 40
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_cgnr_on_the_wilson_operator_matches_dense_lu():
+    from oracle.krylov import cgls
+    op = _op(seed=2, m0=0.2)
+    g5 = op.gamma5
+    b = synth.random_spinors(1, DIMS, 3)[0]
+    x, info = cgls(op.apply, lambda v: g5 * op.apply(g5 * v), b, tol=1e-10)
+    assert info.converged
+    D = sparse_matrix(op).toarray()
+    xd = np.linalg.solve(D, b.ravel())
+    s = np.linalg.svd(D, compute_uv=False)
+    assert np.linalg.norm(x.ravel() - xd) <= (s[0] / s[-1]) * 1e-10 * np.linalg.norm(xd)
+
+
+def test_cg_lanczos_ritz_values():
+    """After n CG steps on an n x n Hermitian positive definite matrix the Lanczos matrix built from
+    the CG coefficients has the matrix's eigenvalues; after fewer steps its extreme Ritz values lie
+    inside the spectrum and approach its ends."""
+    from oracle.krylov import cg_lanczos_coefficients, lanczos_tridiagonal
+    rng = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 30)) + 1j * rng.standard_normal((30, 30)))
+    ev = np.linspace(0.05, 4.0, 30)
+    A = (Q * ev) @ Q.conj().T
+    v = rng.standard_normal(30) + 1j * rng.standard_normal(30)
+    a, bt = cg_lanczos_coefficients(lambda u: A @ u, v, 30)
+    rz = np.linalg.eigvalsh(lanczos_tridiagonal(a, bt))
+    assert np.allclose(np.sort(rz), ev, rtol=1e-6, atol=1e-8)
+    a, bt = cg_lanczos_coefficients(lambda u: A @ u, v, 12)
+    rz = np.linalg.eigvalsh(lanczos_tridiagonal(a, bt))
+    assert ev[0] - 1e-12 <= rz[0] and rz[-1] <= ev[-1] + 1e-12
