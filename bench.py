@@ -61,6 +61,12 @@ WORKLOADS = {
         sap=[(4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)],
         mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=1, seed=0, tv_seed=100, rhs_seed=1,
         outer_iterations=15),
+    "rough_16c32": dict(
+        name="three-level 16^3x32, eps 0.8 (rougher fields, nearly real spectrum edge), csw 1.0, 20/28 test "
+             "vectors, SAP 4^4, 1 RHS",
+        dims=(32, 16, 16, 16), eps=0.8, csw=1.0, mass="eps0.8_csw1", levels=3,
+        agg=[(4, 4, 4, 4), (2, 2, 2, 2)], n_tv=[20, 28], sap=[(4, 4, 4, 4), (2, 2, 2, 2)],
+        mr_steps=4, nu=5, n_inv=6, outer_restart=10, nrhs=1, seed=0, tv_seed=100, rhs_seed=1),
     "two_level_8c4": dict(
         name="two-level 8^4, eps 0.3, csw 0, 8 test vectors, SAP 2^4, 1 RHS",
         dims=(8, 8, 8, 8), eps=0.3, csw=0.0, mass="eps0.3_csw0", levels=2,
@@ -745,6 +751,83 @@ def run_serving(args):
     print(json.dumps(out))
 
 
+# ---------------------------------------------------------------------------
+# Mass and error scaling (the paper's Sec. 3.4 / Figs. 4-5 studies, here on the synthetic 16^3 x 32
+# fields): DD-alpha-AMG (mixed, three levels, setup per mass) against the plain Krylov solver
+# (FP64 CGNR) as the bare mass approaches the spectrum's edge, and both against the tolerance.
+SCAN_DELTAS = (0.3, 0.1, 0.03, 0.01, 0.003, 0.0)
+SCAN_TOLS = (1e-2, 1e-4, 1e-6, 1e-8, 1e-10)
+
+
+def run_scan(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1307_6101_gb300 as dd
+    stream = torch.cuda.current_stream()
+    out = {"scan": "mass and error scaling, DD-alpha-AMG (mixed, three levels) vs CGNR (FP64)",
+           "rhs": "one complex N(0,1) field", "cgnr_max_iterations": args.scan_cg_iters, "fields": []}
+    for wname in ("three_level_16c32", "rough_16c32"):
+        out["fields"].append(scan_fields(dd, torch, stream, WORKLOADS[wname], args))
+    print(json.dumps(out))
+
+
+def scan_fields(dd, torch, stream, w, args):
+    U, _, rhs_h = inputs(w)
+    m_edge = mass(w["mass"])
+    rhs = torch.from_numpy(rhs_h[:1].copy()).cuda()
+    x = torch.zeros_like(rhs)
+
+    def params(prec, max_rhs=1):
+        return dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
+                                       mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
+                                       outer_restart=w["outer_restart"], precision=prec, max_rhs=max_rhs,
+                                       seed=w["tv_seed"], outer_max_cycles=400)
+
+    def timed(f):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = f()
+        e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    rows = []
+    for delta in SCAN_DELTAS:
+        m0 = m_edge + delta
+        t0 = time.perf_counter()
+        h = dd.ddamg_setup(U, w["dims"], -1, m0, w["csw"], params(2), None)
+        t_setup = time.perf_counter() - t0
+        dd.ddamg_set_stream(h, stream.cuda_stream)
+        smin, smax, k = dd.ddamg_sigma_extremes(h, args.scan_lanczos, seed=5)
+        dd.ddamg_solve(h, rhs, x, 1, TOL)                      # warm-up (graph capture)
+        st, t_amg = timed(lambda: dd.ddamg_solve(h, rhs, x, 1, TOL))
+        cg, t_cg = timed(lambda: dd.ddamg_cgnr(h, rhs, x, 1, TOL, args.scan_cg_iters))
+        rows.append({"m0": round(m0, 6), "m0_minus_edge": delta, "sigma_min": smin, "sigma_max": smax,
+                     "lanczos_steps": k, "ddamg_setup_s": round(t_setup, 2),
+                     "ddamg_iterations": st[0]["iterations"], "ddamg_s": round(t_amg, 4),
+                     "ddamg_true_residual": st[0]["true_residual"],
+                     "cgnr_iterations": cg[0]["iterations"], "cgnr_s": round(t_cg, 3),
+                     "cgnr_converged": cg[0]["converged"], "cgnr_true_residual": cg[0]["true_residual"],
+                     "cgnr_over_ddamg_time": round(t_cg / t_amg, 1)})
+        h.free()
+    # error scaling at the workload's mass
+    h = dd.ddamg_setup(U, w["dims"], -1, m_edge, w["csw"], params(2), None)
+    dd.ddamg_set_stream(h, stream.cuda_stream)
+    dd.ddamg_solve(h, rhs, x, 1, TOL)
+    err = []
+    for tol in SCAN_TOLS:
+        st, t_amg = timed(lambda: dd.ddamg_solve(h, rhs, x, 1, tol))
+        cg, t_cg = timed(lambda: dd.ddamg_cgnr(h, rhs, x, 1, tol, args.scan_cg_iters))
+        err.append({"tol": tol, "ddamg_iterations": st[0]["iterations"], "ddamg_s": round(t_amg, 4),
+                    "cgnr_iterations": cg[0]["iterations"], "cgnr_s": round(t_cg, 3),
+                    "cgnr_converged": cg[0]["converged"]})
+    h.free()
+    return {"workload": w["name"], "edge_mass": m_edge, "mass_scan": rows, "error_scan": err}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -766,10 +849,17 @@ def main():
                     help="skip the batched 32^3x64 sub-measurement of the default bench")
     ap.add_argument("--large-steps", type=int, default=2,
                     help="timed steps (24 right-hand sides each) of the 32^3x64 sub-measurement")
+    ap.add_argument("--scan", action="store_true",
+                    help="mass- and error-scaling sweeps of DD-alpha-AMG against CGNR (one JSON line)")
+    ap.add_argument("--scan-cg-iters", type=int, default=30000, help="CGNR iteration cap of the sweeps")
+    ap.add_argument("--scan-lanczos", type=int, default=400, help="Lanczos steps of the sigma estimates")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven inner solves instead of captured graphs (for kernel-level profiling)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.scan:
+        run_scan(args)
+        return
     if args.serving:
         run_serving(args)
         return
