@@ -78,6 +78,9 @@ typedef struct ddamg_params {
                                           Dhat_B = D_ee - D_eo D_oo^-1 D_oe, then the odd
                                           back-substitution; needs 4^4 SAP blocks); 0: MR on
                                           D_B (the paper does not say which)              */
+  int setup_batch;                     /* test vectors per batched K-cycle of Alg. 4 (0: 4);
+                                          the level workspaces hold max(max_rhs, this)
+                                          columns; results do not depend on it            */
 } ddamg_params;
 
 typedef struct ddamg_stats {
@@ -122,6 +125,15 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
 int ddamg_solve(ddamg_handle* h, const double* rhs, double* x, int n, double tol, ddamg_stats* per_rhs);
 
 void ddamg_free(ddamg_handle* h);
+
+/* Hierarchy update after a change of the gauge field (as between the steps of a Monte Carlo
+ * chain, where setup cost weighs most: Table 3 of the paper puts it at several times a solve):
+ * imports `gauge` (same layout as ddamg_setup, host or device), rebuilds the clover term and
+ * every FP32/FP16 copy, rebuilds P_l from the current test vectors and every coarse operator
+ * D_{l+1} = P_l^dagger D_l P_l of the new fine operator, then runs n_inv iterative setup phases
+ * (Alg. 4) starting from the current test vectors.  m0, c_sw, the geometry and the parameters
+ * are kept.  Errors: ARG, SINGULAR, CUDA. */
+int ddamg_update_gauge(ddamg_handle* h, const double* gauge, int n_inv);
 
 /* The plain Krylov solver the paper compares the method with (Sec. 3.3, Table 5): CGNR on the
  * fine operator of the handle, in FP64, in its least-squares form (CG on D^+ D x = D^+ b that

@@ -36,6 +36,7 @@ EXPORTED = (
     "ddamg_device_bytes", "ddamg_estimate_bytes", "ddamg_server_create", "ddamg_server_add",
     "ddamg_server_submit", "ddamg_server_poll", "ddamg_server_wait", "ddamg_server_free",
     "ddamg_setup_times", "ddamg_autotune_times", "ddamg_cgnr", "ddamg_sigma_extremes",
+    "ddamg_update_gauge",
 )
 DDAMG_OPT_GRAPHS = 0
 DDAMG_OPT_COARSEST_CLUSTER = 1
@@ -71,6 +72,7 @@ class DdamgParams(C.Structure):
         ("max_rhs", C.c_int),
         ("seed", C.c_uint64),
         ("sap_schur", C.c_int),
+        ("setup_batch", C.c_int),
     ]
 
 
@@ -97,6 +99,7 @@ def _load():
                                 C.POINTER(C.c_void_p), C.POINTER(vp)]
     lib.ddamg_solve.argtypes = [vp, vp, vp, ip, C.c_double, C.POINTER(DdamgStats)]
     lib.ddamg_free.argtypes = [vp]
+    lib.ddamg_update_gauge.argtypes = [vp, vp, ip]
     lib.ddamg_cgnr.argtypes = [vp, vp, vp, ip, C.c_double, ip, C.POINTER(DdamgStats)]
     lib.ddamg_sigma_extremes.argtypes = [vp, ip, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_int)]
@@ -239,6 +242,11 @@ def ddamg_solve(h: Handle, rhs, x, n, tol, with_stats=True, raise_noconv=False):
         _check(rc)
     return [dict(iterations=s.iterations, cycles=s.cycles, converged=bool(s.converged),
                  true_residual=s.true_residual) for s in stats[:n]]
+
+
+def ddamg_update_gauge(h: Handle, gauge, n_inv):
+    """New gauge field into the hierarchy: operators rebuilt from the current test vectors, n_inv Alg. 4 passes."""
+    _check(lib().ddamg_update_gauge(h.raw, _ptr(gauge), int(n_inv)))
 
 
 def ddamg_cgnr(h: Handle, rhs, x, n, tol, max_iter=100000):

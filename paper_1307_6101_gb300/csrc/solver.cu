@@ -58,6 +58,7 @@ struct Work {
   cplx<T>* gout = nullptr; // fixed output of a captured K-cycle starting on this level
   GmresState gs{};
   int m = 0;
+  int batch = 0;              // columns the vectors hold (stride of the Krylov basis: batch * vlen)
   long long host_steps = 0;   // Arnoldi steps taken by the host-driven solver
 };
 
@@ -156,7 +157,8 @@ struct ddamg_handle {
   int* h_done = nullptr;      // pinned
   double* h_scal = nullptr;   // pinned
   int* h_kr = nullptr;        // pinned
-  int max_batch = 0;
+  int max_batch = 0;          // right-hand sides per solve batch (params.max_rhs)
+  int work_batch = 0;         // columns of the level workspaces: max(max_rhs, setup batch of Alg. 4)
   // per-kernel-class CUDA-event timing (ddamg_profile)
   int prof = 0;   // bitmask of recorded kernel classes
   std::vector<cudaEvent_t> ev[DDAMG_PROF_KINDS];
@@ -179,6 +181,7 @@ struct ddamg_handle {
   double tune_ms[3][DDAMG_MAX_LEVELS][5] = {};   // [DDAMG_TUNE_*][level][candidate]
   int tc_force = -1;   // DDAMG_OPT_COARSE_TC: -1 autotune, 0 CUDA cores, k >= 1 that split
   bool sap_schur = false;   // fine-level FP32 SAP block solves on the even-odd Schur complement
+  int setup_batch = 4;      // test vectors per batched K-cycle of Alg. 4
   // plain Krylov solver (CGNR) and sigma_min: four FP64 fine vectors per batch column, per-column
   // coefficients on the device, pinned host scalars
   cplx<double>* cg_vec = nullptr;
@@ -386,7 +389,7 @@ void krylov_host(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cp
   // restart cycles); tol_rhs: one relative tolerance per right-hand side
   cudaStream_t st = h->st;
   const size_t rs = vlen;
-  const size_t vs = (size_t)h->max_batch * vlen;
+  const size_t vs = (size_t)ws.batch * vlen;
   GmresState& gs = ws.gs;
   if (m > ws.m) fail(DDAMG_ERR_ARG, "Krylov length exceeds the workspace");
   GmresState s = gs;
@@ -521,7 +524,7 @@ template <typename T, class AOp, class MOp>
 void krylov_dev(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>* b, int nrhs, int m, double tol,
                 int max_cycles, bool flexible, AOp A, MOp M) {
   if (m > ws.m) fail(DDAMG_ERR_ARG, "Krylov length exceeds the workspace");
-  const size_t vs = (size_t)h->max_batch * vlen;
+  const size_t vs = (size_t)ws.batch * vlen;
   GmresState s = ws.gs;
   s.m = m;
   blas_zero<T>(x, vlen, nrhs, vlen, h->st);
@@ -816,6 +819,7 @@ void alloc_work(ddamg_handle* h, Level& L, Work<T>& w, int m, WorkRole role, int
   const size_t vl = L.vlen * (size_t)batch;
   const bool flexible = role != WORK_COARSEST;
   w.m = m;
+  w.batch = batch;
   w.r = dalloc<cplx<T>>(h, vl);
   if (role != WORK_OUTER) {
     w.gin = dalloc<cplx<T>>(h, vl);
@@ -991,6 +995,18 @@ void schur_bind(ddamg_handle* h) {
   F.f32.schur = h->sap_schur;
   F.f32.mix32 = h->sap_schur ? F.mix32 : nullptr;
   F.f32.mixh = h->sap_schur && h->half ? F.mixh : nullptr;
+}
+
+// the fine operator from a gauge field in the ABI layout: links (FP64, FP32), the clover term
+// with the mass shift (FP64, FP32)
+void import_operator(ddamg_handle* h, const double* gauge) {
+  Level& F = h->lv[0];
+  const size_t gbytes = sizeof(cplx<double>) * 36 * (size_t)F.g.V;
+  const cplx<double>* gd = static_cast<const cplx<double>*>(dev_in(h, gauge, gbytes, 0));
+  links_import<double>(F.f64.U, gd, F.g, h->st);
+  links_import<float>(F.f32.U, gd, F.g, h->st);
+  clover_build(F.f64.clov, gd, F.g, h->m0, h->csw, h->st);
+  real_convert<float>(F.f32.clov, F.f64.clov, (size_t)72 * F.g.V, h->st);
 }
 
 // Autotuner of the kernels that read FP16 operator data for a whole batch: on every level, time
@@ -1221,27 +1237,35 @@ void initial_setup_phase(ddamg_handle* h, int l, const double* const* tv_random)
   if (l < h->L - 2) initial_setup_phase(h, l + 1, tv_random);
 }
 
+// Alg. 4 on level l: every test vector of the level goes through one K-cycle; the results (and the
+// last iterates on the coarser levels) replace the test vectors, normalised.  Within one pass P and
+// the coarse operators do not change, so the K-cycles of different test vectors are independent:
+// they run in batches of up to work_batch columns, with results identical bit for bit to one
+// vector at a time (every kernel treats the columns of a batch independently).
 template <typename T>
 void iterative_setup_phase(ddamg_handle* h, int l, int i) {
   if (l >= h->L - 1) return;
   Level& L = h->lv[l];
   cudaStream_t st = h->st;
-  cplx<T>* bT = static_cast<cplx<T>*>(scratch(h, 5, sizeof(cplx<T>) * L.vlen));
-  cplx<T>* zT = static_cast<cplx<T>*>(scratch(h, 6, sizeof(cplx<T>) * L.vlen));
-  double* nrm = static_cast<double*>(scratch(h, 7, sizeof(double) * 8));
-  for (int j = 0; j < L.N; ++j) {
+  const int cb = std::max(1, std::min(h->work_batch, h->setup_batch));
+  cplx<T>* bT = static_cast<cplx<T>*>(scratch(h, 5, sizeof(cplx<T>) * L.vlen * cb));
+  cplx<T>* zT = static_cast<cplx<T>*>(scratch(h, 6, sizeof(cplx<T>) * L.vlen * cb));
+  double* nrm = static_cast<double*>(scratch(h, 7, sizeof(double) * 64));
+  for (int j0 = 0; j0 < L.N; j0 += cb) {
     SetupTimer tm{h, l, DDAMG_SETUP_KCYCLE};
-    blas_convert<T, double>(bT, L.tv64 + (size_t)j * L.vlen, L.vlen, 1, 0, 0, st);
-    kcycle_run<T>(h, l, zT, bT, 1);
+    const int jb = std::min(cb, L.N - j0);
+    blas_convert<T, double>(bT, L.tv64 + (size_t)j0 * L.vlen, L.vlen, jb, L.vlen, L.vlen, st);
+    kcycle_run<T>(h, l, zT, bT, jb);
     for (int k = l; k < h->L - 1; ++k) {
       Level& K = h->lv[k];
-      if (j >= K.N) continue;
+      const int nk = std::min(jb, K.N - j0);   // columns that are test vectors of level k
+      if (nk <= 0) continue;
       const cplx<T>* src = (k == l) ? zT : work<T>(K).xs;
-      cplx<double>* dst = K.tv64 + (size_t)j * K.vlen;
-      blas_convert<double, T>(dst, src, K.vlen, 1, 0, 0, st);
-      blas_norm2<double>(nrm, dst, K.vlen, 1, 0, st);
-      blas_recip(nrm, 1, st);
-      blas_scale_to<double>(dst, dst, nrm, K.vlen, 1, 0, st);
+      cplx<double>* dst = K.tv64 + (size_t)j0 * K.vlen;
+      blas_convert<double, T>(dst, src, K.vlen, nk, K.vlen, K.vlen, st);
+      blas_norm2<double>(nrm, dst, K.vlen, nk, K.vlen, st);
+      blas_recip(nrm, nk, st);
+      blas_scale_to<double>(dst, dst, nrm, K.vlen, nk, K.vlen, st);
     }
     sync(h);
   }
@@ -1297,7 +1321,7 @@ void ensure_work(ddamg_handle* h) {
     Level& L = h->lv[l];
     const int m = L.coarsest ? h->p.coarse_restart : (l >= 1 ? h->p.kcycle_len : 0);
     const WorkRole role = L.fine ? WORK_FINE : (L.coarsest ? WORK_COARSEST : WORK_COARSE);
-    alloc_work<T>(h, L, work<T>(L), m, role, h->max_batch);
+    alloc_work<T>(h, L, work<T>(L), m, role, h->work_batch);
   }
   ready = true;
 }
@@ -1407,6 +1431,7 @@ void validate(const ddamg_params& p) {
     fail(DDAMG_ERR_ARG, "Krylov lengths must be 1..63");
   if (p.mr_steps < 0 || p.nu < 0 || p.mu < 0 || p.n_inv < 0 || p.eta_passes < 0) fail(DDAMG_ERR_ARG, "negative count");
   if (p.max_rhs < 1 || p.max_rhs > 64) fail(DDAMG_ERR_ARG, "max_rhs must be 1..64");
+  if (p.setup_batch < 0 || p.setup_batch > 64) fail(DDAMG_ERR_ARG, "setup_batch must be 0..64");
   if (p.precision < 0 || p.precision > 2) fail(DDAMG_ERR_ARG, "precision must be 0, 1 or 2");
 }
 
@@ -1864,6 +1889,8 @@ void server_worker(ddamg_server* S, SrvHier* H) {
 size_t estimate_bytes(const int dims0[4], const ddamg_params& p) {
   size_t tot = 0;
   const size_t B = (size_t)p.max_rhs;
+  // level workspaces hold max(max_rhs, setup batch) columns (Alg. 4 runs in batches)
+  const size_t WB = std::max(B, (size_t)std::min(p.setup_batch > 0 ? p.setup_batch : 4, 64));
   int dims[4] = {dims0[0], dims0[1], dims0[2], dims0[3]};
   int nprev = 12, Nprev = 0;
   size_t vlen0 = 0, maxtmp = 0;
@@ -1889,13 +1916,13 @@ size_t estimate_bytes(const int dims0[4], const ddamg_params& p) {
     }
     // workspaces of the configured precision (see alloc_work / ensure_work)
     const int m = coarsest ? p.coarse_restart : (l >= 1 ? p.kcycle_len : 0);
-    const size_t vl = vlen * B;
+    const size_t vl = vlen * WB;
     const size_t tb = p.precision == 0 ? 16 : 8;
     size_t nvec = fine ? 3 : (coarsest ? 12 : 7);
     if (m > 0) nvec += (size_t)(m + 1) + (coarsest ? 0 : (size_t)m);
     tot += nvec * vl * tb;
     const size_t mm = m > 0 ? m : 1;
-    tot += B * ((mm + 1) * mm * 16 + mm * 8 + mm * 16 + 4 * (mm + 1) * 16 + 64);
+    tot += WB * ((mm + 1) * mm * 16 + mm * 8 + mm * 16 + 4 * (mm + 1) * 16 + 64);
     if (!coarsest) {
       for (int d = 0; d < 4; ++d) dims[d] /= p.agg[l][d];
       nprev = n;
@@ -1911,6 +1938,8 @@ size_t estimate_bytes(const int dims0[4], const ddamg_params& p) {
   const size_t V0 = vlen0 / 12;
   tot += std::max({V0 * 576, vlen0 * (size_t)std::min(p.n_tv[0], 4) * 16, vl0 * 16}) + vl0 * 16;
   tot += maxtmp + 2 * maxtmp / 2;
+  // Alg. 4 input and output of one batch of test vectors (setup scratch)
+  tot += 2 * vlen0 * (WB > B ? WB : B) * (p.precision == 0 ? 16 : 8);
   return tot;
 }
 
@@ -1952,6 +1981,7 @@ void ddamg_default_params(ddamg_params* p) {
   p->max_rhs = 1;
   p->seed = 0;
   p->sap_schur = 0;
+  p->setup_batch = 4;
 }
 
 const char* ddamg_last_error(void) { return g_err.c_str(); }
@@ -1972,6 +2002,8 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
     h->m0 = m0;
     h->csw = csw;
     h->max_batch = params->max_rhs;
+    h->setup_batch = params->setup_batch > 0 ? params->setup_batch : 4;
+    h->work_batch = std::max(h->max_batch, std::min(h->setup_batch, 64));
     CK(cudaGetDevice(&h->device));
     CK(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
     h->st = h->own;
@@ -1988,13 +2020,7 @@ int ddamg_setup(const double* gauge, const int dims[4], int bc_t, double m0, dou
     double gg[6 * 16 * 2];
     gamma_products(gg);
     set_gamma_products(gg);
-    Level& F = h->lv[0];
-    const size_t gbytes = sizeof(cplx<double>) * 36 * (size_t)F.g.V;
-    const cplx<double>* gd = static_cast<const cplx<double>*>(dev_in(h, gauge, gbytes, 0));
-    links_import<double>(F.f64.U, gd, F.g, h->st);
-    links_import<float>(F.f32.U, gd, F.g, h->st);
-    clover_build(F.f64.clov, gd, F.g, m0, csw, h->st);
-    real_convert<float>(F.f32.clov, F.f64.clov, (size_t)72 * F.g.V, h->st);
+    import_operator(h, gauge);
     if (h->p.precision == 2) {
       h->half = true;
       half_alloc(h);
@@ -2042,6 +2068,26 @@ void ddamg_free(ddamg_handle* h) {
     for (cudaEvent_t e : v) cudaEventDestroy(e);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
+}
+
+int ddamg_update_gauge(ddamg_handle* h, const double* gauge, int n_inv) {
+  if (!h || !gauge || n_inv < 0) {
+    g_err = "invalid argument";
+    return DDAMG_ERR_ARG;
+  }
+  return guard([&] {
+    sync(h);
+    import_operator(h, gauge);
+    if (h->lv[0].Uh) half_refresh_fine(h);
+    if (h->lv[0].mix32) schur_tables(h);
+    // P from the current test vectors, coarse operators of the new fine operator
+    for (int l = 0; l + 1 < h->L; ++l) rebuild(h, l);
+    for (int i = 1; i <= n_inv; ++i) {
+      if (h->p.precision != 0) iterative_setup_phase<float>(h, 0, i);
+      else iterative_setup_phase<double>(h, 0, i);
+    }
+    sync(h);
+  });
 }
 
 int ddamg_set_stream(ddamg_handle* h, void* stream) {
