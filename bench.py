@@ -77,8 +77,8 @@ TOL = 1e-10
 SERVING = dict(
     name="serving: Poisson requests over resident hierarchies 16^3x32, 24^3x48, 32^3x64 "
          "(eps 0.4, csw 1.0, three levels as the 16^3x32 workload), 1-12 complex N(0,1) RHS per request",
-    lattices=[(32, 16, 16, 16), (48, 24, 24, 24), (64, 32, 32, 32)], rates=(5, 20, 80), seconds=10.0,
-    max_requests=1000, max_rhs_total=48, max_rhs=6, seed=3)
+    lattices=[(32, 16, 16, 16), (48, 24, 24, 24), (64, 32, 32, 32)], rates=(5, 20, 80), requests=100,
+    max_rhs=6, seed=3)
 PAPER_OUTER_ITERATIONS = 22   # three-level outer FGMRES iterations on P2 (Table 3 of the paper)
 # outer_iterations in a workload: the outer FGMRES iterations this method takes on it (measured with
 # the library's FP64 and mixed solves); the oracle's per-iteration time is scaled by it, else by the
@@ -453,7 +453,7 @@ def run_gpu(args, w):
                                               args.large_steps, barrier)
     if rank == 0 and world == 1 and not args.no_serving and default:
         # short serving run on this lattice: Poisson arrivals, 1-12 RHS per request, 6 batch slots
-        out["serving"] = serving_bench(dd, w, [tuple(w["dims"])], (20,), 5.0, 1000, 6, SERVING["seed"], 60)
+        out["serving"] = serving_bench(dd, w, [tuple(w["dims"])], (20,), 30, 6, SERVING["seed"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline and default:
         out["cpu_baseline"] = cpu_baseline(w, out["iterations"][0] if out["iterations"] else None)
     if rank == 0:
@@ -645,23 +645,20 @@ def serving_handle(dd, w, dims, max_rhs, seed):
     return dd.ddamg_setup(U, dims, -1, mass(w["mass"]), w["csw"], p, None)
 
 
-def serving_run(dd, srv, hids, pools, rate, seconds, max_requests, rng, max_rhs_total):
-    """Poisson arrivals at `rate` req/s for `seconds`; each request: a uniform hierarchy and 1-12 RHS.
+def serving_run(dd, srv, hids, pools, rate, n_requests, rng):
+    """n_requests Poisson arrivals at `rate` req/s; each request: a uniform hierarchy and 1-12 RHS.
 
-    Arrivals stop after `seconds` or once `max_rhs_total` right-hand sides were offered, so
-    that an offered load above capacity (the queue grows) still ends in bounded time.
+    The offered load is not capped: above capacity the queue grows, which the record shows as the
+    queueing time of the first and the last quarter of the requests.
     """
     import threading
-    sched, t, tot = [], 0.0, 0
-    while len(sched) < max_requests and tot < max_rhs_total:
+    sched, t = [], 0.0
+    for _ in range(n_requests):
         t += rng.exponential(1.0 / rate)
-        if t > seconds:
-            break
         k = int(rng.integers(len(hids)))
         n = int(rng.integers(1, 13))
         cols = np.sort(rng.choice(pools[k].shape[0], size=n, replace=False))
         sched.append((t, k, n, cols))
-        tot += n
     subs = []
     t0 = time.perf_counter()
 
@@ -695,17 +692,24 @@ def serving_run(dd, srv, hids, pools, rate, seconds, max_requests, rng, max_rhs_
     rhs = sum(r["n"] for r in rec)
     p99 = lat[min(len(lat) - 1, int(np.ceil(0.99 * len(lat))) - 1)]
     arrivals = sched[-1][0] if sched else 0.0
+    q = max(1, len(rec) // 4)
+    per_h = {}
+    for r in rec:
+        per_h.setdefault(r["k"], []).append(r["latency"])
     return {"rate_req_s": rate, "requests": len(rec), "rhs": rhs, "arrival_window_s": round(arrivals, 3),
-            "span_s": round(end, 3),
-            "rhs_per_s": round(rhs / end, 2), "offered_rhs_per_s": round(rate * 6.5, 1),
+            "span_s": round(end, 3), "rhs_per_s": round(rhs / end, 2),
+            "offered_rhs_per_s": round(rhs / max(1e-9, arrivals), 1),
             "p50_latency_s": round(statistics.median(lat), 4),
             ("p99_latency_s" if len(lat) >= 100 else "p99_latency_s_is_max"): round(p99, 4),
             "mean_queue_s": round(statistics.mean(r["queue"] for r in rec), 4),
+            "queue_s_first_quarter": round(statistics.mean(r["queue"] for r in rec[:q]), 4),
+            "queue_s_last_quarter": round(statistics.mean(r["queue"] for r in rec[-q:]), 4),
+            "p50_latency_s_per_lattice": {str(k): round(statistics.median(v), 4) for k, v in sorted(per_h.items())},
             "all_converged": all(r["conv"] and r["rc"] == 0 for r in rec),
             "max_true_residual": max(r["res"] for r in rec)}
 
 
-def serving_bench(dd, w, lattices, rates, seconds, max_requests, max_rhs, seed, max_rhs_total):
+def serving_bench(dd, w, lattices, rates, n_requests, max_rhs, seed):
     import synth
     t0 = time.perf_counter()
     handles = [serving_handle(dd, w, dims, max_rhs, seed + 10 * k) for k, dims in enumerate(lattices)]
@@ -721,7 +725,7 @@ def serving_bench(dd, w, lattices, rates, seconds, max_requests, max_rhs, seed, 
             b = np.ascontiguousarray(pools[k][:n])
             x = np.zeros_like(b)
             srv.wait(srv.submit(hids[k], b, n, TOL), x, n)
-    runs = [serving_run(dd, srv, hids, pools, r, seconds, max_requests, rng, max_rhs_total) for r in rates]
+    runs = [serving_run(dd, srv, hids, pools, r, n_requests, rng) for r in rates]
     srv.free()
     for h in handles:
         h.free()
@@ -737,16 +741,15 @@ def run_serving(args):
     import paper_1307_6101_gb300 as dd
     w = WORKLOADS["three_level_16c32"]
     S = SERVING
-    res = serving_bench(dd, w, S["lattices"], S["rates"], args.serve_seconds or S["seconds"], S["max_requests"],
-                        S["max_rhs"], S["seed"], S["max_rhs_total"])
+    n_req = args.serve_requests or S["requests"]
+    res = serving_bench(dd, w, S["lattices"], S["rates"], n_req, S["max_rhs"], S["seed"])
     tot_rhs = sum(r["rhs"] for r in res["runs"])
     tot_t = sum(r["span_s"] for r in res["runs"])
     out = {"metric": "serving: p50/p99 latency (s) and RHS/s under Poisson load, true rel. residual 1e-10",
            "value": round(tot_rhs / tot_t, 3), "unit": "RHS/s", "n_gpus": 1, "higher_is_better": True,
            "dtype": "f32 preconditioner on f16 storage / f64 outer FGMRES", "data": "synthetic",
-           "config": {"workload": S["name"], "rates_req_s": list(S["rates"]),
-                      "seconds_per_rate": args.serve_seconds or S["seconds"],
-                      "max_rhs_offered_per_rate": S["max_rhs_total"]},
+           "config": {"workload": S["name"], "rates_req_s": list(S["rates"]), "requests_per_rate": n_req,
+                      "batch_slots_per_hierarchy": S["max_rhs"]},
            "serving": res}
     print(json.dumps(out))
 
@@ -842,8 +845,8 @@ def main():
                     help="storage of the mixed path's operator data (default fp16, per-site scales)")
     ap.add_argument("--serving", action="store_true",
                     help="serving benchmark: Poisson request streams over three resident hierarchies")
-    ap.add_argument("--serve-seconds", type=float, default=0.0,
-                    help="seconds of arrivals per rate (serving benchmark; default 20)")
+    ap.add_argument("--serve-requests", type=int, default=0,
+                    help="requests per rate of the serving benchmark (default 100)")
     ap.add_argument("--no-serving", action="store_true", help="skip the short serving run of the default bench")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the batched 32^3x64 sub-measurement of the default bench")
