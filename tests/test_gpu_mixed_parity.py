@@ -126,7 +126,7 @@ def test_half_storage_kcycle_matches_oracle(dd):
     from oracle.smoother import SAP
     from oracle.lattice import red_black_block
     extra = dict(kcycle_tol=1e-30, coarse_tol=1e-30, coarse_cycles=2, kcycle_len=5, kcycle_cycles=2)
-    c = Case(**THREE, n_inv=0, eta_passes=0, nu=2, coarse_restart=10, extra=extra)
+    c = Case(**THREE, n_inv=0, eta_passes=0, nu=2, coarse_restart=10, max_rhs=2, extra=extra)
     U = c.gauge()
     tv = c.random_tv()
     h = c.gpu(0, U, tv)                       # FP64 setup: P and D_l agree with the oracle's to 1e-12
