@@ -48,11 +48,29 @@ def _ptxas_report(src):
 
 def test_fine_sap_4x4_kernel_resources():
     rep = _ptxas_report("fine.cu")
-    b4 = {k: v for k, v in rep.items() if "k_fine_sap_b4" in k}
+    b4 = {k: v for k, v in rep.items() if "k_fine_sap_b4" in k and "k_fine_sap_b4_eo" not in k}
     assert len(b4) == 2                                  # FP16 and FP32 storage
     for k, v in b4.items():
         assert v["regs"] <= 128, (k, v)
         assert v["stack"] == 0 and v["spill_st"] == 0 and v["spill_ld"] == 0, (k, v)
+    # the Schur variant: two 128-thread CTAs per SM, no local memory
+    eo = {k: v for k, v in rep.items() if "k_fine_sap_b4_eo" in k}
+    assert len(eo) == 2
+    for k, v in eo.items():
+        assert v["regs"] * 128 * 2 <= 65536, (k, v)
+        assert v["stack"] == 0 and v["spill_st"] == 0 and v["spill_ld"] == 0, (k, v)
+
+
+def test_tensor_core_kernels_resources():
+    """The tensor-core coarse stencil and restriction keep their fragments and accumulators in
+    registers (no local memory) and fit their largest CTA (1024 threads) in an SM's registers."""
+    for src, name in (("coarse_tc.cu", "k_coarse_apply_tc"), ("transfer_tc.cu", "k_restrict_tc")):
+        rep = _ptxas_report(src)
+        ks = {k: v for k, v in rep.items() if name in k}
+        assert ks, (src, list(rep))
+        for k, v in ks.items():
+            assert v["spill_st"] == 0 and v["spill_ld"] == 0, (k, v)
+            assert v["regs"] * 1024 <= 65536, (k, v)
 
 
 def test_arnoldi_cluster_kernel_resources():
