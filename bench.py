@@ -504,39 +504,9 @@ def large_workload(dd, torch, stream, w, prec, steps, barrier):
 
 
 # ---------------------------------------------------------------------------
-def _oracle_worker(job):
-    """One oracle process: build the hierarchy (untimed), then time `steps` outer FGMRES iterations
-    (K-cycle + D + CGS2) on this worker's own right-hand side.  Returns per-iteration seconds."""
-    name, worker, steps, warmup, with_ops = job
-    import oracle.multigrid as omg
-    from oracle.krylov import fgmres
-    from oracle.wilson import WilsonOp
-    w = WORKLOADS[name]
-    U, tv, rhs = inputs(w, rank=worker, host_tv=True)
-    op = WilsonOp.build(U, mass(w["mass"]), w["csw"], -1)
-    p = omg.Params(levels=w["levels"], agg=tuple(w["agg"]), n_tv=tuple(w["n_tv"]),
-                   sap_block=tuple(w["sap"]) + (None,), mr_steps=w["mr_steps"], nu=w["nu"], n_inv=0,
-                   eta_passes=0, outer_restart=w["outer_restart"])
-    t0 = time.perf_counter()
-    h = omg.Hierarchy(op, p).setup(tv)
-    t_setup = time.perf_counter() - t0
-    b = rhs[0]
-    per_op = oracle_operator_seconds(h, op, p, b) if with_ops else None
-    for _ in range(warmup):
-        fgmres(op.apply, b, M=lambda v: h.kcycle(0, v), m=1, tol=TOL, max_cycles=1, final_residual=False)
-    times = []
-    c0 = time.process_time()
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        fgmres(op.apply, b, M=lambda v: h.kcycle(0, v), m=1, tol=TOL, max_cycles=1, final_residual=False)
-        times.append(time.perf_counter() - t0)
-    used = (time.process_time() - c0) / max(1e-9, sum(times))
-    return {"times": times, "setup_s": t_setup, "cpu_per_wall": used, "per_op": per_op}
-
-
 def _single_thread_env():
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[k] = "1"
+        os.environ.setdefault(k, "1")
 
 
 def host_cores():
@@ -546,37 +516,65 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def oracle_sample(w, steps, warmup, iterations_per_solve, workers=1):
-    """Oracle timing on `workers` host cores: one process per core, each solving its own right-hand
-    side, all timed together; one step = one outer FGMRES iteration on every worker.
+def oracle_sample(w, steps, warmup, iterations_per_solve, workers=1, also=()):
+    """Oracle timing on `workers` host cores: one oracle hierarchy, built once, shared by `workers`
+    threads that each run outer FGMRES iterations (K-cycle + D + CGS2) on their own right-hand side
+    at the same time (numpy releases the interpreter lock inside its array operations); one step =
+    one iteration on every thread.  The cores actually used are measured as the process's CPU
+    seconds over the wall seconds of the timed region.
 
-    The oracle hierarchy is built by the oracle itself, by Alg. 3 without smoothing passes (random
-    test vectors orthonormalised, Galerkin operators), so that its construction stays bounded: the
+    The oracle hierarchy is built by the oracle itself, by Alg. 3 without smoothing passes (its test
+    vectors orthonormalised, Galerkin operators), so that its construction stays bounded: the
     oracle's inputs never come from the CUDA library, and its full setup would take hours here.  The
     per-iteration cost does not depend on the test vectors.
     """
-    import multiprocessing as mp
+    import concurrent.futures as cf
+    import oracle.multigrid as omg
+    from oracle.krylov import fgmres
+    from oracle.wilson import WilsonOp
+    import synth
     _single_thread_env()
-    name = next(k for k, v in WORKLOADS.items() if v is w)
-    jobs = [(name, q, steps, warmup, q == 0) for q in range(workers)]
-    if workers == 1:
-        res = [_oracle_worker(jobs[0])]
-    else:
-        with mp.get_context("spawn").Pool(workers) as pool:
-            res = pool.map(_oracle_worker, jobs)
-    # the slowest worker's iteration time bounds the concurrent throughput
-    t_iter = max(statistics.mean(r["times"]) for r in res)
+    U, tv, _ = inputs(w, host_tv=True, with_rhs=False)
+    op = WilsonOp.build(U, mass(w["mass"]), w["csw"], -1)
+    p = omg.Params(levels=w["levels"], agg=tuple(w["agg"]), n_tv=tuple(w["n_tv"]),
+                   sap_block=tuple(w["sap"]) + (None,), mr_steps=w["mr_steps"], nu=w["nu"], n_inv=0,
+                   eta_passes=0, outer_restart=w["outer_restart"])
+    t0 = time.perf_counter()
+    h = omg.Hierarchy(op, p).setup(tv)
+    t_setup = time.perf_counter() - t0
+    del tv
+    rhs = synth.random_spinors(max((workers,) + tuple(also)), w["dims"], w["rhs_seed"] + 500)
+    per_op = oracle_operator_seconds(h, op, p, rhs[0])
     its = iterations_per_solve or w.get("outer_iterations") or PAPER_OUTER_ITERATIONS
-    used = sum(r["cpu_per_wall"] for r in res)
-    ncols = 1
-    return {"value": workers * ncols / (t_iter * its), "unit": "RHS/s", "cores": workers,
-            "cpu_seconds_per_wall_second": round(used, 2), "host_cores_available": host_cores(),
-            "kind": "oracle",
-            "sample": (f"{steps} outer FGMRES iteration(s) of the FP64 numpy oracle on the same workload, "
-                       f"{workers} single-threaded process(es) each on its own right-hand side "
-                       f"(hierarchy from Alg. 3 without smoothing, built in {max(r['setup_s'] for r in res):.0f} s, "
-                       f"untimed); {t_iter:.2f} s per iteration scaled by {its} iterations per solve"),
-            "seconds_per_iteration": t_iter, "iterations_per_solve": its, "per_operator_s": res[0]["per_op"]}
+
+    def one(q):
+        fgmres(op.apply, rhs[q], M=lambda v: h.kcycle(0, v), m=1, tol=TOL, max_cycles=1, final_residual=False)
+
+    def sample(nw):
+        with cf.ThreadPoolExecutor(max_workers=nw) as ex:
+            for _ in range(warmup):
+                list(ex.map(one, range(nw)))
+            times = []
+            c0 = time.process_time()
+            for _ in range(steps):
+                t0 = time.perf_counter()
+                list(ex.map(one, range(nw)))
+                times.append(time.perf_counter() - t0)
+            used = (time.process_time() - c0) / max(1e-9, sum(times))
+        t_step = statistics.mean(times)
+        return {"value": nw / (t_step * its), "unit": "RHS/s", "cores": max(1, round(used)),
+                "threads": nw, "cpu_seconds_per_wall_second": round(used, 2),
+                "host_cores_available": host_cores(), "kind": "oracle",
+                "sample": (f"{steps} outer FGMRES iteration(s) of the FP64 numpy oracle on the same workload, "
+                           f"{nw} thread(s) each on its own right-hand side over one shared hierarchy "
+                           f"(Alg. 3 without smoothing, built in {t_setup:.0f} s, untimed); {t_step:.2f} s per "
+                           f"step scaled by {its} iterations per solve"),
+                "seconds_per_iteration": t_step, "iterations_per_solve": its, "per_operator_s": per_op}
+
+    out = sample(workers)
+    for nw in also:
+        out[f"threads_{nw}"] = sample(nw)
+    return out
 
 
 def oracle_operator_seconds(h, op, p, b):
@@ -599,13 +597,17 @@ def oracle_operator_seconds(h, op, p, b):
 
 def cpu_baseline(w, its):
     """The oracle on all host cores (the headline baseline) and on one core."""
-    allc = oracle_sample(w, steps=1, warmup=0, iterations_per_solve=its, workers=host_cores())
-    one = oracle_sample(w, steps=1, warmup=0, iterations_per_solve=its, workers=1)
-    allc["one_core"] = {k: one[k] for k in ("value", "unit", "cores", "seconds_per_iteration", "sample")}
-    return allc
+    allc = oracle_sample(w, steps=1, warmup=0, iterations_per_solve=its, workers=host_cores(), also=(1,))
+    one = allc.pop("threads_1")
+    keys = ("value", "unit", "cores", "threads", "cpu_seconds_per_wall_second", "seconds_per_iteration", "sample")
+    # the faster of the two configurations is the baseline; both are reported
+    best = dict(allc if allc["value"] >= one["value"] else one)
+    best["all_cores"] = {k: allc[k] for k in keys}
+    best["one_core"] = {k: one[k] for k in keys}
+    return best
 
 
-REFERENCE_BUDGET_S = 150.0   # timed seconds of the reference arm (its steps are capped to fit)
+REFERENCE_STEPS = 3   # timed steps of the reference arm (each a parallel oracle iteration of ~1 min)
 
 
 def run_reference(args, w):
@@ -613,9 +615,11 @@ def run_reference(args, w):
     if rank != 0:   # under torchrun only rank 0 times the oracle
         return
     workers = host_cores()
-    probe = oracle_sample(w, steps=1, warmup=0, iterations_per_solve=None, workers=1)
-    steps = max(1, min(args.steps, int(REFERENCE_BUDGET_S // max(1e-9, probe["seconds_per_iteration"]))))
-    s = oracle_sample(w, steps=steps, warmup=0, iterations_per_solve=None, workers=workers)
+    steps = max(1, min(args.steps, REFERENCE_STEPS))
+    s = oracle_sample(w, steps=steps, warmup=0, iterations_per_solve=None, workers=workers, also=(1,))
+    one = s.pop("threads_1")
+    if one["value"] > s["value"]:   # the faster configuration is the baseline
+        s, one = dict(one, per_operator_s=s["per_operator_s"]), s
     v = s["value"]
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "RHS/s", "n_gpus": args.gpus,
            "steps": steps, "steps_requested": args.steps, "warmup": args.warmup,
@@ -624,12 +628,15 @@ def run_reference(args, w):
            "data": "synthetic (seeded SU(3) links, complex N(0,1) rhs)",
            "config": {"workload": w["name"], "lattice": "x".join(str(d) for d in w["dims"][::-1]),
                       "levels": w["levels"], "rhs_per_step": workers, "tol": TOL,
-                      "step": f"one outer FGMRES iteration of the oracle on each of {workers} cores "
-                              f"(own right-hand side per core); steps capped at {REFERENCE_BUDGET_S:.0f} s"},
+                      "step": f"one outer FGMRES iteration of the oracle on each of {workers} threads "
+                              f"(own right-hand side per thread, one shared hierarchy); at most "
+                              f"{REFERENCE_STEPS} steps"},
            "cpu_baseline": {"value": v, "unit": "RHS/s", "cores": s["cores"], "kind": "oracle", "sample": s["sample"],
-                            "per_operator_s": probe["per_operator_s"],
-                            "one_core": {"value": probe["value"], "cores": 1,
-                                         "seconds_per_iteration": probe["seconds_per_iteration"]}},
+                            "cpu_seconds_per_wall_second": s["cpu_seconds_per_wall_second"],
+                            "per_operator_s": s["per_operator_s"],
+                            "other_configuration": {"value": one["value"], "threads": one["threads"],
+                                                    "cores": one["cores"],
+                                                    "seconds_per_iteration": one["seconds_per_iteration"]}},
            "e2e": {"value": v, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -212,12 +212,18 @@ def philox_normal_pairs(x, k, j, level, seed):
 
 def philox_fields(n: int, dims, ndof: int, seed: int, level: int = 0, j0: int = 0) -> np.ndarray:
     """n complex N(0,1) fields [n, T, Z, Y, X, ndof] drawn by the counter-based generator
-    (field indices j0 .. j0+n-1 on `level`); the same numbers the CUDA library draws."""
+    (field indices j0 .. j0+n-1 on `level`); the same numbers the CUDA library draws.
+    Drawn in slices of at most 2^20 entries, to bound the temporaries."""
     V = lattice_volume(dims)
-    j = np.arange(j0, j0 + n, dtype=np.uint64)[:, None, None]
-    x = np.arange(V, dtype=np.uint64)[None, :, None]
-    k = np.arange(ndof, dtype=np.uint64)[None, None, :]
-    out = philox_normal_pairs(x, k, j, np.uint64(level), seed)
+    out = np.empty((n, V * ndof), dtype=np.complex128)
+    lin = np.arange(V * ndof, dtype=np.uint64)
+    step = 1 << 20
+    for f in range(n):
+        for a in range(0, V * ndof, step):
+            e = lin[a:a + step]
+            x = e // np.uint64(ndof)
+            k = e - x * np.uint64(ndof)
+            out[f, a:a + step] = philox_normal_pairs(x, k, np.uint64(j0 + f), np.uint64(level), seed)
     return np.ascontiguousarray(out.reshape((n,) + tuple(dims) + (ndof,)))
 
 
