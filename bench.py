@@ -294,7 +294,22 @@ class Timer:
         return out + (sum(ms),)
 
 
-def roofline(prof, prec, kernel_file):
+# FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 (fused multiply-add) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# algorithmic FP32 operations of the 4^4 SAP sweep per site of the colour and right-hand side:
+# one application of D (8 hops x 180: spin projection 12, two SU(3) products 144, reconstruction 24;
+# clover 2 x 252; combination 48) for rho = b - D z (+24), then per MR step one application of D_B
+# and 340 for the two reductions and the two updates
+SAP_FLOP_RHO = 8 * 180 + 2 * 252 + 48 + 24
+SAP_FLOP_STEP = 8 * 180 + 2 * 252 + 48 + 340
+
+
+def sap_flops(w, nrhs):
+    V = w["dims"][0] * w["dims"][1] * w["dims"][2] * w["dims"][3]
+    return V / 2 * nrhs * (SAP_FLOP_RHO + w["mr_steps"] * SAP_FLOP_STEP)
+
+
+def roofline(prof, prec, kernel_file, flops_per_launch=None):
     pk, pk_src = peaks()
     p_ms, p_n, p_bytes, solve_ms = prof
     avg_ms = p_ms / max(1, p_n)
@@ -306,7 +321,13 @@ def roofline(prof, prec, kernel_file):
             "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms, "launches": p_n,
             "share_of_step": round(p_ms / max(1e-9, solve_ms), 4),
             "timing": "CUDA events around every launch of this kernel on its stream, in a separate "
-                      "profiled region of the same solves (value comes from an uninstrumented region)"}
+                      "profiled region of the same solves (value comes from an uninstrumented region)",
+            "alu": None if flops_per_launch is None else {
+                "achieved_tflops": round(flops_per_launch / (avg_ms / 1e3) / 1e12, 2),
+                "peak_tflops": round(FP32_PEAK_TFLOPS, 1), "frac": round(flops_per_launch / (avg_ms / 1e3) / 1e12 /
+                                                                         FP32_PEAK_TFLOPS, 4),
+                "flops_per_launch": flops_per_launch,
+                "peak_source": "unit counts x maximum SM clock (152 SMs, 128 FP32 lanes, FMA, 2.07 GHz)"}}
 
 
 def run_gpu(args, w):
@@ -372,7 +393,7 @@ def run_gpu(args, w):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": ncols * args.steps / (sum(ms_mixed) / 1e3), "unit": "RHS/s",
                               "note": "profiling run (--only-mixed): not a bench line",
-                              "roofline": roofline(prof, mixed_prec, KERNEL_FILE)}))
+                              "roofline": roofline(prof, mixed_prec, KERNEL_FILE, sap_flops(w, nb))}))
         return
     # end to end through the C ABI with host buffers in pinned memory (H2D of the rhs and D2H of x
     # inside every step; L2 flushed before every step, as in the device-timed loop)
@@ -435,7 +456,7 @@ def run_gpu(args, w):
                        "true_residual": max(s["true_residual"] for st in st_fp64 for s in st)},
         "mixed_over_fp64": round(value / value_fp64, 3),
         "setup_s": {k: round(v, 2) for k, v in setup_s.items()},
-        "roofline": roofline(prof, mixed_prec, KERNEL_FILE),
+        "roofline": roofline(prof, mixed_prec, KERNEL_FILE, sap_flops(w, nb)),
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -500,7 +521,7 @@ def large_workload(dd, torch, stream, w, prec, steps, barrier):
             "s_per_rhs": round(tot / 1e3 / (ncols * steps), 5), "ms_per_step": round(tot / steps, 1),
             "iterations": [s["iterations"] for s in stats[0]], "true_residual": res, "all_converged": conv,
             "setup_s": round(t_setup, 1), "device_bytes": int(dev), "gpu_launches": int(launches),
-            "clocks": clocks, "roofline": roofline(prof, prec, KERNEL_FILE)}
+            "clocks": clocks, "roofline": roofline(prof, prec, KERNEL_FILE, sap_flops(w, w["nrhs"]))}
 
 
 # ---------------------------------------------------------------------------
