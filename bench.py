@@ -315,6 +315,10 @@ def roofline(prof, prec, kernel_file, flops_per_launch=None):
     avg_ms = p_ms / max(1, p_n)
     per_launch = p_bytes / max(1, p_n)
     achieved = per_launch / (avg_ms / 1e3) / 1e9
+    # the binding roof: FP32 ALU when the sweep's arithmetic intensity is above the FP32 / HBM ridge
+    ridge = FP32_PEAK_TFLOPS * 1e12 / (pk * 1e9)
+    intensity = (flops_per_launch / per_launch) if flops_per_launch else 0.0
+    bound = "alu" if intensity > ridge else "hbm"
     return {"kernel": ROOF_KERNELS[prec] + " (one SAP colour sweep, 4 MR steps)", "bound": "hbm",
             "achieved": round(achieved, 1), "peak": pk, "unit": "GB/s", "frac": round(achieved / pk, 4),
             "peak_source": pk_src, "traffic": ncu_traffic(kernel_file),
@@ -322,6 +326,7 @@ def roofline(prof, prec, kernel_file, flops_per_launch=None):
             "share_of_step": round(p_ms / max(1e-9, solve_ms), 4),
             "timing": "CUDA events around every launch of this kernel on its stream, in a separate "
                       "profiled region of the same solves (value comes from an uninstrumented region)",
+            "binding_roof": bound, "flop_per_byte": round(intensity, 2), "ridge_flop_per_byte": round(ridge, 2),
             "alu": None if flops_per_launch is None else {
                 "achieved_tflops": round(flops_per_launch / (avg_ms / 1e3) / 1e12, 2),
                 "peak_tflops": round(FP32_PEAK_TFLOPS, 1), "frac": round(flops_per_launch / (avg_ms / 1e3) / 1e12 /
