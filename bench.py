@@ -310,29 +310,40 @@ def sap_flops(w, nrhs):
 
 
 def roofline(prof, prec, kernel_file, flops_per_launch=None):
+    """Roofline of the fine SAP sweep.  Its algorithmic bytes and FLOPs per launch over its average
+    launch time give an HBM and an FP32 ALU fraction; the primary entry is the roof that binds by
+    arithmetic intensity (FLOPs per algorithmic byte against the FP32 / HBM ridge), the other is
+    reported beside it."""
     pk, pk_src = peaks()
     p_ms, p_n, p_bytes, solve_ms = prof
     avg_ms = p_ms / max(1, p_n)
     per_launch = p_bytes / max(1, p_n)
-    achieved = per_launch / (avg_ms / 1e3) / 1e9
-    # the binding roof: FP32 ALU when the sweep's arithmetic intensity is above the FP32 / HBM ridge
+    gbs = per_launch / (avg_ms / 1e3) / 1e9
+    hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk, "unit": "GB/s", "frac": round(gbs / pk, 4),
+           "peak_source": pk_src, "traffic": ncu_traffic(kernel_file), "algorithmic_bytes_per_launch": per_launch}
     ridge = FP32_PEAK_TFLOPS * 1e12 / (pk * 1e9)
-    intensity = (flops_per_launch / per_launch) if flops_per_launch else 0.0
-    bound = "alu" if intensity > ridge else "hbm"
-    return {"kernel": ROOF_KERNELS[prec] + " (one SAP colour sweep, 4 MR steps)", "bound": "hbm",
-            "achieved": round(achieved, 1), "peak": pk, "unit": "GB/s", "frac": round(achieved / pk, 4),
-            "peak_source": pk_src, "traffic": ncu_traffic(kernel_file),
-            "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms, "launches": p_n,
-            "share_of_step": round(p_ms / max(1e-9, solve_ms), 4),
-            "timing": "CUDA events around every launch of this kernel on its stream, in a separate "
-                      "profiled region of the same solves (value comes from an uninstrumented region)",
-            "binding_roof": bound, "flop_per_byte": round(intensity, 2), "ridge_flop_per_byte": round(ridge, 2),
-            "alu": None if flops_per_launch is None else {
-                "achieved_tflops": round(flops_per_launch / (avg_ms / 1e3) / 1e12, 2),
-                "peak_tflops": round(FP32_PEAK_TFLOPS, 1), "frac": round(flops_per_launch / (avg_ms / 1e3) / 1e12 /
-                                                                         FP32_PEAK_TFLOPS, 4),
-                "flops_per_launch": flops_per_launch,
-                "peak_source": "unit counts x maximum SM clock (152 SMs, 128 FP32 lanes, FMA, 2.07 GHz)"}}
+    out = {"kernel": ROOF_KERNELS[prec] + " (one SAP colour sweep, 4 MR steps)", "avg_launch_ms": avg_ms,
+           "launches": p_n, "share_of_step": round(p_ms / max(1e-9, solve_ms), 4),
+           "timing": "CUDA events around every launch of this kernel on its stream, in a separate "
+                     "profiled region of the same solves (value comes from an uninstrumented region)",
+           "ridge_flop_per_byte": round(ridge, 2)}
+    if not flops_per_launch:
+        out.update(hbm)
+        return out
+    tfs = flops_per_launch / (avg_ms / 1e3) / 1e12
+    alu = {"bound": "alu", "achieved": round(tfs, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+           "frac": round(tfs / FP32_PEAK_TFLOPS, 4), "traffic": hbm["traffic"],
+           "peak_source": "unit counts x maximum SM clock (152 SMs, 128 FP32 lanes, FMA, 2.07 GHz)",
+           "flops_per_launch": flops_per_launch}
+    intensity = flops_per_launch / per_launch
+    out["flop_per_byte"] = round(intensity, 2)
+    if intensity > ridge:
+        out.update(alu)
+        out["hbm"] = {k: v for k, v in hbm.items() if k != "bound"}
+    else:
+        out.update(hbm)
+        out["alu"] = {k: v for k, v in alu.items() if k != "bound"}
+    return out
 
 
 def run_gpu(args, w):
