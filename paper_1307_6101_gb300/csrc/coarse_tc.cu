@@ -140,7 +140,10 @@ __global__ void k_coarse_apply_tc(cplx<float>* __restrict__ out, const cplx<floa
   const int ia = mtile * 8 + (gq >> 1), ib = ia + 4;
   const bool imrow = (gq & 1) != 0;
   const unsigned* sAu = reinterpret_cast<const unsigned*>(sA);
+  // FP32 accumulators: the hi products in four chains (k-tile mod 4), the lo products in their own;
+  // the tensor core's accumulation truncates, so short chains keep its bias from adding up along K
   float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  float ach[4][2][4] = {};
   // A-fragment word of complex element (i, cc): (Re a, -Im a) on a real-part row, (Im a, Re a) on an
   // imaginary-part row; zero outside the n x 9n matrix
   auto afrag = [&](int i, int cc) -> unsigned {
@@ -155,17 +158,24 @@ __global__ void k_coarse_apply_tc(cplx<float>* __restrict__ out, const cplx<floa
     a[1] = afrag(ib, c0);
     a[2] = afrag(ia, c1);
     a[3] = afrag(ib, c1);
+    const int ch = kt & 3;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (q < nt) {
         const int r = q * 8 + gq;
         const uint2 x0 = sX[r * Lo.xs + c0];
         const uint2 x1 = sX[r * Lo.xs + c1];
-        mma_16816(acc[q], a, x0.x, x1.x);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c == ch) mma_16816(ach[c][q], a, x0.x, x1.x);
         mma_16816(acc[q], a, x0.y, x1.y);
       }
     }
   }
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[q][v] = ((ach[0][q][v] + ach[1][q][v]) + (ach[2][q][v] + ach[3][q][v])) + acc[q][v];
   // fixed-order reduction of the k shares
   if (ks > 1) {
     if (kq > 0) {

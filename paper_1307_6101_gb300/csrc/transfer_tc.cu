@@ -117,7 +117,10 @@ __global__ void k_restrict_tc(cplx<float>* __restrict__ out, const cplx<float>* 
         sX[r * RT_XS + k] = u;
       }
       __syncthreads();
+      // FP32 accumulators: hi products in four chains (k-tile mod 4), lo products in their own (the
+      // tensor core's accumulation truncates; short chains keep its bias from adding up along K)
       float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+      float ach[4][2][4] = {};
       const int KT = (kc + 7) / 8;
       const int kt0 = (kq * KT) / ks, kt1 = ((kq + 1) * KT) / ks;
       // A word of conj(P)^T: (Re p, Im p) on a real-part row, (-Im p, Re p) on an imaginary-part row
@@ -133,17 +136,25 @@ __global__ void k_restrict_tc(cplx<float>* __restrict__ out, const cplx<float>* 
         a[1] = afrag(jb, k1);
         a[2] = afrag(ja, k2);
         a[3] = afrag(jb, k2);
+        const int ch = kt & 3;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           if (q < nt) {
             const int r = q * 8 + gq;
             const uint2 x0 = sX[r * RT_XS + k1];
             const uint2 x1 = sX[r * RT_XS + k2];
-            mma_16816(acc[q], a, x0.x, x1.x);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (c == ch) mma_16816(ach[c][q], a, x0.x, x1.x);
             mma_16816(acc[q], a, x0.y, x1.y);
           }
         }
       }
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          acc[q][v] = ((ach[0][q][v] + ach[1][q][v]) + (ach[2][q][v] + ach[3][q][v])) + acc[q][v];
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll

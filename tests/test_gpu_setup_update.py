@@ -58,8 +58,8 @@ def _perturbed(U, delta, seed):
 @pytest.mark.parametrize("precision", [1, 2])
 def test_update_gauge(dd, precision):
     from oracle.wilson import WilsonOp
-    c = Case(**SAP4, levels=3, agg=((4, 4, 4, 4), (2, 1, 1, 1)), n_tv=(6, 8), sap=((4, 4, 4, 4), (1, 1, 2, 2)),
-             n_inv=2, eta_passes=2, m0=-0.3, max_rhs=2)
+    c = Case(**{**SAP4, "levels": 3, "agg": ((4, 4, 4, 4), (2, 1, 1, 1)), "n_tv": (6, 8),
+                "sap": ((4, 4, 4, 4), (1, 1, 2, 2))}, n_inv=2, eta_passes=2, m0=-0.3, max_rhs=2)
     U = c.gauge()
     h = c.gpu(precision, U)
     U2 = _perturbed(U, 0.05, 17)
