@@ -86,19 +86,25 @@ __global__ void k_coarse_apply_tc(cplx<float>* __restrict__ out, const cplx<floa
   }
   if (tid < TC_R) smax[tid] = 0u;
   __syncthreads();
-  // stage the neighbour values of every column (zero beyond the batch and the padding)
+  // stage the neighbour values of every column (zero beyond the batch and the padding); the column's
+  // max |Re|, |Im| is reduced per warp by shuffles, then one shared-memory atomic per warp and column
   const int kc = 9 * n;
-  for (int e = tid; e < TC_R * Lo.kcp; e += nth) {
-    const int r = e / Lo.kcp, cc = e - r * Lo.kcp;
-    float2 v = make_float2(0.f, 0.f);
-    if (r < nr && cc < kc) {
-      const int k = cc / n;
-      const cplx<float> x = in[(size_t)(r0 + r) * rstride + (size_t)nbr[k] * n + (cc - k * n)];
-      v = make_float2(x.re, x.im);
-      const float m = fmaxf(fabsf(v.x), fabsf(v.y));
-      if (m > 0.f) atomicMax(&smax[r], __float_as_uint(m));   // order-independent: non-negative floats
+  for (int r = 0; r < TC_R; ++r) {
+    float m = 0.f;
+    float2* dst = reinterpret_cast<float2*>(sX) + (size_t)r * Lo.xs;
+    for (int cc = tid; cc < Lo.kcp; cc += nth) {
+      float2 v = make_float2(0.f, 0.f);
+      if (r < nr && cc < kc) {
+        const int k = cc / n;
+        const cplx<float> x = in[(size_t)(r0 + r) * rstride + (size_t)nbr[k] * n + (cc - k * n)];
+        v = make_float2(x.re, x.im);
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
+      dst[cc] = v;
     }
-    reinterpret_cast<float2*>(sX)[r * Lo.xs + cc] = v;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((tid & 31) == 0 && m > 0.f) atomicMax(&smax[r], __float_as_uint(m));   // order-independent
   }
   __syncthreads();
   if (tid < TC_R) {
@@ -109,18 +115,20 @@ __global__ void k_coarse_apply_tc(cplx<float>* __restrict__ out, const cplx<floa
   }
   __syncthreads();
   // split in place: x / s = hi + lo, both FP16 (the slot of an entry is owned by one thread)
-  for (int e = tid; e < TC_R * Lo.kcp; e += nth) {
-    const int r = e / Lo.kcp, cc = e - r * Lo.kcp;
-    const float2 v = reinterpret_cast<float2*>(sX)[r * Lo.xs + cc];
+  for (int r = 0; r < TC_R; ++r) {
     const float inv = 1.f / sscale[r];               // exact: a power of two
-    const float xr = v.x * inv, xi = v.y * inv;
-    const __half2 hi = __floats2half2_rn(xr, xi);
-    const float2 hf = __half22float2(hi);
-    const __half2 lo = __floats2half2_rn(xr - hf.x, xi - hf.y);
-    uint2 u;
-    u.x = *reinterpret_cast<const unsigned*>(&hi);
-    u.y = *reinterpret_cast<const unsigned*>(&lo);
-    sX[r * Lo.xs + cc] = u;
+    uint2* row = sX + (size_t)r * Lo.xs;
+    for (int cc = tid; cc < Lo.kcp; cc += nth) {
+      const float2 v = reinterpret_cast<float2*>(row)[cc];
+      const float xr = v.x * inv, xi = v.y * inv;
+      const __half2 hi = __floats2half2_rn(xr, xi);
+      const float2 hf = __half22float2(hi);
+      const __half2 lo = __floats2half2_rn(xr - hf.x, xi - hf.y);
+      uint2 u;
+      u.x = *reinterpret_cast<const unsigned*>(&hi);
+      u.y = *reinterpret_cast<const unsigned*>(&lo);
+      row[cc] = u;
+    }
   }
   const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0) ? 1 : 0);
   if (!ok) {

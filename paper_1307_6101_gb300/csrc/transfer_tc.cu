@@ -83,17 +83,23 @@ __global__ void k_restrict_tc(cplx<float>* __restrict__ out, const cplx<float>* 
         sP[j * RT_PS + k] = w;
       }
       __syncthreads();
-      for (int e = tid; e < RT_R * RT_KCH; e += nth) {
-        const int r = e / RT_KCH, k = e - r * RT_KCH;
-        float2 v = make_float2(0.f, 0.f);
-        if (r < nr && k < kc) {
-          const int kk = k0 + k, xl = kk / h, f = s * h + (kk - xl * h);
-          const cplx<float> x = in[(size_t)(r0 + r) * in_rstride + faddr(fine, V, n, agg * gf.vA + xl, f)];
-          v = make_float2(x.re, x.im);
-          const float m = fmaxf(fabsf(v.x), fabsf(v.y));
-          if (m > 0.f) atomicMax(&smax[r], __float_as_uint(m));
+      // the chunk of every column, its max |Re|, |Im| reduced per warp (shuffles), one atomic per warp
+      for (int r = 0; r < RT_R; ++r) {
+        float m = 0.f;
+        float2* dst = reinterpret_cast<float2*>(sX) + (size_t)r * RT_XS;
+        for (int k = tid; k < RT_KCH; k += nth) {
+          float2 v = make_float2(0.f, 0.f);
+          if (r < nr && k < kc) {
+            const int kk = k0 + k, xl = kk / h, f = s * h + (kk - xl * h);
+            const cplx<float> x = in[(size_t)(r0 + r) * in_rstride + faddr(fine, V, n, agg * gf.vA + xl, f)];
+            v = make_float2(x.re, x.im);
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+          }
+          dst[k] = v;
         }
-        reinterpret_cast<float2*>(sX)[r * RT_XS + k] = v;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if ((tid & 31) == 0 && m > 0.f) atomicMax(&smax[r], __float_as_uint(m));
       }
       __syncthreads();
       if (tid < RT_R) {
@@ -103,18 +109,20 @@ __global__ void k_restrict_tc(cplx<float>* __restrict__ out, const cplx<float>* 
         sscale[tid] = m > 0.f ? ldexpf(1.f, ex) : 1.f;
       }
       __syncthreads();
-      for (int e = tid; e < RT_R * RT_KCH; e += nth) {
-        const int r = e / RT_KCH, k = e - r * RT_KCH;
-        const float2 v = reinterpret_cast<float2*>(sX)[r * RT_XS + k];
+      for (int r = 0; r < RT_R; ++r) {
         const float inv = 1.f / sscale[r];
-        const float xr = v.x * inv, xi = v.y * inv;
-        const __half2 hi = __floats2half2_rn(xr, xi);
-        const float2 hf = __half22float2(hi);
-        const __half2 lo = __floats2half2_rn(xr - hf.x, xi - hf.y);
-        uint2 u;
-        u.x = *reinterpret_cast<const unsigned*>(&hi);
-        u.y = *reinterpret_cast<const unsigned*>(&lo);
-        sX[r * RT_XS + k] = u;
+        uint2* row = sX + (size_t)r * RT_XS;
+        for (int k = tid; k < RT_KCH; k += nth) {
+          const float2 v = reinterpret_cast<float2*>(row)[k];
+          const float xr = v.x * inv, xi = v.y * inv;
+          const __half2 hi = __floats2half2_rn(xr, xi);
+          const float2 hf = __half22float2(hi);
+          const __half2 lo = __floats2half2_rn(xr - hf.x, xi - hf.y);
+          uint2 u;
+          u.x = *reinterpret_cast<const unsigned*>(&hi);
+          u.y = *reinterpret_cast<const unsigned*>(&lo);
+          row[k] = u;
+        }
       }
       __syncthreads();
       // FP32 accumulators: hi products in four chains (k-tile mod 4), lo products in their own (the
