@@ -355,8 +355,9 @@ DD_HD SapSmem sap_smem_layout(int vB, int n, int spc, int nsl, size_t bs, size_t
 template <typename T, typename BS>
 __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc,
                                      const BS* __restrict__ blk, const float* __restrict__ bscale, Geom g, int n,
-                                     size_t rstride, const int* __restrict__ blocks, int k_mr, int spc, int nsl,
-                                     int* err, const int* __restrict__ bsite, const int* __restrict__ bloc) {
+                                     size_t rstride, int nrhs, const int* __restrict__ blocks, int k_mr, int spc,
+                                     int nsl, int* err, const int* __restrict__ bsite,
+                                     const int* __restrict__ bloc) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
   const int CLS = (int)cluster.num_blocks();
@@ -374,7 +375,6 @@ __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restri
   T* sh = reinterpret_cast<T*>(smem_raw + L.sh);                              // [32][3] + 3
   int* slot = reinterpret_cast<int*>(smem_raw + L.slot);                      // [spc][9]
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + L.bar);
-  const size_t ro = (size_t)blockIdx.y * rstride;
   const int* own = bsite + (size_t)b * vB + rank * spc;   // own sites, block-local order
   // slot of block k of own site sl in the staged array (-1: the hop leaves the SAP block)
   if (threadIdx.x < spc) {
@@ -418,97 +418,107 @@ __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restri
     nloc = q >= 0 ? bloc[nb] : 0;
   }
   const BS* Ms = stage + ((size_t)sl * nsl + (q >= 0 ? q : 0)) * nn + i;   // staged row i (column-major)
-  // rho = b - D z on the own rows: hops leaving the block from global memory ...
-  cplx<T> acc = czero<T>();
-  if (k < 9 && q < 0) {
-    const BS* M = blk + ((size_t)site * 9 + k) * nn + i;
-    const cplx<T>* v = z + ro + (size_t)nb * n;
-#pragma unroll 8
-    for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), v[j]);
-  }
-  const int ok = __syncthreads_and(mbar_wait_bounded(bar, 0) ? 1 : 0);
-  if (!ok && threadIdx.x == 0) atomicExch(err, 2);
-  // ... and the blocks inside it from shared memory
-  if (k < 9 && q >= 0) {
-    const cplx<T>* v = z + ro + (size_t)nb * n;
-#pragma unroll 8
-    for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(Ms, (size_t)j * n), v[j]);
-  }
-  if (k < 9) part[k * rows + rl] = sc * acc;
-  __syncthreads();
-  cplx<T> r = czero<T>(), xs = czero<T>();
-  if (threadIdx.x < rows) {
-    cplx<T> d = czero<T>();
-#pragma unroll
-    for (int m = 0; m < 9; ++m) d = d + part[m * rows + threadIdx.x];
-    r = bsrc[ro + (size_t)own[threadIdx.x / n] * n + threadIdx.x % n] - d;
-    for (int c = 0; c < CLS; ++c) cluster.map_shared_rank(rfull, c)[(size_t)rank * rows + threadIdx.x] = r;
-  }
-  cluster.sync();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  for (int it = 0; it < k_mr; ++it) {
-    const int buf = it & 1;
-    cplx<T>* pb = pbuf + (size_t)buf * vB * n;
-    T* rb = red + buf * 64;
-    // p = D_B r on the own rows, from the staged blocks and the local copy of r
-    if (k < 9) {
-      cplx<T> a = czero<T>();
-      if (q >= 0) {
-        const cplx<T>* v = rfull + (size_t)nloc * n;
+  int ok = 1;
+  // the right-hand sides of the batch one after the other, on the blocks staged once
+  for (int rh = 0; rh < nrhs; ++rh) {
+    const size_t ro = (size_t)rh * rstride;
+    // rho = b - D z on the own rows: hops leaving the block from global memory ...
+    cplx<T> acc = czero<T>();
+    if (k < 9 && q < 0) {
+      const BS* M = blk + ((size_t)site * 9 + k) * nn + i;
+      const cplx<T>* v = z + ro + (size_t)nb * n;
 #pragma unroll 8
-        for (int j = 0; j < n; ++j) cfma(a, ld_cplx(Ms, (size_t)j * n), v[j]);
-      }
-      part[k * rows + rl] = sc * a;
+      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), v[j]);
     }
+    if (rh == 0) {
+      ok = __syncthreads_and(mbar_wait_bounded(bar, 0) ? 1 : 0);
+      if (!ok && threadIdx.x == 0) atomicExch(err, 2);
+    }
+    // ... and the blocks inside it from shared memory
+    if (k < 9 && q >= 0) {
+      const cplx<T>* v = z + ro + (size_t)nb * n;
+#pragma unroll 8
+      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(Ms, (size_t)j * n), v[j]);
+    }
+    if (k < 9) part[k * rows + rl] = sc * acc;
     __syncthreads();
-    cplx<T> p = czero<T>();
-    T nre = T(0), nim = T(0), den = T(0);
+    cplx<T> r = czero<T>(), xs = czero<T>();
     if (threadIdx.x < rows) {
+      cplx<T> d = czero<T>();
 #pragma unroll
-      for (int m = 0; m < 9; ++m) p = p + part[m * rows + threadIdx.x];
-      const cplx<T> t = cdotc(p, r);
-      nre = t.re;
-      nim = t.im;
-      den = cnorm2(p);
-      for (int c = 0; c < CLS; ++c) cluster.map_shared_rank(pb, c)[(size_t)rank * rows + threadIdx.x] = p;
-    }
-    for (int off = 16; off >= 1; off >>= 1) {
-      nre += __shfl_xor_sync(0xffffffffu, nre, off);
-      nim += __shfl_xor_sync(0xffffffffu, nim, off);
-      den += __shfl_xor_sync(0xffffffffu, den, off);
-    }
-    if (lane == 0) { sh[3 * warp] = nre; sh[3 * warp + 1] = nim; sh[3 * warp + 2] = den; }
-    __syncthreads();
-    if (warp == 0) {   // warp partials summed by a shuffle tree (fixed order), then sent to every CTA
-      T a = lane < nw ? sh[3 * lane] : T(0);
-      T bb = lane < nw ? sh[3 * lane + 1] : T(0);
-      T cc = lane < nw ? sh[3 * lane + 2] : T(0);
-      for (int off = 16; off >= 1; off >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, off);
-        bb += __shfl_xor_sync(0xffffffffu, bb, off);
-        cc += __shfl_xor_sync(0xffffffffu, cc, off);
-      }
-      if (lane < CLS) {
-        T* dst = cluster.map_shared_rank(rb, lane) + rank * 4;
-        dst[0] = a;
-        dst[1] = bb;
-        dst[2] = cc;
-      }
+      for (int m = 0; m < 9; ++m) d = d + part[m * rows + threadIdx.x];
+      r = bsrc[ro + (size_t)own[threadIdx.x / n] * n + threadIdx.x % n] - d;
+      for (int c = 0; c < CLS; ++c) cluster.map_shared_rank(rfull, c)[(size_t)rank * rows + threadIdx.x] = r;
     }
     cluster.sync();
-    T a = T(0), bb = T(0), cc = T(0);
-    for (int c = 0; c < CLS; ++c) { a += rb[c * 4]; bb += rb[c * 4 + 1]; cc += rb[c * 4 + 2]; }
-    const cplx<T> alpha = cc > T(0) ? cmk<T>(a / cc, bb / cc) : czero<T>();
-    if (threadIdx.x < rows) {
-      cfma(xs, alpha, r);
-      r = r - alpha * p;
+    for (int it = 0; it < k_mr; ++it) {
+      const int buf = it & 1;
+      cplx<T>* pb = pbuf + (size_t)buf * vB * n;
+      T* rb = red + buf * 64;
+      // p = D_B r on the own rows, from the staged blocks and the local copy of r
+      if (k < 9) {
+        cplx<T> a = czero<T>();
+        if (q >= 0) {
+          const cplx<T>* v = rfull + (size_t)nloc * n;
+#pragma unroll 8
+          for (int j = 0; j < n; ++j) cfma(a, ld_cplx(Ms, (size_t)j * n), v[j]);
+        }
+        part[k * rows + rl] = sc * a;
+      }
+      __syncthreads();
+      cplx<T> p = czero<T>();
+      T nre = T(0), nim = T(0), den = T(0);
+      if (threadIdx.x < rows) {
+#pragma unroll
+        for (int m = 0; m < 9; ++m) p = p + part[m * rows + threadIdx.x];
+        const cplx<T> t = cdotc(p, r);
+        nre = t.re;
+        nim = t.im;
+        den = cnorm2(p);
+        for (int c = 0; c < CLS; ++c) cluster.map_shared_rank(pb, c)[(size_t)rank * rows + threadIdx.x] = p;
+      }
+      for (int off = 16; off >= 1; off >>= 1) {
+        nre += __shfl_xor_sync(0xffffffffu, nre, off);
+        nim += __shfl_xor_sync(0xffffffffu, nim, off);
+        den += __shfl_xor_sync(0xffffffffu, den, off);
+      }
+      if (lane == 0) { sh[3 * warp] = nre; sh[3 * warp + 1] = nim; sh[3 * warp + 2] = den; }
+      __syncthreads();
+      if (warp == 0) {   // warp partials summed by a shuffle tree (fixed order), then sent to every CTA
+        T a = lane < nw ? sh[3 * lane] : T(0);
+        T bb = lane < nw ? sh[3 * lane + 1] : T(0);
+        T cc = lane < nw ? sh[3 * lane + 2] : T(0);
+        for (int off = 16; off >= 1; off >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, off);
+          bb += __shfl_xor_sync(0xffffffffu, bb, off);
+          cc += __shfl_xor_sync(0xffffffffu, cc, off);
+        }
+        if (lane < CLS) {
+          T* dst = cluster.map_shared_rank(rb, lane) + rank * 4;
+          dst[0] = a;
+          dst[1] = bb;
+          dst[2] = cc;
+        }
+      }
+      cluster.sync();
+      T a = T(0), bb = T(0), cc = T(0);
+      for (int c = 0; c < CLS; ++c) { a += rb[c * 4]; bb += rb[c * 4 + 1]; cc += rb[c * 4 + 2]; }
+      const cplx<T> alpha = cc > T(0) ? cmk<T>(a / cc, bb / cc) : czero<T>();
+      if (threadIdx.x < rows) {
+        cfma(xs, alpha, r);
+        r = r - alpha * p;
+      }
+      for (int e = threadIdx.x; e < vB * n; e += blockDim.x) rfull[e] = rfull[e] - alpha * pb[e];
+      __syncthreads();
     }
-    for (int e = threadIdx.x; e < vB * n; e += blockDim.x) rfull[e] = rfull[e] - alpha * pb[e];
-    __syncthreads();
-  }
-  if (ok && threadIdx.x < rows) {
-    const size_t a = ro + (size_t)own[threadIdx.x / n] * n + threadIdx.x % n;
-    z[a] = z[a] + xs;
+    if (ok && threadIdx.x < rows) {
+      const size_t a = ro + (size_t)own[threadIdx.x / n] * n + threadIdx.x % n;
+      z[a] = z[a] + xs;
+    }
+    // every CTA is done with its copies of r, p and the partials before the next right-hand side
+    // writes into them
+    if (rh + 1 < nrhs) cluster.sync();
   }
   if (!ok && threadIdx.x == 0) mbar_wait_bounded(bar, 0);   // no copy may still be in flight at exit
 }
@@ -779,7 +789,7 @@ cudaError_t coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op
     attr[0].val.clusterDim.x = op.sap_cls;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(nblocks * op.sap_cls, nrhs, 1);
+    cfg.gridDim = dim3(nblocks * op.sap_cls, 1, 1);   // one cluster per SAP block loops over the batch
     cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes =
         sap_smem_layout(op.g.vB, op.n, spc, op.sap_nsl, half ? sizeof(__half2) : sizeof(cplx<T>), sizeof(T)).total;
@@ -791,15 +801,15 @@ cudaError_t coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op
     if constexpr (sizeof(T) == 4) {
       if (half)
         e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<float, __half2>, z, b, op.blkh, op.bscale, op.g, op.n,
-                               rstride, blocks, k_mr, spc, op.sap_nsl, op.err, op.bsite, op.bloc);
+                               rstride, nrhs, blocks, k_mr, spc, op.sap_nsl, op.err, op.bsite, op.bloc);
       else
         e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
-                               (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc, op.sap_nsl, op.err,
-                               op.bsite, op.bloc);
+                               (const float*)nullptr, op.g, op.n, rstride, nrhs, blocks, k_mr, spc, op.sap_nsl,
+                               op.err, op.bsite, op.bloc);
     } else {
       e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
-                             (const float*)nullptr, op.g, op.n, rstride, blocks, k_mr, spc, op.sap_nsl, op.err,
-                             op.bsite, op.bloc);
+                             (const float*)nullptr, op.g, op.n, rstride, nrhs, blocks, k_mr, spc, op.sap_nsl,
+                             op.err, op.bsite, op.bloc);
     }
     if (e == cudaSuccess) return cudaSuccess;
     cudaGetLastError();   // cluster launch refused: run the one-CTA-per-block kernel instead
