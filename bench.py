@@ -346,6 +346,16 @@ def roofline(prof, prec, kernel_file, flops_per_launch=None):
     return out
 
 
+def autotune_record(dd, h, levels):
+    """The autotuner's timings (ms per candidate) and choices of a handle, per kernel class and level."""
+    out = {}
+    for kind, lv in (("coarse", range(1, levels)), ("restrict", range(levels - 1)), ("prolong", range(levels - 1))):
+        for l in lv:
+            ms, ch = dd.ddamg_autotune_times(h, kind, l)
+            out[f"{kind}_l{l}"] = {"ms": [round(x, 4) for x in ms if x >= 0] if ms[0] >= 0 else [], "chosen": ch}
+    return out
+
+
 def run_gpu(args, w):
     import torch
     rank, world, local = replica_env()
@@ -400,6 +410,7 @@ def run_gpu(args, w):
     clk.start()
     steps0 = [dd.ddamg_krylov_steps(handles["mixed"], l, 1) for l in range(w["levels"])]
     ms_mixed, st_mixed, launches = tm.timed(handles["mixed"], args.steps, args.warmup, tag="timed_mixed")
+    tuned = autotune_record(dd, handles["mixed"], w["levels"]) if mixed_prec == 2 else None
     steps1 = [dd.ddamg_krylov_steps(handles["mixed"], l, 1) for l in range(w["levels"])]
     clocks = clk.stop()
     prof = tm.profiled(handles["mixed"], args.steps)
@@ -477,6 +488,7 @@ def run_gpu(args, w):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "krylov_steps_per_solve": [round((b - a) / args.steps, 1) for a, b in zip(steps0, steps1)],
+        "autotuner": tuned,
     }
     for h in list(handles.values()):
         h.free()
@@ -524,6 +536,7 @@ def large_workload(dd, torch, stream, w, prec, steps, barrier):
     ms, stats, launches = tm.timed(h, steps, 1)
     clocks = clk.stop()
     prof = tm.profiled(h, 1)
+    tuned = autotune_record(dd, h, w["levels"]) if prec == 2 else None
     res = max(s["true_residual"] for st in stats for s in st)
     conv = all(s["converged"] for st in stats for s in st)
     dev = dd.ddamg_device_bytes(h)
@@ -537,7 +550,8 @@ def large_workload(dd, torch, stream, w, prec, steps, barrier):
             "s_per_rhs": round(tot / 1e3 / (ncols * steps), 5), "ms_per_step": round(tot / steps, 1),
             "iterations": [s["iterations"] for s in stats[0]], "true_residual": res, "all_converged": conv,
             "setup_s": round(t_setup, 1), "device_bytes": int(dev), "gpu_launches": int(launches),
-            "clocks": clocks, "roofline": roofline(prof, prec, KERNEL_FILE, sap_flops(w, w["nrhs"]))}
+            "clocks": clocks, "roofline": roofline(prof, prec, KERNEL_FILE, sap_flops(w, w["nrhs"])),
+            "autotuner": tuned}
 
 
 # ---------------------------------------------------------------------------
@@ -814,7 +828,10 @@ def serving_bench(dd, w, lattices, rates, n_requests, max_rhs, seed):
             b = np.ascontiguousarray(pools[k][:n])
             x = np.zeros_like(b)
             srv.wait(srv.submit(hids[k], b, n, TOL), x, n)
-    runs = [serving_run(dd, srv, hids, pools, r, n_requests, rng) for r in rates]
+    runs = []
+    for r in rates:
+        runs.append(serving_run(dd, srv, hids, pools, r, n_requests, rng))
+        print(json.dumps({"serving_rate": runs[-1]}), file=sys.stderr, flush=True)
     srv.free()
     for h in handles:
         h.free()
@@ -897,13 +914,15 @@ def scan_fields(dd, torch, stream, w, args):
         dd.ddamg_solve(h, rhs, x, 1, TOL)                      # warm-up (graph capture)
         st, t_amg = timed(lambda: dd.ddamg_solve(h, rhs, x, 1, TOL))
         cg, t_cg = timed(lambda: dd.ddamg_cgnr(h, rhs, x, 1, TOL, args.scan_cg_iters))
-        rows.append({"m0": round(m0, 6), "m0_minus_edge": delta, "sigma_min": smin, "sigma_max": smax,
+        rows.append({"fields": w["name"], "m0": round(m0, 6), "m0_minus_edge": delta, "sigma_min": smin,
+                     "sigma_max": smax,
                      "lanczos_steps": k, "ddamg_setup_s": round(t_setup, 2),
                      "ddamg_iterations": st[0]["iterations"], "ddamg_s": round(t_amg, 4),
                      "ddamg_true_residual": st[0]["true_residual"],
                      "cgnr_iterations": cg[0]["iterations"], "cgnr_s": round(t_cg, 3),
                      "cgnr_converged": cg[0]["converged"], "cgnr_true_residual": cg[0]["true_residual"],
                      "cgnr_over_ddamg_time": round(t_cg / t_amg, 1)})
+        print(json.dumps({"mass_scan_row": rows[-1]}), flush=True)
         h.free()
     # error scaling at the workload's mass
     h = dd.ddamg_setup(U, w["dims"], -1, m_edge, w["csw"], params(2), None)
@@ -913,9 +932,10 @@ def scan_fields(dd, torch, stream, w, args):
     for tol in SCAN_TOLS:
         st, t_amg = timed(lambda: dd.ddamg_solve(h, rhs, x, 1, tol))
         cg, t_cg = timed(lambda: dd.ddamg_cgnr(h, rhs, x, 1, tol, args.scan_cg_iters))
-        err.append({"tol": tol, "ddamg_iterations": st[0]["iterations"], "ddamg_s": round(t_amg, 4),
-                    "cgnr_iterations": cg[0]["iterations"], "cgnr_s": round(t_cg, 3),
+        err.append({"fields": w["name"], "tol": tol, "ddamg_iterations": st[0]["iterations"],
+                    "ddamg_s": round(t_amg, 4), "cgnr_iterations": cg[0]["iterations"], "cgnr_s": round(t_cg, 3),
                     "cgnr_converged": cg[0]["converged"]})
+        print(json.dumps({"error_scan_row": err[-1]}), flush=True)
     h.free()
     return {"workload": w["name"], "edge_mass": m_edge, "mass_scan": rows, "error_scan": err}
 
