@@ -940,6 +940,62 @@ def scan_fields(dd, torch, stream, w, args):
     return {"workload": w["name"], "edge_mass": m_edge, "mass_scan": rows, "error_scan": err}
 
 
+# ---------------------------------------------------------------------------
+# Small cases for kernel profiling (ncu captures of one kernel on a few GB of device memory)
+def run_probe(args):
+    """--probe sap: fine SAP sweeps on a two-level handle of --probe-dims (default 24^3x48, beyond L2),
+    --probe-rhs right-hand sides; --probe coarse: coarse stencil applications of 12 right-hand sides on
+    an 8^3x16 level of 40 dof (FP16 blocks, 472 MB) under the autotuned kernel.  Prints one line with
+    the CUDA-event time per launch; not a bench line."""
+    import torch
+    import synth
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1307_6101_gb300 as dd
+    reps = 3
+    if args.probe == "sap":
+        dims = tuple(int(x) for x in args.probe_dims.split(","))
+        nrhs = args.probe_rhs
+        U = synth.su3_field(dims, 0.4, 0)
+        p = dd.ddamg_default_params(levels=2, agg=[(4, 4, 4, 4)], n_tv=[2], sap_block=[(4, 4, 4, 4)], mr_steps=4,
+                                    nu=5, n_inv=0, eta_passes=0, precision=2, max_rhs=nrhs, seed=1,
+                                    sap_schur=1 if args.probe_schur else 0)
+        h = dd.ddamg_setup(U, dims, -1, mass("eps0.4_csw1"), 1.0, p, None)
+        b = torch.from_numpy(np.ascontiguousarray(synth.random_spinors(nrhs, dims, 2))).cuda()
+        z = torch.zeros_like(b)
+        for _ in range(reps):
+            dd.ddamg_smooth(h, 0, 1, b, z, nrhs, 1)
+        torch.cuda.synchronize()
+        dd.ddamg_profile(h, 1 << dd.PROF_KINDS["fine_sap"])
+        dd.ddamg_smooth(h, 0, 1, b, z, nrhs, 2)
+        ms, n, by = dd.ddamg_profile_read(h, "fine_sap")
+        print(json.dumps({"probe": "fine SAP sweep", "dims": dims, "nrhs": nrhs, "schur": bool(args.probe_schur),
+                          "us_per_launch": round(ms / n * 1e3, 2), "algorithmic_mb": round(by / n / 1e6, 2),
+                          "gbs": round(by / n / (ms / n / 1e3) / 1e9, 1),
+                          "device_gb": round(dd.ddamg_device_bytes(h) / 1e9, 2)}))
+    else:
+        dims = (32, 16, 16, 16)
+        U = synth.su3_field(dims, 0.4, 0)
+        p = dd.ddamg_default_params(levels=2, agg=[(2, 2, 2, 2)], n_tv=[20], sap_block=[(4, 4, 4, 4)], mr_steps=4,
+                                    nu=5, n_inv=0, eta_passes=0, precision=2, max_rhs=12, seed=1)
+        h = dd.ddamg_setup(U, dims, -1, mass("eps0.4_csw1"), 1.0, p, None)
+        cd, n, _ = h.level_info(1)
+        f = torch.from_numpy(np.ascontiguousarray(synth.random_fields(12, cd, n, 2))).cuda()
+        out = torch.zeros_like(f)
+        for _ in range(reps):
+            dd.ddamg_apply(h, 1, 1, f, out, 12)
+        torch.cuda.synchronize()
+        dd.ddamg_profile(h, 1 << dd.PROF_KINDS["coarse_apply"])
+        dd.ddamg_apply(h, 1, 1, f, out, 12)
+        ms, nl, by = dd.ddamg_profile_read(h, "coarse_apply")
+        print(json.dumps({"probe": "coarse stencil, 8^3x16 sites x 40 dof, 12 rhs", "us_per_launch": round(ms / nl * 1e3, 2),
+                          "algorithmic_mb": round(by / nl / 1e6, 1), "gbs": round(by / nl / (ms / nl / 1e3) / 1e9, 1),
+                          "autotuner": autotune_record(dd, h, 2),
+                          "device_gb": round(dd.ddamg_device_bytes(h) / 1e9, 2)}))
+    h.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -961,6 +1017,11 @@ def main():
                     help="skip the batched 32^3x64 sub-measurement of the default bench")
     ap.add_argument("--large-steps", type=int, default=2,
                     help="timed steps (24 right-hand sides each) of the 32^3x64 sub-measurement")
+    ap.add_argument("--probe", choices=("sap", "coarse"), default=None,
+                    help="small single-kernel cases for profiling (one line; not a bench line)")
+    ap.add_argument("--probe-dims", default="48,24,24,24", help="lattice T,Z,Y,X of --probe sap")
+    ap.add_argument("--probe-rhs", type=int, default=1, help="right-hand sides of --probe sap")
+    ap.add_argument("--probe-schur", action="store_true", help="--probe sap with Schur block solves")
     ap.add_argument("--scan", action="store_true",
                     help="mass- and error-scaling sweeps of DD-alpha-AMG against CGNR (one JSON line)")
     ap.add_argument("--scan-cg-iters", type=int, default=30000, help="CGNR iteration cap of the sweeps")
@@ -969,6 +1030,9 @@ def main():
                     help="host-driven inner solves instead of captured graphs (for kernel-level profiling)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.probe:
+        run_probe(args)
+        return
     if args.scan:
         run_scan(args)
         return
