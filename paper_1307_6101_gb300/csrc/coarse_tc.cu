@@ -238,11 +238,28 @@ namespace dd {
 
 size_t coarse_tc_smem(int n, int ks) { return tc_layout(n, ks).total; }
 
+// largest CTA both variants can launch with their register counts (queried once)
+int tc_max_threads() {
+  static std::atomic<int> cached{0};
+  int v = cached.load(std::memory_order_acquire);
+  if (v > 0) return v;
+  cudaFuncAttributes a0, a1;
+  if (cudaFuncGetAttributes(&a0, k_coarse_apply_tc<false>) != cudaSuccess ||
+      cudaFuncGetAttributes(&a1, k_coarse_apply_tc<true>) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  v = a0.maxThreadsPerBlock < a1.maxThreadsPerBlock ? a0.maxThreadsPerBlock : a1.maxThreadsPerBlock;
+  cached.store(v, std::memory_order_release);
+  return v;
+}
+
 bool coarse_tc_fits(int n, int ks) {
-  // bulk copy of one site's blocks: at most 2^20 - 1 bytes on one mbarrier; 227 KB of shared memory
+  // bulk copy of one site's blocks: at most 2^20 - 1 bytes on one mbarrier; 227 KB of shared memory;
+  // the CTA (one warp per 16-row tile and k-split) within what the kernel's registers allow
   const TcLayout L = tc_layout(n, ks);
   return ks >= 1 && ks <= 4 && (size_t)36 * n * n < (1u << 20) && L.total + 512 <= 227 * 1024 &&
-         32 * L.mt * ks <= 1024;
+         32 * L.mt * ks <= tc_max_threads();
 }
 
 cudaError_t coarse_apply_tc(cplx<float>* out, const cplx<float>* in, const cplx<float>* b, const CoarseOp<float>& op,

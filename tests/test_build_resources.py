@@ -63,14 +63,17 @@ def test_fine_sap_4x4_kernel_resources():
 
 def test_tensor_core_kernels_resources():
     """The tensor-core coarse stencil and restriction keep their fragments and accumulators in
-    registers (no local memory) and fit their largest CTA (1024 threads) in an SM's registers."""
-    for src, name in (("coarse_tc.cu", "k_coarse_apply_tc"), ("transfer_tc.cu", "k_restrict_tc")):
+    registers (no local memory).  The restriction's largest CTA (N <= 32 test vectors, 4 tiles x 4
+    k-splits = 512 threads) fits an SM's registers; the coarse stencil's launcher rejects CTAs above
+    the kernel's register-limited maximum, and the largest CTA of the 56-dof levels (7 tiles x 4
+    k-splits = 896 threads) must fit (registers are allocated per warp in units of 8 per thread)."""
+    for src, name, threads in (("coarse_tc.cu", "k_coarse_apply_tc", 896), ("transfer_tc.cu", "k_restrict_tc", 512)):
         rep = _ptxas_report(src)
         ks = {k: v for k, v in rep.items() if name in k}
         assert ks, (src, list(rep))
         for k, v in ks.items():
             assert v["spill_st"] == 0 and v["spill_ld"] == 0, (k, v)
-            assert v["regs"] * 1024 <= 65536, (k, v)
+            assert ((v["regs"] + 7) // 8 * 8) * threads <= 65536, (k, v)
 
 
 def test_arnoldi_cluster_kernel_resources():
