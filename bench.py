@@ -212,17 +212,23 @@ def kernel_sha(kernel_file, markers=SAP_SRC):
     return hashlib.sha256(s[i:s.index(markers[1], i)].encode()).hexdigest()
 
 
-def ncu_traffic(kernel_file):
-    """DRAM bytes per launch of the fine SAP sweep from the committed ncu summary, if the kernel is unchanged."""
+def ncu_traffic(kernel_file, workload):
+    """DRAM bytes per launch of the fine SAP sweep on a workload from the committed ncu summary
+    (a capture of that workload, or of a smaller lattice scaled by sites), None once the kernel's
+    source has changed since the capture or when no capture covers the workload."""
     path = os.path.join(ROOT, "profiles", "fine_sap_sweep_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("source_sha256") != kernel_sha(kernel_file):
             return None
-        return d.get("dram_bytes_per_launch_scaled")
+        return d.get("captures", {}).get(workload, {}).get("dram_bytes_per_launch")
     except (OSError, ValueError):
         return None
+
+
+def workload_key(w):
+    return next(k for k, v in WORKLOADS.items() if v is w)
 
 
 # ---------------------------------------------------------------------------
@@ -309,7 +315,7 @@ def sap_flops(w, nrhs):
     return V / 2 * nrhs * (SAP_FLOP_RHO + w["mr_steps"] * SAP_FLOP_STEP)
 
 
-def roofline(prof, prec, kernel_file, flops_per_launch=None):
+def roofline(prof, prec, kernel_file, flops_per_launch=None, workload=None):
     """Roofline of the fine SAP sweep.  Its algorithmic bytes and FLOPs per launch over its average
     launch time give an HBM and an FP32 ALU fraction; the primary entry is the roof that binds by
     arithmetic intensity (FLOPs per algorithmic byte against the FP32 / HBM ridge), the other is
@@ -320,7 +326,8 @@ def roofline(prof, prec, kernel_file, flops_per_launch=None):
     per_launch = p_bytes / max(1, p_n)
     gbs = per_launch / (avg_ms / 1e3) / 1e9
     hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk, "unit": "GB/s", "frac": round(gbs / pk, 4),
-           "peak_source": pk_src, "traffic": ncu_traffic(kernel_file), "algorithmic_bytes_per_launch": per_launch}
+           "peak_source": pk_src, "traffic": ncu_traffic(kernel_file, workload),
+           "algorithmic_bytes_per_launch": per_launch}
     ridge = FP32_PEAK_TFLOPS * 1e12 / (pk * 1e9)
     out = {"kernel": ROOF_KERNELS[prec] + " (one SAP colour sweep, 4 MR steps)", "avg_launch_ms": avg_ms,
            "launches": p_n, "share_of_step": round(p_ms / max(1e-9, solve_ms), 4),
@@ -349,10 +356,12 @@ def roofline(prof, prec, kernel_file, flops_per_launch=None):
 def autotune_record(dd, h, levels):
     """The autotuner's timings (ms per candidate) and choices of a handle, per kernel class and level."""
     out = {}
-    for kind, lv in (("coarse", range(1, levels)), ("restrict", range(levels - 1)), ("prolong", range(levels - 1))):
+    for kind, lv, nc in (("coarse", range(1, levels), 5), ("restrict", range(levels - 1), 5),
+                         ("prolong", range(levels - 1), 2), ("sap", range(1, levels - 1), 2)):
         for l in lv:
             ms, ch = dd.ddamg_autotune_times(h, kind, l)
-            out[f"{kind}_l{l}"] = {"ms": [round(x, 4) for x in ms if x >= 0] if ms[0] >= 0 else [], "chosen": ch}
+            # ms per candidate (None: the candidate does not fit here or was not timed)
+            out[f"{kind}_l{l}"] = {"ms": [round(x, 4) if x >= 0 else None for x in ms[:nc]], "chosen": ch}
     return out
 
 
@@ -414,13 +423,32 @@ def run_gpu(args, w):
     steps1 = [dd.ddamg_krylov_steps(handles["mixed"], l, 1) for l in range(w["levels"])]
     clocks = clk.stop()
     prof = tm.profiled(handles["mixed"], args.steps)
+    outer_df = None
+    if mixed_prec == 2 and not args.only_mixed:
+        # the same solves with the outer FGMRES's D z_j and Gram-Schmidt in double-FP32 arithmetic
+        # (DDAMG_OPT_OUTER_DF; residuals b - D x stay FP64), timed the same way
+        dd.ddamg_set_option(handles["mixed"], dd.DDAMG_OPT_OUTER_DF, 1)
+        ms_df, st_df, _ = tm.timed(handles["mixed"], args.steps, args.warmup, tag="timed_mixed_df")
+        dd.ddamg_set_option(handles["mixed"], dd.DDAMG_OPT_OUTER_DF, 0)
+        for st in st_df:
+            for s in st:
+                if not (s["converged"] and s["true_residual"] <= TOL):
+                    raise SystemExit(f"solve (double-FP32 outer) missed the tolerance: {s}")
+        tot_df = reduce_max(sum(ms_df), dist, "cuda")
+        outer_df = {"value": round(whole_job_rate(ncols, args.steps, world, tot_df / 1e3), 4), "unit": "RHS/s",
+                    "ms_per_step": round(tot_df / args.steps, 3),
+                    "iterations": [s["iterations"] for st in st_df[:1] for s in st],
+                    "true_residual": max(s["true_residual"] for st in st_df for s in st),
+                    "what": "option DDAMG_OPT_OUTER_DF: outer D z_j and CGS2 in double-FP32 arithmetic on FP64 "
+                            "vectors, restart and final residuals in FP64 (not the headline value)"}
     if args.only_mixed:
         for h in handles.values():
             h.free()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": ncols * args.steps / (sum(ms_mixed) / 1e3), "unit": "RHS/s",
                               "note": "profiling run (--only-mixed): not a bench line",
-                              "roofline": roofline(prof, mixed_prec, KERNEL_FILE, sap_flops(w, nb))}))
+                              "roofline": roofline(prof, mixed_prec, KERNEL_FILE, sap_flops(w, nb),
+                                                   workload_key(w))}))
         return
     # end to end through the C ABI with host buffers in pinned memory (H2D of the rhs and D2H of x
     # inside every step; L2 flushed before every step, as in the device-timed loop)
@@ -483,12 +511,13 @@ def run_gpu(args, w):
                        "true_residual": max(s["true_residual"] for st in st_fp64 for s in st)},
         "mixed_over_fp64": round(value / value_fp64, 3),
         "setup_s": {k: round(v, 2) for k, v in setup_s.items()},
-        "roofline": roofline(prof, mixed_prec, KERNEL_FILE, sap_flops(w, nb)),
+        "roofline": roofline(prof, mixed_prec, KERNEL_FILE, sap_flops(w, nb), workload_key(w)),
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "krylov_steps_per_solve": [round((b - a) / args.steps, 1) for a, b in zip(steps0, steps1)],
         "autotuner": tuned,
+        "outer_double_fp32": outer_df,
     }
     for h in list(handles.values()):
         h.free()
@@ -550,7 +579,7 @@ def large_workload(dd, torch, stream, w, prec, steps, barrier):
             "s_per_rhs": round(tot / 1e3 / (ncols * steps), 5), "ms_per_step": round(tot / steps, 1),
             "iterations": [s["iterations"] for s in stats[0]], "true_residual": res, "all_converged": conv,
             "setup_s": round(t_setup, 1), "device_bytes": int(dev), "gpu_launches": int(launches),
-            "clocks": clocks, "roofline": roofline(prof, prec, KERNEL_FILE, sap_flops(w, w["nrhs"])),
+            "clocks": clocks, "roofline": roofline(prof, prec, KERNEL_FILE, sap_flops(w, w["nrhs"]), workload_key(w)),
             "autotuner": tuned}
 
 
@@ -959,7 +988,7 @@ def run_probe(args):
         nrhs = args.probe_rhs
         U = synth.su3_field(dims, 0.4, 0)
         p = dd.ddamg_default_params(levels=2, agg=[(4, 4, 4, 4)], n_tv=[2], sap_block=[(4, 4, 4, 4)], mr_steps=4,
-                                    nu=5, n_inv=0, eta_passes=0, precision=2, max_rhs=nrhs, seed=1,
+                                    nu=5, n_inv=0, eta_passes=0, precision=2, max_rhs=nrhs, seed=1, outer_restart=2,
                                     sap_schur=1 if args.probe_schur else 0)
         h = dd.ddamg_setup(U, dims, -1, mass("eps0.4_csw1"), 1.0, p, None)
         b = torch.from_numpy(np.ascontiguousarray(synth.random_spinors(nrhs, dims, 2))).cuda()
@@ -974,6 +1003,29 @@ def run_probe(args):
                           "us_per_launch": round(ms / n * 1e3, 2), "algorithmic_mb": round(by / n / 1e6, 2),
                           "gbs": round(by / n / (ms / n / 1e3) / 1e9, 1),
                           "device_gb": round(dd.ddamg_device_bytes(h) / 1e9, 2)}))
+    elif args.probe == "dslash":
+        # the fine operator on FP64 vectors: FP64 arithmetic (precision 0) and double-FP32 (2)
+        dims = tuple(int(x) for x in args.probe_dims.split(","))
+        nrhs = args.probe_rhs
+        U = synth.su3_field(dims, 0.4, 0)
+        p = dd.ddamg_default_params(levels=2, agg=[(4, 4, 4, 4)], n_tv=[2], sap_block=[(4, 4, 4, 4)], mr_steps=4,
+                                    nu=5, n_inv=0, eta_passes=0, precision=0, max_rhs=nrhs, seed=1)
+        h = dd.ddamg_setup(U, dims, -1, mass("eps0.4_csw1"), 1.0, p, None)
+        f = torch.from_numpy(np.ascontiguousarray(synth.random_spinors(nrhs, dims, 2))).cuda()
+        out = torch.zeros_like(f)
+        rec = {"probe": "fine operator on FP64 vectors", "dims": dims, "nrhs": nrhs}
+        for prec, name in ((0, "fp64"), (2, "double_fp32")):
+            for _ in range(reps):
+                dd.ddamg_apply(h, 0, prec, f, out, nrhs)
+            torch.cuda.synchronize()
+            dd.ddamg_profile(h, 1 << dd.PROF_KINDS["fine_dslash"])
+            for _ in range(reps):
+                dd.ddamg_apply(h, 0, prec, f, out, nrhs)
+            ms, n, by = dd.ddamg_profile_read(h, "fine_dslash")
+            dd.ddamg_profile(h, 0)
+            rec[name] = {"us_per_launch": round(ms / n * 1e3, 2), "algorithmic_mb": round(by / n / 1e6, 2)}
+        rec["device_gb"] = round(dd.ddamg_device_bytes(h) / 1e9, 2)
+        print(json.dumps(rec))
     else:
         dims = (32, 16, 16, 16)
         U = synth.su3_field(dims, 0.4, 0)
@@ -1017,10 +1069,10 @@ def main():
                     help="skip the batched 32^3x64 sub-measurement of the default bench")
     ap.add_argument("--large-steps", type=int, default=2,
                     help="timed steps (24 right-hand sides each) of the 32^3x64 sub-measurement")
-    ap.add_argument("--probe", choices=("sap", "coarse"), default=None,
+    ap.add_argument("--probe", choices=("sap", "coarse", "dslash"), default=None,
                     help="small single-kernel cases for profiling (one line; not a bench line)")
-    ap.add_argument("--probe-dims", default="48,24,24,24", help="lattice T,Z,Y,X of --probe sap")
-    ap.add_argument("--probe-rhs", type=int, default=1, help="right-hand sides of --probe sap")
+    ap.add_argument("--probe-dims", default="48,24,24,24", help="lattice T,Z,Y,X of --probe sap and --probe dslash")
+    ap.add_argument("--probe-rhs", type=int, default=1, help="right-hand sides of --probe sap and --probe dslash")
     ap.add_argument("--probe-schur", action="store_true", help="--probe sap with Schur block solves")
     ap.add_argument("--scan", action="store_true",
                     help="mass- and error-scaling sweeps of DD-alpha-AMG against CGNR (one JSON line)")

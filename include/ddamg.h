@@ -181,13 +181,28 @@ enum {
                                      kernels; 1..4: the tensor-core kernels with the k dimension
                                      split over that many warp groups (and the batch
                                      prolongation), where they fit */
-  DDAMG_OPT_SAP_SCHUR = 5         /* 0/1: params.sap_schur switched after setup (the per-site
+  DDAMG_OPT_SAP_SCHUR = 5,        /* 0/1: params.sap_schur switched after setup (the per-site
                                      inverse tables are built on first use)            */
+  DDAMG_OPT_SAP_PERSIST = 6,      /* coarse-level SAP on FP16 blocks (levels 1..L-2): -1 (default):
+                                     autotuned per level between one cluster launch per colour
+                                     sweep (0) and one persistent cooperative launch for all
+                                     sweeps of a smoother call (1), where all clusters of the
+                                     level fit on the device at once; 0/1 force the choice (1
+                                     only where it fits).  Same arithmetic either way. */
+  DDAMG_OPT_OUTER_DF = 7          /* 0 (default) / 1: the outer FGMRES forms D z_j and its CGS2
+                                     Gram-Schmidt products in double-FP32 arithmetic (Dekker
+                                     pairs, about 48 significand bits) on its FP64 vectors; the
+                                     restart and final residuals b - D x stay FP64.  GB300's FP64
+                                     rate is 1/64 of its FP32 rate, which bounds the FP64
+                                     operator and Gram-Schmidt kernels.  The paper's outer solver
+                                     is double precision (Sec. 3); this option trades its last
+                                     bits (relative error of D about 1e-14) for speed. */
 };
 int ddamg_set_option(ddamg_handle* h, int option, int value);
 /* Effective setting: GRAPHS 0/1; COARSEST_CLUSTER and SAP_CLUSTER the cluster size in use on the
  * coarsest level / on level 1 (FP32 path), 0 when the one-CTA kernels run; HALF_STORAGE 0/1;
- * COARSE_TC the kernel in use on level 1 (0 CUDA cores, k >= 1 tensor cores with k-split k). */
+ * COARSE_TC the kernel in use on level 1 (0 CUDA cores, k >= 1 tensor cores with k-split k);
+ * SAP_PERSIST 1 when level 1's smoother calls run as one persistent launch; OUTER_DF 0/1. */
 int ddamg_get_option(ddamg_handle* h, int option, int* value);
 
 /* ---- measurement ----------------------------------------------------------- */
@@ -247,11 +262,14 @@ int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double
  *   tensor-core kernel with k-split 1..4 (P read once per batch);
  * kind DDAMG_TUNE_PROLONG (level l+1 -> l): the per-right-hand-side kernel (0) and the kernel that
  *   reads P once for the batch (1).
+ * kind DDAMG_TUNE_SAP (levels 1..L-2): one smoother call (nu SAP applications on the batch) as one
+ *   launch per colour sweep (0) and as one persistent launch (1; timed only where it fits and an
+ *   eager and a graph-captured trial run without error).
  * ms[0..4] = milliseconds of one application of the handle's batch size per candidate (-1 where
  * the candidate does not fit or was not timed); *chosen = the candidate in use.  The tuner runs at
- * setup and when DDAMG_OPT_HALF_STORAGE or DDAMG_OPT_COARSE_TC is set; its choice holds for every
- * batch size.  Errors: ARG. */
-enum { DDAMG_TUNE_COARSE = 0, DDAMG_TUNE_RESTRICT = 1, DDAMG_TUNE_PROLONG = 2 };
+ * setup and when DDAMG_OPT_HALF_STORAGE, DDAMG_OPT_COARSE_TC or DDAMG_OPT_SAP_PERSIST is set; its
+ * choice holds for every batch size.  Errors: ARG. */
+enum { DDAMG_TUNE_COARSE = 0, DDAMG_TUNE_RESTRICT = 1, DDAMG_TUNE_PROLONG = 2, DDAMG_TUNE_SAP = 3 };
 int ddamg_autotune_times(ddamg_handle* h, int kind, int level, double* ms, int* chosen);
 
 /* ---- building blocks of the method, exposed for parity tests ------------ */
@@ -265,7 +283,9 @@ int ddamg_level_info(ddamg_handle* h, int level, int dims[4], int* ndof, int* nt
  * Galerkin operator D_l = P_{l-1}^dagger D_{l-1} P_{l-1} of Sec. 1, applied as its
  * 9-point stencil of dense blocks (Sec. 2).  precision 0 = FP64, 1 = FP32 arithmetic
  * on the FP32 path's storage (FP16 while DDAMG_OPT_HALF_STORAGE is on); the same for
- * the precision argument of the calls below.  Other values: ARG. */
+ * the precision argument of the calls below.  Here only, precision 2 = double-FP32
+ * arithmetic on FP64 vectors (level 0; the operator of DDAMG_OPT_OUTER_DF).  Other
+ * values: ARG. */
 int ddamg_apply(ddamg_handle* h, int level, int precision, const double* in, double* out, int n);
 
 /* iterations x { z <- z + M_SAP (b - D_l z) } on level l < L-1 (z in/out): the SAP

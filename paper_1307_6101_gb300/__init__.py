@@ -44,6 +44,8 @@ DDAMG_OPT_SAP_CLUSTER = 2
 DDAMG_OPT_HALF_STORAGE = 3
 DDAMG_OPT_COARSE_TC = 4
 DDAMG_OPT_SAP_SCHUR = 5
+DDAMG_OPT_SAP_PERSIST = 6
+DDAMG_OPT_OUTER_DF = 7
 SETUP_KINDS = ("smooth", "kcycle", "rebuild")   # DDAMG_SETUP_* order
 PROF_KINDS = {"fine_sap": 0, "fine_dslash": 1, "coarse_apply": 2, "coarse_sap": 3, "transfer": 4, "precond": 5,
               "outer_ortho": 6}
@@ -364,7 +366,7 @@ def ddamg_setup_times(h):
     return [dict(zip(SETUP_KINDS, buf[l * len(SETUP_KINDS):(l + 1) * len(SETUP_KINDS)])) for l in range(MAX_LEVELS)]
 
 
-TUNE_KINDS = {"coarse": 0, "restrict": 1, "prolong": 2}
+TUNE_KINDS = {"coarse": 0, "restrict": 1, "prolong": 2, "sap": 3}
 
 
 def ddamg_autotune_times(h, kind, level):

@@ -111,6 +111,48 @@ __global__ void k_multidot1(double* __restrict__ part, const cplx<T>* __restrict
   }
 }
 
+// stage 1 of the multidot in double-FP32 arithmetic on FP64 vectors: the elements are split on
+// load, products and the per-thread sums are double-FP32, the CTA sum is FP64 (partials as above)
+__global__ void k_multidot1_df(double* __restrict__ part, const cplx<double>* __restrict__ V, size_t vstride,
+                               int m, const cplx<double>* __restrict__ w, size_t len, size_t rstride, int nc) {
+  __shared__ double sh[32 * 8];
+  const int chunk = blockIdx.x, rhs = blockIdx.y;
+  size_t lo, hi;
+  chunk_range(len, nc, chunk, lo, hi);
+  const cplx<double>* pw = w + (size_t)rhs * rstride;
+  for (int d0 = 0; d0 < m; d0 += 4) {
+    dfl at[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) at[k] = dfl(0);
+    for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+      const cplx<double> wd = pw[e];
+      const dfl wr = df_from_double(wd.re), wi = df_from_double(wd.im);
+#pragma unroll
+      for (int dd = 0; dd < 4; ++dd) {
+        if (d0 + dd < m) {
+          const cplx<double> vd = V[(size_t)(d0 + dd) * vstride + (size_t)rhs * rstride + e];
+          const dfl vr = df_from_double(vd.re), vi = df_from_double(vd.im);
+          // conj(v) w
+          at[2 * dd] = fma(vr, wr, at[2 * dd]);
+          at[2 * dd] = fma(vi, wi, at[2 * dd]);
+          at[2 * dd + 1] = fma(vr, wi, at[2 * dd + 1]);
+          at[2 * dd + 1] = fma(-vi, wr, at[2 * dd + 1]);
+        }
+      }
+    }
+    double acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = df_to_double(at[k]);
+    cta_sum(acc, 8, sh);
+    if (threadIdx.x == 0)
+      for (int dd = 0; dd < 4 && d0 + dd < m; ++dd) {
+        double* p = part + (((size_t)rhs * m + d0 + dd) * nc + chunk) * 2;
+        p[0] = acc[2 * dd];
+        p[1] = acc[2 * dd + 1];
+      }
+  }
+}
+
 // stage 2: res[rhs * m + d] = sum over chunks, fixed order
 __global__ void k_multidot2(cplx<double>* __restrict__ res, const double* __restrict__ part, int m, int nc,
                             int res_stride) {
@@ -173,6 +215,34 @@ __global__ void k_multiaxpy(cplx<T>* __restrict__ y, const cplx<T>* __restrict__
     cfma(acc, cs[i], V[(size_t)i * vstride + o]);
   }
   y[o] = acc;
+}
+
+// y += sign * sum_i c_i V_i in double-FP32 arithmetic on FP64 vectors (result rounded to FP64)
+__global__ void k_multiaxpy_df(cplx<double>* __restrict__ y, const cplx<double>* __restrict__ V, size_t vstride,
+                               int m, const cplx<double>* __restrict__ c, int cstride, double sign, size_t len,
+                               size_t rstride) {
+  __shared__ cplx<dfl> cs[64];
+  __shared__ int use[64];
+  const int rhs = blockIdx.y;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const cplx<double> ci = c[(size_t)rhs * cstride + i];
+    use[i] = !(ci.re == 0.0 && ci.im == 0.0);
+    const double a = sign * ci.re, b = sign * ci.im;
+    const float ah = __double2float_rn(a), bh = __double2float_rn(b);
+    cs[i] = cmk<dfl>(dfl(ah, __double2float_rn(a - (double)ah)), dfl(bh, __double2float_rn(b - (double)bh)));
+  }
+  __syncthreads();
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  const size_t o = (size_t)rhs * rstride + e;
+  const cplx<double> yd = y[o];
+  cplx<dfl> acc = cmk<dfl>(df_from_double(yd.re), df_from_double(yd.im));
+  for (int i = 0; i < m; ++i) {
+    if (!use[i]) continue;
+    const cplx<double> vd = V[(size_t)i * vstride + o];
+    cfma(acc, cs[i], cmk<dfl>(df_from_double(vd.re), df_from_double(vd.im)));
+  }
+  y[o] = cmk<double>(df_to_double(acc.re), df_to_double(acc.im));
 }
 
 template <typename T>
@@ -314,6 +384,25 @@ void blas_multidot(cplx<double>* res, int res_stride, const cplx<T>* V, size_t v
   k_multidot1<T><<<dim3(nc, nrhs), RT, 0, st>>>(part, V, vstride, m, w, len, rstride, nc);
   count_launch();
   k_multidot2<<<dim3(m, nrhs), 128, 0, st>>>(res, part, m, nc, res_stride);
+}
+
+void blas_multidot_df(cplx<double>* res, int res_stride, const cplx<double>* V, size_t vstride, int m,
+                      const cplx<double>* w, size_t len, int nrhs, size_t rstride, cudaStream_t st) {
+  if (m <= 0) return;
+  const int nc = nchunks(len);
+  double* part = partials((size_t)nrhs * m * nc * 2);
+  count_launch();
+  k_multidot1_df<<<dim3(nc, nrhs), RT, 0, st>>>(part, V, vstride, m, w, len, rstride, nc);
+  count_launch();
+  k_multidot2<<<dim3(m, nrhs), 128, 0, st>>>(res, part, m, nc, res_stride);
+}
+
+void blas_multiaxpy_df(cplx<double>* y, const cplx<double>* V, size_t vstride, int m, const cplx<double>* c,
+                       int cstride, double sign, size_t len, int nrhs, size_t rstride, cudaStream_t st) {
+  if (m <= 0) return;
+  if (m > 64) throw std::runtime_error("blas_multiaxpy_df: at most 64 vectors");
+  count_launch();
+  k_multiaxpy_df<<<dim3(div_up(len, 256), nrhs), 256, 0, st>>>(y, V, vstride, m, c, cstride, sign, len, rstride);
 }
 
 void reserve_partials(int nrhs, int m) { partials((size_t)nrhs * (m + 1) * MAXCHUNKS * 2); }

@@ -523,6 +523,272 @@ __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restri
   if (!ok && threadIdx.x == 0) mbar_wait_bounded(bar, 0);   // no copy may still be in flight at exit
 }
 
+// ---------------------------------------------------------------------------
+// Persistent coarse SAP: all `iters` SAP applications (a red then a black sweep each) of one
+// smoother call in one launch, for levels whose SAP blocks of both colours are resident at once.
+// Cluster c owns red block blocks0[c] and black block blocks1[c]; each CTA stages the blocks
+// inside both SAP blocks of its sites once, for the whole call.  A colour sweep is the sweep of
+// k_coarse_sap_cluster (same arithmetic, same order); sweeps are separated by a barrier over all
+// clusters, which the cooperative launch makes safe (all CTAs co-resident).  z is read through
+// L2 (ld.global.cg): values written by other SMs in the previous sweep are never taken from a
+// stale L1 line.
+
+// z in L2 only (values written by other CTAs of the launch)
+__device__ __forceinline__ cplx<float> ldz(const cplx<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return cmk<float>(v.x, v.y);
+}
+__device__ __forceinline__ cplx<double> ldz(const cplx<double>* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return cmk<double>(v.x, v.y);
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier over the clusters of a persistent launch.  Rank 0 of every cluster counts its cluster
+// in (the counter is zeroed before the launch; round r is complete at ncl * (r + 1)) and waits
+// for the others; the wait is bounded (about a second at the maximum clock), after which
+// *err = 3 and every CTA of the cluster gets false.
+__device__ bool persist_grid_sync(unsigned* cnt, unsigned target, cg::cluster_group& cluster, int* flag, int* err) {
+  cluster.sync();   // the sweep's writes of every CTA of the cluster precede the arrival
+  if (cluster.block_rank() == 0 && threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(cnt, 1u);
+    const long long t0 = clock64();
+    int ok = 1;
+    while (ld_acquire_gpu(cnt) < target) {
+      if (clock64() - t0 > 2000000000LL) {
+        ok = 0;
+        atomicExch(err, 3);
+        break;
+      }
+      __nanosleep(64);
+    }
+    *flag = ok;
+  }
+  cluster.sync();
+  return *cluster.map_shared_rank(flag, 0) != 0;
+}
+
+struct PSapSmem {
+  size_t rfull, pbuf, part, red, sh, slot, flag, bar, total;
+};
+DD_HD PSapSmem psap_smem_layout(int vB, int n, int spc, int nsl, size_t bs, size_t ts) {
+  PSapSmem L;
+  size_t o = al16((size_t)2 * spc * nsl * n * n * bs);
+  L.rfull = o;
+  o = al16(o + (size_t)vB * n * 2 * ts);
+  L.pbuf = o;
+  o = al16(o + (size_t)2 * vB * n * 2 * ts);
+  L.part = o;
+  o = al16(o + (size_t)9 * spc * n * 2 * ts);
+  L.red = o;
+  o = al16(o + (size_t)2 * 16 * 4 * ts);
+  L.sh = o;
+  o = al16(o + (size_t)(32 * 3 + 4) * ts);
+  L.slot = o;
+  o = al16(o + (size_t)2 * spc * 9 * sizeof(int));
+  L.flag = o;
+  o = al16(o + 16);
+  L.bar = o;
+  L.total = al16(o + 8);
+  return L;
+}
+
+template <typename T, typename BS>
+__global__ void __launch_bounds__(768, 1) k_coarse_sap_persist(
+    cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc, const BS* __restrict__ blk,
+    const float* __restrict__ bscale, Geom g, int n, size_t rstride, int nrhs, const int* __restrict__ blocks0,
+    int nb0, const int* __restrict__ blocks1, int nb1, int k_mr, int spc, int nsl, int iters, int* err,
+    const int* __restrict__ bsite, const int* __restrict__ bloc, unsigned* gcnt) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CLS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int cid = blockIdx.x / CLS;
+  const unsigned ncl = gridDim.x / CLS;
+  const int vB = g.vB;
+  const int rows = spc * n;
+  const size_t nn = (size_t)n * n;
+  const PSapSmem L = psap_smem_layout(vB, n, spc, nsl, sizeof(BS), sizeof(T));
+  BS* stage = reinterpret_cast<BS*>(smem_raw);                                // [2][spc][nsl][n][n]
+  cplx<T>* rfull = reinterpret_cast<cplx<T>*>(smem_raw + L.rfull);            // [vB*n]
+  cplx<T>* pbuf = reinterpret_cast<cplx<T>*>(smem_raw + L.pbuf);              // [2][vB*n]
+  cplx<T>* part = reinterpret_cast<cplx<T>*>(smem_raw + L.part);              // [9][rows]
+  T* red = reinterpret_cast<T*>(smem_raw + L.red);                            // [2][16][4]
+  T* sh = reinterpret_cast<T*>(smem_raw + L.sh);                              // [32][3] + 3
+  int* slot = reinterpret_cast<int*>(smem_raw + L.slot);                      // [2][spc][9]
+  int* flag = reinterpret_cast<int*>(smem_raw + L.flag);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + L.bar);
+  const int blk0 = cid < nb0 ? blocks0[cid] : -1, blk1 = cid < nb1 ? blocks1[cid] : -1;
+  // slots of the staged blocks of both colours (k order: self, forward mu, backward mu)
+  if (threadIdx.x < 2 * spc) {
+    const int c = threadIdx.x / spc, s = threadIdx.x - c * spc;
+    int* sl9 = slot + (c * spc + s) * 9;
+    const int bc = c ? blk1 : blk0;
+    if (bc >= 0) {
+      int co[4];
+      geom_coords(g, bsite[(size_t)bc * vB + rank * spc + s], co);
+      int ns = 0;
+      sl9[0] = ns++;
+      for (int sd = 0; sd < 2; ++sd)
+        for (int mu = 0; mu < 4; ++mu)
+          sl9[(sd ? 5 : 1) + mu] = hop_internal(g, co, mu, sd ? -1 : +1, g.B) ? ns++ : -1;
+    } else {
+      for (int e = 0; e < 9; ++e) sl9[e] = -1;
+    }
+  }
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int cnt = 0;
+    for (int e = 0; e < 2 * spc * 9; ++e) cnt += slot[e] >= 0 ? 1 : 0;
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (unsigned)(cnt * nn * sizeof(BS)));
+    __syncwarp();
+    for (int e = threadIdx.x; e < 2 * spc * 9; e += 32) {
+      const int cs = e / 9, k = e % 9, q = slot[e];   // cs = c * spc + s
+      if (q >= 0) {
+        const int c = cs / spc, s = cs - c * spc;
+        const int site = bsite[(size_t)(c ? blk1 : blk0) * vB + rank * spc + s];
+        bulk_g2s(stage + ((size_t)cs * nsl + q) * nn, blk + ((size_t)site * 9 + k) * nn,
+                 (unsigned)(nn * sizeof(BS)), bar);
+      }
+    }
+  }
+  const int ok = __syncthreads_and(mbar_wait_bounded(bar, 0) ? 1 : 0);
+  if (!ok && threadIdx.x == 0) atomicExch(err, 2);
+  const int k = threadIdx.x / rows;
+  const int rl = threadIdx.x - k * rows;
+  const int sl = rl / n, i = rl - (rl / n) * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  unsigned round = 0;
+  bool alive = true;
+  for (int it = 0; it < iters && alive; ++it)
+    for (int c = 0; c < 2 && alive; ++c) {
+      const int bc = c ? blk1 : blk0;
+      if (bc >= 0) {   // uniform over the cluster
+        const int* own = bsite + (size_t)bc * vB + rank * spc;
+        const int site = own[sl];
+        const T sc = bscale ? T(bscale[site]) : T(1);
+        int q = -1, nb = site, nloc = 0;
+        if (k < 9) {
+          q = slot[(c * spc + sl) * 9 + k];
+          if (k > 0) {
+            int co[4];
+            geom_coords(g, site, co);
+            nb = geom_neighbor(g, co, (k - 1) % 4, k <= 4 ? +1 : -1);
+          }
+          nloc = q >= 0 ? bloc[nb] : 0;
+        }
+        const BS* Ms = stage + ((size_t)(c * spc + sl) * nsl + (q >= 0 ? q : 0)) * nn + i;
+        for (int rh = 0; rh < nrhs; ++rh) {
+          const size_t ro = (size_t)rh * rstride;
+          // rho = b - D z on the own rows (z through L2)
+          cplx<T> acc = czero<T>();
+          if (k < 9) {
+            const cplx<T>* v = z + ro + (size_t)nb * n;
+            if (q < 0) {
+              const BS* M = blk + ((size_t)site * 9 + k) * nn + i;
+#pragma unroll 8
+              for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), ldz(v + j));
+            } else {
+#pragma unroll 8
+              for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(Ms, (size_t)j * n), ldz(v + j));
+            }
+            part[k * rows + rl] = sc * acc;
+          }
+          __syncthreads();
+          cplx<T> r = czero<T>(), xs = czero<T>();
+          if (threadIdx.x < rows) {
+            cplx<T> d = czero<T>();
+#pragma unroll
+            for (int m = 0; m < 9; ++m) d = d + part[m * rows + threadIdx.x];
+            r = bsrc[ro + (size_t)own[threadIdx.x / n] * n + threadIdx.x % n] - d;
+            for (int cc = 0; cc < CLS; ++cc) cluster.map_shared_rank(rfull, cc)[(size_t)rank * rows + threadIdx.x] = r;
+          }
+          cluster.sync();
+          for (int mr = 0; mr < k_mr; ++mr) {
+            const int buf = mr & 1;
+            cplx<T>* pb = pbuf + (size_t)buf * vB * n;
+            T* rb = red + buf * 64;
+            // p = D_B r on the own rows, from the staged blocks and the local copy of r
+            if (k < 9) {
+              cplx<T> a = czero<T>();
+              if (q >= 0) {
+                const cplx<T>* v = rfull + (size_t)nloc * n;
+#pragma unroll 8
+                for (int j = 0; j < n; ++j) cfma(a, ld_cplx(Ms, (size_t)j * n), v[j]);
+              }
+              part[k * rows + rl] = sc * a;
+            }
+            __syncthreads();
+            cplx<T> p = czero<T>();
+            T nre = T(0), nim = T(0), den = T(0);
+            if (threadIdx.x < rows) {
+#pragma unroll
+              for (int m = 0; m < 9; ++m) p = p + part[m * rows + threadIdx.x];
+              const cplx<T> t = cdotc(p, r);
+              nre = t.re;
+              nim = t.im;
+              den = cnorm2(p);
+              for (int cc = 0; cc < CLS; ++cc) cluster.map_shared_rank(pb, cc)[(size_t)rank * rows + threadIdx.x] = p;
+            }
+            for (int off = 16; off >= 1; off >>= 1) {
+              nre += __shfl_xor_sync(0xffffffffu, nre, off);
+              nim += __shfl_xor_sync(0xffffffffu, nim, off);
+              den += __shfl_xor_sync(0xffffffffu, den, off);
+            }
+            if (lane == 0) { sh[3 * warp] = nre; sh[3 * warp + 1] = nim; sh[3 * warp + 2] = den; }
+            __syncthreads();
+            if (warp == 0) {   // warp partials summed by a shuffle tree (fixed order), sent to every CTA
+              T a = lane < nw ? sh[3 * lane] : T(0);
+              T bb = lane < nw ? sh[3 * lane + 1] : T(0);
+              T cc = lane < nw ? sh[3 * lane + 2] : T(0);
+              for (int off = 16; off >= 1; off >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, off);
+                bb += __shfl_xor_sync(0xffffffffu, bb, off);
+                cc += __shfl_xor_sync(0xffffffffu, cc, off);
+              }
+              if (lane < CLS) {
+                T* dst = cluster.map_shared_rank(rb, lane) + rank * 4;
+                dst[0] = a;
+                dst[1] = bb;
+                dst[2] = cc;
+              }
+            }
+            cluster.sync();
+            T a = T(0), bb = T(0), cc = T(0);
+            for (int q2 = 0; q2 < CLS; ++q2) { a += rb[q2 * 4]; bb += rb[q2 * 4 + 1]; cc += rb[q2 * 4 + 2]; }
+            const cplx<T> alpha = cc > T(0) ? cmk<T>(a / cc, bb / cc) : czero<T>();
+            if (threadIdx.x < rows) {
+              cfma(xs, alpha, r);
+              r = r - alpha * p;
+            }
+            for (int e = threadIdx.x; e < vB * n; e += blockDim.x) rfull[e] = rfull[e] - alpha * pb[e];
+            __syncthreads();
+          }
+          if (ok && threadIdx.x < rows) {
+            const size_t a = ro + (size_t)own[threadIdx.x / n] * n + threadIdx.x % n;
+            z[a] = ldz(z + a) + xs;
+          }
+          // every CTA is done with its copies of r, p and the partials before the next right-hand
+          // side writes into them
+          if (rh + 1 < nrhs) cluster.sync();
+        }
+      }
+      if (it + 1 < iters || c == 0) {
+        ++round;
+        alive = persist_grid_sync(gcnt, ncl * round, cluster, flag, err);
+      }
+    }
+  if (!ok && threadIdx.x == 0) mbar_wait_bounded(bar, 0);   // no copy may still be in flight at exit
+  cluster.sync();   // no CTA exits while others may still write into its shared memory
+}
+
 // Gauss-Jordan inversion with partial pivoting of every self block (FP64).
 __global__ void k_selfinv_build(cplx<double>* __restrict__ inv, const cplx<double>* __restrict__ blk, int n,
                                 int* err) {
@@ -774,6 +1040,75 @@ int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out, in
     return 1;
   }
   return 0;
+}
+
+// Persistent SAP on FP16 blocks (FP32 compute): the launch's shared memory, and whether all
+// clusters (max(nb0, nb1) of op.sap_cls CTAs) can be resident at once on this device.
+size_t coarse_sap_persist_smem(const CoarseOp<float>& op) {
+  if (op.sap_cls <= 0) return 0;
+  const int spc = op.g.vB / op.sap_cls;
+  return psap_smem_layout(op.g.vB, op.n, spc, op.sap_nsl, sizeof(__half2), sizeof(float)).total;
+}
+
+bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1) {
+  if (op.sap_cls <= 0 || !op.blkh || nb0 <= 0 || nb1 <= 0) return false;
+  const int CLS = op.sap_cls, spc = op.g.vB / CLS;
+  const int threads = ((9 * spc * op.n + 31) / 32) * 32;
+  const size_t sm = coarse_sap_persist_smem(op);
+  if (threads > 768 || sm > 227 * 1024) return false;
+  if (cudaFuncSetAttribute(k_coarse_sap_persist<float, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm) != cudaSuccess ||
+      (CLS > 8 && cudaFuncSetAttribute(k_coarse_sap_persist<float, __half2>,
+                                       cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CLS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(CLS, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_sap_persist<float, __half2>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return nclusters >= (nb0 > nb1 ? nb0 : nb1);
+}
+
+cudaError_t coarse_sap_persist(cplx<float>* z, const cplx<float>* b, const CoarseOp<float>& op, const int* blocks0,
+                               int nb0, const int* blocks1, int nb1, int nrhs, size_t rstride, int k_mr, int iters,
+                               unsigned* gcnt, cudaStream_t st) {
+  if (nrhs <= 0 || iters <= 0) return cudaSuccess;
+  if (op.sap_cls <= 0 || !op.blkh || nb0 <= 0 || nb1 <= 0) return cudaErrorInvalidValue;
+  const int CLS = op.sap_cls, spc = op.g.vB / CLS;
+  const int threads = ((9 * spc * op.n + 31) / 32) * 32;
+  cudaError_t e = cudaMemsetAsync(gcnt, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CLS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;   // all clusters co-resident (they wait on one another)
+  attr[1].val.cooperative = 1;
+  cfg.gridDim = dim3((nb0 > nb1 ? nb0 : nb1) * CLS, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = coarse_sap_persist_smem(op);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, k_coarse_sap_persist<float, __half2>, z, b, op.blkh, op.bscale, op.g, op.n,
+                            rstride, nrhs, blocks0, nb0, blocks1, nb1, k_mr, spc, op.sap_nsl, iters, op.err, op.bsite,
+                            op.bloc, gcnt);
 }
 
 template <typename T>

@@ -15,6 +15,7 @@
 //   backward (1 + gamma_k): h = up - i sigma_k dn,  lower = +i sigma_k h
 // The antiperiodic sign of the time direction multiplies the hop that wraps.
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "kernels.h"
 #include "tma.cuh"
 
@@ -237,6 +238,77 @@ __global__ void k_fine_dslash(cplx<T>* __restrict__ out, const cplx<T>* __restri
 #pragma unroll
     for (int k = 0; k < 12; ++k) po[(size_t)k * V + x] = d[k] - T(0.5) * acc[k];
   }
+}
+
+// ---------------------------------------------------------------------------
+// The full operator in double-FP32 arithmetic on FP64 vectors: the same hop and clover code as
+// k_fine_dslash instantiated for the double-FP32 type, links and clover term (with the mass shift)
+// stored as double-FP32 pairs, the FP64 input split on load and the result rounded to FP64.
+__device__ __forceinline__ void load_spinor_df(const cplx<double>* __restrict__ p, int V, int x, cplx<dfl> s[12],
+                                               bool neg) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const cplx<double> v = p[(size_t)k * V + x];
+    s[k] = cmk<dfl>(df_from_double(sign_flip(v.re, neg)), df_from_double(sign_flip(v.im, neg)));
+  }
+}
+
+template <bool RESID>
+__global__ void __launch_bounds__(128) k_fine_dslash_df(cplx<double>* __restrict__ out,
+                                                         const cplx<double>* __restrict__ in,
+                                                         const cplx<double>* __restrict__ bsrc,
+                                                         const cplx<dfl>* __restrict__ U,
+                                                         const dfl* __restrict__ clov, Geom g, int bc_t,
+                                                         size_t rstride) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.V) return;
+  const size_t ro = (size_t)blockIdx.y * rstride;
+  const cplx<double>* ps = in + ro;
+  const int V = g.V;
+  int c[4];
+  geom_coords(g, x, c);
+  cplx<dfl> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = czero<dfl>();
+  cplx<dfl> nb[12], u[9];
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    {
+      const int n = geom_neighbor(g, c, mu, +1);
+      load_spinor_df(ps, V, n, nb, mu == 0 && c[0] == g.L[0] - 1 && bc_t < 0);
+      load_link(U, V, mu, x, u);
+      hop_accumulate(mu, true, u, nb, acc);
+    }
+    {
+      const int n = geom_neighbor(g, c, mu, -1);
+      load_spinor_df(ps, V, n, nb, mu == 0 && c[0] == 0 && bc_t < 0);
+      load_link(U, V, mu, n, u);
+      hop_accumulate(mu, false, u, nb, acc);
+    }
+  }
+  cplx<dfl> d[12];
+  load_spinor_df(ps, V, x, nb, false);
+  clover_apply(clov, V, x, nb, d, dfl(0));
+  cplx<double>* po = out + ro;
+  const dfl half(0.5f);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    cplx<dfl> v = d[k] - half * acc[k];
+    if (RESID) {
+      const cplx<double> bb = bsrc[ro + (size_t)k * V + x];
+      v = cmk<dfl>(df_from_double(bb.re), df_from_double(bb.im)) - v;
+    }
+    po[(size_t)k * V + x] = cmk<double>(df_to_double(v.re), df_to_double(v.im));
+  }
+}
+
+// FP64 -> double-FP32 pairs rounded to nearest (operator data, converted once)
+__global__ void k_double_to_df(dfl* __restrict__ dst, const double* __restrict__ src, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = src[i];
+  const float hi = __double2float_rn(x);
+  dst[i] = dfl(hi, __double2float_rn(__dsub_rn(x, (double)hi)));
 }
 
 // ---------------------------------------------------------------------------
@@ -1545,6 +1617,21 @@ void clover_mix(float* mix32, __half2* mixh, const double* clov, const double* i
     count_launch();
     k_clover_mix_half<<<div_up((size_t)36 * g.V, 256), 256, 0, st>>>(mixh, clov, inv, g, shift);
   }
+}
+
+void double_to_df(dfl* dst, const double* src, size_t n, cudaStream_t st) {
+  if (n == 0) return;
+  count_launch();
+  k_double_to_df<<<(unsigned)div_up(n, 256), 256, 0, st>>>(dst, src, n);
+}
+
+void fine_dslash_df(cplx<double>* out, const cplx<double>* in, const cplx<double>* b, const cplx<dfl>* Udf,
+                    const dfl* clovdf, const Geom& g, int bc_t, int nrhs, size_t rstride, cudaStream_t st) {
+  if (nrhs <= 0) return;
+  const dim3 grid(div_up(g.V, 128), nrhs);
+  count_launch();
+  if (b) k_fine_dslash_df<true><<<grid, 128, 0, st>>>(out, in, b, Udf, clovdf, g, bc_t, rstride);
+  else k_fine_dslash_df<false><<<grid, 128, 0, st>>>(out, in, b, Udf, clovdf, g, bc_t, rstride);
 }
 
 void links_to_half(__half2* dst, const cplx<double>* U, size_t n, cudaStream_t st) {

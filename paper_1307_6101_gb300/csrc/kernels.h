@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace dd {
 
@@ -64,6 +65,12 @@ void clover_build(double* clov, const cplx<double>* gauge_lex, const Geom& g, do
                   cudaStream_t st);
 // out = Gamma_5 in on nrhs fine FP64 fields (may be in place)
 void fine_gamma5(cplx<double>* out, const cplx<double>* in, int V, int nrhs, size_t rstride, cudaStream_t st);
+// double-FP32 operator data (pairs rounded to nearest) and the full operator in double-FP32
+// arithmetic on FP64 vectors (out = D in, or out = b - D in when b is set); Udf [4][9][V],
+// clovdf [2][36][V] with the mass shift
+void double_to_df(dfl* dst, const double* src, size_t n, cudaStream_t st);
+void fine_dslash_df(cplx<double>* out, const cplx<double>* in, const cplx<double>* b, const cplx<dfl>* Udf,
+                    const dfl* clovdf, const Geom& g, int bc_t, int nrhs, size_t rstride, cudaStream_t st);
 // per-site inverse of the packed Hermitian 6x6 blocks (LDL^+ in FP64); *err = 1 on a zero pivot
 void clover_inverse(double* inv, const double* clov, int V, int* err, cudaStream_t st);
 // the Schur SAP tables (either pointer may be null)
@@ -93,6 +100,13 @@ size_t coarse_tc_smem(int n, int ks);
 template <typename T>
 cudaError_t coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks,
                       int nrhs, size_t rstride, int k_mr, cudaStream_t st);
+// all `iters` SAP applications (red then black sweep) in one cooperative launch of clusters that
+// stay resident (FP16 blocks, FP32 compute); *gcnt: a device counter for the launch's barriers
+size_t coarse_sap_persist_smem(const CoarseOp<float>& op);
+bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1);
+cudaError_t coarse_sap_persist(cplx<float>* z, const cplx<float>* b, const CoarseOp<float>& op, const int* blocks0,
+                               int nb0, const int* blocks1, int nb1, int nrhs, size_t rstride, int k_mr, int iters,
+                               unsigned* gcnt, cudaStream_t st);
 void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int n, int* err, cudaStream_t st);
 template <typename T>
 // prefer: a cluster size (2, 4, 8, 16) to try first, anything else for the default order
@@ -196,6 +210,11 @@ void blas_recip(double* a, int n, cudaStream_t st);
 template <typename T>
 void blas_multiaxpy(cplx<T>* y, const cplx<T>* V, size_t vstride, int m, const cplx<double>* c, int cstride,
                     double sign, size_t len, int nrhs, size_t rstride, cudaStream_t st);
+// the same two operations in double-FP32 arithmetic on FP64 vectors (outer Gram-Schmidt option)
+void blas_multidot_df(cplx<double>* res, int res_stride, const cplx<double>* V, size_t vstride, int m,
+                      const cplx<double>* w, size_t len, int nrhs, size_t rstride, cudaStream_t st);
+void blas_multiaxpy_df(cplx<double>* y, const cplx<double>* V, size_t vstride, int m, const cplx<double>* c,
+                       int cstride, double sign, size_t len, int nrhs, size_t rstride, cudaStream_t st);
 // y = a[rhs] * x   (a real, from device memory)
 template <typename T>
 void blas_scale_to(cplx<T>* y, const cplx<T>* x, const double* a, size_t len, int nrhs, size_t rstride,

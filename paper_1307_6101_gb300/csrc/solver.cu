@@ -84,6 +84,8 @@ struct Level {
   __half2* blkh = nullptr;    // coarse blocks, one scale per site in bscale
   float* bscale = nullptr;
   float* mix32 = nullptr;     // fine level, Schur SAP: clover (even sites) / inverse (odd sites), FP32
+  cplx<dfl>* Udf = nullptr;   // fine level: links as double-FP32 pairs (outer operator option)
+  dfl* clovdf = nullptr;      // fine level: (m0 + 4) + clover as double-FP32 pairs
   __half2* mixh = nullptr;    // the same tables in FP16
   int* blocks[2] = {nullptr, nullptr};
   int nblocks[2] = {0, 0};
@@ -92,6 +94,8 @@ struct Level {
   bool eo = true;             // coarsest level: odd-even solve possible (even extents)
   int tr_ks = 0;              // restriction to l+1 on FP16 P: 0 per-rhs kernel, k tensor cores with k-split k
   int pr_batch = 0;           // prolongation from l+1 on FP16 P: 1 = the batch kernel (P read once)
+  int sap_persist = 0;        // coarse levels on FP16 blocks: 1 = a smoother call is one persistent launch
+  unsigned* sap_gcnt = nullptr;   // barrier counter of that launch
   Work<double> w64;
   Work<float> w32;
 };
@@ -178,8 +182,10 @@ struct ddamg_handle {
   bool work_ready[2] = {false, false};   // Work<double>, Work<float> allocated on every level
   // autotuner of the coarse stencil kernels: milliseconds per application at the batch size for
   // [level][candidate] (candidate 0 = CUDA-core kernel, k = tensor cores with k-split k; -1 = not run)
-  double tune_ms[3][DDAMG_MAX_LEVELS][5] = {};   // [DDAMG_TUNE_*][level][candidate]
+  double tune_ms[4][DDAMG_MAX_LEVELS][5] = {};   // [DDAMG_TUNE_*][level][candidate]
   int tc_force = -1;   // DDAMG_OPT_COARSE_TC: -1 autotune, 0 CUDA cores, k >= 1 that split
+  int persist_force = -1;   // DDAMG_OPT_SAP_PERSIST: -1 autotune, 0 per-sweep launches, 1 persistent
+  bool outer_df = false;    // DDAMG_OPT_OUTER_DF: outer D z_j and Gram-Schmidt in double-FP32 arithmetic
   bool sap_schur = false;   // fine-level FP32 SAP block solves on the even-odd Schur complement
   int setup_batch = 4;      // test vectors per batched K-cycle of Alg. 4
   // plain Krylov solver (CGNR) and sigma_min: four FP64 fine vectors per batch column, per-column
@@ -336,6 +342,16 @@ template <typename T> bool half_on(const ddamg_handle* h) { return sizeof(T) == 
 // iterations x { z <- z + M_SAP (b - D z) }: each SAP application is a red then a black sweep
 template <typename T>
 void sap(ddamg_handle* h, Level& L, cplx<T>* z, const cplx<T>* b, int nrhs, int iterations) {
+  if constexpr (sizeof(T) == 4) {
+    if (!L.fine && L.sap_persist && half_on<T>(h) && iterations > 0) {
+      // every sweep of the call in one launch (the tuner checked that it runs, eagerly and in a graph)
+      Prof pr(h, DDAMG_PROF_COARSE_SAP,
+              iterations * (sap_bytes<T>(L, 0, nrhs, true) + sap_bytes<T>(L, 1, nrhs, true)));
+      CK(coarse_sap_persist(z, b, L.c32, L.blocks[0], L.nblocks[0], L.blocks[1], L.nblocks[1], nrhs, L.vlen,
+                            h->p.mr_steps, iterations, L.sap_gcnt, h->st));
+      return;
+    }
+  }
   for (int it = 0; it < iterations; ++it)
     for (int c = 0; c < 2; ++c) {
       if (L.nblocks[c] == 0) continue;
@@ -384,7 +400,7 @@ struct KrylovResult {
 template <typename T, class AOp, class MOp>
 void krylov_host(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cplx<T>* b, int nrhs, int m, double tol,
                  int max_cycles, bool final_residual, bool flexible, AOp A, MOp M, KrylovResult* res,
-                 bool resume = false, const double* tol_rhs = nullptr) {
+                 bool resume = false, const double* tol_rhs = nullptr, bool df = false) {
   // resume: x and ws.r already hold an iterate and its residual b - A x (continued
   // restart cycles); tol_rhs: one relative tolerance per right-hand side
   cudaStream_t st = h->st;
@@ -426,10 +442,22 @@ void krylov_host(ddamg_handle* h, Work<T>& ws, size_t vlen, cplx<T>* x, const cp
       A(w, zj, nullptr);
       {
         Prof pr(h, DDAMG_PROF_OUTER_ORTHO, (double)(2 * (j + 1) + 3) * 2 * vlen * nrhs * 2.0 * sizeof(T));
-        blas_multidot<T>(s.h1, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
-        blas_multiaxpy<T>(w, ws.V, vs, j + 1, s.h1, m + 1, -1.0, vlen, nrhs, rs, st);
-        blas_multidot<T>(s.h2, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
-        blas_multiaxpy<T>(w, ws.V, vs, j + 1, s.h2, m + 1, -1.0, vlen, nrhs, rs, st);
+        bool done = false;
+        if constexpr (sizeof(T) == 8) {
+          if (df) {   // CGS2 in double-FP32 arithmetic on the FP64 basis
+            blas_multidot_df(s.h1, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
+            blas_multiaxpy_df(w, ws.V, vs, j + 1, s.h1, m + 1, -1.0, vlen, nrhs, rs, st);
+            blas_multidot_df(s.h2, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
+            blas_multiaxpy_df(w, ws.V, vs, j + 1, s.h2, m + 1, -1.0, vlen, nrhs, rs, st);
+            done = true;
+          }
+        }
+        if (!done) {
+          blas_multidot<T>(s.h1, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
+          blas_multiaxpy<T>(w, ws.V, vs, j + 1, s.h1, m + 1, -1.0, vlen, nrhs, rs, st);
+          blas_multidot<T>(s.h2, m + 1, ws.V, vs, j + 1, w, vlen, nrhs, rs, st);
+          blas_multiaxpy<T>(w, ws.V, vs, j + 1, s.h2, m + 1, -1.0, vlen, nrhs, rs, st);
+        }
         blas_norm2<T>(s.wnorm, w, vlen, nrhs, rs, st);
         gmres_step(s, j, nrhs, st);
         blas_scale_to<T>(w, w, s.inv, vlen, nrhs, rs, st);
@@ -799,6 +827,7 @@ void build_block_lists(ddamg_handle* h, Level& L) {
     CK(cudaMemcpy(L.bloc, bloc.data(), sizeof(int) * bloc.size(), cudaMemcpyHostToDevice));
     L.c64.bsite = L.c32.bsite = L.bsite;
     L.c64.bloc = L.c32.bloc = L.bloc;
+    L.sap_gcnt = dalloc<unsigned>(h, 1);
   }
   for (int c = 0; c < 2; ++c) {
     L.nblocks[c] = (int)lists[c].size();
@@ -936,6 +965,17 @@ void half_alloc(ddamg_handle* h) {
   }
 }
 
+// double-FP32 copies of the fine links and clover term (allocated on first use)
+void df_refresh(ddamg_handle* h) {
+  Level& F = h->lv[0];
+  if (!F.Udf) {
+    F.Udf = dalloc<cplx<dfl>>(h, (size_t)36 * F.g.V);
+    F.clovdf = dalloc<dfl>(h, (size_t)72 * F.g.V);
+  }
+  double_to_df(reinterpret_cast<dfl*>(F.Udf), reinterpret_cast<const double*>(F.f64.U), (size_t)72 * F.g.V, h->st);
+  double_to_df(F.clovdf, F.f64.clov, (size_t)72 * F.g.V, h->st);
+}
+
 void half_refresh_fine(ddamg_handle* h) {
   Level& F = h->lv[0];
   links_to_half(F.Uh, F.f64.U, (size_t)36 * F.g.V, h->st);
@@ -1047,16 +1087,76 @@ int time_candidates(ddamg_handle* h, double* ms_out, int ncand, Run run) {
   return best;
 }
 
+// Whether the persistent SAP launch of level L runs on this device: one eager call and one call
+// from an instantiated graph (cooperative cluster launches in stream capture), both without error
+// and without a barrier time-out.
+bool persist_works(ddamg_handle* h, Level& L) {
+  Work<float>& w = work<float>(L);
+  const int mr = h->p.mr_steps;
+  sync(h);
+  bool ok = coarse_sap_persist(w.gout, w.gin, L.c32, L.blocks[0], L.nblocks[0], L.blocks[1], L.nblocks[1], 1, L.vlen,
+                               mr, 1, L.sap_gcnt, h->st) == cudaSuccess;
+  cudaGetLastError();
+  sync(h);
+  int e = 0;
+  CK(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    ok = false;
+  }
+  if (!ok) return false;
+  cudaStream_t s = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const cudaError_t e1 = coarse_sap_persist(w.gout, w.gin, L.c32, L.blocks[0], L.nblocks[0], L.blocks[1],
+                                              L.nblocks[1], 1, L.vlen, mr, 1, L.sap_gcnt, s);
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    ok = e1 == cudaSuccess && e2 == cudaSuccess && g != nullptr;
+  }
+  if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+  if (ok) ok = cudaGraphLaunch(ge, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(s);
+  cudaGetLastError();
+  CK(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    ok = false;
+  }
+  return ok;
+}
+
 void tune_kernels(ddamg_handle* h) {
   const int B = h->max_batch;
   for (int l = 0; l < h->L; ++l) {
     Level& L = h->lv[l];
-    for (int t = 0; t < 3; ++t)
+    for (int t = 0; t < 4; ++t)
       for (int k = 0; k < 5; ++k) h->tune_ms[t][l][k] = -1.0;
     L.c32.tc_ks = 0;
     L.tr_ks = 0;
     L.pr_batch = 0;
+    L.sap_persist = 0;
     if (!h->half) continue;
+    // coarse SAP: one launch per colour sweep (0) or one persistent launch per smoother call (1)
+    if (!L.fine && !L.coarsest && h->persist_force != 0 &&
+        coarse_sap_persist_fits(L.c32, L.nblocks[0], L.nblocks[1]) && persist_works(h, L)) {
+      if (h->persist_force == 1) {
+        L.sap_persist = 1;
+      } else {
+        Work<float>& w = work<float>(L);
+        blas_zero<float>(w.gin, L.vlen, B, L.vlen, h->st);
+        blas_zero<float>(w.gout, L.vlen, B, L.vlen, h->st);
+        L.sap_persist = time_candidates(h, h->tune_ms[DDAMG_TUNE_SAP][l], 2, [&](int k, bool) {
+          L.sap_persist = k;
+          sap<float>(h, L, w.gout, w.gin, B, h->p.nu);
+          return true;
+        });
+      }
+    }
     if (h->tc_force >= 0) {
       const int f = h->tc_force;
       if (!L.fine) L.c32.tc_ks = (f > 0 && coarse_tc_fits(L.n, f)) ? f : 0;
@@ -1702,15 +1802,21 @@ namespace {
 void outer_fgmres(ddamg_handle* h, int nb, double tol, int max_cycles, KrylovResult* res, bool resume = false,
                   const double* tol_rhs = nullptr) {
   Level& F = h->lv[0];
+  const bool df = h->outer_df && F.Udf;
   auto A = [&](cplx<double>* o, const cplx<double>* in, const cplx<double>* bb) {
-    apply_D<double>(h, F, o, in, bb, nb);
+    if (df && !bb) {   // D z_j of the Arnoldi step; residuals b - D x stay FP64
+      Prof pr(h, DDAMG_PROF_FINE_DSLASH, (double)F.vlen * 16 * nb * 2 + (double)F.g.V * (36 * 16 + 72 * 8));
+      fine_dslash_df(o, in, nullptr, F.Udf, F.clovdf, F.g, F.f64.bc_t, nb, F.vlen, h->st);
+    } else {
+      apply_D<double>(h, F, o, in, bb, nb);
+    }
   };
   auto M = [&](cplx<double>* z, const cplx<double>* v) {
     if (h->p.precision != 0) precond_outer<float>(h, z, v, nb);
     else precond_outer<double>(h, z, v, nb);
   };
   krylov_host<double>(h, h->outer, F.vlen, h->ox, h->ob, nb, h->p.outer_restart, tol, max_cycles, true, true, A, M,
-                      res, resume, tol_rhs);
+                      res, resume, tol_rhs, df);
 }
 
 // ---------------------------------------------------------------------------
@@ -2085,6 +2191,7 @@ int ddamg_update_gauge(ddamg_handle* h, const double* gauge, int n_inv) {
     import_operator(h, gauge);
     if (h->lv[0].Uh) half_refresh_fine(h);
     if (h->lv[0].mix32) schur_tables(h);
+    if (h->lv[0].Udf) df_refresh(h);
     // P from the current test vectors, coarse operators of the new fine operator
     for (int l = 0; l + 1 < h->L; ++l) rebuild(h, l);
     for (int i = 1; i <= n_inv; ++i) {
@@ -2254,6 +2361,16 @@ int ddamg_set_option(ddamg_handle* h, int option, int value) {
       ensure_work<float>(h);
       tune_kernels(h);
       free_graphs(h);
+    } else if (option == DDAMG_OPT_OUTER_DF) {
+      if (value && !h->lv[0].Udf) df_refresh(h);
+      h->outer_df = value != 0;
+      sync(h);
+    } else if (option == DDAMG_OPT_SAP_PERSIST) {
+      if (value < -1 || value > 1) fail(DDAMG_ERR_ARG, "persistent SAP option must be -1, 0 or 1");
+      h->persist_force = value;
+      ensure_work<float>(h);
+      tune_kernels(h);
+      free_graphs(h);
     } else {
       fail(DDAMG_ERR_ARG, "unknown option");
     }
@@ -2275,6 +2392,10 @@ int ddamg_get_option(ddamg_handle* h, int option, int* value) {
       *value = h->L > 1 ? h->lv[1].c32.tc_ks : 0;
     } else if (option == DDAMG_OPT_SAP_SCHUR) {
       *value = h->sap_schur ? 1 : 0;
+    } else if (option == DDAMG_OPT_SAP_PERSIST) {
+      *value = h->L > 2 ? h->lv[1].sap_persist : 0;
+    } else if (option == DDAMG_OPT_OUTER_DF) {
+      *value = h->outer_df ? 1 : 0;
     } else {
       fail(DDAMG_ERR_ARG, "unknown option");
     }
@@ -2355,12 +2476,17 @@ int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double
 int ddamg_autotune_times(ddamg_handle* h, int kind, int level, double* ms, int* chosen) {
   return guard([&] {
     Level& L = level_of(h, level);
-    if (kind < 0 || kind > 2) fail(DDAMG_ERR_ARG, "unknown autotuned kernel");
+    if (kind < 0 || kind > 3) fail(DDAMG_ERR_ARG, "unknown autotuned kernel");
+    if (kind == DDAMG_TUNE_SAP && (L.fine || L.coarsest)) fail(DDAMG_ERR_ARG, "the coarse SAP runs on levels 1..L-2");
     if (kind == DDAMG_TUNE_COARSE && L.fine) fail(DDAMG_ERR_ARG, "the coarse stencil runs on levels >= 1");
     if (kind != DDAMG_TUNE_COARSE && L.coarsest) fail(DDAMG_ERR_ARG, "no transfer below the coarsest level");
     if (ms)
       for (int k = 0; k < 5; ++k) ms[k] = h->tune_ms[kind][level][k];
-    if (chosen) *chosen = kind == DDAMG_TUNE_COARSE ? L.c32.tc_ks : (kind == DDAMG_TUNE_RESTRICT ? L.tr_ks : L.pr_batch);
+    if (chosen)
+      *chosen = kind == DDAMG_TUNE_COARSE     ? L.c32.tc_ks
+                : kind == DDAMG_TUNE_RESTRICT ? L.tr_ks
+                : kind == DDAMG_TUNE_PROLONG  ? L.pr_batch
+                                              : L.sap_persist;
   });
 }
 
@@ -2378,12 +2504,20 @@ int ddamg_apply(ddamg_handle* h, int level, int precision, const double* in, dou
   return guard([&] {
     Level& L = level_of(h, level);
     if (n < 1 || !in || !out) fail(DDAMG_ERR_ARG, "invalid fields");
-    if (fp32_compute(precision))
+    if (precision == 2) {   // double-FP32 arithmetic on FP64 vectors (fine level)
+      if (!L.fine) fail(DDAMG_ERR_ARG, "double-FP32 application is on the fine level only");
+      if (!L.Udf) df_refresh(h);
+      hook<double>(h, level, in, out, n, false, level, [&](cplx<double>* o, cplx<double>* i) {
+        Prof pr(h, DDAMG_PROF_FINE_DSLASH, (double)L.vlen * 16 * n * 2 + (double)L.g.V * (36 * 16 + 72 * 8));
+        fine_dslash_df(o, i, nullptr, L.Udf, L.clovdf, L.g, L.f64.bc_t, n, L.vlen, h->st);
+      });
+    } else if (fp32_compute(precision)) {
       hook<float>(h, level, in, out, n, false, level,
                   [&](cplx<float>* o, cplx<float>* i) { apply_D<float>(h, L, o, i, nullptr, n); });
-    else
+    } else {
       hook<double>(h, level, in, out, n, false, level,
                    [&](cplx<double>* o, cplx<double>* i) { apply_D<double>(h, L, o, i, nullptr, n); });
+    }
   });
 }
 
