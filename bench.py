@@ -382,20 +382,20 @@ def run_gpu(args, w):
     nb = w["nrhs"]
     ncols = rhs_h.shape[0]
 
-    def params(precision):
+    def params(precision, sap_schur=0):
         return dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
                                        mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
                                        outer_restart=w["outer_restart"], precision=precision, max_rhs=nb,
-                                       seed=w["tv_seed"])
+                                       seed=w["tv_seed"], sap_schur=sap_schur)
 
     stream = torch.cuda.current_stream()
     setup_s = {}
     handles = {}
     mixed_prec = 2 if args.mixed_storage == "fp16" else 1
 
-    def make(name, prec):
+    def make(name, prec, sap_schur=0):
         t0 = time.perf_counter()
-        h = dd.ddamg_setup(U, w["dims"], -1, m0, w["csw"], params(prec), tv)
+        h = dd.ddamg_setup(U, w["dims"], -1, m0, w["csw"], params(prec, sap_schur), tv)
         setup_s[name] = time.perf_counter() - t0
         dd.ddamg_set_stream(h, stream.cuda_stream)
         if args.eager:
@@ -423,7 +423,7 @@ def run_gpu(args, w):
     steps1 = [dd.ddamg_krylov_steps(handles["mixed"], l, 1) for l in range(w["levels"])]
     clocks = clk.stop()
     prof = tm.profiled(handles["mixed"], args.steps)
-    outer_df = None
+    outer_df = sap_schur = None
     if mixed_prec == 2 and not args.only_mixed:
         # the same solves with the outer FGMRES's D z_j and Gram-Schmidt in double-FP32 arithmetic
         # (DDAMG_OPT_OUTER_DF; residuals b - D x stay FP64), timed the same way
@@ -435,6 +435,23 @@ def run_gpu(args, w):
                 if not (s["converged"] and s["true_residual"] <= TOL):
                     raise SystemExit(f"solve (double-FP32 outer) missed the tolerance: {s}")
         tot_df = reduce_max(sum(ms_df), dist, "cuda")
+        # the other reading of the fine SAP block solve (MR on the block's even-odd Schur complement),
+        # on a hierarchy whose setup used that smoother too
+        make("mixed_schur", mixed_prec, sap_schur=1)
+        ms_sc, st_sc, _ = tm.timed(handles["mixed_schur"], args.steps, args.warmup, tag="timed_mixed_schur")
+        handles.pop("mixed_schur").free()
+        for st in st_sc:
+            for s in st:
+                if not (s["converged"] and s["true_residual"] <= TOL):
+                    raise SystemExit(f"solve (Schur SAP) missed the tolerance: {s}")
+        tot_sc = reduce_max(sum(ms_sc), dist, "cuda")
+        sap_schur = {"value": round(whole_job_rate(ncols, args.steps, world, tot_sc / 1e3), 4), "unit": "RHS/s",
+                     "ms_per_step": round(tot_sc / args.steps, 3),
+                     "iterations": [s["iterations"] for st in st_sc[:1] for s in st],
+                     "true_residual": max(s["true_residual"] for st in st_sc for s in st),
+                     "setup_s": round(setup_s["mixed_schur"], 2),
+                     "what": "fine SAP blocks solved by MR on their even-odd Schur complement (params.sap_schur = 1, "
+                             "setup included; the headline uses MR on D_B)"}
         outer_df = {"value": round(whole_job_rate(ncols, args.steps, world, tot_df / 1e3), 4), "unit": "RHS/s",
                     "ms_per_step": round(tot_df / args.steps, 3),
                     "iterations": [s["iterations"] for st in st_df[:1] for s in st],
@@ -518,6 +535,7 @@ def run_gpu(args, w):
         "krylov_steps_per_solve": [round((b - a) / args.steps, 1) for a, b in zip(steps0, steps1)],
         "autotuner": tuned,
         "outer_double_fp32": outer_df,
+        "fine_sap_schur": sap_schur,
     }
     for h in list(handles.values()):
         h.free()
@@ -814,6 +832,9 @@ def serving_run(dd, srv, hids, pools, rate, n_requests, rng):
             rec.append(dict(k=k, n=n, submit=ts - t0, latency=times[1], queue=times[0], rc=rc,
                             res=max(q["true_residual"] for q in st), conv=all(q["converged"] for q in st)))
             i += 1
+            if i % 10 == 0:
+                print(json.dumps({"serving_progress": f"rate {rate}: {i} of {n_requests} requests done",
+                                  "t_s": round(time.perf_counter() - t0, 1)}), file=sys.stderr, flush=True)
         elif not th.is_alive() and i >= len(subs):
             break
         else:
@@ -844,9 +865,18 @@ def serving_run(dd, srv, hids, pools, rate, n_requests, rng):
 def serving_bench(dd, w, lattices, rates, n_requests, max_rhs, seed):
     import synth
     t0 = time.perf_counter()
-    handles = [serving_handle(dd, w, dims, max_rhs, seed + 10 * k) for k, dims in enumerate(lattices)]
+
+    def note(what):   # progress on stderr (the record itself is printed at the end)
+        print(json.dumps({"serving_progress": what, "t_s": round(time.perf_counter() - t0, 1)}), file=sys.stderr,
+              flush=True)
+
+    handles = []
+    for k, dims in enumerate(lattices):
+        handles.append(serving_handle(dd, w, dims, max_rhs, seed + 10 * k))
+        note(f"hierarchy {k} ({'x'.join(str(d) for d in dims[::-1])}) set up")
     t_setup = time.perf_counter() - t0
     pools = [np.ascontiguousarray(synth.random_spinors(12, dims, seed + 500 + k)) for k, dims in enumerate(lattices)]
+    note("right-hand side pools drawn")
     srv = dd.Server()
     hids = [srv.add(h) for h in handles]
     footprint = sum(dd.ddamg_device_bytes(h) for h in handles)
@@ -857,6 +887,7 @@ def serving_bench(dd, w, lattices, rates, n_requests, max_rhs, seed):
             b = np.ascontiguousarray(pools[k][:n])
             x = np.zeros_like(b)
             srv.wait(srv.submit(hids[k], b, n, TOL), x, n)
+        note(f"hierarchy {k} warmed up")
     runs = []
     for r in rates:
         runs.append(serving_run(dd, srv, hids, pools, r, n_requests, rng))
@@ -918,10 +949,11 @@ def scan_fields(dd, torch, stream, w, args):
     x = torch.zeros_like(rhs)
 
     def params(prec, max_rhs=1):
+        # outer_max_cycles caps a solve that stops converging near the edge at 600 iterations
         return dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
                                        mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
                                        outer_restart=w["outer_restart"], precision=prec, max_rhs=max_rhs,
-                                       seed=w["tv_seed"], outer_max_cycles=400)
+                                       seed=w["tv_seed"], outer_max_cycles=args.scan_max_cycles)
 
     def timed(f):
         torch.cuda.synchronize()
@@ -953,15 +985,18 @@ def scan_fields(dd, torch, stream, w, args):
                      "cgnr_over_ddamg_time": round(t_cg / t_amg, 1)})
         print(json.dumps({"mass_scan_row": rows[-1]}), flush=True)
         h.free()
-    # error scaling at the workload's mass
-    h = dd.ddamg_setup(U, w["dims"], -1, m_edge, w["csw"], params(2), None)
+    # error scaling at the mass closest to the edge where the solve converged
+    ok = [r for r in rows if r["ddamg_true_residual"] <= TOL]
+    m_err = m_edge + min(r["m0_minus_edge"] for r in ok) if ok else m_edge + max(SCAN_DELTAS)
+    h = dd.ddamg_setup(U, w["dims"], -1, m_err, w["csw"], params(2), None)
     dd.ddamg_set_stream(h, stream.cuda_stream)
     dd.ddamg_solve(h, rhs, x, 1, TOL)
     err = []
     for tol in SCAN_TOLS:
         st, t_amg = timed(lambda: dd.ddamg_solve(h, rhs, x, 1, tol))
         cg, t_cg = timed(lambda: dd.ddamg_cgnr(h, rhs, x, 1, tol, args.scan_cg_iters))
-        err.append({"fields": w["name"], "tol": tol, "ddamg_iterations": st[0]["iterations"],
+        err.append({"fields": w["name"], "m0_minus_edge": round(m_err - m_edge, 6), "tol": tol,
+                    "ddamg_iterations": st[0]["iterations"],
                     "ddamg_s": round(t_amg, 4), "cgnr_iterations": cg[0]["iterations"], "cgnr_s": round(t_cg, 3),
                     "cgnr_converged": cg[0]["converged"]})
         print(json.dumps({"error_scan_row": err[-1]}), flush=True)
@@ -1078,6 +1113,8 @@ def main():
                     help="mass- and error-scaling sweeps of DD-alpha-AMG against CGNR (one JSON line)")
     ap.add_argument("--scan-cg-iters", type=int, default=30000, help="CGNR iteration cap of the sweeps")
     ap.add_argument("--scan-lanczos", type=int, default=400, help="Lanczos steps of the sigma estimates")
+    ap.add_argument("--scan-max-cycles", type=int, default=60,
+                    help="outer restart cycles (of 10 iterations) a DD-alpha-AMG solve of the sweeps may take")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven inner solves instead of captured graphs (for kernel-level profiling)")
     args = ap.parse_args()

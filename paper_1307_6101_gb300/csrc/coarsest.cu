@@ -121,19 +121,30 @@ struct RegRows {
 template <typename T>
 __device__ __forceinline__ cplx<T> block_row(const Ctx<T>& cx, int site, int k, int i, const cplx<T>* xv) {
   const int n = cx.n;
-  cplx<T> acc = czero<T>();
+  // two accumulators (even and odd columns): two independent chains of fused multiply-adds
+  cplx<T> acc = czero<T>(), acc1 = czero<T>();
   if constexpr (sizeof(T) == 4) {
     if (cx.blkh) {
       const __half2* M = cx.blkh + bidx(site, k, n, i, 0);
-#pragma unroll 8
-      for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), xv[j]);
-      return T(cx.bscale[site]) * acc;
+      int j = 0;
+#pragma unroll 4
+      for (; j + 1 < n; j += 2) {
+        cfma(acc, ld_cplx(M, (size_t)j * n), xv[j]);
+        cfma(acc1, ld_cplx(M, (size_t)(j + 1) * n), xv[j + 1]);
+      }
+      if (j < n) cfma(acc, ld_cplx(M, (size_t)j * n), xv[j]);
+      return T(cx.bscale[site]) * (acc + acc1);
     }
   }
   const cplx<T>* M = cx.blk + bidx(site, k, n, i, 0);
-#pragma unroll 8
-  for (int j = 0; j < n; ++j) cfma(acc, M[(size_t)j * n], xv[j]);
-  return acc;
+  int j = 0;
+#pragma unroll 4
+  for (; j + 1 < n; j += 2) {
+    cfma(acc, M[(size_t)j * n], xv[j]);
+    cfma(acc1, M[(size_t)(j + 1) * n], xv[j + 1]);
+  }
+  if (j < n) cfma(acc, M[(size_t)j * n], xv[j]);
+  return acc + acc1;
 }
 
 // t(own odd) = S^{-1} ( a*bo + c * sum_k D_k(o) v(even nbr_k) ), v read from the owners' array `src`
@@ -272,9 +283,15 @@ __device__ void even_phase(const Ctx<T>& cx, const Smem<T>& s, cg::cluster_group
           if constexpr (NR > 0) {   // the own even site's blocks are in shared memory
             const __half2* M = s.eblk + (size_t)k * n * n + i;
             const cplx<T>* xv = s.xs + k * n;
-#pragma unroll 8
-            for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), xv[j]);
-            acc = T(cx.bscale[site]) * acc;
+            cplx<T> acc1 = czero<T>();
+            int j = 0;
+#pragma unroll 4
+            for (; j + 1 < n; j += 2) {
+              cfma(acc, ld_cplx(M, (size_t)j * n), xv[j]);
+              cfma(acc1, ld_cplx(M, (size_t)(j + 1) * n), xv[j + 1]);
+            }
+            if (j < n) cfma(acc, ld_cplx(M, (size_t)j * n), xv[j]);
+            acc = T(cx.bscale[site]) * (acc + acc1);
           } else {
             acc = block_row(cx, site, k, i, s.xs + k * n);
           }
@@ -449,13 +466,12 @@ __global__ void __launch_bounds__(512, 1) k_coarsest_cluster(Ctx<T> cx0, const c
       // (w'' = w' - V h2 with h2 = V^+ w' and V orthonormal), which saves a reduction
       for (int pass = 0; pass < 2; ++pass) {
         cluster_dots<T>(cx, s, cluster, s.wv, j, pass, len, pass == 1);
-        if (threadIdx.x == 0) {
+        for (int d = threadIdx.x; d <= j; d += blockDim.x) s.htot[d] = pass == 0 ? s.hsum[d] : s.htot[d] + s.hsum[d];
+        if (pass == 1 && threadIdx.x < 32) {   // sum_d |h2_d|^2 by warp 0 (strided partials, shuffle tree)
           T h2 = T(0);
-          for (int d = 0; d <= j; ++d) {
-            s.htot[d] = pass == 0 ? s.hsum[d] : s.htot[d] + s.hsum[d];
-            h2 += cnorm2(s.hsum[d]);
-          }
-          if (pass == 1) s.scal[5] = s.hsum[j + 1].re - h2;
+          for (int d = threadIdx.x; d <= j; d += 32) h2 += cnorm2(s.hsum[d]);
+          for (int off = 16; off >= 1; off >>= 1) h2 += __shfl_xor_sync(0xffffffffu, h2, off);
+          if (threadIdx.x == 0) s.scal[5] = s.hsum[j + 1].re - h2;
         }
         // w -= sum_d h_d V_d: 8 lanes per element, each a strided share of d, summed by shuffles
         // (the loop runs to a multiple of 32 so that whole warps take part in the shuffles)
@@ -476,31 +492,31 @@ __global__ void __launch_bounds__(512, 1) k_coarsest_cluster(Ctx<T> cx0, const c
       const T hn = sqrt(s.scal[5] > T(0) ? s.scal[5] : T(0));
       // Givens update, identical in every CTA
       if (threadIdx.x == 0) {
-        cplx<T> h[MAXM + 1];
-        for (int i = 0; i <= j; ++i) h[i] = s.htot[i];
-        h[j + 1] = cmk<T>(hn, T(0));
+        // the previous rotations applied to the new column, the running entry carried in registers
+        cplx<T> cur = s.htot[0];
         for (int i = 0; i < j; ++i) {
-          const cplx<T> t = s.cs[i] * h[i] + s.sn[i] * h[i + 1];
-          h[i + 1] = s.cs[i] * h[i + 1] - cconj(s.sn[i]) * h[i];
-          h[i] = t;
+          const cplx<T> nx = s.htot[i + 1];
+          const cplx<T> t = s.cs[i] * cur + s.sn[i] * nx;
+          cur = s.cs[i] * nx - cconj(s.sn[i]) * cur;
+          s.H[(size_t)i * m + j] = t;
         }
-        const T aa = sqrt(cnorm2(h[j])), bb = sqrt(cnorm2(h[j + 1]));
+        cplx<T> h[2] = {cur, cmk<T>(hn, T(0))};   // entries j and j + 1
+        const T aa = sqrt(cnorm2(h[0])), bb = sqrt(cnorm2(h[1]));
         const T rr = sqrt(aa * aa + bb * bb);
         T c;
         cplx<T> sg;
         if (rr == T(0)) { c = T(1); sg = czero<T>(); }
-        else if (aa == T(0)) { c = T(0); sg = bb == T(0) ? cmk<T>(T(1), T(0)) : cmk<T>(h[j + 1].re / bb, -h[j + 1].im / bb); }
+        else if (aa == T(0)) { c = T(0); sg = bb == T(0) ? cmk<T>(T(1), T(0)) : cmk<T>(h[1].re / bb, -h[1].im / bb); }
         else {
           c = aa / rr;
-          const cplx<T> ph = cmk<T>(h[j].re / aa, h[j].im / aa);
-          sg = (T(1) / rr) * (ph * cconj(h[j + 1]));
+          const cplx<T> ph = cmk<T>(h[0].re / aa, h[0].im / aa);
+          sg = (T(1) / rr) * (ph * cconj(h[1]));
         }
         s.cs[j] = c;
         s.sn[j] = sg;
-        h[j] = c * h[j] + sg * h[j + 1];
+        s.H[(size_t)j * m + j] = c * h[0] + sg * h[1];
         s.g[j + 1] = T(-1) * (cconj(sg) * s.g[j]);
         s.g[j] = c * s.g[j];
-        for (int i = 0; i <= j; ++i) s.H[(size_t)i * m + j] = h[i];
         const T est = sqrt(cnorm2(s.g[j + 1]));
         const int stop = (est <= target || hn == T(0) || j + 1 == m) ? 1 : 0;
         s.scal[2] = stop ? T(1) : T(0);
