@@ -264,7 +264,8 @@ int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double
  *   reads P once for the batch (1).
  * kind DDAMG_TUNE_SAP (levels 1..L-2): one smoother call (nu SAP applications on the batch) as one
  *   launch per colour sweep (0) and as one persistent launch (1; timed only where it fits and an
- *   eager and a graph-captured trial run without error).
+ *   eager and a graph-captured trial run without error); ms[2] = the clusters of the persistent
+ *   launch's shape the device holds at once (-1: not queried), ms[3] = the clusters it needs.
  * ms[0..4] = milliseconds of one application of the handle's batch size per candidate (-1 where
  * the candidate does not fit or was not timed); *chosen = the candidate in use.  The tuner runs at
  * setup and when DDAMG_OPT_HALF_STORAGE, DDAMG_OPT_COARSE_TC or DDAMG_OPT_SAP_PERSIST is set; its

@@ -1050,7 +1050,8 @@ size_t coarse_sap_persist_smem(const CoarseOp<float>& op) {
   return psap_smem_layout(op.g.vB, op.n, spc, op.sap_nsl, sizeof(__half2), sizeof(float)).total;
 }
 
-bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1) {
+bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1, int* max_clusters) {
+  if (max_clusters) *max_clusters = -1;
   if (op.sap_cls <= 0 || !op.blkh || nb0 <= 0 || nb1 <= 0) return false;
   const int CLS = op.sap_cls, spc = op.g.vB / CLS;
   const int threads = ((9 * spc * op.n + 31) / 32) * 32;
@@ -1079,6 +1080,7 @@ bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1) {
     cudaGetLastError();
     return false;
   }
+  if (max_clusters) *max_clusters = nclusters;
   return nclusters >= (nb0 > nb1 ? nb0 : nb1);
 }
 

@@ -103,7 +103,8 @@ cudaError_t coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op
 // all `iters` SAP applications (red then black sweep) in one cooperative launch of clusters that
 // stay resident (FP16 blocks, FP32 compute); *gcnt: a device counter for the launch's barriers
 size_t coarse_sap_persist_smem(const CoarseOp<float>& op);
-bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1);
+// *max_clusters: clusters of the launch's shape the device holds at once (-1: not queried)
+bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1, int* max_clusters = nullptr);
 cudaError_t coarse_sap_persist(cplx<float>* z, const cplx<float>* b, const CoarseOp<float>& op, const int* blocks0,
                                int nb0, const int* blocks1, int nb1, int nrhs, size_t rstride, int k_mr, int iters,
                                unsigned* gcnt, cudaStream_t st);

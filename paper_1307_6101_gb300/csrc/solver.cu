@@ -311,11 +311,14 @@ void apply_D(ddamg_handle* h, Level& L, cplx<T>* out, const cplx<T>* in, const c
              int sel = SEL_FULL, int mu = 0, int chir = -1) {
   const double cs = 2.0 * sizeof(T);
   const double vec = (double)L.vlen * cs * nrhs * (b ? 3 : 2);
+  // operator data in its storage format: FP16 copies (4 bytes per complex, 2 per real) when in use
+  const bool hf = sizeof(T) == 4 && h->half;
+  const double os = hf ? 4.0 : cs, rs = hf ? 2.0 : (double)sizeof(T);
   if (L.fine) {
-    Prof pr(h, DDAMG_PROF_FINE_DSLASH, vec + (double)L.g.V * (36 * cs + 72 * sizeof(T)));
+    Prof pr(h, DDAMG_PROF_FINE_DSLASH, vec + (double)L.g.V * (36 * os + 72 * rs));
     fine_dslash<T>(out, in, b, fop<T>(L), nrhs, L.vlen, sel, mu, chir, h->st);
   } else {
-    Prof pr(h, DDAMG_PROF_COARSE_APPLY, vec + (double)L.g.V * 9 * L.n * L.n * cs);
+    Prof pr(h, DDAMG_PROF_COARSE_APPLY, vec + (double)L.g.V * 9 * L.n * L.n * os);
     coarse_apply<T>(out, in, b, cop<T>(L), nrhs, L.vlen, sel, mu, chir, h->st);
   }
 }
@@ -343,7 +346,7 @@ template <typename T> bool half_on(const ddamg_handle* h) { return sizeof(T) == 
 template <typename T>
 void sap(ddamg_handle* h, Level& L, cplx<T>* z, const cplx<T>* b, int nrhs, int iterations) {
   if constexpr (sizeof(T) == 4) {
-    if (!L.fine && L.sap_persist && half_on<T>(h) && iterations > 0) {
+    if (!L.fine && L.sap_persist && L.c32.sap_cls > 0 && half_on<T>(h) && iterations > 0) {
       // every sweep of the call in one launch (the tuner checked that it runs, eagerly and in a graph)
       Prof pr(h, DDAMG_PROF_COARSE_SAP,
               iterations * (sap_bytes<T>(L, 0, nrhs, true) + sap_bytes<T>(L, 1, nrhs, true)));
@@ -1141,9 +1144,16 @@ void tune_kernels(ddamg_handle* h) {
     L.pr_batch = 0;
     L.sap_persist = 0;
     if (!h->half) continue;
-    // coarse SAP: one launch per colour sweep (0) or one persistent launch per smoother call (1)
-    if (!L.fine && !L.coarsest && h->persist_force != 0 &&
-        coarse_sap_persist_fits(L.c32, L.nblocks[0], L.nblocks[1]) && persist_works(h, L)) {
+    // coarse SAP: one launch per colour sweep (0) or one persistent launch per smoother call (1);
+    // entries 2 and 3 of the record: clusters the device holds at once, clusters the level needs
+    int maxcl = -1;
+    const bool pfits = !L.fine && !L.coarsest && h->persist_force != 0 &&
+                       coarse_sap_persist_fits(L.c32, L.nblocks[0], L.nblocks[1], &maxcl);
+    if (!L.fine && !L.coarsest) {
+      h->tune_ms[DDAMG_TUNE_SAP][l][2] = maxcl;
+      h->tune_ms[DDAMG_TUNE_SAP][l][3] = L.nblocks[0] > L.nblocks[1] ? L.nblocks[0] : L.nblocks[1];
+    }
+    if (pfits && persist_works(h, L)) {
       if (h->persist_force == 1) {
         L.sap_persist = 1;
       } else {
@@ -2333,6 +2343,10 @@ int ddamg_set_option(ddamg_handle* h, int option, int value) {
             (value && coarse_sap_cluster_plan<double>(L.g, L.n, &cls, &spc, &L.c64.sap_nsl, value)) ? cls : 0;
       }
       cudaGetLastError();
+      if (h->half) {   // the persistent SAP launch follows the cluster plan
+        ensure_work<float>(h);
+        tune_kernels(h);
+      }
       free_graphs(h);
     } else if (option == DDAMG_OPT_HALF_STORAGE) {
       if (value && !h->lv[0].Uh) {
