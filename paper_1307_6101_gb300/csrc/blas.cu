@@ -8,6 +8,7 @@
 #include "kernels.h"
 
 #include <stdexcept>
+#include <unordered_map>
 
 #include <cstdio>
 #include <atomic>
@@ -18,25 +19,31 @@ namespace {
 constexpr int RT = 256;         // threads per reduction CTA
 constexpr int MAXCHUNKS = 512;  // partials per rhs (and per dot in a multidot)
 
-// scratch for the partials, grown on demand (library-owned device memory).  A
-// buffer that was replaced is kept until the library is unloaded, because
-// captured CUDA graphs may still refer to it.
-double* g_partials = nullptr;
-size_t g_partials_cap = 0;
+// scratch for the partials, one buffer per stream (reductions issued on different streams, as by
+// the serving workers of several hierarchies, never share scratch), grown on demand
+// (library-owned device memory).  A buffer that was replaced is kept until the library is
+// unloaded, because captured CUDA graphs may still refer to it.
+struct PartialBuf {
+  double* p = nullptr;
+  size_t cap = 0;
+};
 std::mutex g_partials_mu;
+std::unordered_map<cudaStream_t, PartialBuf> g_partials;
 
-double* partials(size_t count) {
+double* partials(size_t count, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_partials_mu);
-  if (count > g_partials_cap) {
-    size_t cap = count < (1u << 20) ? (1u << 20) : count;
-    if (cudaMalloc(&g_partials, cap * sizeof(double)) != cudaSuccess) {
-      g_partials = nullptr;
-      g_partials_cap = 0;
-      return nullptr;
+  PartialBuf& b = g_partials[st];
+  if (count > b.cap) {
+    const size_t cap = count < (1u << 17) ? (1u << 17) : count;
+    double* p = nullptr;
+    if (cudaMalloc(&p, cap * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      throw std::runtime_error("out of device memory for reduction partials");
     }
-    g_partials_cap = cap;
+    b.p = p;
+    b.cap = cap;
   }
-  return g_partials;
+  return b.p;
 }
 
 int nchunks(size_t len) {
@@ -379,7 +386,7 @@ void blas_multidot(cplx<double>* res, int res_stride, const cplx<T>* V, size_t v
                    size_t len, int nrhs, size_t rstride, cudaStream_t st) {
   if (m <= 0) return;
   const int nc = nchunks(len);
-  double* part = partials((size_t)nrhs * m * nc * 2);
+  double* part = partials((size_t)nrhs * m * nc * 2, st);
   count_launch();
   k_multidot1<T><<<dim3(nc, nrhs), RT, 0, st>>>(part, V, vstride, m, w, len, rstride, nc);
   count_launch();
@@ -390,7 +397,7 @@ void blas_multidot_df(cplx<double>* res, int res_stride, const cplx<double>* V, 
                       const cplx<double>* w, size_t len, int nrhs, size_t rstride, cudaStream_t st) {
   if (m <= 0) return;
   const int nc = nchunks(len);
-  double* part = partials((size_t)nrhs * m * nc * 2);
+  double* part = partials((size_t)nrhs * m * nc * 2, st);
   count_launch();
   k_multidot1_df<<<dim3(nc, nrhs), RT, 0, st>>>(part, V, vstride, m, w, len, rstride, nc);
   count_launch();
@@ -405,7 +412,7 @@ void blas_multiaxpy_df(cplx<double>* y, const cplx<double>* V, size_t vstride, i
   k_multiaxpy_df<<<dim3(div_up(len, 256), nrhs), 256, 0, st>>>(y, V, vstride, m, c, cstride, sign, len, rstride);
 }
 
-void reserve_partials(int nrhs, int m) { partials((size_t)nrhs * (m + 1) * MAXCHUNKS * 2); }
+void reserve_partials(int nrhs, int m, cudaStream_t st) { partials((size_t)nrhs * (m + 1) * MAXCHUNKS * 2, st); }
 
 template <typename T>
 void blas_dot(cplx<double>* res, const cplx<T>* x, const cplx<T>* y, size_t len, int nrhs, size_t rstride,
@@ -416,7 +423,7 @@ void blas_dot(cplx<double>* res, const cplx<T>* x, const cplx<T>* y, size_t len,
 template <typename T>
 void blas_norm2(double* res, const cplx<T>* x, size_t len, int nrhs, size_t rstride, cudaStream_t st) {
   const int nc = nchunks(len);
-  double* part = partials((size_t)nrhs * nc);
+  double* part = partials((size_t)nrhs * nc, st);
   count_launch();
   k_norm1<T><<<dim3(nc, nrhs), RT, 0, st>>>(part, x, len, rstride, nc);
   count_launch();

@@ -204,7 +204,7 @@ void blas_norm2(double* res, const cplx<T>* x, size_t len, int nrhs, size_t rstr
 template <typename T>
 void blas_multidot(cplx<double>* res, int res_stride, const cplx<T>* V, size_t vstride, int m, const cplx<T>* w,
                    size_t len, int nrhs, size_t rstride, cudaStream_t st);
-void reserve_partials(int nrhs, int m);
+void reserve_partials(int nrhs, int m, cudaStream_t st);   // per stream
 // a[i] = 1 / a[i] (0 where a[i] = 0)
 void blas_recip(double* a, int n, cudaStream_t st);
 // y += sign * sum_i c[rhs*cstride + i] V_i

@@ -1437,6 +1437,17 @@ void ensure_work(ddamg_handle* h) {
   ready = true;
 }
 
+// reduction scratch of a stream this handle launches on, sized for its largest reductions
+// (reserved before any capture, so that captured graphs never see it grow)
+void reserve_stream_partials(ddamg_handle* h, cudaStream_t st) {
+  int mx = h->p.outer_restart;
+  if (h->p.coarse_restart > mx) mx = h->p.coarse_restart;
+  int bmax = h->max_batch > h->work_batch ? h->max_batch : h->work_batch;
+  for (auto& L : h->lv)
+    if (L.N > bmax) bmax = L.N;
+  reserve_partials(bmax, mx + 1, st);
+}
+
 void allocate_hierarchy(ddamg_handle* h) {
   kry_prepare();
   const int B = h->max_batch;
@@ -1527,12 +1538,9 @@ void allocate_hierarchy(ddamg_handle* h) {
   h->ox = dalloc<cplx<double>>(h, h->lv[0].vlen * B);
   h->pin32 = dalloc<cplx<float>>(h, h->lv[0].vlen * B);
   h->pout32 = dalloc<cplx<float>>(h, h->lv[0].vlen * B);
-  int mx = h->p.outer_restart;
-  if (h->p.coarse_restart > mx) mx = h->p.coarse_restart;
-  int bmax = B;
-  for (auto& L : h->lv)
-    if (L.N > bmax) bmax = L.N;
-  reserve_partials(bmax, mx + 1);
+  reserve_stream_partials(h, h->st);
+  for (int d = 0; d < 12; ++d)
+    if (h->cap.s[d]) reserve_stream_partials(h, h->cap.s[d]);
 }
 
 void validate(const ddamg_params& p) {
@@ -2217,6 +2225,7 @@ int ddamg_set_stream(ddamg_handle* h, void* stream) {
   return guard([&] {
     sync(h);
     h->st = stream ? static_cast<cudaStream_t>(stream) : h->own;
+    reserve_stream_partials(h, h->st);
   });
 }
 

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import synth
-from cases import Case, SMALL2, THREE
+from cases import Case, SMALL2, THREE, BIG3, SAP4
 
 pytestmark = pytest.mark.gpu
 
@@ -102,6 +102,36 @@ def test_two_hierarchies_overlap_and_threads_submit(dd):
         assert len(out[k]) == 3
         for rc, st in out[k]:
             assert rc == dd.DDAMG_OK and all(s["converged"] and s["true_residual"] <= 1e-10 for s in st)
+
+
+def test_concurrent_hierarchies_give_the_bits_of_solo_solves(dd):
+    """Two hierarchies whose worker threads run at the same time on their own streams: every
+    request gives the same bits as when its hierarchy serves it alone (reductions of different
+    streams use separate scratch)."""
+    c1 = Case(**BIG3, n_inv=1, eta_passes=2, max_rhs=3, m0=-0.35, nu=2)
+    c2 = Case(**SAP4, n_inv=1, eta_passes=2, max_rhs=3)
+    hs = [c1.gpu(2), c2.gpu(2)]
+    cs = [c1, c2]
+    reqs = [[np.ascontiguousarray(synth.random_spinors(n, c.dims, 90 + 10 * k + j)) for j, n in enumerate((3, 2, 3, 1))]
+            for k, c in enumerate(cs)]
+    srv = dd.Server()
+    ids = [srv.add(h) for h in hs]
+    alone = [[], []]
+    for k in (0, 1):
+        for b in reqs[k]:
+            x = np.zeros_like(b)
+            st, t, rc = srv.wait(srv.submit(ids[k], b, len(b), 1e-10), x, len(b))
+            assert rc == dd.DDAMG_OK and all(q["converged"] for q in st)
+            alone[k].append(x)
+    # all requests of both hierarchies at once
+    rids = [[srv.submit(ids[k], b, len(b), 1e-10) for b in reqs[k]] for k in (0, 1)]
+    for k in (0, 1):
+        for rid, b, xa in zip(rids[k], reqs[k], alone[k]):
+            x = np.zeros_like(b)
+            st, t, rc = srv.wait(rid, x, len(b))
+            assert rc == dd.DDAMG_OK
+            assert np.array_equal(x, xa)
+    srv.free()
 
 
 def test_admission_by_footprint_and_estimate(dd):
