@@ -9,7 +9,9 @@ has not been built (``python -m paper_1307_6101_gb300.build`` or
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
+import weakref
 import os
 
 import numpy as np
@@ -392,6 +394,19 @@ def ddamg_estimate_bytes(dims, params):
     return n.value
 
 
+_live_servers = weakref.WeakSet()
+
+
+@atexit.register
+def _stop_servers():
+    # worker threads must stop before the interpreter (and the CUDA runtime) shut down
+    for s in list(_live_servers):
+        try:
+            s.free()
+        except Exception:
+            pass
+
+
 class Server:
     """Continuous-batching request loop over resident hierarchies (ddamg_server_*)."""
 
@@ -399,6 +414,7 @@ class Server:
         self.raw = C.c_void_p()
         _check(lib().ddamg_server_create(C.c_size_t(int(hbm_budget)), C.byref(self.raw)))
         self._handles = []
+        _live_servers.add(self)
 
     def add(self, h):
         hid = C.c_int()

@@ -1861,6 +1861,7 @@ struct SrvRequest {
   std::vector<ddamg_stats> st;
   int remaining = 0;
   int status = 1;             // 1: pending; 0: done; < 0: DDAMG_ERR_* of the request
+  std::string err;            // the worker's error message of a failed request
   double t_submit = 0, t_start = 0, t_done = 0;
 };
 
@@ -1892,9 +1893,13 @@ struct ddamg_server {
 
 namespace {
 
-void finish_column(ddamg_server* S, SrvRequest* rq, int col, const ddamg_stats& st, int err) {
+void finish_column(ddamg_server* S, SrvRequest* rq, int col, const ddamg_stats& st, int err,
+                   const std::string& msg = std::string()) {
   rq->st[col] = st;
-  if (err) rq->status = err;
+  if (err) {
+    rq->status = err;
+    if (rq->err.empty()) rq->err = msg;
+  }
   if (--rq->remaining == 0) {
     if (rq->status == 1) {
       bool ok = true;
@@ -1989,8 +1994,8 @@ void server_worker(ddamg_server* S, SrvHier* H) {
       sync(h);
     });
     std::lock_guard<std::mutex> lk(S->mu);
-    if (rc != DDAMG_OK) {   // the batch failed: every column in it fails
-      for (int q = 0; q < na; ++q) finish_column(S, H->slots[q].rq, H->slots[q].col, ddamg_stats{}, rc);
+    if (rc != DDAMG_OK) {   // the batch failed: every column in it fails, with the worker's message
+      for (int q = 0; q < na; ++q) finish_column(S, H->slots[q].rq, H->slots[q].col, ddamg_stats{}, rc, g_err);
       H->active = 0;
       continue;
     }
@@ -2815,9 +2820,12 @@ int ddamg_server_wait(ddamg_server* S, long long id, double* x, ddamg_stats* per
     times[2] = rq->t_done - rq->t_start;     // time in the batch
   }
   const int rc = rq->status;
+  const std::string msg = rq->err;
   S->reqs.erase(it);
   delete rq;
-  if (rc != DDAMG_OK) g_err = rc == DDAMG_ERR_NOCONV ? "outer FGMRES did not reach the tolerance" : "request failed";
+  if (rc != DDAMG_OK)
+    g_err = rc == DDAMG_ERR_NOCONV ? std::string("outer FGMRES did not reach the tolerance")
+                                   : "request failed: " + (msg.empty() ? std::string("(no message)") : msg);
   return rc;
 }
 

@@ -115,23 +115,25 @@ def test_concurrent_hierarchies_give_the_bits_of_solo_solves(dd):
     reqs = [[np.ascontiguousarray(synth.random_spinors(n, c.dims, 90 + 10 * k + j)) for j, n in enumerate((3, 2, 3, 1))]
             for k, c in enumerate(cs)]
     srv = dd.Server()
-    ids = [srv.add(h) for h in hs]
-    alone = [[], []]
-    for k in (0, 1):
-        for b in reqs[k]:
-            x = np.zeros_like(b)
-            st, t, rc = srv.wait(srv.submit(ids[k], b, len(b), 1e-10), x, len(b))
-            assert rc == dd.DDAMG_OK and all(q["converged"] for q in st)
-            alone[k].append(x)
-    # all requests of both hierarchies at once
-    rids = [[srv.submit(ids[k], b, len(b), 1e-10) for b in reqs[k]] for k in (0, 1)]
-    for k in (0, 1):
-        for rid, b, xa in zip(rids[k], reqs[k], alone[k]):
-            x = np.zeros_like(b)
-            st, t, rc = srv.wait(rid, x, len(b))
-            assert rc == dd.DDAMG_OK
-            assert np.array_equal(x, xa)
-    srv.free()
+    try:
+        ids = [srv.add(h) for h in hs]
+        alone = [[], []]
+        for k in (0, 1):
+            for b in reqs[k]:
+                x = np.zeros_like(b)
+                st, t, rc = srv.wait(srv.submit(ids[k], b, len(b), 1e-10), x, len(b))
+                assert rc == dd.DDAMG_OK and all(q["converged"] for q in st)
+                alone[k].append(x)
+        # all requests of both hierarchies at once
+        rids = [[srv.submit(ids[k], b, len(b), 1e-10) for b in reqs[k]] for k in (0, 1)]
+        for k in (0, 1):
+            for rid, b, xa in zip(rids[k], reqs[k], alone[k]):
+                x = np.zeros_like(b)
+                st, t, rc = srv.wait(rid, x, len(b))
+                assert rc == dd.DDAMG_OK
+                assert np.array_equal(x, xa)
+    finally:
+        srv.free()
 
 
 def test_admission_by_footprint_and_estimate(dd):
