@@ -995,9 +995,16 @@ int coarse_sap_slots(const Geom& g) {
   return best;
 }
 
+// The dynamic shared-memory limit of a kernel is a process-wide attribute: it is raised to the
+// device maximum (not to this plan's size), so that a hierarchy set up later with smaller blocks
+// cannot lower it below what an earlier hierarchy's launches use.
 template <typename T, typename BS>
 void sap_cluster_attrs(size_t smem, int CLS) {
-  cudaFuncSetAttribute(k_coarse_sap_cluster<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaFuncSetAttribute(k_coarse_sap_cluster<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    cudaFuncSetAttribute(k_coarse_sap_cluster<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
   if (CLS > 8) cudaFuncSetAttribute(k_coarse_sap_cluster<T, BS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
@@ -1058,7 +1065,7 @@ bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1, int* m
   const size_t sm = coarse_sap_persist_smem(op);
   if (threads > 768 || sm > 227 * 1024) return false;
   if (cudaFuncSetAttribute(k_coarse_sap_persist<float, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm) != cudaSuccess ||
+                           227 * 1024) != cudaSuccess ||   // process-wide limit: the device maximum
       (CLS > 8 && cudaFuncSetAttribute(k_coarse_sap_persist<float, __half2>,
                                        cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
     cudaGetLastError();

@@ -588,9 +588,15 @@ size_t smem_bytes(int m, int nep, int nop, int n, int CL, bool resident) {
 
 namespace dd {
 
+// the dynamic shared-memory limit is a process-wide attribute of the kernel: raised to the device
+// maximum, so that hierarchies set up later with a smaller coarsest level do not lower it
 template <typename T, int NR>
 bool cluster_fits(int CL, int threads, size_t sm) {
-  cudaFuncSetAttribute(k_coarsest_cluster<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (cudaFuncSetAttribute(k_coarsest_cluster<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    cudaFuncSetAttribute(k_coarsest_cluster<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  }
   if (CL > 8) cudaFuncSetAttribute(k_coarsest_cluster<T, NR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];

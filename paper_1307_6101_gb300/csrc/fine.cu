@@ -1487,11 +1487,10 @@ void launch_sap_b4(cplx<float>* z, const cplx<float>* b, const LS* U, const CS* 
   constexpr int VB = 256;
   const size_t sm = (size_t)VB * (36 * sizeof(LS) + 2 * ClovRows<CS>::per_chir * sizeof(CS) + 12 * sizeof(cplx<float>)) +
                     16 + 2 * 24 * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_fine_sap_b4<LS, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
+  });
   count_launch();
   k_fine_sap_b4<LS, CS><<<nblocks, VB, sm, st>>>(z, b, U, clov, op.g, op.bc_t, rstride, nrhs, blocks, k_mr, op.err,
                                                  shift);
