@@ -357,7 +357,7 @@ def autotune_record(dd, h, levels):
     """The autotuner's timings (ms per candidate) and choices of a handle, per kernel class and level."""
     out = {}
     for kind, lv, nc in (("coarse", range(1, levels), 5), ("restrict", range(levels - 1), 5),
-                         ("prolong", range(levels - 1), 2), ("sap", range(1, levels - 1), 4)):
+                         ("prolong", range(levels - 1), 2), ("sap", range(1, levels - 1), 5)):
         for l in lv:
             ms, ch = dd.ddamg_autotune_times(h, kind, l)
             # ms per candidate (None: the candidate does not fit here or was not timed)

@@ -187,8 +187,10 @@ enum {
                                      autotuned per level between one cluster launch per colour
                                      sweep (0) and one persistent cooperative launch for all
                                      sweeps of a smoother call (1), where all clusters of the
-                                     level fit on the device at once; 0/1 force the choice (1
-                                     only where it fits).  Same arithmetic either way. */
+                                     level fit on the device at once (one or, if one does not
+                                     fit, two SAP blocks of each colour per cluster); 0/1 force
+                                     the choice (1 only where it fits); 2: persistent with two
+                                     blocks per cluster.  Same arithmetic in every form. */
   DDAMG_OPT_OUTER_DF = 7          /* 0 (default) / 1: the outer FGMRES forms D z_j and its CGS2
                                      Gram-Schmidt products in double-FP32 arithmetic (Dekker
                                      pairs, about 48 significand bits) on its FP64 vectors; the
@@ -265,7 +267,8 @@ int ddamg_residual_norm_noalloc(ddamg_handle* h, const double* rhs, const double
  * kind DDAMG_TUNE_SAP (levels 1..L-2): one smoother call (nu SAP applications on the batch) as one
  *   launch per colour sweep (0) and as one persistent launch (1; timed only where it fits and an
  *   eager and a graph-captured trial run without error); ms[2] = the clusters of the persistent
- *   launch's shape the device holds at once (-1: not queried), ms[3] = the clusters it needs.
+ *   launch's shape the device holds at once (-1: not queried), ms[3] = the clusters it needs,
+ *   ms[4] = the SAP blocks of each colour per cluster (1 or 2; 0: no shape fits).
  * ms[0..4] = milliseconds of one application of the handle's batch size per candidate (-1 where
  * the candidate does not fit or was not timed); *chosen = the candidate in use.  The tuner runs at
  * setup and when DDAMG_OPT_HALF_STORAGE, DDAMG_OPT_COARSE_TC or DDAMG_OPT_SAP_PERSIST is set; its

@@ -577,21 +577,22 @@ __device__ bool persist_grid_sync(unsigned* cnt, unsigned target, cg::cluster_gr
 struct PSapSmem {
   size_t rfull, pbuf, part, red, sh, slot, flag, bar, total;
 };
-DD_HD PSapSmem psap_smem_layout(int vB, int n, int spc, int nsl, size_t bs, size_t ts) {
+// nbpc SAP blocks of each colour per cluster; rows = nbpc * spc * n per CTA
+DD_HD PSapSmem psap_smem_layout(int vB, int n, int spc, int nsl, int nbpc, size_t bs, size_t ts) {
   PSapSmem L;
-  size_t o = al16((size_t)2 * spc * nsl * n * n * bs);
+  size_t o = al16((size_t)2 * nbpc * spc * nsl * n * n * bs);
   L.rfull = o;
-  o = al16(o + (size_t)vB * n * 2 * ts);
+  o = al16(o + (size_t)nbpc * vB * n * 2 * ts);
   L.pbuf = o;
-  o = al16(o + (size_t)2 * vB * n * 2 * ts);
+  o = al16(o + (size_t)2 * nbpc * vB * n * 2 * ts);
   L.part = o;
-  o = al16(o + (size_t)9 * spc * n * 2 * ts);
+  o = al16(o + (size_t)9 * nbpc * spc * n * 2 * ts);
   L.red = o;
-  o = al16(o + (size_t)2 * 16 * 4 * ts);
+  o = al16(o + (size_t)2 * nbpc * 16 * 4 * ts);
   L.sh = o;
-  o = al16(o + (size_t)(32 * 3 + 4) * ts);
+  o = al16(o + (size_t)(32 * 3 * nbpc + 4) * ts);
   L.slot = o;
-  o = al16(o + (size_t)2 * spc * 9 * sizeof(int));
+  o = al16(o + (size_t)2 * nbpc * spc * 9 * sizeof(int));
   L.flag = o;
   o = al16(o + 16);
   L.bar = o;
@@ -599,7 +600,10 @@ DD_HD PSapSmem psap_smem_layout(int vB, int n, int spc, int nsl, size_t bs, size
   return L;
 }
 
-template <typename T, typename BS>
+// NB SAP blocks of each colour per cluster (1 or 2): CTA rank q owns sites q*spc .. q*spc+spc-1
+// of each of them; the rows of block j are rows j*spc*n .. (j+1)*spc*n-1 of the CTA, with their
+// own residual copy, MR direction and dot products.
+template <typename T, typename BS, int NB>
 __global__ void __launch_bounds__(768, 1) k_coarse_sap_persist(
     cplx<T>* __restrict__ z, const cplx<T>* __restrict__ bsrc, const BS* __restrict__ blk,
     const float* __restrict__ bscale, Geom g, int n, size_t rstride, int nrhs, const int* __restrict__ blocks0,
@@ -612,24 +616,30 @@ __global__ void __launch_bounds__(768, 1) k_coarse_sap_persist(
   const int cid = blockIdx.x / CLS;
   const unsigned ncl = gridDim.x / CLS;
   const int vB = g.vB;
-  const int rows = spc * n;
+  const int rb = spc * n;          // rows of one block in this CTA
+  const int rows = NB * rb;
   const size_t nn = (size_t)n * n;
-  const PSapSmem L = psap_smem_layout(vB, n, spc, nsl, sizeof(BS), sizeof(T));
-  BS* stage = reinterpret_cast<BS*>(smem_raw);                                // [2][spc][nsl][n][n]
-  cplx<T>* rfull = reinterpret_cast<cplx<T>*>(smem_raw + L.rfull);            // [vB*n]
-  cplx<T>* pbuf = reinterpret_cast<cplx<T>*>(smem_raw + L.pbuf);              // [2][vB*n]
+  const PSapSmem L = psap_smem_layout(vB, n, spc, nsl, NB, sizeof(BS), sizeof(T));
+  BS* stage = reinterpret_cast<BS*>(smem_raw);                                // [2][NB*spc][nsl][n][n]
+  cplx<T>* rfull = reinterpret_cast<cplx<T>*>(smem_raw + L.rfull);            // [NB][vB*n]
+  cplx<T>* pbuf = reinterpret_cast<cplx<T>*>(smem_raw + L.pbuf);              // [2][NB][vB*n]
   cplx<T>* part = reinterpret_cast<cplx<T>*>(smem_raw + L.part);              // [9][rows]
-  T* red = reinterpret_cast<T*>(smem_raw + L.red);                            // [2][16][4]
-  T* sh = reinterpret_cast<T*>(smem_raw + L.sh);                              // [32][3] + 3
-  int* slot = reinterpret_cast<int*>(smem_raw + L.slot);                      // [2][spc][9]
+  T* red = reinterpret_cast<T*>(smem_raw + L.red);                            // [2][NB][16][4]
+  T* sh = reinterpret_cast<T*>(smem_raw + L.sh);                              // [32][3*NB] + 4
+  int* slot = reinterpret_cast<int*>(smem_raw + L.slot);                      // [2][NB*spc][9]
   int* flag = reinterpret_cast<int*>(smem_raw + L.flag);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + L.bar);
-  const int blk0 = cid < nb0 ? blocks0[cid] : -1, blk1 = cid < nb1 ? blocks1[cid] : -1;
-  // slots of the staged blocks of both colours (k order: self, forward mu, backward mu)
-  if (threadIdx.x < 2 * spc) {
-    const int c = threadIdx.x / spc, s = threadIdx.x - c * spc;
-    int* sl9 = slot + (c * spc + s) * 9;
-    const int bc = c ? blk1 : blk0;
+  // block of colour c, slot j of this cluster (-1: none)
+  auto block_of = [&](int c, int j) -> int {
+    const int q = cid * NB + j;
+    return c ? (q < nb1 ? blocks1[q] : -1) : (q < nb0 ? blocks0[q] : -1);
+  };
+  // slots of the staged blocks (k order: self, forward mu, backward mu)
+  if (threadIdx.x < 2 * NB * spc) {
+    const int c = threadIdx.x / (NB * spc), js = threadIdx.x - c * NB * spc;
+    const int j = js / spc, s = js - j * spc;
+    int* sl9 = slot + (c * NB * spc + js) * 9;
+    const int bc = block_of(c, j);
     if (bc >= 0) {
       int co[4];
       geom_coords(g, bsite[(size_t)bc * vB + rank * spc + s], co);
@@ -646,15 +656,16 @@ __global__ void __launch_bounds__(768, 1) k_coarse_sap_persist(
   __syncthreads();
   if (threadIdx.x < 32) {
     int cnt = 0;
-    for (int e = 0; e < 2 * spc * 9; ++e) cnt += slot[e] >= 0 ? 1 : 0;
+    for (int e = 0; e < 2 * NB * spc * 9; ++e) cnt += slot[e] >= 0 ? 1 : 0;
     if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (unsigned)(cnt * nn * sizeof(BS)));
     __syncwarp();
-    for (int e = threadIdx.x; e < 2 * spc * 9; e += 32) {
-      const int cs = e / 9, k = e % 9, q = slot[e];   // cs = c * spc + s
+    for (int e = threadIdx.x; e < 2 * NB * spc * 9; e += 32) {
+      const int cjs = e / 9, k = e % 9, q = slot[e];   // cjs = (c * NB + j) * spc + s
       if (q >= 0) {
-        const int c = cs / spc, s = cs - c * spc;
-        const int site = bsite[(size_t)(c ? blk1 : blk0) * vB + rank * spc + s];
-        bulk_g2s(stage + ((size_t)cs * nsl + q) * nn, blk + ((size_t)site * 9 + k) * nn,
+        const int c = cjs / (NB * spc), js = cjs - c * NB * spc;
+        const int j = js / spc, s = js - j * spc;
+        const int site = bsite[(size_t)block_of(c, j) * vB + rank * spc + s];
+        bulk_g2s(stage + ((size_t)cjs * nsl + q) * nn, blk + ((size_t)site * 9 + k) * nn,
                  (unsigned)(nn * sizeof(BS)), bar);
       }
     }
@@ -663,20 +674,26 @@ __global__ void __launch_bounds__(768, 1) k_coarse_sap_persist(
   if (!ok && threadIdx.x == 0) atomicExch(err, 2);
   const int k = threadIdx.x / rows;
   const int rl = threadIdx.x - k * rows;
-  const int sl = rl / n, i = rl - (rl / n) * n;
+  const int jb = rl / rb, rj = rl - jb * rb;      // block of the row, row inside that block's share
+  const int sl = rj / n, i = rj - (rj / n) * n;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  // the rows this thread owns as a residual row (threadIdx.x < rows): block jr, local row rr
+  const int jr = threadIdx.x / rb, rr = threadIdx.x - (threadIdx.x / rb) * rb;
   unsigned round = 0;
   bool alive = true;
   for (int it = 0; it < iters && alive; ++it)
     for (int c = 0; c < 2 && alive; ++c) {
-      const int bc = c ? blk1 : blk0;
-      if (bc >= 0) {   // uniform over the cluster
-        const int* own = bsite + (size_t)bc * vB + rank * spc;
-        const int site = own[sl];
-        const T sc = bscale ? T(bscale[site]) : T(1);
-        int q = -1, nb = site, nloc = 0;
-        if (k < 9) {
-          q = slot[(c * spc + sl) * 9 + k];
+      const int bk = k < 9 ? block_of(c, jb) : -1;            // this thread's (row, k) block
+      const int bres = threadIdx.x < rows ? block_of(c, jr) : -1;   // this thread's residual row's block
+      const bool any = block_of(c, 0) >= 0;                    // uniform over the cluster
+      if (any) {
+        int site = 0, q = -1, nb = 0, nloc = 0;
+        T sc = T(1);
+        if (bk >= 0) {
+          site = bsite[(size_t)bk * vB + rank * spc + sl];
+          sc = bscale ? T(bscale[site]) : T(1);
+          nb = site;
+          q = slot[((c * NB + jb) * spc + sl) * 9 + k];
           if (k > 0) {
             int co[4];
             geom_coords(g, site, co);
@@ -684,42 +701,46 @@ __global__ void __launch_bounds__(768, 1) k_coarse_sap_persist(
           }
           nloc = q >= 0 ? bloc[nb] : 0;
         }
-        const BS* Ms = stage + ((size_t)(c * spc + sl) * nsl + (q >= 0 ? q : 0)) * nn + i;
+        const BS* Ms = stage + ((size_t)((c * NB + jb) * spc + sl) * nsl + (q >= 0 ? q : 0)) * nn + i;
+        const int* ownr = bres >= 0 ? bsite + (size_t)bres * vB + rank * spc : nullptr;
         for (int rh = 0; rh < nrhs; ++rh) {
           const size_t ro = (size_t)rh * rstride;
           // rho = b - D z on the own rows (z through L2)
-          cplx<T> acc = czero<T>();
           if (k < 9) {
-            const cplx<T>* v = z + ro + (size_t)nb * n;
-            if (q < 0) {
-              const BS* M = blk + ((size_t)site * 9 + k) * nn + i;
+            cplx<T> acc = czero<T>();
+            if (bk >= 0) {
+              const cplx<T>* v = z + ro + (size_t)nb * n;
+              if (q < 0) {
+                const BS* M = blk + ((size_t)site * 9 + k) * nn + i;
 #pragma unroll 8
-              for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), ldz(v + j));
-            } else {
+                for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(M, (size_t)j * n), ldz(v + j));
+              } else {
 #pragma unroll 8
-              for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(Ms, (size_t)j * n), ldz(v + j));
+                for (int j = 0; j < n; ++j) cfma(acc, ld_cplx(Ms, (size_t)j * n), ldz(v + j));
+              }
             }
             part[k * rows + rl] = sc * acc;
           }
           __syncthreads();
           cplx<T> r = czero<T>(), xs = czero<T>();
-          if (threadIdx.x < rows) {
+          if (bres >= 0) {
             cplx<T> d = czero<T>();
 #pragma unroll
             for (int m = 0; m < 9; ++m) d = d + part[m * rows + threadIdx.x];
-            r = bsrc[ro + (size_t)own[threadIdx.x / n] * n + threadIdx.x % n] - d;
-            for (int cc = 0; cc < CLS; ++cc) cluster.map_shared_rank(rfull, cc)[(size_t)rank * rows + threadIdx.x] = r;
+            r = bsrc[ro + (size_t)ownr[rr / n] * n + rr % n] - d;
+            for (int cc = 0; cc < CLS; ++cc)
+              cluster.map_shared_rank(rfull + (size_t)jr * vB * n, cc)[(size_t)rank * rb + rr] = r;
           }
           cluster.sync();
           for (int mr = 0; mr < k_mr; ++mr) {
             const int buf = mr & 1;
-            cplx<T>* pb = pbuf + (size_t)buf * vB * n;
-            T* rb = red + buf * 64;
+            cplx<T>* pb = pbuf + (size_t)buf * NB * vB * n;
+            T* rbf = red + buf * NB * 64;
             // p = D_B r on the own rows, from the staged blocks and the local copy of r
             if (k < 9) {
               cplx<T> a = czero<T>();
-              if (q >= 0) {
-                const cplx<T>* v = rfull + (size_t)nloc * n;
+              if (bk >= 0 && q >= 0) {
+                const cplx<T>* v = rfull + (size_t)jb * vB * n + (size_t)nloc * n;
 #pragma unroll 8
                 for (int j = 0; j < n; ++j) cfma(a, ld_cplx(Ms, (size_t)j * n), v[j]);
               }
@@ -727,52 +748,78 @@ __global__ void __launch_bounds__(768, 1) k_coarse_sap_persist(
             }
             __syncthreads();
             cplx<T> p = czero<T>();
-            T nre = T(0), nim = T(0), den = T(0);
-            if (threadIdx.x < rows) {
+            T v3[3 * NB];
+#pragma unroll
+            for (int e = 0; e < 3 * NB; ++e) v3[e] = T(0);
+            if (bres >= 0) {
 #pragma unroll
               for (int m = 0; m < 9; ++m) p = p + part[m * rows + threadIdx.x];
               const cplx<T> t = cdotc(p, r);
-              nre = t.re;
-              nim = t.im;
-              den = cnorm2(p);
-              for (int cc = 0; cc < CLS; ++cc) cluster.map_shared_rank(pb, cc)[(size_t)rank * rows + threadIdx.x] = p;
+#pragma unroll
+              for (int jj = 0; jj < NB; ++jj)
+                if (jj == jr) {
+                  v3[3 * jj] = t.re;
+                  v3[3 * jj + 1] = t.im;
+                  v3[3 * jj + 2] = cnorm2(p);
+                }
+              for (int cc = 0; cc < CLS; ++cc)
+                cluster.map_shared_rank(pb + (size_t)jr * vB * n, cc)[(size_t)rank * rb + rr] = p;
             }
-            for (int off = 16; off >= 1; off >>= 1) {
-              nre += __shfl_xor_sync(0xffffffffu, nre, off);
-              nim += __shfl_xor_sync(0xffffffffu, nim, off);
-              den += __shfl_xor_sync(0xffffffffu, den, off);
-            }
-            if (lane == 0) { sh[3 * warp] = nre; sh[3 * warp + 1] = nim; sh[3 * warp + 2] = den; }
+#pragma unroll
+            for (int e = 0; e < 3 * NB; ++e)
+              for (int off = 16; off >= 1; off >>= 1) v3[e] += __shfl_xor_sync(0xffffffffu, v3[e], off);
+            if (lane == 0)
+#pragma unroll
+              for (int e = 0; e < 3 * NB; ++e) sh[3 * NB * warp + e] = v3[e];
             __syncthreads();
             if (warp == 0) {   // warp partials summed by a shuffle tree (fixed order), sent to every CTA
-              T a = lane < nw ? sh[3 * lane] : T(0);
-              T bb = lane < nw ? sh[3 * lane + 1] : T(0);
-              T cc = lane < nw ? sh[3 * lane + 2] : T(0);
-              for (int off = 16; off >= 1; off >>= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, off);
-                bb += __shfl_xor_sync(0xffffffffu, bb, off);
-                cc += __shfl_xor_sync(0xffffffffu, cc, off);
+#pragma unroll
+              for (int e = 0; e < 3 * NB; ++e) {
+                T a = lane < nw ? sh[3 * NB * lane + e] : T(0);
+                for (int off = 16; off >= 1; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+                v3[e] = a;
               }
-              if (lane < CLS) {
-                T* dst = cluster.map_shared_rank(rb, lane) + rank * 4;
-                dst[0] = a;
-                dst[1] = bb;
-                dst[2] = cc;
-              }
+              if (lane < CLS)
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj) {
+                  T* dst = cluster.map_shared_rank(rbf + jj * 64, lane) + rank * 4;
+                  dst[0] = v3[3 * jj];
+                  dst[1] = v3[3 * jj + 1];
+                  dst[2] = v3[3 * jj + 2];
+                }
             }
             cluster.sync();
-            T a = T(0), bb = T(0), cc = T(0);
-            for (int q2 = 0; q2 < CLS; ++q2) { a += rb[q2 * 4]; bb += rb[q2 * 4 + 1]; cc += rb[q2 * 4 + 2]; }
-            const cplx<T> alpha = cc > T(0) ? cmk<T>(a / cc, bb / cc) : czero<T>();
-            if (threadIdx.x < rows) {
-              cfma(xs, alpha, r);
-              r = r - alpha * p;
+            cplx<T> alpha[NB];
+#pragma unroll
+            for (int jj = 0; jj < NB; ++jj) {
+              T a = T(0), bb = T(0), cc = T(0);
+              for (int q2 = 0; q2 < CLS; ++q2) {
+                a += rbf[jj * 64 + q2 * 4];
+                bb += rbf[jj * 64 + q2 * 4 + 1];
+                cc += rbf[jj * 64 + q2 * 4 + 2];
+              }
+              alpha[jj] = cc > T(0) ? cmk<T>(a / cc, bb / cc) : czero<T>();
             }
-            for (int e = threadIdx.x; e < vB * n; e += blockDim.x) rfull[e] = rfull[e] - alpha * pb[e];
+            if (bres >= 0) {
+              cplx<T> al = alpha[0];
+#pragma unroll
+              for (int jj = 1; jj < NB; ++jj)
+                if (jj == jr) al = alpha[jj];
+              cfma(xs, al, r);
+              r = r - al * p;
+            }
+            for (int e = threadIdx.x; e < NB * vB * n; e += blockDim.x) {
+              const int jj = e / (vB * n);
+              cplx<T> al = alpha[0];
+#pragma unroll
+              for (int j2 = 1; j2 < NB; ++j2)
+                if (j2 == jj) al = alpha[j2];
+              rfull[e] = rfull[e] - al * pb[e];
+            }
             __syncthreads();
           }
-          if (ok && threadIdx.x < rows) {
-            const size_t a = ro + (size_t)own[threadIdx.x / n] * n + threadIdx.x % n;
+          if (ok && bres >= 0) {
+            const size_t a = ro + (size_t)ownr[rr / n] * n + rr % n;
             z[a] = ldz(z + a) + xs;
           }
           // every CTA is done with its copies of r, p and the partials before the next right-hand
@@ -1049,55 +1096,76 @@ int coarse_sap_cluster_plan(const Geom& g, int n, int* CLS_out, int* spc_out, in
   return 0;
 }
 
-// Persistent SAP on FP16 blocks (FP32 compute): the launch's shared memory, and whether all
-// clusters (max(nb0, nb1) of op.sap_cls CTAs) can be resident at once on this device.
-size_t coarse_sap_persist_smem(const CoarseOp<float>& op) {
+// Persistent SAP on FP16 blocks (FP32 compute): the launch's shared memory and threads for nbpc
+// SAP blocks of each colour per cluster, and whether all clusters (max(nb0, nb1) / nbpc of
+// op.sap_cls CTAs) can be resident at once on this device.
+size_t coarse_sap_persist_smem(const CoarseOp<float>& op, int nbpc) {
   if (op.sap_cls <= 0) return 0;
   const int spc = op.g.vB / op.sap_cls;
-  return psap_smem_layout(op.g.vB, op.n, spc, op.sap_nsl, sizeof(__half2), sizeof(float)).total;
+  return psap_smem_layout(op.g.vB, op.n, spc, op.sap_nsl, nbpc, sizeof(__half2), sizeof(float)).total;
 }
 
-bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1, int* max_clusters) {
+namespace {
+int persist_threads(const CoarseOp<float>& op, int nbpc) {
+  const int spc = op.g.vB / op.sap_cls;
+  return ((9 * nbpc * spc * op.n + 31) / 32) * 32;
+}
+const void* persist_kernel(int nbpc) {
+  return nbpc == 2 ? (const void*)k_coarse_sap_persist<float, __half2, 2>
+                   : (const void*)k_coarse_sap_persist<float, __half2, 1>;
+}
+}  // namespace
+
+bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1, int* max_clusters, int* nbpc_out,
+                             int min_nbpc) {
   if (max_clusters) *max_clusters = -1;
+  if (nbpc_out) *nbpc_out = 0;
   if (op.sap_cls <= 0 || !op.blkh || nb0 <= 0 || nb1 <= 0) return false;
-  const int CLS = op.sap_cls, spc = op.g.vB / CLS;
-  const int threads = ((9 * spc * op.n + 31) / 32) * 32;
-  const size_t sm = coarse_sap_persist_smem(op);
-  if (threads > 768 || sm > 227 * 1024) return false;
-  if (cudaFuncSetAttribute(k_coarse_sap_persist<float, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           227 * 1024) != cudaSuccess ||   // process-wide limit: the device maximum
-      (CLS > 8 && cudaFuncSetAttribute(k_coarse_sap_persist<float, __half2>,
-                                       cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
-    cudaGetLastError();
-    return false;
+  const int CLS = op.sap_cls;
+  const int nb = nb0 > nb1 ? nb0 : nb1;
+  for (int nbpc = min_nbpc < 1 ? 1 : min_nbpc; nbpc <= 2; ++nbpc) {
+    const int threads = persist_threads(op, nbpc);
+    const size_t sm = coarse_sap_persist_smem(op, nbpc);
+    if (threads > 768 || sm > 227 * 1024) continue;
+    const void* fn = persist_kernel(nbpc);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024) != cudaSuccess ||   // process-wide limit: the device maximum
+        (CLS > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CLS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CLS, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (max_clusters) *max_clusters = nclusters;
+    if (nclusters >= (nb + nbpc - 1) / nbpc) {
+      if (nbpc_out) *nbpc_out = nbpc;
+      return true;
+    }
   }
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CLS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(CLS, 1, 1);
-  cfg.blockDim = dim3(threads, 1, 1);
-  cfg.dynamicSmemBytes = sm;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_sap_persist<float, __half2>, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (max_clusters) *max_clusters = nclusters;
-  return nclusters >= (nb0 > nb1 ? nb0 : nb1);
+  return false;
 }
 
 cudaError_t coarse_sap_persist(cplx<float>* z, const cplx<float>* b, const CoarseOp<float>& op, const int* blocks0,
                                int nb0, const int* blocks1, int nb1, int nrhs, size_t rstride, int k_mr, int iters,
-                               unsigned* gcnt, cudaStream_t st) {
+                               int nbpc, unsigned* gcnt, cudaStream_t st) {
   if (nrhs <= 0 || iters <= 0) return cudaSuccess;
-  if (op.sap_cls <= 0 || !op.blkh || nb0 <= 0 || nb1 <= 0) return cudaErrorInvalidValue;
+  if (op.sap_cls <= 0 || !op.blkh || nb0 <= 0 || nb1 <= 0 || nbpc < 1 || nbpc > 2) return cudaErrorInvalidValue;
   const int CLS = op.sap_cls, spc = op.g.vB / CLS;
-  const int threads = ((9 * spc * op.n + 31) / 32) * 32;
+  const int nb = nb0 > nb1 ? nb0 : nb1;
   cudaError_t e = cudaMemsetAsync(gcnt, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -1108,14 +1176,18 @@ cudaError_t coarse_sap_persist(cplx<float>* z, const cplx<float>* b, const Coars
   attr[0].val.clusterDim.z = 1;
   attr[1].id = cudaLaunchAttributeCooperative;   // all clusters co-resident (they wait on one another)
   attr[1].val.cooperative = 1;
-  cfg.gridDim = dim3((nb0 > nb1 ? nb0 : nb1) * CLS, 1, 1);
-  cfg.blockDim = dim3(threads, 1, 1);
-  cfg.dynamicSmemBytes = coarse_sap_persist_smem(op);
+  cfg.gridDim = dim3(((nb + nbpc - 1) / nbpc) * CLS, 1, 1);
+  cfg.blockDim = dim3(persist_threads(op, nbpc), 1, 1);
+  cfg.dynamicSmemBytes = coarse_sap_persist_smem(op, nbpc);
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
   count_launch();
-  return cudaLaunchKernelEx(&cfg, k_coarse_sap_persist<float, __half2>, z, b, op.blkh, op.bscale, op.g, op.n,
+  if (nbpc == 2)
+    return cudaLaunchKernelEx(&cfg, k_coarse_sap_persist<float, __half2, 2>, z, b, op.blkh, op.bscale, op.g, op.n,
+                              rstride, nrhs, blocks0, nb0, blocks1, nb1, k_mr, spc, op.sap_nsl, iters, op.err,
+                              op.bsite, op.bloc, gcnt);
+  return cudaLaunchKernelEx(&cfg, k_coarse_sap_persist<float, __half2, 1>, z, b, op.blkh, op.bscale, op.g, op.n,
                             rstride, nrhs, blocks0, nb0, blocks1, nb1, k_mr, spc, op.sap_nsl, iters, op.err, op.bsite,
                             op.bloc, gcnt);
 }

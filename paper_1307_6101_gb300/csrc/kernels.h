@@ -101,13 +101,16 @@ template <typename T>
 cudaError_t coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op, const int* blocks, int nblocks,
                       int nrhs, size_t rstride, int k_mr, cudaStream_t st);
 // all `iters` SAP applications (red then black sweep) in one cooperative launch of clusters that
-// stay resident (FP16 blocks, FP32 compute); *gcnt: a device counter for the launch's barriers
-size_t coarse_sap_persist_smem(const CoarseOp<float>& op);
-// *max_clusters: clusters of the launch's shape the device holds at once (-1: not queried)
-bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1, int* max_clusters = nullptr);
+// stay resident (FP16 blocks, FP32 compute), nbpc (1 or 2) SAP blocks of each colour per cluster;
+// *gcnt: a device counter for the launch's barriers.  fits: the smallest nbpc for which all
+// clusters are resident at once (*max_clusters: clusters of that shape the device holds, -1: not
+// queried)
+size_t coarse_sap_persist_smem(const CoarseOp<float>& op, int nbpc);
+bool coarse_sap_persist_fits(const CoarseOp<float>& op, int nb0, int nb1, int* max_clusters = nullptr,
+                             int* nbpc = nullptr, int min_nbpc = 1);
 cudaError_t coarse_sap_persist(cplx<float>* z, const cplx<float>* b, const CoarseOp<float>& op, const int* blocks0,
                                int nb0, const int* blocks1, int nb1, int nrhs, size_t rstride, int k_mr, int iters,
-                               unsigned* gcnt, cudaStream_t st);
+                               int nbpc, unsigned* gcnt, cudaStream_t st);
 void coarse_selfinv_build(cplx<double>* inv, const cplx<double>* blk, int V, int n, int* err, cudaStream_t st);
 template <typename T>
 // prefer: a cluster size (2, 4, 8, 16) to try first, anything else for the default order

@@ -95,6 +95,7 @@ struct Level {
   int tr_ks = 0;              // restriction to l+1 on FP16 P: 0 per-rhs kernel, k tensor cores with k-split k
   int pr_batch = 0;           // prolongation from l+1 on FP16 P: 1 = the batch kernel (P read once)
   int sap_persist = 0;        // coarse levels on FP16 blocks: 1 = a smoother call is one persistent launch
+  int sap_nbpc = 0;           // SAP blocks of each colour per cluster of that launch (1 or 2)
   unsigned* sap_gcnt = nullptr;   // barrier counter of that launch
   Work<double> w64;
   Work<float> w32;
@@ -184,7 +185,8 @@ struct ddamg_handle {
   // [level][candidate] (candidate 0 = CUDA-core kernel, k = tensor cores with k-split k; -1 = not run)
   double tune_ms[4][DDAMG_MAX_LEVELS][5] = {};   // [DDAMG_TUNE_*][level][candidate]
   int tc_force = -1;   // DDAMG_OPT_COARSE_TC: -1 autotune, 0 CUDA cores, k >= 1 that split
-  int persist_force = -1;   // DDAMG_OPT_SAP_PERSIST: -1 autotune, 0 per-sweep launches, 1 persistent
+  int persist_force = -1;   // DDAMG_OPT_SAP_PERSIST: -1 autotune, 0 per-sweep launches, 1 persistent,
+                            // 2 persistent with two SAP blocks of each colour per cluster
   bool outer_df = false;    // DDAMG_OPT_OUTER_DF: outer D z_j and Gram-Schmidt in double-FP32 arithmetic
   bool sap_schur = false;   // fine-level FP32 SAP block solves on the even-odd Schur complement
   int setup_batch = 4;      // test vectors per batched K-cycle of Alg. 4
@@ -351,7 +353,7 @@ void sap(ddamg_handle* h, Level& L, cplx<T>* z, const cplx<T>* b, int nrhs, int 
       Prof pr(h, DDAMG_PROF_COARSE_SAP,
               iterations * (sap_bytes<T>(L, 0, nrhs, true) + sap_bytes<T>(L, 1, nrhs, true)));
       CK(coarse_sap_persist(z, b, L.c32, L.blocks[0], L.nblocks[0], L.blocks[1], L.nblocks[1], nrhs, L.vlen,
-                            h->p.mr_steps, iterations, L.sap_gcnt, h->st));
+                            h->p.mr_steps, iterations, L.sap_nbpc, L.sap_gcnt, h->st));
       return;
     }
   }
@@ -1098,7 +1100,7 @@ bool persist_works(ddamg_handle* h, Level& L) {
   const int mr = h->p.mr_steps;
   sync(h);
   bool ok = coarse_sap_persist(w.gout, w.gin, L.c32, L.blocks[0], L.nblocks[0], L.blocks[1], L.nblocks[1], 1, L.vlen,
-                               mr, 1, L.sap_gcnt, h->st) == cudaSuccess;
+                               mr, 1, L.sap_nbpc, L.sap_gcnt, h->st) == cudaSuccess;
   cudaGetLastError();
   sync(h);
   int e = 0;
@@ -1115,7 +1117,7 @@ bool persist_works(ddamg_handle* h, Level& L) {
   ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   if (ok) {
     const cudaError_t e1 = coarse_sap_persist(w.gout, w.gin, L.c32, L.blocks[0], L.nblocks[0], L.blocks[1],
-                                              L.nblocks[1], 1, L.vlen, mr, 1, L.sap_gcnt, s);
+                                              L.nblocks[1], 1, L.vlen, mr, 1, L.sap_nbpc, L.sap_gcnt, s);
     const cudaError_t e2 = cudaStreamEndCapture(s, &g);
     ok = e1 == cudaSuccess && e2 == cudaSuccess && g != nullptr;
   }
@@ -1145,16 +1147,21 @@ void tune_kernels(ddamg_handle* h) {
     L.sap_persist = 0;
     if (!h->half) continue;
     // coarse SAP: one launch per colour sweep (0) or one persistent launch per smoother call (1);
-    // entries 2 and 3 of the record: clusters the device holds at once, clusters the level needs
+    // entries 2..4 of the record: clusters of the persistent launch's shape the device holds at
+    // once, clusters the level needs, SAP blocks of each colour per cluster (0: no shape fits)
     int maxcl = -1;
+    L.sap_nbpc = 0;
     const bool pfits = !L.fine && !L.coarsest && h->persist_force != 0 &&
-                       coarse_sap_persist_fits(L.c32, L.nblocks[0], L.nblocks[1], &maxcl);
+                       coarse_sap_persist_fits(L.c32, L.nblocks[0], L.nblocks[1], &maxcl, &L.sap_nbpc,
+                                               h->persist_force == 2 ? 2 : 1);
     if (!L.fine && !L.coarsest) {
+      const int nb = L.nblocks[0] > L.nblocks[1] ? L.nblocks[0] : L.nblocks[1];
       h->tune_ms[DDAMG_TUNE_SAP][l][2] = maxcl;
-      h->tune_ms[DDAMG_TUNE_SAP][l][3] = L.nblocks[0] > L.nblocks[1] ? L.nblocks[0] : L.nblocks[1];
+      h->tune_ms[DDAMG_TUNE_SAP][l][3] = pfits ? (nb + L.sap_nbpc - 1) / L.sap_nbpc : nb;
+      h->tune_ms[DDAMG_TUNE_SAP][l][4] = L.sap_nbpc;
     }
     if (pfits && persist_works(h, L)) {
-      if (h->persist_force == 1) {
+      if (h->persist_force >= 1) {
         L.sap_persist = 1;
       } else {
         Work<float>& w = work<float>(L);
@@ -2394,7 +2401,7 @@ int ddamg_set_option(ddamg_handle* h, int option, int value) {
       h->outer_df = value != 0;
       sync(h);
     } else if (option == DDAMG_OPT_SAP_PERSIST) {
-      if (value < -1 || value > 1) fail(DDAMG_ERR_ARG, "persistent SAP option must be -1, 0 or 1");
+      if (value < -1 || value > 2) fail(DDAMG_ERR_ARG, "persistent SAP option must be -1, 0, 1 or 2");
       h->persist_force = value;
       ensure_work<float>(h);
       tune_kernels(h);

@@ -28,8 +28,9 @@ def _fields(n, dims, ndof, seed):
     return np.ascontiguousarray(synth.random_fields(n, dims, ndof, seed))
 
 
-@pytest.mark.parametrize("spec", [THREE, BIG3])
-def test_persistent_sap_matches_per_sweep_launches_and_oracle(dd, spec):
+@pytest.mark.parametrize("spec,form", [(THREE, 1), (BIG3, 1), (BIG3, 2)])
+def test_persistent_sap_matches_per_sweep_launches_and_oracle(dd, spec, form):
+    """form 1: one SAP block of each colour per cluster; form 2: two (half the clusters)."""
     from oracle.precision import stencil_half
     from oracle.smoother import SAP
     c = Case(**spec)
@@ -42,16 +43,18 @@ def test_persistent_sap_matches_per_sweep_launches_and_oracle(dd, spec):
     b = _fields(3, dims, n, 61)
     z0 = _fields(3, dims, n, 62)
     out = {}
-    for persist in (0, 1):
+    for persist in (0, form):
         dd.ddamg_set_option(h, dd.DDAMG_OPT_SAP_PERSIST, persist)
-        assert dd.ddamg_get_option(h, dd.DDAMG_OPT_SAP_PERSIST) == persist
+        assert dd.ddamg_get_option(h, dd.DDAMG_OPT_SAP_PERSIST) == (1 if persist else 0)
+        if persist:
+            assert dd.ddamg_autotune_times(h, "sap", 1)[0][4] == form   # blocks per cluster in use
         z = z0.copy()
         dd.ddamg_smooth(h, 1, 1, b, z, 3, 3)
         out[persist] = z
-    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[form])
     sap = SAP(stencil_half(o.levels[1].op), c.sap[1], c.mr_steps)
     zref = np.stack([sap.smooth(b[i], z0[i], 3) for i in range(3)])
-    assert rel(out[1], zref) <= TOL32, rel(out[1], zref)
+    assert rel(out[form], zref) <= TOL32, rel(out[form], zref)
 
 
 def test_autotuner_records_the_sap_candidates(dd):
@@ -70,12 +73,12 @@ def test_solve_with_persistent_sap_is_bitwise_the_same(dd):
     h = c.gpu(2, U)
     b = np.ascontiguousarray(synth.random_spinors(2, c.dims, 5))
     xs, its = [], []
-    for persist in (0, 1):
+    for persist in (0, 1, 2):
         dd.ddamg_set_option(h, dd.DDAMG_OPT_SAP_PERSIST, persist)
         x = np.zeros_like(b)
         st = dd.ddamg_solve(h, b, x, 2, 1e-10)
         assert all(s["converged"] for s in st)
         xs.append(x)
         its.append([s["iterations"] for s in st])
-    assert its[0] == its[1]
-    assert np.array_equal(xs[0], xs[1])
+    assert its[0] == its[1] == its[2]
+    assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[0], xs[2])
