@@ -359,6 +359,9 @@ __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restri
                                      int nsl, int* err, const int* __restrict__ bsite,
                                      const int* __restrict__ bloc) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  // the next sweep (launched with programmatic stream serialization) may stage its blocks while
+  // this one runs; it waits for this grid before reading z or b
+  pdl_launch_dependents();
   cg::cluster_group cluster = cg::this_cluster();
   const int CLS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -420,6 +423,7 @@ __global__ void __launch_bounds__(768, 2) k_coarse_sap_cluster(cplx<T>* __restri
   const BS* Ms = stage + ((size_t)sl * nsl + (q >= 0 ? q : 0)) * nn + i;   // staged row i (column-major)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   int ok = 1;
+  pdl_wait();   // the previous kernel's z and b are complete from here on
   // the right-hand sides of the batch one after the other, on the blocks staged once
   for (int rh = 0; rh < nrhs; ++rh) {
     const size_t ro = (size_t)rh * rstride;
@@ -1200,18 +1204,21 @@ cudaError_t coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op
     const int threads = ((9 * spc * op.n + 31) / 32) * 32;
     const bool half = sizeof(T) == 4 && op.blkh;
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = op.sap_cls;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    // consecutive colour sweeps: the next one stages its blocks while this one finishes
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.gridDim = dim3(nblocks * op.sap_cls, 1, 1);   // one cluster per SAP block loops over the batch
     cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes =
         sap_smem_layout(op.g.vB, op.n, spc, op.sap_nsl, half ? sizeof(__half2) : sizeof(cplx<T>), sizeof(T)).total;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     count_launch();
     cudaError_t e;
     if constexpr (sizeof(T) == 4) {

@@ -675,6 +675,9 @@ __global__ void __launch_bounds__(256, 2) k_fine_sap_b4(cplx<float>* __restrict_
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(Rs + 12 * VB);
   float* scratch = reinterpret_cast<float*>(bar + 2);             // [2][8 warps][3]
   const int loc = threadIdx.x, lane = loc & 31, warp = loc >> 5;
+  // the next sweep (launched with programmatic stream serialization) may start staging its
+  // links and clover term while this one runs; it waits for this grid before reading z or b
+  pdl_launch_dependents();
   const int blk = blocks[blockIdx.x];
   const int V = g.V;
   const int x = blk * VB + loc;
@@ -683,23 +686,23 @@ __global__ void __launch_bounds__(256, 2) k_fine_sap_b4(cplx<float>* __restrict_
     mbar_init(&bar[1], 1);
   }
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 0) {   // links and clover term: never written by the kernels this launch may overlap
     if (lane == 0) {
       mbar_arrive_expect_tx(&bar[0], (unsigned)(VB * (36 * sizeof(LS) + CR * sizeof(CS))));
       mbar_arrive_expect_tx(&bar[1], (unsigned)(12 * VB * sizeof(C)));
     }
     __syncwarp();
-    for (int cpy = lane; cpy < 36 + CR + 12; cpy += 32) {
+    for (int cpy = lane; cpy < 36 + CR; cpy += 32) {
       if (cpy < 36)
         bulk_g2s(Ls + (size_t)cpy * VB, U + (size_t)cpy * V + (size_t)blk * VB, VB * sizeof(LS), &bar[0]);
-      else if (cpy < 36 + CR)
+      else
         bulk_g2s(Cs + (size_t)(cpy - 36) * VB, clov + (size_t)(cpy - 36) * V + (size_t)blk * VB, VB * sizeof(CS),
                  &bar[0]);
-      else
-        bulk_g2s(Rs + (size_t)(cpy - 36 - CR) * VB, z + (size_t)(cpy - 36 - CR) * V + (size_t)blk * VB,
-                 VB * sizeof(C), &bar[1]);
     }
   }
+  pdl_wait();   // the previous kernel's z and b are complete from here on
+  if (warp == 0 && lane < 12)
+    bulk_g2s(Rs + (size_t)lane * VB, z + (size_t)lane * V + (size_t)blk * VB, VB * sizeof(C), &bar[1]);
   // site geometry (overlaps the copies): local coordinates l_mu = (loc / st_mu) % 4,
   // st = (64, 16, 4, 1); a hop is internal if it stays in the block, or wraps
   // around a lattice direction of extent 4 that the block spans
@@ -1492,8 +1495,21 @@ void launch_sap_b4(cplx<float>* z, const cplx<float>* b, const LS* U, const CS* 
     cudaFuncSetAttribute(k_fine_sap_b4<LS, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   });
   count_launch();
-  k_fine_sap_b4<LS, CS><<<nblocks, VB, sm, st>>>(z, b, U, clov, op.g, op.bc_t, rstride, nrhs, blocks, k_mr, op.err,
-                                                 shift);
+  // programmatic stream serialization: consecutive colour sweeps overlap the next sweep's operator
+  // staging with the end of the previous one (the kernel waits for the previous grid before it
+  // reads z or b)
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3(nblocks, 1, 1);
+  cfg.blockDim = dim3(VB, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cfg.attrs = pdl;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_fine_sap_b4<LS, CS>, z, b, U, clov, op.g, op.bc_t, rstride, nrhs, blocks, k_mr, op.err,
+                     shift);
 }
 
 template <typename LS, typename CS>

@@ -42,3 +42,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     if (clock64() - t0 > 4000000000LL) return false;
   return true;
 }
+// Programmatic dependent launch: let the next kernel of the stream (launched with programmatic
+// stream serialization) start its independent prologue early, and, in that kernel, wait for the
+// previous grid to complete (and its memory to be visible) before touching what it wrote.  Both
+// are no-ops for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
