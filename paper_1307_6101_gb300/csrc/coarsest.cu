@@ -462,24 +462,16 @@ __global__ void __launch_bounds__(512, 1) k_coarsest_cluster(Ctx<T> cx0, const c
       odd_phase<T, NR>(cx, s, cluster, vj, T(0), T(1), orow);
       cluster.sync();
       even_phase<T, NR>(cx, s, cluster, vj, s.wv, T(0), T(1), T(-1));
-      // Classical Gram-Schmidt with a second pass when the first one cancels: each pass also sums
-      // the norm of the vector it projects, and the norm after the pass is ||w||^2 - sum_d |h_d|^2
-      // (V orthonormal).  The second pass runs only when the first removed more than about half
-      // of ||w||^2 (||w'|| < 0.7 ||w||, the criterion of Daniel, Gragg, Kaufman and Stewart 1976);
-      // otherwise w' is orthogonal to working accuracy and one cluster reduction is saved.  The
-      // decision is made on sums that every CTA forms in the same order, so all CTAs take it alike.
+      // CGS2; the second pass also sums ||w'||^2, and ||w''||^2 = ||w'||^2 - sum_d |h2_d|^2
+      // (w'' = w' - V h2 with h2 = V^+ w' and V orthonormal), which saves a reduction
       for (int pass = 0; pass < 2; ++pass) {
-        cluster_dots<T>(cx, s, cluster, s.wv, j, pass, len, true);
+        cluster_dots<T>(cx, s, cluster, s.wv, j, pass, len, pass == 1);
         for (int d = threadIdx.x; d <= j; d += blockDim.x) s.htot[d] = pass == 0 ? s.hsum[d] : s.htot[d] + s.hsum[d];
-        if (threadIdx.x < 32) {   // sum_d |h_d|^2 by warp 0 (strided partials, shuffle tree)
+        if (pass == 1 && threadIdx.x < 32) {   // sum_d |h2_d|^2 by warp 0 (strided partials, shuffle tree)
           T h2 = T(0);
           for (int d = threadIdx.x; d <= j; d += 32) h2 += cnorm2(s.hsum[d]);
           for (int off = 16; off >= 1; off >>= 1) h2 += __shfl_xor_sync(0xffffffffu, h2, off);
-          if (threadIdx.x == 0) {
-            const T rest = s.hsum[j + 1].re - h2;
-            s.scal[5] = rest;
-            s.scal[6] = (pass == 0 && rest < T(0.49) * s.hsum[j + 1].re) ? T(1) : T(0);
-          }
+          if (threadIdx.x == 0) s.scal[5] = s.hsum[j + 1].re - h2;
         }
         // w -= sum_d h_d V_d: 8 lanes per element, each a strided share of d, summed by shuffles
         // (the loop runs to a multiple of 32 so that whole warps take part in the shuffles)
@@ -496,7 +488,6 @@ __global__ void __launch_bounds__(512, 1) k_coarsest_cluster(Ctx<T> cx0, const c
           if (q == 0 && e < len) s.wv[e] = s.wv[e] - acc;
         }
         __syncthreads();
-        if (s.scal[6] == T(0)) break;   // no second pass (uniform in the cluster)
       }
       const T hn = sqrt(s.scal[5] > T(0) ? s.scal[5] : T(0));
       // Givens update, identical in every CTA
