@@ -1220,22 +1220,27 @@ cudaError_t coarse_sap_sweep(cplx<T>* z, const cplx<T>* b, const CoarseOp<T>& op
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     count_launch();
-    cudaError_t e;
-    if constexpr (sizeof(T) == 4) {
-      if (half)
-        e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<float, __half2>, z, b, op.blkh, op.bscale, op.g, op.n,
-                               rstride, nrhs, blocks, k_mr, spc, op.sap_nsl, op.err, op.bsite, op.bloc);
-      else
+    // with programmatic serialization first, then (if the attribute is refused) without it
+    for (int na = 2; na >= 1; --na) {
+      cfg.numAttrs = na;
+      cudaError_t e;
+      if constexpr (sizeof(T) == 4) {
+        if (half)
+          e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<float, __half2>, z, b, op.blkh, op.bscale, op.g, op.n,
+                                 rstride, nrhs, blocks, k_mr, spc, op.sap_nsl, op.err, op.bsite, op.bloc);
+        else
+          e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
+                                 (const float*)nullptr, op.g, op.n, rstride, nrhs, blocks, k_mr, spc, op.sap_nsl,
+                                 op.err, op.bsite, op.bloc);
+      } else {
         e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
                                (const float*)nullptr, op.g, op.n, rstride, nrhs, blocks, k_mr, spc, op.sap_nsl,
                                op.err, op.bsite, op.bloc);
-    } else {
-      e = cudaLaunchKernelEx(&cfg, k_coarse_sap_cluster<T, cplx<T>>, z, b, (const cplx<T>*)op.blk,
-                             (const float*)nullptr, op.g, op.n, rstride, nrhs, blocks, k_mr, spc, op.sap_nsl,
-                             op.err, op.bsite, op.bloc);
+      }
+      if (e == cudaSuccess) return cudaSuccess;
+      cudaGetLastError();
     }
-    if (e == cudaSuccess) return cudaSuccess;
-    cudaGetLastError();   // cluster launch refused: run the one-CTA-per-block kernel instead
+    // cluster launch refused: run the one-CTA-per-block kernel instead
   }
   // one CTA per SAP block with rpt rows per thread: the fewest of 1, 4, 8 for which
   // the CTA stays within the threads the kernel's registers allow

@@ -1508,8 +1508,12 @@ void launch_sap_b4(cplx<float>* z, const cplx<float>* b, const LS* U, const CS* 
   cfg.stream = st;
   cfg.attrs = pdl;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_fine_sap_b4<LS, CS>, z, b, U, clov, op.g, op.bc_t, rstride, nrhs, blocks, k_mr, op.err,
-                     shift);
+  if (cudaLaunchKernelEx(&cfg, k_fine_sap_b4<LS, CS>, z, b, U, clov, op.g, op.bc_t, rstride, nrhs, blocks, k_mr,
+                         op.err, shift) != cudaSuccess) {
+    cudaGetLastError();   // the attribute refused here: the same sweep as a plain launch
+    k_fine_sap_b4<LS, CS><<<nblocks, VB, sm, st>>>(z, b, U, clov, op.g, op.bc_t, rstride, nrhs, blocks, k_mr, op.err,
+                                                   shift);
+  }
 }
 
 template <typename LS, typename CS>
