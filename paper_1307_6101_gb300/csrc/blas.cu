@@ -92,35 +92,15 @@ __global__ void k_multidot1(double* __restrict__ part, const cplx<T>* __restrict
   size_t lo, hi;
   chunk_range(len, nc, chunk, lo, hi);
   const cplx<T>* pw = w + (size_t)rhs * rstride;
-  const size_t bd = blockDim.x;
   for (int d0 = 0; d0 < m; d0 += 4) {
     // per-thread partials in the precision of the data (FP32 data: FP32 sums)
     T at[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const cplx<T>* Vr = V + (size_t)rhs * rstride;
-    size_t e = lo + threadIdx.x;
-    // four of the thread's elements at a time: all their loads are issued before the products
-    // (which are summed in the same element order as one at a time, so the bits do not change)
-    for (; e + 3 * bd < hi; e += 4 * bd) {
-      cplx<T> wv[4], vv[4][4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) wv[u] = pw[e + u * bd];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int dd = 0; dd < 4; ++dd)
-          vv[u][dd] = d0 + dd < m ? Vr[(size_t)(d0 + dd) * vstride + e + u * bd] : czero<T>();
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int dd = 0; dd < 4; ++dd)
-          if (d0 + dd < m) cdotc_acc(at[2 * dd], at[2 * dd + 1], vv[u][dd], wv[u]);
-    }
-    for (; e < hi; e += bd) {
+    for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
       const cplx<T> we = pw[e];
 #pragma unroll
       for (int dd = 0; dd < 4; ++dd) {
         if (d0 + dd < m) {
-          const cplx<T> v = Vr[(size_t)(d0 + dd) * vstride + e];
+          const cplx<T> v = V[(size_t)(d0 + dd) * vstride + (size_t)rhs * rstride + e];
           cdotc_acc(at[2 * dd], at[2 * dd + 1], v, we);
         }
       }
