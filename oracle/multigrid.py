@@ -29,8 +29,11 @@ the restricted ones first and fresh random ones for the rest.  The random
 start vectors are inputs.
 
 Parity of the setup against the paper is pinned by the call sequence it
-makes (a test replays Alg. 3/4 by hand on a tiny hierarchy); its numerical
-outcome is "parity unpinned" beyond "given identical test vectors".
+makes (a test replays Alg. 3/4 by hand on a tiny hierarchy) and, for one pass
+of Alg. 4 on a two-level hierarchy with exact block and coarse solves, by the
+dense two-level cycle applied to every test vector; with inexact inner
+solves on deeper hierarchies its numerical outcome is "parity unpinned"
+beyond "given identical test vectors".
 """
 from __future__ import annotations
 

@@ -96,6 +96,39 @@ def test_setup_call_sequence_replays_alg3_alg4():
             assert abs(norm(v) - 1.0) < 1e-12
 
 
+def test_alg4_pass_applies_the_fixed_two_level_cycle_to_every_test_vector():
+    """One pass of Alg. 4 on a two-level hierarchy with exact block solves and an exact coarse
+    solve: every test vector becomes M v_j / ||M v_j||, M the linear two-level cycle of the P
+    built before the pass (z_0 = P Dc^{-1} P^+ b, then nu steps z <- z + S (b - D z)), written out
+    densely here; then P is rebuilt from the new vectors.  Rebuilding P inside the pass, taking
+    another iterate than the cycle's result, or skipping the normalisation all fail this."""
+    nu = 2
+    op, h = _two_level(nu=nu, exact_sap=True)
+    h.p.n_inv = 1
+    D = sparse_matrix(op).toarray()
+    n = D.shape[0]
+    Pd = _dense_P(h.levels[0].P, (2, 2, 2, 2))
+    Dc = Pd.conj().T @ D @ Pd
+    S = np.stack([h.levels[0].sap(col.reshape(DIMS + (12,))).ravel() for col in np.eye(n)], axis=1)
+    C = Pd @ np.linalg.solve(Dc, Pd.conj().T)
+    G = np.eye(n) - S @ D
+    M = np.linalg.matrix_power(G, nu) @ C + sum(np.linalg.matrix_power(G, k) @ S for k in range(nu))
+    old = [v.copy() for v in h.levels[0].tv]
+    h.trace = None
+    h.iterative_setup_phase(0, 1)
+    for v_old, v_new in zip(old, h.levels[0].tv):
+        ref = M @ v_old.ravel()
+        ref = ref / norm(ref)
+        assert norm(v_new.ravel() - ref) <= 1e-10, norm(v_new.ravel() - ref)
+    # P of the new vectors: the coarse operator equals P^+ D P of the dense interpolation
+    Pn = _dense_P(h.levels[0].P, (2, 2, 2, 2))
+    assert np.abs(Pn.conj().T @ Pn - np.eye(Pn.shape[1])).max() < 1e-12
+    cd = coarse_dims(DIMS, (2, 2, 2, 2))
+    nc = Pn.shape[1] // int(np.prod(cd))
+    Dc_new = np.stack([h.levels[1].op.apply(e.reshape(cd + (nc,))).ravel() for e in np.eye(Pn.shape[1])], axis=1)
+    assert np.abs(Dc_new - Pn.conj().T @ D @ Pn).max() <= 1e-12 * np.abs(D).max()
+
+
 def test_two_level_solve_matches_dense_lu():
     op = WilsonOp.build(synth.su3_field(DIMS, 0.3, 0), -0.35, 0.0, -1)
     p = Params(levels=2, agg=((2, 2, 2, 2),), n_tv=(6,), sap_block=((2, 2, 2, 2), None),
