@@ -386,7 +386,7 @@ def run_gpu(args, w):
         return dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
                                        mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
                                        outer_restart=w["outer_restart"], precision=precision, max_rhs=nb,
-                                       seed=w["tv_seed"], sap_schur=sap_schur)
+                                       seed=w["tv_seed"], sap_schur=sap_schur, setup_batch=w.get("setup_batch", 0))
 
     stream = torch.cuda.current_stream()
     setup_s = {}

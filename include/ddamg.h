@@ -80,7 +80,10 @@ typedef struct ddamg_params {
                                           D_B (the paper does not say which)              */
   int setup_batch;                     /* test vectors per batched K-cycle of Alg. 4 (0: 4);
                                           the level workspaces hold max(max_rhs, this)
-                                          columns; results do not depend on it            */
+                                          columns; results do not depend on it (passes
+                                          that update test vectors two or more levels below
+                                          the cycle's start level, L >= 4, run one vector at
+                                          a time)                                          */
 } ddamg_params;
 
 typedef struct ddamg_stats {

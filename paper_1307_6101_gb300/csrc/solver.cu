@@ -1359,13 +1359,18 @@ void initial_setup_phase(ddamg_handle* h, int l, const double* const* tv_random)
 // last iterates on the coarser levels) replace the test vectors, normalised.  Within one pass P and
 // the coarse operators do not change, so the K-cycles of different test vectors are independent:
 // they run in batches of up to work_batch columns, with results identical bit for bit to one
-// vector at a time (every kernel treats the columns of a batch independently).
+// vector at a time (every kernel treats the columns of a batch independently).  That holds for the
+// levels l and l+1, whose values are the cycle's output and the result of the one level-(l+1)
+// solve.  A level l+2 or deeper takes the last iterate of a solver that the level-(l+1) FGMRES
+// calls once per step, and in a batch those calls go on for a column after its own level-(l+1)
+// solve has converged (with a zero direction), which overwrites its last iterate; so a pass that
+// updates such levels (l <= L-4) runs one test vector at a time.
 template <typename T>
 void iterative_setup_phase(ddamg_handle* h, int l, int i) {
   if (l >= h->L - 1) return;
   Level& L = h->lv[l];
   cudaStream_t st = h->st;
-  const int cb = std::max(1, std::min(h->work_batch, h->setup_batch));
+  const int cb = l + 2 <= h->L - 2 ? 1 : std::max(1, std::min(h->work_batch, h->setup_batch));
   cplx<T>* bT = static_cast<cplx<T>*>(scratch(h, 5, sizeof(cplx<T>) * L.vlen * cb));
   cplx<T>* zT = static_cast<cplx<T>*>(scratch(h, 6, sizeof(cplx<T>) * L.vlen * cb));
   double* nrm = static_cast<double*>(scratch(h, 7, sizeof(double) * 64));

@@ -50,7 +50,7 @@ def _params(dd, w, precision, max_rhs):
     return dd.ddamg_default_params(levels=w["levels"], agg=w["agg"], n_tv=w["n_tv"], sap_block=w["sap"],
                                    mr_steps=w["mr_steps"], nu=w["nu"], n_inv=w["n_inv"],
                                    outer_restart=w["outer_restart"], precision=precision, max_rhs=max_rhs,
-                                   seed=w["tv_seed"])
+                                   seed=w["tv_seed"], setup_batch=w.get("setup_batch", 0))
 
 
 def _sites(dims, n, seed, extra=()):

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from cases import Case, THREE, SAP4
+from cases import Case, THREE, SAP4, FOUR
 
 pytestmark = pytest.mark.gpu
 
@@ -29,9 +29,9 @@ def _interp(dd, h, c):
     return out
 
 
-@pytest.mark.parametrize("precision", [0, 2])
-def test_batched_alg4_equals_one_vector_at_a_time(dd, precision):
-    c = Case(**THREE, n_inv=2, eta_passes=2)
+@pytest.mark.parametrize("spec,precision", [(THREE, 0), (THREE, 2), (FOUR, 2)])
+def test_batched_alg4_equals_one_vector_at_a_time(dd, spec, precision):
+    c = Case(**spec, n_inv=2, eta_passes=2)
     U = c.gauge()
     tv = c.random_tv()
     p1 = c.gpu_params(precision)
