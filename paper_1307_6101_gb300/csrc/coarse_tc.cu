@@ -22,6 +22,7 @@
 #include "tma.cuh"
 
 #include <atomic>
+#include <mutex>
 
 namespace {
 
@@ -222,10 +223,15 @@ __global__ void k_coarse_apply_tc(cplx<float>* __restrict__ out, const cplx<floa
   }
 }
 
+// The dynamic shared-memory limit is a process-wide attribute of the kernel: it only ever grows
+// (under a lock, so that two threads preparing different sizes cannot leave it at the smaller)
 template <bool RESID>
 cudaError_t prepare_tc(size_t bytes) {
   static std::atomic<size_t> set_to{0};
+  static std::mutex mu;
   if (set_to.load(std::memory_order_acquire) >= bytes) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(mu);
+  if (set_to.load(std::memory_order_relaxed) >= bytes) return cudaSuccess;
   const cudaError_t e =
       cudaFuncSetAttribute(k_coarse_apply_tc<RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) set_to.store(bytes, std::memory_order_release);

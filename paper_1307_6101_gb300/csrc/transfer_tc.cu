@@ -17,6 +17,7 @@
 #include "kernels.h"
 
 #include <atomic>
+#include <mutex>
 
 namespace {
 
@@ -254,9 +255,13 @@ __global__ void k_prolong_batch(cplx<float>* __restrict__ out, const cplx<float>
   }
 }
 
+// the kernel's dynamic shared-memory limit (process-wide) only ever grows, under a lock
 cudaError_t prepare_restrict_tc(size_t bytes) {
   static std::atomic<size_t> set_to{0};
+  static std::mutex mu;
   if (set_to.load(std::memory_order_acquire) >= bytes) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(mu);
+  if (set_to.load(std::memory_order_relaxed) >= bytes) return cudaSuccess;
   const cudaError_t e = cudaFuncSetAttribute(k_restrict_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) set_to.store(bytes, std::memory_order_release);
   return e;
